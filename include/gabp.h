@@ -1,0 +1,184 @@
+/*
+ * gabp.h -- C ABI of the GB300 (sm_103a) Gaussian belief propagation solver.
+ *
+ * The solver computes x = A^{-1} b for a sparse symmetric A by synchronous
+ * Gaussian belief propagation (GaBP), the message-passing method of
+ * D. Bickson, "Gaussian Belief Propagation: Theory and Application":
+ *   - the linear system is read as a Gaussian Markov random field whose
+ *     marginal means are A^{-1} b (Sec. "From Linear Algebra to Probabilistic
+ *     Inference", Proposition on linear systems and inference);
+ *   - every directed edge i->j carries a precision message P_ij and a mean
+ *     message mu_ij (eq_prec_message, eq_mean_message; Algorithm 1);
+ *   - each message is node i's aggregate minus the reverse message j->i, the
+ *     broadcast form (Algorithm 2, Sec. "GaBP Broadcast Variant");
+ *   - all messages of a round are computed from the previous round's
+ *     messages (parallel / synchronous schedule, Sec. "The Gaussian BP
+ *     Algorithm", scheduling paragraph);
+ *   - the answer is the marginal mean vector and, optionally, the marginal
+ *     precisions (Algorithm 1, steps 4-5).
+ *
+ * Conventions for every function below
+ *   - Return value: a gabp_status.  Negative values are errors; on an error
+ *     no output is written unless stated.
+ *   - Device pointers are CUDA device (or managed) addresses on the device
+ *     that was current when the handle was created.  Host pointers are plain
+ *     host memory.  The caller owns every array it passes; the library copies
+ *     what it keeps.
+ *   - Work is enqueued on the handle's stream (gabp_create / gabp_set_stream).
+ *     Solves synchronise on that stream before they return, because the
+ *     convergence decision is read back to the host.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ *   - int32 indices: n < 2^31 and nnz < 2^31.
+ */
+#ifndef GABP_H_
+#define GABP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gabp_handle_s *gabp_handle;
+
+typedef enum {
+  GABP_OK = 0,             /* converged: relative residual <= tol */
+  GABP_NOT_CONVERGED = 1,  /* max_iter rounds ran; x holds the last iterate */
+  GABP_DIVERGED = 2,       /* a non-finite value appeared; x holds the last finite-checked iterate */
+  GABP_BREAKDOWN = 3,      /* a cavity precision P_{i\j} (or a marginal precision) was exactly 0 */
+  GABP_TIMEOUT = 4,        /* a bounded device-side wait gave up (multi-system persistent kernel) */
+  GABP_ERR_INVALID = -1,   /* bad argument or matrix (see gabp_create) */
+  GABP_ERR_CUDA = -2,      /* a CUDA runtime call failed; gabp_last_error() has the text */
+  GABP_ERR_NOMEM = -3      /* device allocation failed */
+} gabp_status;
+
+/* Message arithmetic of a solve. */
+typedef enum {
+  GABP_PREC_FP64 = 0,        /* plain FP64 GaBP: precision and mean messages in FP64 */
+  GABP_PREC_FP32_REFINE = 1  /* FP32 precision and mean messages; FP64 residual r = b - A x and
+                                update x += d (iterative refinement) are the only FP64 steps */
+} gabp_precision;
+
+/* How a round is organised on the GPU; both compute Algorithm 2. */
+typedef enum {
+  GABP_VARIANT_NODE = 0,  /* fused node-centric kernel: a sub-warp per row forms the aggregate and
+                             every message into the row; the reverse message is recomputed from the
+                             row's own state, so no edge array is gathered or scattered */
+  GABP_VARIANT_EDGE = 1   /* two kernels per round: row aggregates, then one thread per directed edge
+                             reading the reverse message through the reverse-edge index */
+} gabp_variant;
+
+typedef struct {
+  int variant;          /* gabp_variant, default GABP_VARIANT_NODE */
+  int precision;        /* gabp_precision, default GABP_PREC_FP64 */
+  int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16 */
+  int freeze_precisions;/* 1: once every precision message is stationary to ~4 ulp between two
+                           rounds, stop re-computing precisions (FP64 path), default 1 */
+  double inner_tol;     /* FP32 inner-solve relative residual target, default 1e-4 */
+  int inner_max_iter;   /* rounds per inner solve, default 400 */
+  int max_refine;       /* refinement steps, default 30 */
+  int gamma_mode;       /* convergence fix: 0 off, 1 Gamma = gamma * diag(A),
+                           2 Gamma_ii = max(0, sum_j |A_ij| - A_ii) + gamma * A_ii; default 0 */
+  double gamma;         /* loading parameter for gamma_mode, default 0.25 */
+  int lanes;            /* lanes per row for R = 1 kernels (1..32, power of two); 0 = autotune */
+  int reserved[8];
+} gabp_options;
+
+/* Fill *o with the defaults listed above. */
+gabp_status gabp_options_default(gabp_options *o);
+
+/*
+ * gabp_create -- validate A, upload it and build the device graph.
+ *
+ * A is given as FULL symmetric CSR: rowptr[n+1], col[nnz], val[nnz], the
+ * diagonal included, column indices strictly increasing within each row.
+ * mem_space 0: the three arrays are host memory; 1: device memory.
+ * The graph of A: nodes are variables, edges are the nonzero off-diagonal
+ * entries (Sec. "From Linear Algebra to Probabilistic Inference").
+ *
+ * Returns GABP_ERR_INVALID (and no handle) when: n < 1, nnz out of range,
+ * rowptr not monotone, a column index out of range or not strictly increasing,
+ * a row without a diagonal entry or with A_ii = 0, a stored zero off the
+ * diagonal, an asymmetric pattern or value (A_ij != A_ji bit for bit), or a
+ * non-finite value.  The handle owns all device memory it allocates; free it
+ * with gabp_destroy.  stream is a cudaStream_t (NULL = legacy default stream).
+ * opt may be NULL (defaults).
+ */
+gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t *rowptr,
+                        const int32_t *col, const double *val, int mem_space, void *stream,
+                        const gabp_options *opt);
+
+/* Replace the handle's options (validated) / stream. */
+gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt);
+gabp_status gabp_set_stream(gabp_handle h, void *stream);
+
+/*
+ * gabp_solve -- solve A x = b (b, x: device arrays of n doubles).
+ *
+ * Messages start at zero (Algorithm 1, step 1).  After round t the tentative
+ * means x_t are formed (Algorithm 1, step 4) and the run stops at the first t
+ * with ||b - A x_t||_2 <= tol ||b||_2, or at t = max_iter.  With the FP32
+ * refinement precision, tol is the target of the outer FP64 loop.  With
+ * gamma_mode != 0 the convergence fix runs: x <- x + (A + Gamma)^{-1} (b - A x)
+ * (Chapter "Fixing convergence of GaBP", double loop), GaBP being run on
+ * A + Gamma.
+ * iters_out (nullable): rounds of the returned iterate (FP64) or total inner
+ * rounds (FP32 refinement / convergence fix).  relres_out (nullable): final
+ * ||b - A x|| / ||b||.  On GABP_NOT_CONVERGED / GABP_DIVERGED x holds the last
+ * iterate.  b = 0 gives x = 0 and 0 rounds.
+ */
+gabp_status gabp_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                       int32_t *iters_out, double *relres_out);
+
+/* As gabp_solve with b and x in host memory; the copies run on the handle's stream. */
+gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                            int32_t *iters_out, double *relres_out);
+
+/*
+ * gabp_solve_batched -- nrhs right-hand sides in one launch sequence, FP32
+ * messages + FP64 refinement (the precision messages depend on A only, eq_prec
+ * and eq_prec_message, so they are converged once and shared).
+ * B, X: device, column r at B + r*ld (ld >= n).  iters_out: total inner rounds.
+ * relres_out (nullable, device or host per mem_space of the handle? no: HOST
+ * array of nrhs doubles) receives each column's final relative residual.
+ * Returns the worst status over the columns.
+ */
+gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
+                               double tol, int32_t max_iter, int32_t *iters_out, double *relres_out);
+
+/* Marginal precisions P_i = A_ii + sum_k P_ki of the last solve (Algorithm 1,
+ * step 4), device array of n doubles.  Exact (= 1/(A^{-1})_ii) on trees; an
+ * approximation on loopy graphs.  GABP_ERR_INVALID before the first solve. */
+gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi);
+
+/* Messages of the last FP64 solve at its returned round, in the receiver
+ * layout of the input CSR: for slot p of row i with col[p] = k != i,
+ * P[p] = P_ki and hm[p] = P_ki * mu_ki (the information-form mean message);
+ * diagonal slots get 0.  Device arrays of nnz doubles. */
+gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm);
+
+/* Gradient of a scalar loss through x = A^{-1} b, given lambda = A^{-1} dL/dx
+ * (obtain it with a second gabp_solve on dL/dx: A is symmetric) and x:
+ * grad_val[p] for every CSR slot p = (i, j) of the input:
+ *   off-diagonal: -(lambda_i x_j + lambda_j x_i) / 2   (symmetrised),
+ *   diagonal:     -lambda_i x_i.
+ * dL/db is lambda itself.  Device arrays. */
+gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val);
+
+/* Rounds (edge-update passes) executed by the last solve, including
+ * precision-phase and refinement inner rounds, and the directed-edge count E
+ * (off-diagonal nnz).  edge-updates of the solve = rounds * E * nrhs. */
+gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int32_t *refine_steps);
+
+/* Free everything the handle owns.  NULL is accepted. */
+gabp_status gabp_destroy(gabp_handle h);
+
+/* Static text for a status; thread-local text of the last CUDA error. */
+const char *gabp_status_string(gabp_status s);
+const char *gabp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GABP_H_ */

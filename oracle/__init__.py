@@ -1,0 +1,233 @@
+"""FP64 CPU oracle for the GaBP solver -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  The product (``paper_0811_2518_gb300``) never imports
+it, and it never imports the product: the two share no code.
+
+Paper: D. Bickson, "Gaussian Belief Propagation: Theory and Application".
+
+Contents and the passage each follows:
+
+* :func:`gabp_naive`      -- Algorithm 1, parallel (synchronous) schedule, in C.
+* :func:`gabp_broadcast`  -- Algorithm 2 (broadcast variant), in C.
+* :func:`dense_solve`     -- x* = A^{-1} b by LU (Proposition "linear system =
+  inference": the GaBP fixed point is the marginal-mean vector A^{-1} b).
+* :func:`marginal_precisions_exact` -- 1/(A^{-1})_ii, the exact marginal
+  precisions, which GaBP reaches on trees (Sec. "Convergence and Exactness").
+* :func:`rho_abs_normalized` -- rho(|I - D^{-1/2} A D^{-1/2}|), the
+  walk-summability quantity of the spectral-radius theorem.
+* :func:`rate_bound_rounds` -- the round bound of Sec. "Upper Bound on
+  Convergence Rate" for diagonally dominant A.
+* :func:`diagonal_loading` / :func:`convergence_fix` -- Chapter "Fixing
+  convergence of GaBP": J' = J + Gamma and the double loop
+  x^(t+1) = (J + Gamma)^{-1} (h + Gamma x^(t)) whose inner solve is GaBP.
+* :func:`dense_gradient`  -- gradients of 0.5 ||x - x*||^2 for x = A^{-1} b,
+  written from the adjoint identity (no counterpart in the paper; it pins the
+  differentiable solve).
+
+Status codes: 0 converged, 1 not converged, 2 diverged, 3 breakdown, -1 invalid.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from types import SimpleNamespace
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gabp_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libgabp_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+OK, NOT_CONVERGED, DIVERGED, BREAKDOWN, INVALID = 0, 1, 2, 3, -1
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with the host gcc (plain -O2, portable flags)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name in ("orc_gabp_naive", "orc_gabp_broadcast"):
+                f = getattr(lib, name)
+                f.restype = ctypes.c_int
+                f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_void_p, ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _run(name, m, b, max_iter, tol, stop_rule, messages):
+    lib = _load()
+    rowptr = np.ascontiguousarray(m.rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(m.col, dtype=np.int32)
+    val = np.ascontiguousarray(m.val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if b.shape != (m.n,):
+        raise ValueError("b has the wrong shape")
+    x = np.zeros(m.n)
+    P = np.zeros(m.n)
+    Pm = np.zeros(m.nnz) if messages else None
+    Mm = np.zeros(m.nnz) if messages else None
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = getattr(lib, name)(m.n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), int(max_iter), float(tol),
+                            int(stop_rule), _ptr(x), _ptr(P), ctypes.byref(it), ctypes.byref(rel),
+                            _ptr(Pm) if messages else None, _ptr(Mm) if messages else None)
+    out = {"status": rc, "x": x, "P": P, "iters": it.value, "relres": rel.value}
+    if messages:
+        out["Pmsg"] = Pm
+        out["mumsg"] = Mm
+    return out
+
+
+def gabp_naive(m, b, max_iter=1000, tol=1e-12, stop_rule="residual", messages=False):
+    """Algorithm 1 (naive GaBP), synchronous schedule, FP64.
+
+    ``m`` is a full symmetric CSR (``synth.CSR``).  Returns a dict with
+    ``status``, ``x`` (marginal means), ``P`` (marginal precisions), ``iters``,
+    ``relres`` and, with ``messages=True``, ``Pmsg`` / ``mumsg``: for every CSR
+    slot p of row i with col k != i, the message k -> i after the last round.
+    ``stop_rule`` is "residual" (||b - A x_t|| <= tol ||b||) or "message"
+    (max |message change| < tol, the rule of the paper's numerical examples).
+    """
+    return _run("orc_gabp_naive", m, b, max_iter, tol, 0 if stop_rule == "residual" else 1, messages)
+
+
+def gabp_broadcast(m, b, max_iter=1000, tol=1e-12, stop_rule="residual", messages=False):
+    """Algorithm 2 (broadcast GaBP), synchronous schedule, FP64; same interface as :func:`gabp_naive`."""
+    return _run("orc_gabp_broadcast", m, b, max_iter, tol, 0 if stop_rule == "residual" else 1, messages)
+
+
+# --------------------------------------------------------------------------- dense references
+def to_dense(m) -> np.ndarray:
+    A = np.zeros((m.n, m.n))
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    A[rows, m.col] = m.val
+    return A
+
+
+def dense_solve(A, b) -> np.ndarray:
+    """x* = A^{-1} b (LAPACK LU with partial pivoting)."""
+    return np.linalg.solve(np.asarray(A, dtype=np.float64), np.asarray(b, dtype=np.float64))
+
+
+def marginal_precisions_exact(A) -> np.ndarray:
+    """Exact marginal precisions P_i = 1 / (A^{-1})_ii."""
+    return 1.0 / np.diag(np.linalg.inv(np.asarray(A, dtype=np.float64)))
+
+
+def rho_abs_normalized(A) -> float:
+    """rho(|I - D^{-1/2} A D^{-1/2}|) with D = diag(A) (spectral-radius theorem)."""
+    A = np.asarray(A, dtype=np.float64)
+    d = 1.0 / np.sqrt(np.diag(A))
+    R = np.abs(np.eye(A.shape[0]) - d[:, None] * A * d[None, :])
+    return float(np.max(np.abs(np.linalg.eigvalsh(R))))
+
+
+def rate_bound_rounds(A, eps: float) -> int:
+    """Sec. "Upper Bound on Convergence Rate": with eps_i = |a_ii| - sum_j |a_ij| > 0
+    and gamma = max_ij 1 / (1 + eps_i / (|a_ij| |N(i)|)), GaBP reaches
+    |x* - x_t| < eps ||b||_inf after at most ceil(log eps / log gamma) rounds."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    gamma = 0.0
+    for i in range(n):
+        off = [j for j in range(n) if j != i and A[i, j] != 0.0]
+        e = abs(A[i, i]) - sum(abs(A[i, j]) for j in off)
+        if e <= 0:
+            raise ValueError("not strictly diagonally dominant")
+        for j in off:
+            gamma = max(gamma, 1.0 / (1.0 + e / (abs(A[i, j]) * len(off))))
+    return int(np.ceil(np.log(eps) / np.log(gamma)))
+
+
+def diagonal_loading(A, mode: str = "uniform", gamma: float = 0.25, delta: float = 0.0) -> np.ndarray:
+    """Diagonal Gamma of the convergence fix.
+
+    "uniform": Gamma = gamma * diag(A) -- the unit-diagonal model J = I - R loaded
+    by gamma I, written back in A's scaling; walk-summable for gamma > rho(|R|) - 1.
+    "dd": Gamma_ii = max(0, sum_j |A_ij| - A_ii) + delta * A_ii, which makes
+    A + Gamma diagonally dominant (hence walk-summable) for delta > 0.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    d = np.diag(A).copy()
+    if mode == "uniform":
+        return gamma * d
+    off = np.sum(np.abs(A), axis=1) - np.abs(d)
+    return np.maximum(0.0, off - d) + delta * d
+
+
+def convergence_fix(m, b, Gamma, tol=1e-10, inner_tol=1e-12, max_outer=500, inner_max_iter=2000,
+                    variant="broadcast"):
+    """Chapter "Fixing convergence of GaBP", iterative correction (double loop):
+    x^(t+1) = (A + Gamma)^{-1} (b + Gamma x^(t)), x^(0) = 0, the inner solve being
+    GaBP on A + Gamma.  Stops when ||b - A x|| <= tol ||b||.
+
+    Returns dict(x, outer, inner_total, status, history) where history holds
+    ||x^(t) - x*||_2 per outer step when the dense solution is cheap (n <= 4096).
+    """
+    Gamma = np.asarray(Gamma, dtype=np.float64)
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    val = m.val.copy()
+    diag_slots = np.nonzero(rows == m.col)[0]
+    val[diag_slots] += Gamma[rows[diag_slots]]
+    mp = SimpleNamespace(n=m.n, rowptr=m.rowptr, col=m.col, val=val, nnz=int(m.rowptr[-1]))
+    A = to_dense(m) if m.n <= 4096 else None
+    xs = dense_solve(A, b) if A is not None else None
+    solve = gabp_broadcast if variant == "broadcast" else gabp_naive
+    x = np.zeros(m.n)
+    bn = np.linalg.norm(b)
+    inner_total, hist, status = 0, [], NOT_CONVERGED
+    for t in range(1, max_outer + 1):
+        r = solve(mp, b + Gamma * x, max_iter=inner_max_iter, tol=inner_tol)
+        if r["status"] not in (OK, NOT_CONVERGED):
+            status = r["status"]
+            break
+        inner_total += r["iters"]
+        x = r["x"]
+        if xs is not None:
+            hist.append(float(np.linalg.norm(x - xs)))
+        ax = np.zeros(m.n)
+        np.add.at(ax, rows, m.val * x[m.col])
+        if np.linalg.norm(b - ax) <= tol * bn:
+            status = OK
+            break
+    return {"x": x, "outer": t, "inner_total": inner_total, "status": status, "history": hist}
+
+
+def dense_gradient(A, b, xstar):
+    """Gradients of L = 0.5 ||x - x*||^2 with x = A^{-1} b, A symmetric.
+
+    lambda = A^{-T} (x - x*) = A^{-1} (x - x*);  dL/db = lambda;  dL/dA = -lambda x^T.
+    Restricted to A's pattern and symmetrised (A stays symmetric): for a stored
+    off-diagonal entry (i, j), g_ij = -(lambda_i x_j + lambda_j x_i) / 2; for the
+    diagonal, g_ii = -lambda_i x_i.  Returns (x, dL/db, G) with G dense (zeros
+    off the pattern).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    x = np.linalg.solve(A, b)
+    lam = np.linalg.solve(A.T, x - xstar)
+    G = -0.5 * (np.outer(lam, x) + np.outer(x, lam))
+    G[A == 0.0] = 0.0
+    return x, lam, G

@@ -1,0 +1,347 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix (CPU only).
+
+Each test names the passage it checks.  None of them compares the oracle with
+itself through a retyped formula: the references are printed values, dense
+linear algebra, closed forms and theorems.
+"""
+import math
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+
+def _slot(m, i, k):
+    lo, hi = m.rowptr[i], m.rowptr[i + 1]
+    hits = np.nonzero(m.col[lo:hi] == k)[0]
+    assert hits.size == 1
+    return lo + hits[0]
+
+
+# ----------------------------------------------------------------------------- worked example
+@pytest.mark.parametrize("variant", ["naive", "broadcast"])
+def test_toy_tables_exact(variant):
+    """Sec. "Toy Linear System": every message and tentative mean of the printed
+    tables at t = 0..3 (parallel schedule), and the marginal precisions."""
+    g = read_golden("toy3x3_tables.txt")
+    A, b = synth.toy3x3()
+    m = synth.from_dense(A)
+    run = oracle.gabp_naive if variant == "naive" else oracle.gabp_broadcast
+    names = {"x": 0, "y": 1, "z": 2}
+    for t in range(0, 4):
+        r = run(m, b, max_iter=t, tol=0.0, messages=True)
+        for key, vals in g.items():
+            if key.startswith("P_") or key.startswith("mu_"):
+                kind, pair = key.split("_")
+                snd, rcv = names[pair[0]], names[pair[1]]
+                p = _slot(m, rcv, snd)  # message snd -> rcv lives in row rcv
+                got = r["Pmsg"][p] if kind == "P" else r["mumsg"][p]
+                assert abs(got - vals[t]) <= 1e-15, (key, t, got, vals[t])
+            elif key.startswith("mean_"):
+                assert abs(r["x"][names[key[-1]]] - vals[t]) <= 1e-15, (key, t)
+    r = run(m, b, max_iter=3, tol=0.0)
+    for key in ("Pm_x", "Pm_y", "Pm_z"):
+        assert abs(r["P"][names[key[-1]]] - g[key][0]) <= 1e-15
+    # and both agree with the dense inverse: x* = (1, 2, -1), P_i = 1/(A^-1)_ii
+    assert np.allclose(r["x"], oracle.dense_solve(A, b), rtol=0, atol=1e-15)
+    assert np.allclose(r["P"], oracle.marginal_precisions_exact(A), rtol=1e-14)
+
+
+def test_toy_converges_in_diameter_rounds():
+    """Sec. "Toy Linear System": on the 3-node tree GaBP converges in two rounds,
+    the tree's diameter; the residual stop rule fires at t = 2."""
+    A, b = synth.toy3x3()
+    r = oracle.gabp_naive(synth.from_dense(A), b, max_iter=10, tol=1e-15)
+    assert r["status"] == oracle.OK and r["iters"] == 2
+
+
+# ----------------------------------------------------------------------------- trees
+def _diameter(m):
+    def bfs(s):
+        dist = np.full(m.n, -1)
+        dist[s] = 0
+        q = deque([s])
+        while q:
+            u = q.popleft()
+            for p in range(m.rowptr[u], m.rowptr[u + 1]):
+                v = m.col[p]
+                if v != u and dist[v] < 0:
+                    dist[v] = dist[u] + 1
+                    q.append(v)
+        return dist
+    d0 = bfs(0)
+    return int(bfs(int(np.argmax(d0))).max())
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", ["naive", "broadcast"])
+def test_tree_exact_after_diameter_rounds(seed, variant):
+    """Sec. "Convergence and Exactness" and the Gaussian-elimination proposition:
+    on a tree GaBP is exact -- means A^{-1} b and precisions 1/(A^{-1})_ii -- and
+    its messages stop changing once information has crossed the tree."""
+    m = synth.random_tree(31, seed, dd=(seed % 2 == 0), diag_scale=2.0)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 100 + seed)
+    diam = _diameter(m)
+    run = oracle.gabp_naive if variant == "naive" else oracle.gabp_broadcast
+    r = run(m, b, max_iter=diam, tol=0.0, messages=True)
+    xs = oracle.dense_solve(A, b)
+    assert np.linalg.norm(r["x"] - xs) <= 1e-12 * np.linalg.norm(xs)
+    assert np.allclose(r["P"], oracle.marginal_precisions_exact(A), rtol=1e-11, atol=0)
+    r2 = run(m, b, max_iter=diam + 1, tol=0.0, messages=True)
+    if variant == "naive":
+        # the explicit sum over N(i)\j sees only converged inputs: bit-for-bit stationary
+        assert np.array_equal(r2["Pmsg"], r["Pmsg"]) and np.array_equal(r2["mumsg"], r["mumsg"])
+    else:
+        # the broadcast form subtracts the reverse message from the full aggregate;
+        # the cancellation rounds differently once that message has settled
+        assert np.allclose(r2["Pmsg"], r["Pmsg"], rtol=1e-12, atol=1e-15)
+        assert np.allclose(r2["mumsg"], r["mumsg"], rtol=1e-12, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- fixed point
+@pytest.mark.parametrize("variant", ["naive", "broadcast"])
+def test_fixed_point_diagonally_dominant_grid(variant):
+    """Diagonal-dominance theorem (Sec. "Convergence and Exactness"): the means
+    converge to A^{-1} b.  32 x 32 5-point grid, diagonal 4.5."""
+    m = synth.grid2d(32, -1.0, 4.5)
+    b = synth.rhs(m.n, 1)
+    run = oracle.gabp_naive if variant == "naive" else oracle.gabp_broadcast
+    r = run(m, b, max_iter=2000, tol=1e-13)
+    assert r["status"] == oracle.OK
+    xs = oracle.dense_solve(oracle.to_dense(m), b)
+    assert np.linalg.norm(r["x"] - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_fixed_point_walk_summable_random():
+    """Spectral-radius theorem: rho(|R|) < 1 gives convergence to A^{-1} b."""
+    m = synth.random_sym(400, 4, 1.1, 7)
+    A = oracle.to_dense(m)
+    assert oracle.rho_abs_normalized(A) < 1
+    b = synth.rhs(m.n, 7)
+    r = oracle.gabp_broadcast(m, b, max_iter=2000, tol=1e-13)
+    assert r["status"] == oracle.OK
+    xs = oracle.dense_solve(A, b)
+    assert np.linalg.norm(r["x"] - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_run_gabp_appendix_example():
+    """Appendix example (A with couplings 0.3 / 0.1, b = 1): the solution equals inv(A) b."""
+    A, b = synth.run_gabp_3x3()
+    r = oracle.gabp_naive(synth.from_dense(A), b, max_iter=100, tol=1e-14)
+    assert r["status"] == oracle.OK
+    assert np.allclose(r["x"], np.linalg.inv(A) @ b, rtol=1e-13)
+
+
+def test_broadcast_equals_naive():
+    """Sec. "GaBP Broadcast Variant": subtracting the reverse message from the full
+    aggregate gives the same messages as the explicit sum over N(i)\\j."""
+    m = synth.random_sym(300, 4, 1.1, 3)
+    b = synth.rhs(m.n, 3)
+    for t in (1, 2, 7, 25):
+        a = oracle.gabp_naive(m, b, max_iter=t, tol=0.0, messages=True)
+        c = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0, messages=True)
+        assert np.allclose(a["Pmsg"], c["Pmsg"], rtol=1e-12, atol=1e-15)
+        hm_a, hm_c = a["Pmsg"] * a["mumsg"], c["Pmsg"] * c["mumsg"]
+        assert np.allclose(hm_a, hm_c, rtol=1e-11, atol=1e-13)
+        assert np.allclose(a["x"], c["x"], rtol=1e-12, atol=1e-14)
+
+
+def test_info_form_messages_match_paper_mean_form():
+    """eq_mean_message: P_ij mu_ij = -A_ij mu_{i\\j}; at the fixed point of a tree the
+    information-form mean message therefore equals -A_ij times the cavity mean,
+    which on a tree is the exact conditional mean with x_j removed."""
+    A, b = synth.toy3x3()
+    m = synth.from_dense(A)
+    r = oracle.gabp_naive(m, b, max_iter=3, tol=0.0, messages=True)
+    # message x -> y: cavity of x without y is (P_xx, mu_xx) combined with z -> x
+    p = _slot(m, 1, 0)
+    Pcav = 1.0 + r["Pmsg"][_slot(m, 0, 2)]
+    hcav = -6.0 + r["Pmsg"][_slot(m, 0, 2)] * r["mumsg"][_slot(m, 0, 2)]
+    assert abs(r["Pmsg"][p] * r["mumsg"][p] - (-A[0, 1] * hcav / Pcav)) <= 1e-14
+
+
+# ----------------------------------------------------------------------------- walk-summability
+def test_rho_cdma_printed_values():
+    """Sec. "Linear Detection": rho(|I - R3|) = 0.9008, rho(|I - R4|) = 0.8747 (printed to 4 decimals)."""
+    g = read_golden("cdma_rho.txt")
+    for key, make in (("R3", synth.cdma_r3), ("R4", synth.cdma_r4)):
+        A, _ = make()
+        assert abs(oracle.rho_abs_normalized(A) - g[key][0]) <= 5e-5
+
+
+@pytest.mark.parametrize("c", [1.05, 1.1, 1.2, 0.9])
+def test_rho_closed_form_row_sum_diagonal(c):
+    """For A_ii = c * sum_j |A_ij|, D^{-1}|A_off| has constant row sums 1/c and is
+    similar to |R|, so rho(|R|) = 1/c exactly (Perron-Frobenius)."""
+    m = synth.random_sym(300, 3, c, 11)
+    assert abs(oracle.rho_abs_normalized(oracle.to_dense(m)) - 1.0 / c) <= 1e-12
+
+
+def test_rho_closed_form_grid():
+    """32 x 32 grid, diagonal 4.5: |R| = (path Laplacian adjacency)/4.5, whose
+    largest eigenvalue is 4 cos(pi / 33) / 4.5."""
+    m = synth.grid2d(32, -1.0, 4.5)
+    want = 4.0 * math.cos(math.pi / 33) / 4.5
+    assert abs(oracle.rho_abs_normalized(oracle.to_dense(m)) - want) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- rate bound
+def test_rate_bound_diagonally_dominant():
+    """Sec. "Upper Bound on Convergence Rate": after ceil(log eps / log gamma)
+    rounds, |x* - x_t| < eps ||b||_inf."""
+    m = synth.grid2d(12, -1.0, 4.5)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 4)
+    eps = 1e-8
+    t = oracle.rate_bound_rounds(A, eps)
+    # interior node: eps_i = 0.5, |N(i)| = 4, gamma = 1 / (1 + 0.5 / 4)
+    assert t == math.ceil(math.log(eps) / math.log(1.0 / (1.0 + 0.5 / 4)))
+    r = oracle.gabp_naive(m, b, max_iter=t, tol=0.0)
+    xs = oracle.dense_solve(A, b)
+    assert np.max(np.abs(xs - r["x"])) < eps * np.max(np.abs(b))
+
+
+# ----------------------------------------------------------------------------- iteration counts (soft)
+def _soft(got, paper):
+    return 0.7 * paper <= got <= 1.3 * paper
+
+
+def test_soft_counts_nonpsd():
+    """Table tab_nonPSD: parallel GaBP converges on the symmetric non-PSD 3x3 (paper: 38 rounds)."""
+    g = read_golden("iteration_counts.txt")
+    A, b = synth.nonpsd3x3()
+    r = oracle.gabp_naive(synth.from_dense(A), b, max_iter=1000, tol=1e-6, stop_rule="message")
+    assert r["status"] == oracle.OK and _soft(r["iters"], g["nonpsd3x3"][0])
+    assert np.allclose(r["x"], np.linalg.solve(A, b), atol=1e-4)
+
+
+def test_soft_counts_poisson():
+    """Table tab_2D_Poisson: 2-D Poisson, p = 10, f = -1, b = -f h^2 (paper: 134 rounds)."""
+    g = read_golden("iteration_counts.txt")
+    p = 10
+    m = synth.poisson2d(p)
+    b = np.full(m.n, (1.0 / (p + 1)) ** 2)
+    r = oracle.gabp_naive(m, b, max_iter=1000, tol=1e-6, stop_rule="message")
+    assert r["status"] == oracle.OK and _soft(r["iters"], g["poisson10"][0])
+
+
+@pytest.mark.parametrize("name", ["cdma_r3", "cdma_r4"])
+def test_soft_counts_cdma(name):
+    """Table tab_1: parallel GaBP on the CDMA correlation matrices (paper: 23 / 24)."""
+    g = read_golden("iteration_counts.txt")
+    A, b = getattr(synth, name)()
+    r = oracle.gabp_naive(synth.from_dense(A), b, max_iter=1000, tol=1e-6, stop_rule="message")
+    assert r["status"] == oracle.OK and _soft(r["iters"], g[name][0])
+    assert np.allclose(r["x"], np.linalg.solve(A, b), atol=1e-4)
+
+
+# ----------------------------------------------------------------------------- failure modes
+def test_breakdown_zero_cavity():
+    """A cavity precision that is exactly zero stops the run (the paper's listing
+    asserts P_{i\\j} != 0).  Star y with leaves x, z, w: in round 2
+    P_{y\\x} = A_yy - A_yz^2 / A_zz - A_yw^2 / A_ww = 3 - 1 - 2 = 0 exactly, while
+    every marginal precision of round 1 is nonzero."""
+    A = np.array([[2.0, 1.0, 0.0, 0.0], [1.0, 3.0, 1.0, 1.0], [0.0, 1.0, 1.0, 0.0], [0.0, 1.0, 0.0, 0.5]])
+    for run in (oracle.gabp_naive, oracle.gabp_broadcast):
+        r = run(synth.from_dense(A), np.ones(4), max_iter=10, tol=1e-14)
+        assert r["status"] == oracle.BREAKDOWN and r["iters"] == 2
+
+
+def test_invalid_inputs():
+    A, b = synth.toy3x3()
+    bad = A.copy()
+    bad[0, 1] = 5.0  # asymmetric value
+    assert oracle.gabp_naive(synth.from_dense(bad), b)["status"] == oracle.INVALID
+    bad = A.copy()
+    bad[1, 1] = 0.0  # zero diagonal
+    assert oracle.gabp_naive(synth.from_dense(bad), b)["status"] == oracle.INVALID
+
+
+def test_zero_rhs():
+    m = synth.grid2d(4)
+    r = oracle.gabp_naive(m, np.zeros(m.n))
+    assert r["status"] == oracle.OK and r["iters"] == 0 and not np.any(r["x"])
+
+
+# ----------------------------------------------------------------------------- convergence fix
+def _H_radius(A, G):
+    import scipy.linalg as sl
+    return float(np.max(sl.eigh(np.diag(G), A + np.diag(G), eigvals_only=True)))
+
+
+@pytest.mark.parametrize("gamma", [0.25, 0.5])
+def test_convergence_fix_non_walk_summable(gamma):
+    """Chapter "Fixing convergence of GaBP": J + Gamma is walk-summable for
+    gamma > rho(|R|) - 1, the double loop converges to J^{-1} h, and its error
+    contracts by rho((J + Gamma)^{-1} Gamma) < 1 per outer step (the lemma's proof).
+    A: n = 1024, 3 picks per row, diagonal 0.9 x row abs-sum (rho(|R|) = 1/0.9), SPD."""
+    m = synth.random_sym(1024, 3, 0.9, 5)
+    A = oracle.to_dense(m)
+    np.linalg.cholesky(A)
+    assert oracle.rho_abs_normalized(A) > 1.0
+    G = oracle.diagonal_loading(A, "uniform", gamma)
+    assert oracle.rho_abs_normalized(A + np.diag(G)) < 1.0
+    b = synth.rhs(m.n, 5)
+    f = oracle.convergence_fix(m, b, G, tol=1e-10, inner_tol=1e-13)
+    assert f["status"] == oracle.OK
+    xs = oracle.dense_solve(A, b)
+    assert np.linalg.norm(f["x"] - xs) <= 1e-9 * np.linalg.norm(xs)
+    h = f["history"]
+    ratio = float(np.median([h[i + 1] / h[i] for i in range(len(h) // 2, len(h) - 1)]))
+    rho_h = _H_radius(A, G)
+    assert rho_h < 1.0
+    assert abs(ratio - rho_h) <= 0.1 * rho_h
+
+
+def test_convergence_fix_where_plain_gabp_fails():
+    """An SPD matrix on which plain GaBP does not converge (diagonal 0.8 x row abs-sum):
+    the double loop still reaches A^{-1} b."""
+    m = synth.random_sym(1024, 3, 0.8, 7)
+    A = oracle.to_dense(m)
+    np.linalg.cholesky(A)
+    b = synth.rhs(m.n, 5)
+    plain = oracle.gabp_broadcast(m, b, max_iter=300, tol=1e-10)
+    assert plain["status"] != oracle.OK
+    G = oracle.diagonal_loading(A, "uniform", 0.3)
+    f = oracle.convergence_fix(m, b, G, tol=1e-8, inner_tol=1e-11, max_outer=3000)
+    assert f["status"] == oracle.OK
+    xs = oracle.dense_solve(A, b)
+    assert np.linalg.norm(f["x"] - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+# ----------------------------------------------------------------------------- gradient reference
+def test_dense_gradient_against_finite_differences():
+    """dL/db and the symmetrised dL/dA of L = 0.5 ||A^{-1} b - x*||^2 against central
+    differences (b_i; the pair A_ij = A_ji moved together; A_ii)."""
+    m = synth.random_sym(30, 3, 1.2, 9)
+    A = oracle.to_dense(m)
+    b = synth.rhs(30, 9)
+    xstar = synth.rhs(30, 10)
+    x, gb, G = oracle.dense_gradient(A, b, xstar)
+
+    def loss(A_, b_):
+        y = np.linalg.solve(A_, b_)
+        return 0.5 * np.sum((y - xstar) ** 2)
+
+    h = 1e-6
+    for i in (0, 7, 29):
+        e = np.zeros(30)
+        e[i] = h
+        fd = (loss(A, b + e) - loss(A, b - e)) / (2 * h)
+        assert abs(fd - gb[i]) <= 1e-7 * max(1.0, abs(fd))
+    rows, cols = np.nonzero(np.triu(A, 1))
+    for i, j in list(zip(rows, cols))[:6]:
+        E = np.zeros_like(A)
+        E[i, j] = E[j, i] = h
+        fd = (loss(A + E, b) - loss(A - E, b)) / (2 * h)
+        assert abs(fd - (G[i, j] + G[j, i])) <= 1e-7 * max(1.0, abs(fd))
+    for i in (3, 11):
+        E = np.zeros_like(A)
+        E[i, i] = h
+        fd = (loss(A + E, b) - loss(A - E, b)) / (2 * h)
+        assert abs(fd - G[i, i]) <= 1e-7 * max(1.0, abs(fd))
