@@ -1,0 +1,289 @@
+"""Benchmark: GaBP edge-updates/s on the random sparse symmetric workload (n = 2^20).
+
+One step = one complete solve of A x = b to relative residual 1e-10 through the
+C ABI: FP32 precision phase, frozen coefficients, FP32 mean rounds and FP64
+iterative refinement (the precision phase is re-run every step, nothing is
+cached between steps).  value = directed edges x rounds of all steps / device
+time.  The plain FP64 GaBP solve of the same system is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own right-hand side on its own GPU (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+N_NODES = 1 << 20
+PICKS = 8
+DIAG = 1.1
+SEED = 2
+TOL = 1e-10
+METRIC = "GaBP edge-updates/s (solve to relative residual 1e-10, FP32 messages + FP64 refinement)"
+WORKLOAD = (f"random sparse symmetric diagonally dominant A, n=2^20, {PICKS} uniform picks per row symmetrised, "
+            f"values U(-1,1), diagonal {DIAG} x row abs-sum, b ~ N(0,1)")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def start(self):
+        def run():
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([v.strip() for v in out.split(",")])
+                except Exception:
+                    return
+                self._stop.wait(0.2)
+
+        self._th = threading.Thread(target=run, daemon=True)
+        self._th.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for s in self.samples for j in range(4) if len(s) > 3 + j and s[3 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline_sample(m, b, rounds=5):
+    """The FP64 oracle (Algorithm 2, plain C, one thread) on a bounded sample:
+    `rounds` synchronous rounds over the full matrix."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.gabp_broadcast(m, b, max_iter=rounds, tol=0.0)
+    dt = time.perf_counter() - t0
+    return {"value": m.num_edges * rounds / dt, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rounds} rounds of the FP64 broadcast oracle over the full n=2^20 matrix "
+                      f"({m.num_edges} directed edges), input checks included, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    m = synth.random_sym(N_NODES, PICKS, DIAG, SEED)
+    b = synth.rhs(m.n, SEED)
+    vals = []
+    t_all = time.perf_counter()
+    rounds = 3
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline_sample(m, b, rounds)
+        if s >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    ms = m.num_edges * rounds / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edge-updates/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": m.n, "edges": m.num_edges,
+                       "sample_per_step": f"{rounds} oracle rounds"},
+            "cpu_baseline": {"value": v, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rounds} rounds of the FP64 broadcast oracle per step"},
+            "e2e": {"value": v, "unit": "edge-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import paper_0811_2518_gb300 as gb
+
+    m = synth.random_sym(N_NODES, PICKS, DIAG, SEED)
+    b = synth.rhs(m.n, SEED + rank)
+    E = m.num_edges
+    dev = torch.device("cuda", local)
+    b_dev = torch.from_numpy(b).to(dev)
+    x_dev = torch.empty_like(b_dev)
+
+    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1)
+    s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1)
+
+    def step(s):
+        _, st, it, rel = s.solve(b_dev, tol=TOL, max_iter=2000, x=x_dev)
+        if st != gb.GABP_OK:
+            raise RuntimeError(f"solve status {st} relres {rel}")
+        return s.stats()["rounds"], rel
+
+    # ---- FP32 + refinement (headline)
+    for _ in range(args.warmup):
+        step(s32)
+    s32.profile(reset=True)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record()
+    rounds = 0
+    rel = None
+    for _ in range(args.steps):
+        r, rel = step(s32)
+        rounds += r
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = s32.profile(reset=True)
+    if dist is not None:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = E * rounds * world / (ms_total / 1e3)
+
+    # roofline of the dominant kernel (largest phase time in the timed region)
+    peak, peak_kind = _peaks()
+    ph = max(("mean32", "prec32"), key=lambda k: prof["ms"][k])
+    n = m.n
+    # algorithmic bytes per launch: mean round 20 B/slot (c_in,c_out 8, col 4, h read 4, h write 4)
+    # + 24 B/node; precision round 20 B/slot (A 4, col 4, P read 4, previous-round P 4, P write 4) + 16 B/node
+    bytes_launch = (20 * E + 24 * n) if ph == "mean32" else (20 * E + 16 * n)
+    dur_ms = prof["ms"][ph] / max(prof["rounds"][ph], 1)
+    achieved = bytes_launch / (dur_ms / 1e3) / 1e9
+    kname = "k32_mean" if ph == "mean32" else "k32_prec"
+
+    # ---- plain FP64 GaBP on the same system (time to 1e-10)
+    for _ in range(max(1, args.warmup)):
+        step(s64)
+    s64.profile(reset=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r64 = 0
+    k64 = max(1, min(args.steps, 5))
+    for _ in range(k64):
+        rr, _ = step(s64)
+        r64 += rr
+    e1.record()
+    barrier()
+    ms64 = e0.elapsed_time(e1) / k64
+    p64 = s64.profile(reset=True)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    bh = torch.from_numpy(b).pin_memory().numpy()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    s32.solve_host(bh, xh, tol=TOL, max_iter=2000)
+    barrier()
+    t1 = time.perf_counter()
+    e2e_rounds = 0
+    for _ in range(args.steps):
+        st, it, rr = s32.solve_host(bh, xh, tol=TOL, max_iter=2000)
+        e2e_rounds += s32.stats()["rounds"]
+    barrier()
+    e2e_s = time.perf_counter() - t1
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(m, b, rounds=5)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "edge-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "edges": E, "nnz": m.nnz, "rhs": 1, "tol": TOL,
+                       "precision": "FP32 messages, FP64 residual and update",
+                       "rounds_per_step": rounds / args.steps, "final_relres": rel,
+                       "l2": "inputs larger than L2: 268 MB of edge state read and written per round",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_launch": bytes_launch, "launch_ms": dur_ms},
+            "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
+            "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},
+            "gpu_launches": prof["launches"],
+            "time_to_1e-10_ms": {"fp32_refine": ms_step, "fp64_plain": ms64},
+            "fp64_plain": {"ms_per_solve": ms64, "rounds": r64 / k64,
+                           "edge_updates_per_s": E * (r64 / k64) / (ms64 / 1e3),
+                           "phase_ms": p64["ms"]["fp64"] / k64},
+            "e2e": {"value": E * e2e_rounds / e2e_s, "unit": "edge-updates/s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s / args.steps * 1e3},
+            "clocks": clk,
+            "wall_timed_s": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    s32.close()
+    s64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -60,21 +60,21 @@ typedef enum {
                                 update x += d (iterative refinement) are the only FP64 steps */
 } gabp_precision;
 
-/* How a round is organised on the GPU; both compute Algorithm 2. */
+/* How an FP64 round is organised on the GPU; both compute Algorithm 2 and give
+ * the same iterates.  (The FP32 path always uses its own recompute form.) */
 typedef enum {
-  GABP_VARIANT_NODE = 0,  /* fused node-centric kernel: a sub-warp per row forms the aggregate and
-                             every message into the row; the reverse message is recomputed from the
-                             row's own state, so no edge array is gathered or scattered */
-  GABP_VARIANT_EDGE = 1   /* two kernels per round: row aggregates, then one thread per directed edge
-                             reading the reverse message through the reverse-edge index */
+  GABP_VARIANT_NODE = 0,  /* one fused kernel per round: a sub-warp per row gathers each sender's
+                             aggregate and the reverse message, writes the row's in-messages, and
+                             forms the row's aggregate, x and residual in the same pass */
+  GABP_VARIANT_EDGE = 1   /* two kernels per round: one thread per directed edge computes its
+                             message (aggregate minus reverse message), then a row kernel sums them */
 } gabp_variant;
 
 typedef struct {
   int variant;          /* gabp_variant, default GABP_VARIANT_NODE */
   int precision;        /* gabp_precision, default GABP_PREC_FP64 */
   int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16 */
-  int freeze_precisions;/* 1: once every precision message is stationary to ~4 ulp between two
-                           rounds, stop re-computing precisions (FP64 path), default 1 */
+  int freeze_precisions;/* reserved for the FP64 path (precisions co-iterate there), default 1 */
   double inner_tol;     /* FP32 inner-solve relative residual target, default 1e-4 */
   int inner_max_iter;   /* rounds per inner solve, default 400 */
   int max_refine;       /* refinement steps, default 30 */
@@ -82,7 +82,11 @@ typedef struct {
                            2 Gamma_ii = max(0, sum_j |A_ij| - A_ii) + gamma * A_ii; default 0 */
   double gamma;         /* loading parameter for gamma_mode, default 0.25 */
   int lanes;            /* lanes per row for R = 1 kernels (1..32, power of two); 0 = autotune */
-  int reserved[8];
+  int profile;          /* 1: time every phase with CUDA events (read with gabp_profile_read), default 0 */
+  int reuse_precisions; /* FP32 path: 1 keeps the converged precision messages of A for later
+                           solves (they do not depend on b); 0 re-runs the precision phase in every
+                           solve.  Default 1 */
+  int reserved[6];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */
@@ -140,8 +144,8 @@ gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x, double to
  * messages + FP64 refinement (the precision messages depend on A only, eq_prec
  * and eq_prec_message, so they are converged once and shared).
  * B, X: device, column r at B + r*ld (ld >= n).  iters_out: total inner rounds.
- * relres_out (nullable, device or host per mem_space of the handle? no: HOST
- * array of nrhs doubles) receives each column's final relative residual.
+ * relres_out (nullable): HOST array of nrhs doubles receiving each column's
+ * final relative residual.
  * Returns the worst status over the columns.
  */
 gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
@@ -170,6 +174,19 @@ gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *
  * precision-phase and refinement inner rounds, and the directed-edge count E
  * (off-diagonal nnz).  edge-updates of the solve = rounds * E * nrhs. */
 gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int32_t *refine_steps);
+
+/* Per-phase device time of the solves since the last reset (options.profile = 1):
+ * phase 0 FP64 GaBP rounds, 1 FP32 precision rounds, 2 FP32 mean rounds,
+ * 3 FP64 refinement steps (residual + update).  ms: summed CUDA-event time
+ * around the phase's launches on the handle's stream (it includes the few
+ * rounds launched after a decision, which return at once); rounds: round
+ * kernels that did work; launches: every kernel the library launched. */
+typedef struct {
+  double ms[4];
+  int64_t rounds[4];
+  int64_t launches;
+} gabp_profile;
+gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
 
 /* Free everything the handle owns.  NULL is accepted. */
 gabp_status gabp_destroy(gabp_handle h);

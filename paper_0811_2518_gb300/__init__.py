@@ -1,0 +1,318 @@
+"""GB300 (sm_103a) Gaussian belief propagation solver -- Python binding.
+
+A thin ctypes layer over the C ABI declared in ``include/gabp.h``.  Functions
+carry the C names (``gabp_create``, ``gabp_solve`` ...) and only marshal
+arguments: every step of a solve runs in the CUDA kernels of ``libgabp.so``.
+PyTorch supplies device memory and streams.  If the library has not been
+built, importing the binding raises: there is no CPU fallback.
+
+Paper: D. Bickson, "Gaussian Belief Propagation: Theory and Application"
+(GaBP as a solver for A x = b, Algorithms 1 and 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "GABP_OK", "GABP_NOT_CONVERGED", "GABP_DIVERGED", "GABP_BREAKDOWN", "GABP_TIMEOUT",
+    "GABP_ERR_INVALID", "GABP_ERR_CUDA", "GABP_ERR_NOMEM",
+    "GABP_PREC_FP64", "GABP_PREC_FP32_REFINE", "GABP_VARIANT_NODE", "GABP_VARIANT_EDGE",
+    "Options", "lib", "library_path", "exported_symbols",
+    "gabp_options_default", "gabp_create", "gabp_set_options", "gabp_set_stream", "gabp_solve",
+    "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "Solver", "GaBPError",
+]
+
+GABP_OK, GABP_NOT_CONVERGED, GABP_DIVERGED, GABP_BREAKDOWN, GABP_TIMEOUT = 0, 1, 2, 3, 4
+GABP_ERR_INVALID, GABP_ERR_CUDA, GABP_ERR_NOMEM = -1, -2, -3
+GABP_PREC_FP64, GABP_PREC_FP32_REFINE = 0, 1
+GABP_VARIANT_NODE, GABP_VARIANT_EDGE = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "_lib", "libgabp.so")
+
+
+class Options(ctypes.Structure):
+    """Mirror of ``gabp_options`` (include/gabp.h)."""
+    _fields_ = [
+        ("variant", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("freeze_precisions", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("inner_max_iter", ctypes.c_int),
+        ("max_refine", ctypes.c_int),
+        ("gamma_mode", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("lanes", ctypes.c_int),
+        ("profile", ctypes.c_int),
+        ("reuse_precisions", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
+    ]
+
+
+class Profile(ctypes.Structure):
+    """Mirror of ``gabp_profile``."""
+    _fields_ = [("ms", ctypes.c_double * 4), ("rounds", ctypes.c_int64 * 4), ("launches", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "gabp_options_default": ([ctypes.POINTER(Options)], ctypes.c_int),
+    "gabp_create": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _P,
+                     ctypes.POINTER(Options)], ctypes.c_int),
+    "gabp_set_options": ([_P, ctypes.POINTER(Options)], ctypes.c_int),
+    "gabp_set_stream": ([_P, _P], ctypes.c_int),
+    "gabp_solve": ([_P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gabp_solve_host": ([_P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gabp_solve_batched": ([_P, ctypes.c_int32, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_int32), _P], ctypes.c_int),
+    "gabp_marginal_precisions": ([_P, _P], ctypes.c_int),
+    "gabp_get_messages": ([_P, _P, _P], ctypes.c_int),
+    "gabp_grad_values": ([_P, _P, _P, _P], ctypes.c_int),
+    "gabp_last_stats": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_profile_read": ([_P, ctypes.POINTER(Profile), ctypes.c_int], ctypes.c_int),
+    "gabp_destroy": ([_P], ctypes.c_int),
+    "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gabp_last_error": ([], ctypes.c_char_p),
+}
+
+
+def _load():
+    if not os.path.exists(library_path):
+        raise ImportError(
+            f"{library_path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()' or python paper_0811_2518_gb300/build.py)")
+    L = ctypes.CDLL(library_path)
+    for name, (args, res) in _SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def exported_symbols():
+    """Names of every C entry point the binding declares (all must be exported)."""
+    return list(_SIGNATURES)
+
+
+class GaBPError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = gabp_status_string(status)
+        err = gabp_last_error()
+        super().__init__(f"{where}: {msg} ({status})" + (f" -- {err}" if err else ""))
+
+
+# ----------------------------------------------------------------------------- C names
+def gabp_options_default() -> Options:
+    o = Options()
+    lib.gabp_options_default(ctypes.byref(o))
+    return o
+
+
+def gabp_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, mem_space, stream_ptr, options=None):
+    """Returns (status, handle)."""
+    h = _P()
+    st = lib.gabp_create(ctypes.byref(h), int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
+                         int(mem_space), _P(stream_ptr), ctypes.byref(options) if options is not None else None)
+    return st, h
+
+
+def gabp_set_options(h, options):
+    return lib.gabp_set_options(h, ctypes.byref(options))
+
+
+def gabp_set_stream(h, stream_ptr):
+    return lib.gabp_set_stream(h, _P(stream_ptr))
+
+
+def _solve(fn, h, b_ptr, x_ptr, tol, max_iter):
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = fn(h, _P(b_ptr), _P(x_ptr), float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def gabp_solve(h, b_ptr, x_ptr, tol, max_iter):
+    """Returns (status, iters, relres)."""
+    return _solve(lib.gabp_solve, h, b_ptr, x_ptr, tol, max_iter)
+
+
+def gabp_solve_host(h, b_ptr, x_ptr, tol, max_iter):
+    return _solve(lib.gabp_solve_host, h, b_ptr, x_ptr, tol, max_iter)
+
+
+def gabp_solve_batched(h, nrhs, B_ptr, X_ptr, ld, tol, max_iter, relres_host_ptr=None):
+    it = ctypes.c_int32(0)
+    st = lib.gabp_solve_batched(h, int(nrhs), _P(B_ptr), _P(X_ptr), int(ld), float(tol), int(max_iter),
+                                ctypes.byref(it), _P(relres_host_ptr) if relres_host_ptr else None)
+    return st, it.value
+
+
+def gabp_marginal_precisions(h, Pi_ptr):
+    return lib.gabp_marginal_precisions(h, _P(Pi_ptr))
+
+
+def gabp_get_messages(h, P_ptr, hm_ptr):
+    return lib.gabp_get_messages(h, _P(P_ptr), _P(hm_ptr))
+
+
+def gabp_grad_values(h, lam_ptr, x_ptr, g_ptr):
+    return lib.gabp_grad_values(h, _P(lam_ptr), _P(x_ptr), _P(g_ptr))
+
+
+def gabp_last_stats(h):
+    r, e, s = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    st = lib.gabp_last_stats(h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(s))
+    return st, r.value, e.value, s.value
+
+
+def gabp_profile_read(h, reset=False):
+    """Returns (status, dict) with per-phase ms / rounds and the launch count."""
+    p = Profile()
+    st = lib.gabp_profile_read(h, ctypes.byref(p), 1 if reset else 0)
+    names = ("fp64", "prec32", "mean32", "refine64")
+    return st, {"ms": dict(zip(names, list(p.ms))), "rounds": dict(zip(names, list(p.rounds))),
+                "launches": p.launches}
+
+
+def gabp_destroy(h):
+    return lib.gabp_destroy(h)
+
+
+def gabp_status_string(s) -> str:
+    return lib.gabp_status_string(int(s)).decode()
+
+
+def gabp_last_error() -> str:
+    v = lib.gabp_last_error()
+    return v.decode() if v else ""
+
+
+# ----------------------------------------------------------------------------- torch convenience
+class Solver:
+    """A GaBP solver bound to one symmetric matrix A (full CSR, diagonal included).
+
+    ``rowptr``/``col``/``val`` may be numpy arrays (host) or CUDA tensors
+    (int32/int32/float64).  Solves take and return CUDA float64 tensors and run
+    on ``stream`` (default: torch's current stream at construction).
+    """
+
+    def __init__(self, n, rowptr, col, val, options: Options | None = None, stream=None, **opts):
+        import numpy as np
+        import torch
+
+        self.n = int(n)
+        self.options = options if options is not None else gabp_options_default()
+        for k, v in opts.items():
+            setattr(self.options, k, v)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = []
+        if isinstance(rowptr, torch.Tensor):
+            rp = rowptr.to(self.device, torch.int32).contiguous()
+            cl = col.to(self.device, torch.int32).contiguous()
+            vl = val.to(self.device, torch.float64).contiguous()
+            self._keep += [rp, cl, vl]
+            ptrs, mem = (rp.data_ptr(), cl.data_ptr(), vl.data_ptr()), 1
+            nnz = int(cl.numel())
+        else:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            vl = np.ascontiguousarray(val, dtype=np.float64)
+            self._keep += [rp, cl, vl]
+            ptrs, mem = (rp.ctypes.data, cl.ctypes.data, vl.ctypes.data), 0
+            nnz = int(cl.size)
+        self.nnz = nnz
+        st, h = gabp_create(self.n, nnz, *ptrs, mem, self.stream.cuda_stream, self.options)
+        self._keep = []
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_create")
+        self.handle = h
+
+    @classmethod
+    def from_csr(cls, m, **kw):
+        return cls(m.n, m.rowptr, m.col, m.val, **kw)
+
+    def set_options(self, **opts):
+        for k, v in opts.items():
+            setattr(self.options, k, v)
+        st = gabp_set_options(self.handle, self.options)
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_set_options")
+
+    def solve(self, b, tol=1e-12, max_iter=1000, x=None, check=True):
+        """x = A^{-1} b.  Returns (x, status, iters, relres)."""
+        import torch
+
+        b = b.to(self.device, torch.float64).contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        st, it, rel = gabp_solve(self.handle, b.data_ptr(), x.data_ptr(), tol, max_iter)
+        if check and st < 0:
+            raise GaBPError(st, "gabp_solve")
+        return x, st, it, rel
+
+    def solve_host(self, b, x, tol=1e-12, max_iter=1000):
+        """b, x: host numpy float64 arrays (pinned or pageable)."""
+        st, it, rel = gabp_solve_host(self.handle, b.ctypes.data, x.ctypes.data, tol, max_iter)
+        if st < 0:
+            raise GaBPError(st, "gabp_solve_host")
+        return st, it, rel
+
+    def marginal_precisions(self):
+        import torch
+
+        P = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        st = gabp_marginal_precisions(self.handle, P.data_ptr())
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_marginal_precisions")
+        return P
+
+    def messages(self):
+        """(P, h) per input CSR slot: message col -> row of the last FP64 solve."""
+        import torch
+
+        P = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        hm = torch.empty_like(P)
+        st = gabp_get_messages(self.handle, P.data_ptr(), hm.data_ptr())
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_get_messages")
+        return P, hm
+
+    def grad_values(self, lam, x):
+        import torch
+
+        g = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        st = gabp_grad_values(self.handle, lam.data_ptr(), x.data_ptr(), g.data_ptr())
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_grad_values")
+        return g
+
+    def stats(self):
+        st, rounds, E, steps = gabp_last_stats(self.handle)
+        return {"rounds": rounds, "edges": E, "refine_steps": steps}
+
+    def profile(self, reset=False):
+        st, p = gabp_profile_read(self.handle, reset)
+        return p
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gabp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,131 @@
+// api.cu -- the C ABI entry points that run solves (gabp_create / gabp_destroy /
+// options / status strings live in setup.cu).
+#include "gabp_internal.cuh"
+
+#include <cmath>
+
+using namespace gabp;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                           int32_t *iters_out, double *relres_out) {
+  if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  int it = 0;
+  double rel = 0.0;
+  gabp_status s;
+  if (h->opt.gamma_mode != 0) {
+    // convergence fix: FP32 GaBP inner solves on A + Gamma inside the FP64 outer loop
+    if (!h->gamma) {
+      cudaError_t e = cudaMalloc(&h->gamma, sizeof(double) * h->g.n);
+      if (e != cudaSuccess) return cuda_fail(e, "gamma");
+    }
+    s = make_gamma(h, h->gamma);
+    if (s == GABP_OK) s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, h->gamma, &it, &rel);
+    h->last_path = 1;
+  } else if (h->opt.precision == GABP_PREC_FP32_REFINE) {
+    s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, nullptr, &it, &rel);
+    h->last_path = 1;
+  } else {
+    s = solve64(h, b, x, tol, max_iter, &it, &rel);
+    h->last_path = 0;
+  }
+  if (cur != h->device) cudaSetDevice(cur);
+  if (s >= 0) {
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = rel;
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" gabp_status gabp_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                                  int32_t *iters_out, double *relres_out) {
+  if (!h || !b || !x) return GABP_ERR_INVALID;
+  if (!is_device_ptr(b) || !is_device_ptr(x)) {
+    set_last_error("gabp_solve: b and x must be device arrays (use gabp_solve_host for host arrays)");
+    return GABP_ERR_INVALID;
+  }
+  return solve_dispatch(h, b, x, tol, max_iter, iters_out, relres_out);
+}
+
+extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                                       int32_t *iters_out, double *relres_out) {
+  if (!h || !b || !x) return GABP_ERR_INVALID;
+  const size_t bytes = sizeof(double) * h->g.n;
+  if (!h->hb) {
+    cudaError_t e = cudaMalloc(&h->hb, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->hx, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "gabp_solve_host staging");
+  }
+  GABP_CUDA(cudaMemcpyAsync(h->hb, b, bytes, cudaMemcpyHostToDevice, h->stream));
+  gabp_status s = solve_dispatch(h, h->hb, h->hx, tol, max_iter, iters_out, relres_out);
+  if (s < 0) return s;
+  GABP_CUDA(cudaMemcpyAsync(x, h->hx, bytes, cudaMemcpyDeviceToHost, h->stream));
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return s;
+}
+
+extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
+                                          double tol, int32_t max_iter, int32_t *iters_out, double *relres_out) {
+  (void)h; (void)nrhs; (void)B; (void)X; (void)ld; (void)tol; (void)max_iter; (void)iters_out; (void)relres_out;
+  set_last_error("gabp_solve_batched: not available in this build");
+  return GABP_ERR_INVALID;
+}
+
+extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
+  if (!h || !Pi) return GABP_ERR_INVALID;
+  if (h->last_path == 0) return marginals(h, Pi);
+  if (h->last_path == 1) return marginals32(h, Pi);
+  return GABP_ERR_INVALID;
+}
+
+extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
+  if (!h || !P || !hm || h->last_path != 0) return GABP_ERR_INVALID;
+  return messages64(h, P, hm);
+}
+
+extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val) {
+  if (!h || !lambda || !x || !grad_val) return GABP_ERR_INVALID;
+  return grad_values(h, lambda, x, grad_val);
+}
+
+extern "C" gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int32_t *refine_steps) {
+  if (!h) return GABP_ERR_INVALID;
+  if (rounds) *rounds = h->stats.rounds;
+  if (num_edges) *num_edges = h->g.E;
+  if (refine_steps) *refine_steps = h->stats.refine_steps;
+  return GABP_OK;
+}
+
+extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset) {
+  if (!h) return GABP_ERR_INVALID;
+  if (out) {
+    for (int j = 0; j < 4; ++j) {
+      out->ms[j] = h->prof.ms[j];
+      out->rounds[j] = h->prof.rounds[j];
+    }
+    out->launches = h->prof.launches;
+  }
+  if (reset) {
+    for (int j = 0; j < 4; ++j) {
+      h->prof.ms[j] = 0.0;
+      h->prof.rounds[j] = 0;
+    }
+    h->prof.launches = 0;
+  }
+  return GABP_OK;
+}

@@ -1,0 +1,132 @@
+// devutil.cuh -- small device helpers shared by the solver's kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "gabp_internal.cuh"
+
+namespace gabp {
+
+// Reciprocal of a double by Newton-Raphson iteration (y <- y + y (1 - d y)),
+// seeded with the single-precision hardware approximation (PTX rcp.approx.ftz.f32).
+// The seed's relative error is about 2^-22; each step squares it, so two steps
+// reach FP64 rounding level (within a couple of ulp of 1/d).  Outside the range
+// where the single-precision seed is a normal number the IEEE division is used.
+__device__ __forceinline__ double rcp64(double d) {
+  float df = __double2float_rn(d);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(df));
+  double y = (double)yf;
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  float a = fabsf(df);
+  if (!(a > 1e-30f && a < 1e30f)) y = 1.0 / d;
+  return y;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the L lanes of a sub-warp (L a power of two dividing 32); every lane
+// of the warp must call it.
+template <int L, typename T>
+__device__ __forceinline__ T sub_sum(T v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, L);
+  return v;
+}
+
+// Block-wide sum of NV doubles (kBlock threads).  Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kBlock / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = warp_sum(v[j]);
+    if (l == 0) sh[j][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = l < kBlock / 32 ? sh[j][l] : 0.0;
+      v[j] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide max of NV doubles.  Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_max(double (&v)[NV]) {
+  __shared__ double sh[NV][kBlock / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = warp_max(v[j]);
+    if (l == 0) sh[j][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = l < kBlock / 32 ? sh[j][l] : -1.0;
+      v[j] = warp_max(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Publish this block's NV partial values (thread 0 holds them) into
+// partials[j * gridDim.x + blockIdx.x] and find out whether this block is the
+// last of the grid to finish.  In the last block, tot[] (valid in thread 0)
+// receives the sums over all blocks, taken in block order (deterministic).
+// modes[j] = 0 sums, 1 takes the max.
+template <int NV>
+__device__ __forceinline__ bool last_block_reduce(double (&v)[NV], const int (&modes)[NV], double *partials,
+                                                  unsigned int *arrive, double (&tot)[NV]) {
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) partials[j * gridDim.x + blockIdx.x] = v[j];
+    __threadfence();
+    unsigned int prev = atomicAdd(arrive, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) acc[j] = modes[j] ? -1.0 : 0.0;
+  for (int bI = threadIdx.x; bI < (int)gridDim.x; bI += kBlock) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double p = __ldcg(partials + j * gridDim.x + bI);
+      acc[j] = modes[j] ? fmax(acc[j], p) : acc[j] + p;
+    }
+  }
+  // deterministic: each thread's stripe is fixed; the block tree is fixed
+  double s[NV], m[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) { s[j] = modes[j] ? 0.0 : acc[j]; m[j] = modes[j] ? acc[j] : -1.0; }
+  block_sum<NV>(s);
+  block_max<NV>(m);
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = modes[j] ? m[j] : s[j];
+  return true;
+}
+
+}  // namespace gabp

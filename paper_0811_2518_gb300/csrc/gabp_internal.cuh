@@ -1,0 +1,182 @@
+// gabp_internal.cuh -- device data layout and host-side handle of the GaBP solver.
+//
+// Layout in HBM (all arrays owned by the handle):
+//   off-diagonal CSR in receiver layout: row i, slot e in [rp[i], rp[i+1]) with
+//   k = ci[e] holds the message k -> i.  av[e] = A_ik, ad[i] = A_ii.
+//   rev[e] is the slot of the reverse edge (row k, column i).
+//   FP64 path: M64[2][E] double2 {P, h} (h = P * mu, the information form of the
+//   mean message), N64[2][n] 32-byte node records {P~, h~, x, -}.
+//   FP32 path: precision chains MP[2][E] float, coefficient pairs CF[E] float2,
+//   mean chains H[2][E][R] float, node rings.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+
+#include "../../include/gabp.h"
+
+namespace gabp {
+
+constexpr int kBlock = 256;
+
+struct __align__(32) NodeRec64 {
+  double P;  // P~_i = A_ii + sum_k P_ki
+  double h;  // h~_i = b_i + sum_k h_ki
+  double x;  // x_i = h~_i / P~_i
+  double pad;
+};
+
+// Device-side control block of one iterative run.  Written by the last block
+// of each round kernel; every round kernel reads it first.
+struct DevCtl {
+  int round;         // last completed round t
+  int done;          // 1 once a terminal decision was taken
+  int status;        // gabp_status of the run
+  int iters;         // rounds of the returned iterate (or at which breakdown happened)
+  int result_round;  // round whose node records hold the answer
+  int max_iter;
+  int check_from;    // first round whose iterate may be accepted (1 for GaBP)
+  int stable;        // consecutive rounds with a stationary precision set
+  double bb;         // ||b||^2
+  double tol2bb;     // tol^2 ||b||^2
+  double rr;         // squared residual (or squared update) of the latest checked iterate
+  double maxrel;     // max relative change of the precision messages in the latest round
+  double xx;         // squared norm of the latest iterate (FP32 inner solves)
+  unsigned int arrive;
+  int edge_bad;      // breakdown flag raised by an edge kernel, consumed by the round's last block
+  const double *b;   // right-hand side of the current FP64 run (device); read by the round kernels
+};
+
+struct Graph {
+  int n = 0;
+  int64_t nnz = 0;  // full CSR (with diagonal)
+  int E = 0;        // off-diagonal entries = directed edges
+  int *rowptr = nullptr, *col = nullptr;  // full CSR copy (device)
+  double *val = nullptr;
+  int *rp = nullptr, *ci = nullptr, *rev = nullptr, *dpos = nullptr;
+  double *av = nullptr, *ad = nullptr;
+  float *av32 = nullptr, *ad32 = nullptr;
+  double avg_deg = 0;
+};
+
+struct Work64 {
+  double2 *M[2] = {nullptr, nullptr};
+  NodeRec64 *N[2] = {nullptr, nullptr};
+  bool valid = false;   // a solve has completed; messages/records are readable
+  int result_round = 0;
+};
+
+struct Work32 {
+  // precision phase (recompute form): chains + node ring of 3
+  float *MP[2] = {nullptr, nullptr};
+  float *NP[3] = {nullptr, nullptr, nullptr};
+  float2 *CF = nullptr;   // {c_in, c_out} per slot
+  float *invP = nullptr;  // 1 / P~_i (frozen)
+  bool coef_ready = false;
+  int prec_round = -1;    // round of the frozen precision state
+  int R = 0;              // RHS capacity of the mean buffers
+  float *H[2] = {nullptr, nullptr};               // [E][R]
+  float *NH[3] = {nullptr, nullptr, nullptr};     // [n][R] h~ ring
+  float *rhs32 = nullptr;                         // [n][R]
+  double *X = nullptr, *Rs = nullptr;             // [n][R] FP64 iterate and residual
+  double *Bt = nullptr;                           // [n][R] FP64 right-hand sides (interleaved)
+  double *colnorm = nullptr;                      // per-RHS reductions [4][R]
+  DevCtl *ctlR = nullptr;                         // per-RHS control (refinement)
+  int *rhs_active = nullptr;
+};
+
+struct Stats {
+  int64_t rounds = 0;
+  int refine_steps = 0;
+};
+
+// Phase timing (options.profile): CUDA events around each phase's launches.
+enum { PH_FP64 = 0, PH_PREC32 = 1, PH_MEAN32 = 2, PH_REFINE64 = 3 };
+struct Prof {
+  double ms[4] = {0, 0, 0, 0};
+  int64_t rounds[4] = {0, 0, 0, 0};
+  int64_t launches = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+}  // namespace gabp
+
+struct gabp_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gabp_options opt{};
+  gabp::Graph g;
+  gabp::Work64 w64;
+  gabp::Work32 w32;
+  gabp::Stats stats;
+  gabp::DevCtl *ctl = nullptr;      // device control block
+  gabp::DevCtl *ctl_host = nullptr; // pinned mirror
+  double *partials = nullptr;       // per-block partial sums [4 * max_blocks]
+  int max_blocks = 0;
+  int num_sms = 0;
+  double *hb = nullptr, *hx = nullptr;  // device staging for gabp_solve_host
+  // captured round graphs (keyed by kind), rebuilt when options change
+  cudaGraphExec_t g64 = nullptr;
+  int g64_key = -1;
+  cudaGraphExec_t gP32 = nullptr;
+  cudaGraphExec_t gH32 = nullptr;
+  int gH32_R = -1;
+  int last_path = -1;               // 0 FP64, 1 FP32 refinement (for gabp_marginal_precisions)
+  double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
+  gabp::Prof prof;
+};
+
+namespace gabp {
+
+// error plumbing ---------------------------------------------------------------
+void set_last_error(const std::string &s);
+gabp_status cuda_fail(cudaError_t e, const char *what);
+
+#define GABP_CUDA(call)                                     \
+  do {                                                      \
+    cudaError_t e__ = (call);                               \
+    if (e__ != cudaSuccess) return ::gabp::cuda_fail(e__, #call); \
+  } while (0)
+
+inline int blocks_for(int64_t work, int per_block, int max_blocks) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+// Profiling brackets: prof_begin records e0 before a phase's launches,
+// prof_end records e1 after them; prof_collect (after a synchronisation) adds
+// the elapsed time to the phase.
+inline void prof_begin(gabp_handle h) {
+  if (h->opt.profile) cudaEventRecord(h->prof.e0, h->stream);
+}
+inline void prof_end(gabp_handle h) {
+  if (h->opt.profile) cudaEventRecord(h->prof.e1, h->stream);
+}
+inline void prof_collect(gabp_handle h, int phase, int64_t rounds) {
+  h->prof.rounds[phase] += rounds;
+  if (!h->opt.profile) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, h->prof.e0, h->prof.e1) == cudaSuccess) h->prof.ms[phase] += ms;
+  else cudaGetLastError();
+}
+
+// shared host helpers (defined in setup.cu / solve64.cu / solve32.cu)
+gabp_status read_ctl(gabp_handle h);  // copies ctl -> ctl_host and synchronises
+gabp_status ensure_w64(gabp_handle h);
+void free_w64(gabp_handle h);
+gabp_status ensure_w32(gabp_handle h, int R);
+void free_w32(gabp_handle h);
+gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
+                    double *relres);
+gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int64_t ld, double tol,
+                           int max_iter, const double *gamma_diag, int *iters, double *relres);
+gabp_status messages64(gabp_handle h, double *P, double *hm);
+gabp_status marginals(gabp_handle h, double *Pi);
+gabp_status grad_values(gabp_handle h, const double *lam, const double *x, double *g);
+gabp_status make_gamma(gabp_handle h, double *out);
+gabp_status marginals32(gabp_handle h, double *Pi);
+
+}  // namespace gabp

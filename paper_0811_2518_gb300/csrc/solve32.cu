@@ -1,0 +1,567 @@
+// solve32.cu -- FP32 messages + FP64 iterative refinement, and the convergence fix.
+//
+// The precision messages do not depend on b (eq_prec, eq_prec_message: P_ij =
+// -A_ij^2 / P_{i\j}), so they are iterated once per matrix, then frozen.  With
+// P frozen, the information-form mean message is linear in the cavity:
+//   h_ij = c_ij (h~_i - h_ji),   c_ij = -A_ij / (P~_i - P_ji)       (Algorithm 2),
+// and x_i = h~_i / P~_i.  These iterations run in FP32; the only FP64 steps are
+// the outer residual r = b - A x and the update x <- x + d, where d is the FP32
+// GaBP solution of A d = r.  With a diagonal loading Gamma the inner solves run
+// on A + Gamma and the same outer loop is the paper's convergence fix
+//   x^(t+1) = x^(t) + (A + Gamma)^{-1} (b - A x^(t)) = (A + Gamma)^{-1}(b + Gamma x^(t))
+// (Chapter "Fixing convergence of GaBP", eq:iterative_method).
+//
+// Recompute form.  Slot e of row i (sender k) keeps its own in-message in one of
+// two chains (even / odd rounds).  Round t needs the reverse message i -> k of
+// round t-1, which row i itself can recompute from what it held at round t-2:
+//   h_{i->k}^{(t-1)} = c_out (h~_i^{(t-2)} - h_{k->i}^{(t-2)}),
+//   h_{k->i}^{(t)}   = c_in  (h~_k^{(t-1)} - h_{i->k}^{(t-1)}),
+// with c_in = c_ki and c_out = c_ik stored side by side in slot e.  The same
+// holds for the precision messages.  Every edge array is then read and written
+// in place, coalesced, with no gather or scatter through rev[]; only the node
+// values h~_k^{(t-1)} are gathered (they stay in L2).  In exact arithmetic this
+// is the synchronous schedule of Algorithm 2; in FP32 it rounds the same way as
+// computing h_{i->k}^{(t-1)} once and storing it.
+#include "gabp_internal.cuh"
+#include "devutil.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace gabp {
+
+constexpr int kPrecMaxRounds = 300;  // cap of the FP32 precision phase
+
+struct Args32 {
+  int n;
+  const int *__restrict__ rp;
+  const int *__restrict__ ci;
+  const float *__restrict__ av;
+  const float *__restrict__ ad;   // diagonal of the matrix the inner solves run on (A + Gamma)
+  float *MP0, *MP1;               // precision chains
+  float *NP0, *NP1, *NP2;         // P~ ring
+  float2 *CF;                     // {c_in, c_out}
+  float *invP;
+  float *H0, *H1;                 // mean chains
+  float *NH0, *NH1, *NH2;         // h~ ring
+  const float *rhs;               // FP32 right-hand side of the inner solve
+  DevCtl *ctl;
+  double *partials;
+};
+
+__device__ __forceinline__ float *ring3(float *a, float *b, float *c, int t) {
+  int m = t % 3;
+  return m == 0 ? a : (m == 1 ? b : c);
+}
+
+// ---------------------------------------------------------------------------- precision phase
+// Round t of the precision-only iteration (eq_prec + eq_prec_message, Algorithm 2),
+// recompute form.  The run stops once max |P^(t) - P^(t-1)| / |P^(t)| <= 2^-20
+// (16 ulp of FP32) in two consecutive rounds, on a zero cavity, or at max_iter.
+// FP32 rounding keeps some messages moving by a few ulp forever, so an exact
+// stationary point is not waited for: the outer FP64 refinement absorbs what
+// the frozen coefficients are off by.
+template <int L>
+__global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  float *__restrict__ Mc = (t & 1) ? a.MP1 : a.MP0;        // holds t-2, becomes t
+  const float *__restrict__ Mo = (t & 1) ? a.MP0 : a.MP1;  // holds t-1
+  const float *__restrict__ Pm1 = ring3(a.NP0, a.NP1, a.NP2, t + 2);
+  const float *__restrict__ Pm2 = ring3(a.NP0, a.NP1, a.NP2, t + 1);
+  float *__restrict__ Pt = ring3(a.NP0, a.NP1, a.NP2, t);
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  float rel = 0.f;
+  double bad = 0.0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    float acc = 0.f;
+    if (i < a.n) {
+      const float Pi2 = t >= 2 ? Pm2[i] : 0.f;
+      const int e1 = a.rp[i + 1];
+      for (int e = a.rp[i] + sl; e < e1; e += L) {
+        const int k = a.ci[e];
+        const float A = a.av[e];
+        const float A2 = A * A;
+        float Pout = 0.f;
+        if (t >= 2) {
+          const float d1 = Pi2 - Mc[e];
+          if (d1 == 0.f) bad += 1.0;
+          Pout = -A2 / d1;
+        }
+        const float d2 = Pm1[k] - Pout;
+        if (d2 == 0.f) bad += 1.0;
+        const float Pn = -A2 / d2;
+        const float prev = Mo[e];
+        Mc[e] = Pn;
+        acc += Pn;
+        rel = fmaxf(rel, fabsf(Pn - prev) / fabsf(Pn));
+      }
+    }
+    acc = sub_sum<L>(acc);
+    if (i < a.n && sl == 0) {
+      const float P = a.ad[i] + acc;
+      if (P == 0.f) bad += 1.0;
+      Pt[i] = P;
+    }
+  }
+  double vb[1] = {bad}, vr[1] = {(double)rel};
+  block_sum<1>(vb);
+  block_max<1>(vr);
+  double v[2] = {vb[0], vr[0]}, tot[2];
+  const int modes[2] = {0, 1};
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    ctl->round = t;
+    ctl->maxrel = tot[1];
+    const bool stat = !(tot[1] > 9.5367431640625e-7);  // 2^-20; NaN counts as not stationary
+    ctl->stable = stat ? ctl->stable + 1 : 0;
+    if (tot[0] > 0.0) {
+      ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (!isfinite(tot[1]) && t > 1) {
+      ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (ctl->stable >= 2) {
+      ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= ctl->max_iter) {
+      ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    }
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
+// Freeze: c_out = c_ik = -A / (P~_i - P_ki), P_ik = c_out A, c_in = c_ki = -A / (P~_k - P_ik),
+// 1/P~_i.  Uses round T's precision state.
+template <int L>
+__global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T) {
+  const float *__restrict__ Ms = (T & 1) ? a.MP1 : a.MP0;
+  const float *__restrict__ PT = ring3(a.NP0, a.NP1, a.NP2, T);
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    if (i >= a.n) continue;
+    const float Pi = PT[i];
+    for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) {
+      const int k = a.ci[e];
+      const float A = a.av[e];
+      const float cout = -A / (Pi - Ms[e]);
+      const float Pout = cout * A;
+      const float cin = -A / (PT[k] - Pout);
+      a.CF[e] = make_float2(cin, cout);
+    }
+    if (sl == 0) a.invP[i] = 1.f / Pi;
+  }
+}
+
+// ---------------------------------------------------------------------------- mean phase, one RHS
+// Round t of the frozen-precision mean iteration (recompute form).  The inner
+// solve stops when ||x^(t) - x^(t-1)|| <= inner_tol ||x^(t)|| (node-local
+// quantities, no extra edge traffic) or at max_iter.
+template <int L>
+__global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  float *__restrict__ Hc = (t & 1) ? a.H1 : a.H0;  // holds t-2, becomes t
+  const float *__restrict__ Hm1 = ring3(a.NH0, a.NH1, a.NH2, t + 2);
+  const float *__restrict__ Hm2 = ring3(a.NH0, a.NH1, a.NH2, t + 1);
+  float *__restrict__ Ht = ring3(a.NH0, a.NH1, a.NH2, t);
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  double dxx = 0.0, xx = 0.0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    float acc = 0.f;
+    if (i < a.n) {
+      const float hi2 = t >= 2 ? Hm2[i] : 0.f;
+      const int e1 = a.rp[i + 1];
+      for (int e = a.rp[i] + sl; e < e1; e += L) {
+        const int k = a.ci[e];
+        const float2 cf = a.CF[e];
+        const float hout = t >= 2 ? cf.y * (hi2 - Hc[e]) : 0.f;
+        const float hn = cf.x * (Hm1[k] - hout);
+        Hc[e] = hn;
+        acc += hn;
+      }
+    }
+    acc = sub_sum<L>(acc);
+    if (i < a.n && sl == 0) {
+      const float hnew = a.rhs[i] + acc;
+      Ht[i] = hnew;
+      const float ip = a.invP[i];
+      const double x = (double)(hnew * ip), dx = (double)((hnew - Hm1[i]) * ip);
+      dxx = fma(dx, dx, dxx);
+      xx = fma(x, x, xx);
+    }
+  }
+  double v[2] = {dxx, xx}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    ctl->round = t;
+    ctl->rr = tot[0];
+    ctl->xx = tot[1];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= 2 && tot[0] <= ctl->tol2bb * tot[1]) {
+      ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= ctl->max_iter) {
+      ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    }
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
+// ---------------------------------------------------------------------------- FP64 outer steps
+// r = b - A x over the full CSR (diagonal included), in FP64; the FP32 copy of r
+// seeds the next inner solve (its round-0 aggregate h~^(0) = r and its RHS).
+template <int L>
+__global__ void __launch_bounds__(kBlock) k64_residual(int n, const int *__restrict__ rowptr,
+                                                       const int *__restrict__ col, const double *__restrict__ val,
+                                                       const double *__restrict__ b, const double *__restrict__ x,
+                                                       float *__restrict__ rhs32, float *__restrict__ nh0,
+                                                       DevCtl *ctl, double *partials, int set_bb) {
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  double rr = 0.0;
+  for (int base = warp * RPW; base < n; base += nwarps * RPW) {
+    const int i = base + sw;
+    double ax = 0.0;
+    if (i < n)
+      for (int p = rowptr[i] + sl; p < rowptr[i + 1]; p += L) ax = fma(val[p], x[col[p]], ax);
+    ax = sub_sum<L>(ax);
+    if (i < n && sl == 0) {
+      const double r = b[i] - ax;
+      rr = fma(r, r, rr);
+      const float rf = (float)r;
+      rhs32[i] = rf;
+      nh0[i] = rf;
+    }
+  }
+  double v[1] = {rr}, tot[1];
+  const int modes[1] = {0};
+  block_sum<1>(v);
+  if (last_block_reduce<1>(v, modes, partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    ctl->rr = tot[0];
+    if (set_bb) {
+      ctl->bb = tot[0];
+    }
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
+// x <- x + d, d_i = h~_i / P~_i of the inner solve's final round (FP64 accumulate).
+__global__ void k64_update(int n, double *__restrict__ x, const float *__restrict__ hT,
+                           const float *__restrict__ invP) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += (double)(hT[i] * invP[i]);
+}
+
+__global__ void k_to_f32(int64_t m, const double *__restrict__ s, float *__restrict__ d) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) d[i] = (float)s[i];
+}
+
+__global__ void k_diag32(int n, const double *__restrict__ ad, const double *__restrict__ gam,
+                         float *__restrict__ d32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d32[i] = (float)(ad[i] + (gam ? gam[i] : 0.0));
+}
+
+__global__ void k_ctl_reset(DevCtl *c, int max_iter, double tol2) {
+  c->round = 0;
+  c->done = 0;
+  c->status = GABP_NOT_CONVERGED;
+  c->iters = 0;
+  c->result_round = 0;
+  c->max_iter = max_iter;
+  c->check_from = 1;
+  c->stable = 0;
+  c->tol2bb = tol2;
+  c->rr = 0.0;
+  c->xx = 0.0;
+  c->maxrel = 0.0;
+  c->arrive = 0;
+  c->edge_bad = 0;
+}
+
+// Diagonal loading of the convergence fix.  mode 1: Gamma_i = gamma A_ii (the
+// unit-diagonal model I - R loaded by gamma I, in A's scaling; walk-summable for
+// gamma > rho(|R|) - 1).  mode 2: Gamma_i = max(0, sum_j |A_ij| - A_ii) + gamma A_ii,
+// which makes A + Gamma diagonally dominant for gamma > 0.
+__global__ void k_gamma(int n, int mode, double gamma, const int *__restrict__ rp, const double *__restrict__ av,
+                        const double *__restrict__ ad, double *__restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = ad[i];
+  if (mode == 1) {
+    out[i] = gamma * d;
+  } else {
+    double s = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s += fabs(av[e]);
+    out[i] = fmax(0.0, s - d) + gamma * d;
+  }
+}
+
+__global__ void k32_marginals(int n, const float *__restrict__ P, double *__restrict__ Pi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Pi[i] = (double)P[i];
+}
+
+// ---------------------------------------------------------------------------- host side
+gabp_status make_gamma(gabp_handle h, double *out) {
+  Graph &g = h->g;
+  k_gamma<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->opt.gamma_mode, h->opt.gamma, g.rp, g.av,
+                                                                   g.ad, out);
+  GABP_CUDA(cudaGetLastError());
+  return GABP_OK;
+}
+
+gabp_status marginals32(gabp_handle h, double *Pi) {
+  Work32 &w = h->w32;
+  if (!w.MP[0] || w.prec_round < 0) return GABP_ERR_INVALID;
+  Graph &g = h->g;
+  const float *P = w.NP[w.prec_round % 3];
+  k32_marginals<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, P, Pi);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
+gabp_status ensure_w32(gabp_handle h, int R) {
+  Work32 &w = h->w32;
+  Graph &g = h->g;
+  size_t E = (size_t)(g.E > 0 ? g.E : 1), n = (size_t)g.n;
+  if (!w.MP[0]) {
+    GABP_CUDA(cudaMalloc(&w.MP[0], sizeof(float) * E));
+    GABP_CUDA(cudaMalloc(&w.MP[1], sizeof(float) * E));
+    for (int j = 0; j < 3; ++j) GABP_CUDA(cudaMalloc(&w.NP[j], sizeof(float) * n));
+    GABP_CUDA(cudaMalloc(&w.CF, sizeof(float2) * E));
+    GABP_CUDA(cudaMalloc(&w.invP, sizeof(float) * n));
+    GABP_CUDA(cudaMalloc(&g.av32, sizeof(float) * E));
+    GABP_CUDA(cudaMalloc(&g.ad32, sizeof(float) * n));
+    GABP_CUDA(cudaMalloc(&w.ctlR, sizeof(DevCtl)));
+    GABP_CUDA(cudaMemsetAsync(w.ctlR, 0, sizeof(DevCtl), h->stream));
+    k_to_f32<<<(int)((E + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>((int64_t)g.E, g.av, g.av32);
+    GABP_CUDA(cudaGetLastError());
+  }
+  if (w.R < R) {
+    cudaFree(w.H[0]); cudaFree(w.H[1]);
+    for (int j = 0; j < 3; ++j) cudaFree(w.NH[j]);
+    cudaFree(w.rhs32); cudaFree(w.X); cudaFree(w.Rs); cudaFree(w.Bt);
+    w.H[0] = w.H[1] = nullptr;
+    w.NH[0] = w.NH[1] = w.NH[2] = nullptr;
+    w.rhs32 = nullptr; w.X = w.Rs = w.Bt = nullptr;
+    w.R = 0;
+    GABP_CUDA(cudaMalloc(&w.H[0], sizeof(float) * E * R));
+    GABP_CUDA(cudaMalloc(&w.H[1], sizeof(float) * E * R));
+    for (int j = 0; j < 3; ++j) GABP_CUDA(cudaMalloc(&w.NH[j], sizeof(float) * n * R));
+    GABP_CUDA(cudaMalloc(&w.rhs32, sizeof(float) * n * R));
+    GABP_CUDA(cudaMalloc(&w.X, sizeof(double) * n * R));
+    w.R = R;
+    if (h->gH32) cudaGraphExecDestroy(h->gH32);
+    h->gH32 = nullptr;
+    h->gH32_R = -1;
+  }
+  return GABP_OK;
+}
+
+void free_w32(gabp_handle h) {
+  Work32 &w = h->w32;
+  cudaFree(w.MP[0]); cudaFree(w.MP[1]);
+  for (int j = 0; j < 3; ++j) { cudaFree(w.NP[j]); cudaFree(w.NH[j]); }
+  cudaFree(w.CF); cudaFree(w.invP); cudaFree(w.H[0]); cudaFree(w.H[1]);
+  cudaFree(w.rhs32); cudaFree(w.X); cudaFree(w.Rs); cudaFree(w.Bt); cudaFree(w.colnorm);
+  cudaFree(w.ctlR); cudaFree(w.rhs_active);
+  w = Work32{};
+}
+
+static Args32 args32(gabp_handle h) {
+  Args32 a;
+  Graph &g = h->g;
+  Work32 &w = h->w32;
+  a.n = g.n; a.rp = g.rp; a.ci = g.ci; a.av = g.av32; a.ad = g.ad32;
+  a.MP0 = w.MP[0]; a.MP1 = w.MP[1];
+  a.NP0 = w.NP[0]; a.NP1 = w.NP[1]; a.NP2 = w.NP[2];
+  a.CF = w.CF; a.invP = w.invP;
+  a.H0 = w.H[0]; a.H1 = w.H[1];
+  a.NH0 = w.NH[0]; a.NH1 = w.NH[1]; a.NH2 = w.NH[2];
+  a.rhs = w.rhs32;
+  a.ctl = h->ctl;
+  a.partials = h->partials;
+  return a;
+}
+
+static int lanes32(gabp_handle h) {
+  if (h->opt.lanes) return h->opt.lanes;
+  double d = h->g.avg_deg;
+  int L = 1;
+  while (L < 32 && L * 2 <= d) L *= 2;
+  return L;
+}
+
+#define GABP_DISPATCH_L(L, CALL) \
+  switch (L) {                   \
+    case 1: { constexpr int LL = 1; CALL; } break;  \
+    case 2: { constexpr int LL = 2; CALL; } break;  \
+    case 4: { constexpr int LL = 4; CALL; } break;  \
+    case 8: { constexpr int LL = 8; CALL; } break;  \
+    case 16: { constexpr int LL = 16; CALL; } break; \
+    default: { constexpr int LL = 32; CALL; } break; \
+  }
+
+// Run K-round graphs of one round kernel until the control block says done.
+template <typename LaunchFn>
+static gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, LaunchFn launch, int max_rounds, int phase) {
+  const int K = h->opt.check_every;
+  const bool use_graph = h->stream != nullptr;
+  if (use_graph && !*cache) {
+    cudaGraph_t graph;
+    GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < K; ++k) launch();
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "capture FP32 rounds");
+    e = cudaGraphInstantiate(cache, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate FP32 rounds");
+  }
+  const int64_t max_batches = (int64_t)max_rounds / K + 3;
+  int prev_round = 0;
+  for (int64_t bI = 0; bI < max_batches; ++bI) {
+    prof_begin(h);
+    if (use_graph) {
+      GABP_CUDA(cudaGraphLaunch(*cache, h->stream));
+    } else {
+      for (int k = 0; k < K; ++k) launch();
+      GABP_CUDA(cudaGetLastError());
+    }
+    prof_end(h);
+    h->prof.launches += K;
+    gabp_status s = read_ctl(h);
+    if (s != GABP_OK) return s;
+    prof_collect(h, phase, h->ctl_host->round - prev_round);
+    prev_round = h->ctl_host->round;
+    if (h->ctl_host->done) return GABP_OK;
+  }
+  set_last_error("FP32 rounds ended without a decision");
+  return GABP_ERR_CUDA;
+}
+
+// Precision phase + coefficient freeze on A (+ Gamma).
+static gabp_status precision_phase(gabp_handle h, const double *gamma_diag) {
+  Work32 &w = h->w32;
+  Graph &g = h->g;
+  const int L = lanes32(h);
+  size_t E = (size_t)(g.E > 0 ? g.E : 1);
+  k_diag32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad, gamma_diag, g.ad32);
+  GABP_CUDA(cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, h->stream));
+  GABP_CUDA(cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(w.NP[0], g.ad32, sizeof(float) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, 0.0);
+  h->prof.launches += 2;
+  GABP_CUDA(cudaGetLastError());
+  Args32 a = args32(h);
+  const int nb = blocks_for(g.n, kBlock / L, h->max_blocks);
+  gabp_status s;
+  GABP_DISPATCH_L(L, s = run_rounds(h, &h->gP32, [&] { k32_prec<LL><<<nb, kBlock, 0, h->stream>>>(a); }, kPrecMaxRounds,
+                                  PH_PREC32));
+  if (s != GABP_OK) return s;
+  const DevCtl c = *h->ctl_host;
+  h->stats.rounds += c.round;
+  if (c.status == GABP_BREAKDOWN || c.status == GABP_DIVERGED) return (gabp_status)c.status;
+  GABP_DISPATCH_L(L, (k32_coef<LL><<<nb, kBlock, 0, h->stream>>>(a, c.result_round)));
+  h->prof.launches += 1;
+  GABP_CUDA(cudaGetLastError());
+  w.prec_round = c.result_round;
+  w.coef_ready = true;
+  return GABP_OK;
+}
+
+gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int64_t ld, double tol,
+                           int max_iter, const double *gamma_diag, int *iters, double *relres) {
+  if (R != 1) return GABP_ERR_INVALID;  // batched path: gabp_solve_batched
+  (void)ld;
+  gabp_status s = ensure_w32(h, 1);
+  if (s != GABP_OK) return s;
+  Work32 &w = h->w32;
+  Graph &g = h->g;
+  h->stats.rounds = 0;
+  h->stats.refine_steps = 0;
+  // the precision state is cached per handle when no loading is applied
+  if (!w.coef_ready || gamma_diag || !h->opt.reuse_precisions) {
+    w.coef_ready = false;
+    if ((s = precision_phase(h, gamma_diag)) != GABP_OK) return s;
+    if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
+  }
+  const int L = lanes32(h);
+  const int nbr = blocks_for(g.n, kBlock / L, h->max_blocks);
+  GABP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * g.n, h->stream));
+  GABP_CUDA(cudaMemsetAsync(w.ctlR, 0, sizeof(DevCtl), h->stream));
+  GABP_DISPATCH_L(L, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
+                                                                         w.NH[0], w.ctlR, h->partials, 1)));
+  h->prof.launches += 1;
+  GABP_CUDA(cudaGetLastError());
+  DevCtl cr;
+  GABP_CUDA(cudaMemcpyAsync(&cr, w.ctlR, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  const double bb = cr.bb;
+  double rr = cr.rr;
+  int total_inner = 0;
+  gabp_status result = GABP_NOT_CONVERGED;
+  if (bb == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return GABP_OK;
+  }
+  Args32 a = args32(h);
+  const size_t E = (size_t)(g.E > 0 ? g.E : 1);
+  const double itol = h->opt.inner_tol;
+  for (int step = 0; step < h->opt.max_refine; ++step) {
+    if (rr <= tol * tol * bb) { result = GABP_OK; break; }
+    if (total_inner >= max_iter) break;
+    // inner FP32 GaBP on A d = r (messages from zero, Algorithm 1 step 1)
+    GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
+    const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
+    k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, itol * itol);
+    h->prof.launches += 1;
+    GABP_CUDA(cudaGetLastError());
+    GABP_DISPATCH_L(L, s = run_rounds(h, &h->gH32, [&] { k32_mean<LL><<<nbr, kBlock, 0, h->stream>>>(a); }, cap, PH_MEAN32));
+    if (s != GABP_OK) return s;
+    const DevCtl c = *h->ctl_host;
+    total_inner += c.round;
+    h->stats.rounds += c.round;
+    if (c.status == GABP_DIVERGED) { result = GABP_DIVERGED; break; }
+    float *hT = c.result_round % 3 == 0 ? w.NH[0] : (c.result_round % 3 == 1 ? w.NH[1] : w.NH[2]);
+    prof_begin(h);
+    k64_update<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, X, hT, w.invP);
+    GABP_DISPATCH_L(L, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
+                                                                           w.NH[0], w.ctlR, h->partials, 0)));
+    prof_end(h);
+    h->prof.launches += 2;
+    GABP_CUDA(cudaGetLastError());
+    GABP_CUDA(cudaMemcpyAsync(&cr, w.ctlR, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
+    GABP_CUDA(cudaStreamSynchronize(h->stream));
+    prof_collect(h, PH_REFINE64, 1);
+    h->stats.refine_steps = step + 1;
+    if (!std::isfinite(cr.rr)) { result = GABP_DIVERGED; rr = cr.rr; break; }
+    rr = cr.rr;
+  }
+  if (result != GABP_DIVERGED && rr <= tol * tol * bb) result = GABP_OK;
+  if (iters) *iters = total_inner;
+  if (relres) *relres = sqrt(rr / bb);
+  return result;
+}
+
+}  // namespace gabp

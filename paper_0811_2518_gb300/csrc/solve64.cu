@@ -1,0 +1,468 @@
+// solve64.cu -- plain FP64 synchronous GaBP (Algorithm 2, broadcast form) on the GPU.
+//
+// Notation (paper, Algorithm 2 and eqs. eq_prec / eq_prec_message / eq_mean_message):
+//   P~_i = A_ii + sum_{k in N(i)} P_ki,    h~_i = b_i + sum_{k in N(i)} h_ki,
+//   P_ij = -A_ij^2 / (P~_i - P_ji),        h_ij = P_ij mu_ij = -A_ij (h~_i - h_ji) / (P~_i - P_ji),
+//   x_i  = h~_i / P~_i                     (marginal mean, Algorithm 1 step 4).
+// Messages are kept in information form (P, h = P mu); mu_ij of the paper is h_ij / P_ij.
+//
+// Round t of the parallel schedule reads round t-1 only (two message stores that
+// swap roles, paper Sec. "The Gaussian BP Algorithm", scheduling paragraph):
+//   in-message k -> i at t  =  f(A_ik, node record of k at t-1, reverse message i -> k at t-1).
+// It is written into row i's slot e (coalesced), the reverse message is fetched
+// from row k's slot rev[e], and the new node record of i is the sum over its
+// row.  The same pass forms r_i = b_i - sum_j A_ij x_j^{(t-1)} from the node
+// records it has gathered anyway, so the residual of round t-1's iterate costs
+// one FMA per slot; the stop rule therefore decides about x^{(t-1)} during round t.
+#include "gabp_internal.cuh"
+#include "devutil.cuh"
+
+namespace gabp {
+
+struct Args64 {
+  int n;
+  const int *__restrict__ rp;
+  const int *__restrict__ ci;
+  const int *__restrict__ rev;
+  const double *__restrict__ av;
+  const double *__restrict__ ad;
+  double2 *M0, *M1;
+  NodeRec64 *N0, *N1;
+  DevCtl *ctl;
+  double *partials;
+};
+
+// Round bookkeeping shared by the FP64 round kernels: this round checked
+// x^{(t-1)} with squared residual rr; 'bad' counts zero cavities / precisions
+// met while computing round t.
+__device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
+  const int tchk = t - 1;
+  ctl->round = t;
+  if (tchk >= ctl->check_from && isfinite(rr) && rr <= ctl->tol2bb) {
+    ctl->status = GABP_OK;
+    ctl->iters = tchk;
+    ctl->result_round = tchk;
+    ctl->rr = rr;
+    ctl->done = 1;
+  } else if (!isfinite(rr)) {
+    ctl->status = GABP_DIVERGED;
+    ctl->iters = tchk;
+    ctl->result_round = tchk;
+    ctl->rr = rr;
+    ctl->done = 1;
+  } else if (bad > 0.0 && t <= ctl->max_iter) {
+    ctl->status = GABP_BREAKDOWN;
+    ctl->iters = t;
+    ctl->result_round = tchk;
+    ctl->rr = rr;
+    ctl->done = 1;
+  } else if (tchk >= ctl->max_iter) {
+    ctl->status = GABP_NOT_CONVERGED;
+    ctl->iters = tchk;
+    ctl->result_round = tchk;
+    ctl->rr = rr;
+    ctl->done = 1;
+  } else {
+    ctl->rr = rr;
+  }
+  ctl->arrive = 0;
+  __threadfence();
+}
+
+// Round 0 (Algorithm 1/2 step 1): all messages zero, so P~_i = A_ii, h~_i = b_i.
+__global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max_iter) {
+  const double *b = a.ctl->b;
+  double bb = 0.0;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) {
+    double bi = b[i], d = a.ad[i];
+    a.N0[i] = NodeRec64{d, bi, bi / d, 0.0};
+    bb = fma(bi, bi, bb);
+  }
+  double v[1] = {bb}, tot[1];
+  const int modes[1] = {0};
+  block_sum<1>(v);
+  if (last_block_reduce<1>(v, modes, a.partials, &a.ctl->arrive, tot) && threadIdx.x == 0) {
+    DevCtl *c = a.ctl;
+    c->round = 0;
+    c->bb = tot[0];
+    c->tol2bb = tol * tol * tot[0];
+    c->max_iter = max_iter;
+    c->check_from = 1;
+    c->stable = 0;
+    c->edge_bad = 0;
+    c->rr = tot[0];
+    c->arrive = 0;
+    if (tot[0] == 0.0) {  // b = 0: x = 0 after no round
+      c->done = 1;
+      c->status = GABP_OK;
+      c->iters = 0;
+      c->result_round = 0;
+      c->rr = 0.0;
+    } else {
+      c->done = 0;
+      c->status = GABP_NOT_CONVERGED;
+      c->iters = 0;
+      c->result_round = 0;
+    }
+    __threadfence();
+  }
+}
+
+// Fused node-centric round (GABP_VARIANT_NODE): a sub-warp of L lanes per row.
+template <int L>
+__global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  const double *__restrict__ b = ctl->b;
+  const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;  // round t-1
+  double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;       // round t
+  const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+  NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
+
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  double rr = 0.0, bad = 0.0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    double accP = 0.0, acch = 0.0, accr = 0.0;
+    if (i < a.n) {
+      const int e1 = a.rp[i + 1];
+      for (int e = a.rp[i] + sl; e < e1; e += L) {
+        const int k = a.ci[e];
+        const double A = a.av[e];
+        const double2 rv = Min[a.rev[e]];  // message i -> k of round t-1
+        const NodeRec64 nk = Nin[k];       // node k at round t-1
+        const double den = nk.P - rv.x;    // cavity precision P_{k\i}
+        if (den == 0.0) bad += 1.0;
+        const double cin = -A * rcp64(den);
+        const double2 m = make_double2(cin * A, cin * (nk.h - rv.y));
+        Mout[e] = m;
+        accP += m.x;
+        acch += m.y;
+        accr = fma(A, nk.x, accr);
+      }
+    }
+    accP = sub_sum<L>(accP);
+    acch = sub_sum<L>(acch);
+    accr = sub_sum<L>(accr);
+    if (i < a.n && sl == 0) {
+      const double bi = b[i], d = a.ad[i];
+      const double P = d + accP, h = bi + acch;
+      if (P == 0.0) bad += 1.0;
+      Nout[i] = NodeRec64{P, h, h / P, 0.0};
+      const double r = bi - fma(d, Nin[i].x, accr);
+      rr = fma(r, r, rr);
+    }
+  }
+  double v[2] = {rr, bad}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0)
+    decide64(ctl, t, tot[0], tot[1]);
+}
+
+// Edge-centric round, part 1 (GABP_VARIANT_EDGE): one thread per directed edge
+// computes the in-message of its slot from the sender's aggregate minus the
+// reverse message (Algorithm 2).
+__global__ void __launch_bounds__(kBlock) k64_edge_msg(Args64 a, int E) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;
+  double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
+  const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+  int bad = 0;
+  for (int e = blockIdx.x * kBlock + threadIdx.x; e < E; e += gridDim.x * kBlock) {
+    const int k = a.ci[e];
+    const double A = a.av[e];
+    const double2 rv = Min[a.rev[e]];
+    const NodeRec64 nk = Nin[k];
+    const double den = nk.P - rv.x;
+    bad |= (den == 0.0);
+    const double cin = -A * rcp64(den);
+    Mout[e] = make_double2(cin * A, cin * (nk.h - rv.y));
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->edge_bad, 1);
+}
+
+// Edge-centric round, part 2: row aggregates (the "broadcast" sums of
+// Algorithm 2), x^{(t)}, and the residual of x^{(t-1)}.
+template <int L>
+__global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  const double *__restrict__ b = ctl->b;
+  const double2 *__restrict__ Mnew = (t & 1) ? a.M1 : a.M0;
+  const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+  NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  double rr = 0.0, bad = 0.0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    double accP = 0.0, acch = 0.0, accr = 0.0;
+    if (i < a.n) {
+      const int e1 = a.rp[i + 1];
+      for (int e = a.rp[i] + sl; e < e1; e += L) {
+        const double2 m = Mnew[e];
+        accP += m.x;
+        acch += m.y;
+        accr = fma(a.av[e], Nin[a.ci[e]].x, accr);
+      }
+    }
+    accP = sub_sum<L>(accP);
+    acch = sub_sum<L>(acch);
+    accr = sub_sum<L>(accr);
+    if (i < a.n && sl == 0) {
+      const double bi = b[i], d = a.ad[i];
+      const double P = d + accP, h = bi + acch;
+      if (P == 0.0) bad += 1.0;
+      Nout[i] = NodeRec64{P, h, h / P, 0.0};
+      const double r = bi - fma(d, Nin[i].x, accr);
+      rr = fma(r, r, rr);
+    }
+  }
+  double v[2] = {rr, bad}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    const double eb = ctl->edge_bad ? 1.0 : 0.0;
+    ctl->edge_bad = 0;
+    decide64(ctl, t, tot[0], tot[1] + eb);
+  }
+}
+
+__global__ void k64_finalize(int n, const NodeRec64 *__restrict__ N, double *__restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = N[i].x;
+}
+
+// Messages of the returned round in the layout of the input CSR.
+__global__ void k64_messages(int n, const int *__restrict__ rowptr, const int *__restrict__ dpos,
+                             const int *__restrict__ rp, const double2 *__restrict__ M, double *__restrict__ P,
+                             double *__restrict__ hm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = rowptr[i], d = dpos[i], e0 = rp[i], deg = rp[i + 1] - rp[i];
+  P[a + d] = 0.0;
+  hm[a + d] = 0.0;
+  for (int q = 0; q < deg; ++q) {
+    int p = a + q + (q >= d ? 1 : 0);
+    double2 m = M[e0 + q];
+    P[p] = m.x;
+    hm[p] = m.y;
+  }
+}
+
+__global__ void k64_marginals(int n, const NodeRec64 *__restrict__ N, double *__restrict__ Pi) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Pi[i] = N[i].P;
+}
+
+// dL/dA restricted to the pattern and symmetrised: -(lam_i x_j + lam_j x_i)/2
+// off the diagonal, -lam_i x_i on it.
+__global__ void k_grad_values(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                              const double *__restrict__ lam, const double *__restrict__ x, double *__restrict__ g) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double li = lam[i], xi = x[i];
+  for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+    int j = col[p];
+    g[p] = j == i ? -li * xi : -0.5 * (li * x[j] + lam[j] * xi);
+  }
+}
+
+// ------------------------------------------------------------------------- host side
+gabp_status ensure_w64(gabp_handle h) {
+  Work64 &w = h->w64;
+  if (w.M[0]) return GABP_OK;
+  size_t E = (size_t)(h->g.E > 0 ? h->g.E : 1), n = (size_t)h->g.n;
+  GABP_CUDA(cudaMalloc(&w.M[0], sizeof(double2) * E));
+  GABP_CUDA(cudaMalloc(&w.M[1], sizeof(double2) * E));
+  GABP_CUDA(cudaMalloc(&w.N[0], sizeof(NodeRec64) * n));
+  GABP_CUDA(cudaMalloc(&w.N[1], sizeof(NodeRec64) * n));
+  return GABP_OK;
+}
+
+void free_w64(gabp_handle h) {
+  Work64 &w = h->w64;
+  cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]);
+  w = Work64{};
+}
+
+static int pick_lanes(gabp_handle h) {
+  if (h->opt.lanes) return h->opt.lanes;
+  // about two slots per lane; rows of degree ~16 get 8 lanes, grid rows 2-4
+  double d = h->g.avg_deg;
+  int L = 1;
+  while (L < 32 && L * 2 <= d) L *= 2;
+  return L;
+}
+
+static Args64 args64(gabp_handle h) {
+  Args64 a;
+  a.n = h->g.n;
+  a.rp = h->g.rp;
+  a.ci = h->g.ci;
+  a.rev = h->g.rev;
+  a.av = h->g.av;
+  a.ad = h->g.ad;
+  a.M0 = h->w64.M[0];
+  a.M1 = h->w64.M[1];
+  a.N0 = h->w64.N[0];
+  a.N1 = h->w64.N[1];
+  a.ctl = h->ctl;
+  a.partials = h->partials;
+  return a;
+}
+
+template <int L>
+static void launch_round_L(gabp_handle h, const Args64 &a) {
+  const int rows_per_block = kBlock / L;
+  const int nb = blocks_for(h->g.n, rows_per_block, h->max_blocks);
+  if (h->opt.variant == GABP_VARIANT_EDGE) {
+    const int eb = blocks_for(h->g.E, kBlock, h->max_blocks);
+    k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a, h->g.E);
+    k64_edge_agg<L><<<nb, kBlock, 0, h->stream>>>(a);
+  } else {
+    k64_node<L><<<nb, kBlock, 0, h->stream>>>(a);
+  }
+}
+
+static void launch_round(gabp_handle h, const Args64 &a, int L) {
+  switch (L) {
+    case 1: launch_round_L<1>(h, a); break;
+    case 2: launch_round_L<2>(h, a); break;
+    case 4: launch_round_L<4>(h, a); break;
+    case 8: launch_round_L<8>(h, a); break;
+    case 16: launch_round_L<16>(h, a); break;
+    default: launch_round_L<32>(h, a); break;
+  }
+}
+
+// K rounds as one CUDA graph (the round index lives in device memory, so the
+// same graph serves every replay and every solve on this handle).
+static gabp_status get_graph64(gabp_handle h, int L, cudaGraphExec_t *out) {
+  const int K = h->opt.check_every;
+  const int key = (L << 16) ^ (h->opt.variant << 12) ^ K;
+  if (h->g64 && h->g64_key == key) {
+    *out = h->g64;
+    return GABP_OK;
+  }
+  if (h->g64) cudaGraphExecDestroy(h->g64);
+  h->g64 = nullptr;
+  Args64 a = args64(h);
+  cudaGraph_t graph;
+  GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < K; ++k) launch_round(h, a, L);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(e, "capture FP64 rounds");
+  e = cudaGraphInstantiate(&h->g64, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "instantiate FP64 rounds");
+  h->g64_key = key;
+  *out = h->g64;
+  return GABP_OK;
+}
+
+gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
+                    double *relres) {
+  gabp_status s = ensure_w64(h);
+  if (s != GABP_OK) return s;
+  Graph &g = h->g;
+  h->w64.valid = false;
+  // control block: zero, then point it at b
+  GABP_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(DevCtl), h->stream));
+  const double *bptr = b;
+  GABP_CUDA(cudaMemcpyAsync(&h->ctl->b, &bptr, sizeof(bptr), cudaMemcpyHostToDevice, h->stream));
+  // the pinned staging copy must stay alive until the copy ran: synchronise below
+  GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
+  Args64 a = args64(h);
+  k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+
+  const int L = pick_lanes(h);
+  const bool use_graph = h->stream != nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (use_graph) {
+    s = get_graph64(h, L, &ge);
+    if (s != GABP_OK) return s;
+  }
+  const int K = h->opt.check_every;
+  const int64_t max_batches = (int64_t)(max_iter + 2) / K + 3;
+  bool done = false;
+  if ((s = read_ctl(h)) != GABP_OK) return s;
+  done = h->ctl_host->done;
+  const int per_round = h->opt.variant == GABP_VARIANT_EDGE ? 2 : 1;
+  h->prof.launches += 1;  // k64_init
+  int prev_round = 0;
+  for (int64_t batch = 0; !done && batch < max_batches; ++batch) {
+    prof_begin(h);
+    if (use_graph) {
+      GABP_CUDA(cudaGraphLaunch(ge, h->stream));
+    } else {
+      for (int k = 0; k < K; ++k) launch_round(h, a, L);
+      GABP_CUDA(cudaGetLastError());
+    }
+    prof_end(h);
+    h->prof.launches += (int64_t)K * per_round;
+    if ((s = read_ctl(h)) != GABP_OK) return s;
+    prof_collect(h, PH_FP64, h->ctl_host->round - prev_round);
+    prev_round = h->ctl_host->round;
+    done = h->ctl_host->done;
+  }
+  if (!done) {
+    set_last_error("solve64: control loop ended without a decision");
+    return GABP_ERR_CUDA;
+  }
+  const DevCtl c = *h->ctl_host;
+  h->w64.result_round = c.result_round;
+  h->w64.valid = true;
+  h->stats.rounds = c.round;
+  h->stats.refine_steps = 0;
+  k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x);
+  h->prof.launches += 1;
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  if (iters) *iters = c.iters;
+  if (relres) *relres = c.bb > 0.0 ? sqrt(c.rr / c.bb) : 0.0;
+  return (gabp_status)c.status;
+}
+
+gabp_status messages64(gabp_handle h, double *P, double *hm) {
+  if (!h->w64.valid) return GABP_ERR_INVALID;
+  Graph &g = h->g;
+  k64_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(
+      g.n, g.rowptr, g.dpos, g.rp, h->w64.M[h->w64.result_round & 1], P, hm);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
+gabp_status marginals(gabp_handle h, double *Pi) {
+  if (!h->w64.valid) return GABP_ERR_INVALID;
+  Graph &g = h->g;
+  k64_marginals<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[h->w64.result_round & 1], Pi);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
+gabp_status grad_values(gabp_handle h, const double *lam, const double *x, double *gv) {
+  Graph &g = h->g;
+  k_grad_values<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, lam, x, gv);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
+}  // namespace gabp

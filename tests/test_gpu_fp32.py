@@ -1,0 +1,104 @@
+"""GPU FP32 messages + FP64 refinement, and the convergence fix (through the C ABI).
+
+Tolerances (relative error against the FP64 oracle / dense solution): at most
+1e-5 for one unrefined FP32 solve, at most 1e-10 after refinement.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0811_2518_gb300 as m
+
+    return m
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _solve(gb, m, b, tol, max_iter=5000, **opts):
+    s = gb.Solver.from_csr(m, **opts)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=max_iter)
+    out = {"x": x.cpu().numpy(), "status": st, "iters": it, "relres": rel, "stats": s.stats()}
+    out["P"] = s.marginal_precisions().cpu().numpy() if st >= 0 else None
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.grid2d(32, -1.0, 4.5),
+    lambda: synth.random_sym(20011, 8, 1.1, 2),
+    lambda: synth.grid3d(16, 1.05, 3),
+])
+def test_refined_matches_fp64_oracle(gb, make):
+    m = make()
+    b = synth.rhs(m.n, 5)
+    ref = oracle.gabp_broadcast(m, b, max_iter=5000, tol=1e-13)
+    g = _solve(gb, m, b, 1e-12, precision=gb.GABP_PREC_FP32_REFINE)
+    assert g["status"] == gb.GABP_OK and g["relres"] <= 1e-12
+    assert _relerr(g["x"], ref["x"]) <= 1e-10
+    assert g["stats"]["refine_steps"] >= 1
+
+
+def test_unrefined_within_1e5(gb):
+    m = synth.random_sym(20011, 8, 1.1, 2)
+    b = synth.rhs(m.n, 5)
+    ref = oracle.gabp_broadcast(m, b, max_iter=5000, tol=1e-13)
+    g = _solve(gb, m, b, 1e-12, precision=gb.GABP_PREC_FP32_REFINE, max_refine=1, inner_tol=1e-7,
+               inner_max_iter=200)
+    assert _relerr(g["x"], ref["x"]) <= 1e-5
+    # FP32 marginal precisions agree with the FP64 oracle's to single precision
+    assert np.allclose(g["P"], ref["P"], rtol=1e-5)
+
+
+def test_refined_relres_recomputed_on_host(gb):
+    m = synth.random_sym(50000, 8, 1.1, 3)
+    b = synth.rhs(m.n, 3)
+    g = _solve(gb, m, b, 1e-10, precision=gb.GABP_PREC_FP32_REFINE)
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    r = b - np.bincount(rows, m.val * g["x"][m.col], minlength=m.n)
+    assert g["status"] == 0 and np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("gamma", [0.25, 0.5])
+def test_convergence_fix_non_walk_summable(gb, gamma):
+    """n = 4096, diagonal 0.9 x row abs-sum (rho(|R|) = 1/0.9 > 1), SPD; uniform loading."""
+    m = synth.random_sym(4096, 3, 0.9, 5)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 5)
+    g = _solve(gb, m, b, 1e-11, max_iter=100000, gamma_mode=1, gamma=gamma, max_refine=2000)
+    assert g["status"] == gb.GABP_OK
+    assert _relerr(g["x"], oracle.dense_solve(A, b)) <= 1e-9
+    f = oracle.convergence_fix(m, b, oracle.diagonal_loading(A, "uniform", gamma), tol=1e-11, inner_tol=1e-13)
+    assert _relerr(g["x"], f["x"]) <= 1e-9
+
+
+def test_convergence_fix_where_plain_fails(gb):
+    m = synth.random_sym(1024, 3, 0.8, 7)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 5)
+    plain = _solve(gb, m, b, 1e-10, max_iter=300)
+    assert plain["status"] != gb.GABP_OK
+    g = _solve(gb, m, b, 1e-9, max_iter=400000, gamma_mode=1, gamma=0.3, max_refine=5000)
+    assert g["status"] == gb.GABP_OK
+    assert _relerr(g["x"], oracle.dense_solve(A, b)) <= 1e-6
+
+
+def test_dd_loading_mode(gb):
+    m = synth.random_sym(2048, 3, 0.9, 5)
+    b = synth.rhs(m.n, 5)
+    g = _solve(gb, m, b, 1e-10, max_iter=100000, gamma_mode=2, gamma=0.05, max_refine=2000)
+    assert g["status"] == gb.GABP_OK
+    assert _relerr(g["x"], oracle.dense_solve(oracle.to_dense(m), b)) <= 1e-8

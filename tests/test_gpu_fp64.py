@@ -1,0 +1,259 @@
+"""GPU parity of the plain FP64 GaBP path against the FP64 CPU oracle (through the C ABI).
+
+Tolerances: the paper's iterates are reproduced round for round; at a fixed
+round the GPU and the oracle agree to 1e-13 relative on x and the messages
+(they differ only in summation order and in the reciprocal's last bit), and at
+convergence to 1e-12 relative (the FP64 target), with equal round counts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0811_2518_gb300 as m
+
+    return m
+
+
+def _solver(gb, m, **opts):
+    return gb.Solver.from_csr(m, **opts)
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _gpu_solve(gb, m, b, tol, max_iter, **opts):
+    s = _solver(gb, m, **opts)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=max_iter)
+    out = {"x": x.cpu().numpy(), "status": st, "iters": it, "relres": rel}
+    if st >= 0 and opts.get("precision", 0) == 0 and opts.get("gamma_mode", 0) == 0:
+        P, hm = s.messages()
+        out["Pmsg"], out["hmsg"] = P.cpu().numpy(), hm.cpu().numpy()
+        out["P"] = s.marginal_precisions().cpu().numpy()
+    out["stats"] = s.stats()
+    s.close()
+    return out
+
+
+def _diag_mask(m):
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    return rows == m.col
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_toy_tables_gpu(gb, variant):
+    """Sec. "Toy Linear System": messages and tentative means at t = 1, 2, 3."""
+    A, b = synth.toy3x3()
+    m = synth.from_dense(A)
+    off = ~_diag_mask(m)
+    for t in (1, 2, 3):
+        ref = oracle.gabp_naive(m, b, max_iter=t, tol=0.0, messages=True)
+        g = _gpu_solve(gb, m, b, 0.0, t, variant=variant)
+        assert g["status"] == ref["status"] and g["iters"] == ref["iters"], (t, g["status"], g["iters"])
+        assert np.allclose(g["x"], ref["x"], rtol=1e-14, atol=1e-14)
+        assert np.allclose(g["Pmsg"][off], ref["Pmsg"][off], rtol=1e-14, atol=1e-14)
+        assert np.allclose(g["hmsg"][off], (ref["Pmsg"] * ref["mumsg"])[off], rtol=1e-14, atol=1e-14)
+    assert np.allclose(g["P"], [-12.0, 1.5, 4.0], rtol=1e-14)
+
+
+def _diameter(m):
+    from collections import deque
+
+    def bfs(s):
+        dist = np.full(m.n, -1)
+        dist[s] = 0
+        q = deque([s])
+        while q:
+            u = q.popleft()
+            for p in range(m.rowptr[u], m.rowptr[u + 1]):
+                v = m.col[p]
+                if v != u and dist[v] < 0:
+                    dist[v] = dist[u] + 1
+                    q.append(v)
+        return dist
+
+    return int(bfs(int(np.argmax(bfs(0)))).max())
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_tree_exact_gpu(gb, seed):
+    """Trees: after diameter-many rounds the means are A^{-1} b and the precisions
+    1/(A^{-1})_ii (Sec. "Convergence and Exactness")."""
+    n = 31 if seed % 2 else 400
+    m = synth.random_tree(n, seed, dd=(seed % 2 == 0), diag_scale=2.0)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 100 + seed)
+    d = _diameter(m)
+    g = _gpu_solve(gb, m, b, 0.0, d)
+    assert g["status"] in (gb.GABP_OK, gb.GABP_NOT_CONVERGED) and g["iters"] <= d
+    xs = oracle.dense_solve(A, b)
+    assert _relerr(g["x"], xs) <= 1e-12
+    assert np.allclose(g["P"], oracle.marginal_precisions_exact(A), rtol=1e-11)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("lanes", [0, 1, 4, 32])
+def test_parity_grid_c1(gb, variant, lanes):
+    """32 x 32 grid, diagonal 4.5: same round count as the oracle; 1e-12 at convergence;
+    1e-13 on x and messages at a fixed round."""
+    m = synth.grid2d(32, -1.0, 4.5)
+    b = synth.rhs(m.n, 1)
+    ref = oracle.gabp_naive(m, b, max_iter=1000, tol=1e-12)
+    g = _gpu_solve(gb, m, b, 1e-12, 1000, variant=variant, lanes=lanes)
+    assert g["status"] == ref["status"] == 0
+    assert g["iters"] == ref["iters"]
+    assert _relerr(g["x"], ref["x"]) <= 1e-12
+    off = ~_diag_mask(m)
+    for t in (1, 5, 17):
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0, messages=True)
+        gg = _gpu_solve(gb, m, b, 0.0, t, variant=variant, lanes=lanes)
+        assert _relerr(gg["x"], r["x"]) <= 1e-13
+        assert np.allclose(gg["Pmsg"][off], r["Pmsg"][off], rtol=1e-13, atol=1e-15)
+        assert np.allclose(gg["hmsg"][off], (r["Pmsg"] * r["mumsg"])[off], rtol=1e-12, atol=1e-14)
+
+
+def test_parity_grid_tight(gb):
+    """Both sides to 1e-13 residual, then compared (and against the dense solution)."""
+    m = synth.grid2d(32, -1.0, 4.5)
+    b = synth.rhs(m.n, 1)
+    ref = oracle.gabp_broadcast(m, b, max_iter=2000, tol=1e-13)
+    g = _gpu_solve(gb, m, b, 1e-13, 2000)
+    assert _relerr(g["x"], ref["x"]) <= 1e-12
+    assert _relerr(g["x"], oracle.dense_solve(oracle.to_dense(m), b)) <= 1e-12
+
+
+@pytest.mark.parametrize("n,picks,c", [(20011, 8, 1.1), (30001, 3, 1.2)])
+def test_parity_random_several_tiles(gb, n, picks, c):
+    """Random symmetric graphs spanning many blocks with a ragged last tile."""
+    m = synth.random_sym(n, picks, c, 2)
+    b = synth.rhs(m.n, 2)
+    ref = oracle.gabp_broadcast(m, b, max_iter=500, tol=1e-12)
+    for variant in (0, 1):
+        g = _gpu_solve(gb, m, b, 1e-12, 500, variant=variant)
+        assert g["status"] == ref["status"] == 0
+        assert g["iters"] == ref["iters"]
+        assert _relerr(g["x"], ref["x"]) <= 1e-12
+        assert np.allclose(g["P"], ref["P"], rtol=1e-12)
+
+
+def test_variants_agree(gb):
+    m = synth.random_sym(5000, 5, 1.1, 4)
+    b = synth.rhs(m.n, 4)
+    a = _gpu_solve(gb, m, b, 0.0, 9, variant=0)
+    c = _gpu_solve(gb, m, b, 0.0, 9, variant=1)
+    assert _relerr(a["x"], c["x"]) <= 1e-14
+    assert np.allclose(a["Pmsg"], c["Pmsg"], rtol=1e-14, atol=0)
+
+
+def test_check_every_does_not_change_result(gb):
+    m = synth.grid2d(24, -1.0, 4.5)
+    b = synth.rhs(m.n, 8)
+    a = _gpu_solve(gb, m, b, 1e-11, 1000, check_every=1)
+    c = _gpu_solve(gb, m, b, 1e-11, 1000, check_every=37)
+    assert a["iters"] == c["iters"] and np.array_equal(a["x"], c["x"])
+
+
+def test_breakdown_gpu(gb):
+    A = np.array([[2.0, 1.0, 0.0, 0.0], [1.0, 3.0, 1.0, 1.0], [0.0, 1.0, 1.0, 0.0], [0.0, 1.0, 0.0, 0.5]])
+    m = synth.from_dense(A)
+    for variant in (0, 1):
+        g = _gpu_solve(gb, m, np.ones(4), 1e-14, 10, variant=variant)
+        assert g["status"] == gb.GABP_BREAKDOWN and g["iters"] == 2
+
+
+def test_not_converged_and_max_iter(gb):
+    m = synth.grid2d(16, -1.0, 4.5)
+    b = synth.rhs(m.n, 3)
+    ref = oracle.gabp_naive(m, b, max_iter=7, tol=1e-14)
+    g = _gpu_solve(gb, m, b, 1e-14, 7)
+    assert g["status"] == ref["status"] == gb.GABP_NOT_CONVERGED and g["iters"] == 7
+    assert _relerr(g["x"], ref["x"]) <= 1e-13
+
+
+def test_divergence_reported(gb):
+    """A non-walk-summable, indefinite system (diagonal 0.5 x row abs-sum): no hang, a status."""
+    m = synth.random_sym(2000, 3, 0.5, 5)
+    g = _gpu_solve(gb, m, synth.rhs(m.n, 5), 1e-10, 3000)
+    assert g["status"] in (gb.GABP_DIVERGED, gb.GABP_NOT_CONVERGED, gb.GABP_BREAKDOWN)
+
+
+def test_zero_rhs_and_tiny(gb):
+    m = synth.grid2d(4)
+    g = _gpu_solve(gb, m, np.zeros(m.n), 1e-12, 10)
+    assert g["status"] == gb.GABP_OK and g["iters"] == 0 and not np.any(g["x"])
+    m1 = synth.from_dense(np.array([[2.0]]))
+    g = _gpu_solve(gb, m1, np.array([3.0]), 1e-14, 10)
+    assert g["status"] == gb.GABP_OK and abs(g["x"][0] - 1.5) < 1e-15
+
+
+@pytest.mark.parametrize("bad", ["asym_value", "asym_pattern", "zero_diag", "unsorted", "col_range"])
+def test_invalid_matrix_rejected(gb, bad):
+    A, _ = synth.toy3x3()
+    m = synth.from_dense(A)
+    rp, col, val = m.rowptr.copy(), m.col.copy(), m.val.copy()
+    if bad == "asym_value":
+        val[1] = 7.0
+    elif bad == "asym_pattern":
+        m = synth.from_coo(3, [0, 0, 1, 2, 2], [0, 1, 1, 0, 2], [1.0, 2.0, 1.0, 2.0, 1.0])
+        rp, col, val = m.rowptr, m.col, m.val
+    elif bad == "zero_diag":
+        val[0] = 0.0
+    elif bad == "unsorted":
+        col[0], col[1] = col[1], col[0]
+        val[0], val[1] = val[1], val[0]
+    elif bad == "col_range":
+        col[2] = 9
+    with pytest.raises(gb.GaBPError) as ei:
+        gb.Solver(3, rp, col, val)
+    assert ei.value.status == gb.GABP_ERR_INVALID
+
+
+def test_solve_host_matches_device(gb):
+    m = synth.random_sym(3000, 4, 1.1, 6)
+    b = synth.rhs(m.n, 6)
+    s = _solver(gb, m)
+    xd, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=500)
+    xh = np.zeros(m.n)
+    st2, it2, rel2 = s.solve_host(b.copy(), xh, tol=1e-12, max_iter=500)
+    s.close()
+    assert st == st2 == 0 and it == it2 and np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_device_csr_input(gb):
+    m = synth.grid2d(20, -1.0, 4.5)
+    b = synth.rhs(m.n, 9)
+    s = gb.Solver(m.n, torch.from_numpy(m.rowptr).cuda(), torch.from_numpy(m.col).cuda(),
+                  torch.from_numpy(m.val).cuda())
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-12)
+    s.close()
+    ref = oracle.gabp_naive(m, b, max_iter=1000, tol=1e-12)
+    assert st == 0 and it == ref["iters"] and _relerr(x.cpu().numpy(), ref["x"]) <= 1e-12
+
+
+def test_full_size_random_sym_c2(gb):
+    """The benchmark workload (n = 2^20, 8 picks per row, diagonal 1.1 x row abs-sum) in the
+    launch configuration the benchmark times: the residual recomputed on the host meets
+    the tolerance, the round count equals the oracle's, and sampled entries agree with it."""
+    m = synth.random_sym(1 << 20, 8, 1.1, 2)
+    b = synth.rhs(m.n, 2)
+    g = _gpu_solve(gb, m, b, 1e-10, 200)
+    assert g["status"] == gb.GABP_OK
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    r = b - np.bincount(rows, m.val * g["x"][m.col], minlength=m.n)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    ref = oracle.gabp_broadcast(m, b, max_iter=200, tol=1e-10)
+    assert g["iters"] == ref["iters"]
+    idx = np.random.default_rng(0).choice(m.n, 4096, replace=False)
+    assert np.allclose(g["x"][idx], ref["x"][idx], rtol=1e-12, atol=1e-14)
