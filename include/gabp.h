@@ -188,6 +188,32 @@ typedef struct {
 } gabp_profile;
 gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
 
+/*
+ * gabp_solve_noalloc -- plain FP64 solve of a small system without any device
+ * allocation.  The paper has no counterpart: this is a deployment variant of
+ * gabp_solve for callers that cannot call cudaMalloc at solve time (latency-
+ * critical loops that cannot absorb its device synchronisation, processes
+ * whose device memory another allocator has already reserved, code under
+ * no-allocation-after-start-up rules).
+ *
+ * A is FULL symmetric CSR as for gabp_create; rowptr, col, val, b, x are DEVICE
+ * arrays owned by the caller; stream is a cudaStream_t.  Same iteration, stop
+ * rule and statuses as gabp_solve with GABP_PREC_FP64; iters_out / relres_out
+ * are nullable host pointers.  Returns after synchronising the stream.
+ *
+ * Working memory is one fixed array (about 5.6 MB) inside the library's device
+ * memory, held by every GPU that loads the library until the process exits.
+ * Limits: 1 <= n <= 16384 and n <= nnz <= 131072; larger sizes return
+ * GABP_ERR_INVALID without launching anything.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it:
+ * make that first call before any stream capture on the device.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller.  No cudaMalloc, cudaFree or other allocating call is made.
+ */
+gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
+                               const double *val, const double *b, double *x, double tol,
+                               int32_t max_iter, void *stream, int32_t *iters_out, double *relres_out);
+
 /* Free everything the handle owns.  NULL is accepted. */
 gabp_status gabp_destroy(gabp_handle h);
 

@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -77,6 +77,8 @@ _SIGNATURES = {
     "gabp_last_stats": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_profile_read": ([_P, ctypes.POINTER(Profile), ctypes.c_int], ctypes.c_int),
+    "gabp_solve_noalloc": ([ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32,
+                            _P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -183,6 +185,15 @@ def gabp_profile_read(h, reset=False):
     names = ("fp64", "prec32", "mean32", "refine64")
     return st, {"ms": dict(zip(names, list(p.ms))), "rounds": dict(zip(names, list(p.rounds))),
                 "launches": p.launches}
+
+
+def gabp_solve_noalloc(n, nnz, rowptr_ptr, col_ptr, val_ptr, b_ptr, x_ptr, tol, max_iter, stream_ptr):
+    """Allocation-free FP64 solve of a small system (device arrays); returns (status, iters, relres)."""
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.gabp_solve_noalloc(int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr), _P(b_ptr), _P(x_ptr),
+                                float(tol), int(max_iter), _P(stream_ptr), ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
 
 
 def gabp_destroy(h):
