@@ -5,23 +5,40 @@
 
 namespace gabp {
 
-// Reciprocal of a double by Newton-Raphson iteration (y <- y + y (1 - d y)),
-// seeded with the single-precision hardware approximation (PTX rcp.approx.ftz.f32).
-// The seed's relative error is about 2^-22; each step squares it, so two steps
-// reach FP64 rounding level (within a couple of ulp of 1/d).  Outside the range
-// where the single-precision seed is a normal number the IEEE division is used.
+// IEEE division, kept out of line so that the common path of rcp64 does not
+// carry its instructions.
+static __device__ __noinline__ double rcp64_slow(double d) { return 1.0 / d; }
+
+// Reciprocal of a double by Newton-Raphson iteration, y <- y + y (1 - d y).
+// The seed is the single-precision hardware approximation (PTX rcp.approx.ftz.f32)
+// of d rounded toward zero to 20 mantissa bits.  The float operand and the
+// double seed are assembled from the IEEE-754 fields with integer operations,
+// which keeps the conversions off the (narrow) FP64 pipe.  The seed's relative
+// error is below 2^-19; each step squares it, so two steps reach FP64 rounding
+// level.  Exponents outside [-120, 120] (and 0, subnormals, inf, NaN) take the
+// IEEE division.
 __device__ __forceinline__ double rcp64(double d) {
-  float df = __double2float_rn(d);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023;
+  const unsigned fb = (hi & 0x80000000u) | ((unsigned)(e + 127) << 23) | ((hi & 0xfffffu) << 3);
   float yf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(df));
-  double y = (double)yf;
-  double e = fma(-d, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-d, y, 1.0);
-  y = fma(y, e, y);
-  float a = fabsf(df);
-  if (!(a > 1e-30f && a < 1e30f)) y = 1.0 / d;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(fb)));
+  const unsigned yb = __float_as_uint(yf);
+  const int ey = (int)((yb >> 23) & 0xffu) - 127;
+  const unsigned yhi = (yb & 0x80000000u) | ((unsigned)(ey + 1023) << 20) | ((yb >> 3) & 0xfffffu);
+  double y = __hiloint2double((int)yhi, (int)((yb & 7u) << 29));
+  double r = fma(-d, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-d, y, 1.0);
+  y = fma(y, r, y);
+  if (e < -120 || e > 120) y = rcp64_slow(d);
   return y;
+}
+
+// d == +0 or -0, tested on the bit pattern (integer pipe).
+__device__ __forceinline__ bool is_zero64(double d) {
+  return (((unsigned long long)__double_as_longlong(d)) << 1) == 0ull;
 }
 
 template <typename T>

@@ -46,6 +46,8 @@ struct DevCtl {
   unsigned int arrive;
   int edge_bad;      // breakdown flag raised by an edge kernel, consumed by the round's last block
   const double *b;   // right-hand side of the current FP64 run (device); read by the round kernels
+  int no_stop;       // autotuning runs: advance rounds but never take a terminal decision
+  int pad1;
 };
 
 struct Graph {
@@ -123,6 +125,10 @@ struct gabp_handle_s {
   cudaGraphExec_t gH32 = nullptr;
   int gH32_R = -1;
   int last_path = -1;               // 0 FP64, 1 FP32 refinement (for gabp_marginal_precisions)
+  // autotuned sub-warp widths (0 = not tuned yet) and the scratch control block the tuner uses
+  int tuned_L64 = 0, tuned_Lp32 = 0, tuned_Lm32 = 0;
+  gabp::DevCtl *ctl_tune = nullptr;
+  int gP32_L = -1, gH32_L = -1;
   double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
   gabp::Prof prof;
 };
@@ -138,6 +144,18 @@ gabp_status cuda_fail(cudaError_t e, const char *what);
     cudaError_t e__ = (call);                               \
     if (e__ != cudaSuccess) return ::gabp::cuda_fail(e__, #call); \
   } while (0)
+
+// Grid of one full wave: SMs x CTAs of this kernel resident per SM (grid-stride
+// kernels then give every CTA the same share with no partial second wave).
+template <typename K>
+inline int resident_grid(int num_sms, K kernel) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb * num_sms;
+}
 
 inline int blocks_for(int64_t work, int per_block, int max_blocks) {
   int64_t b = (work + per_block - 1) / per_block;
@@ -162,6 +180,31 @@ inline void prof_collect(gabp_handle h, int phase, int64_t rounds) {
   if (cudaEventElapsedTime(&ms, h->prof.e0, h->prof.e1) == cudaSuccess) h->prof.ms[phase] += ms;
   else cudaGetLastError();
 }
+
+// Autotuner: times `rounds` launches of `launch` (after one warm-up launch) on
+// the handle's stream; the caller points the kernels at a scratch control block
+// with no_stop set, so the launches do real work whatever the buffers hold.
+template <typename F>
+inline float time_launches(gabp_handle h, F launch, int rounds) {
+  launch();
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    return 1e30f;
+  }
+  cudaEventRecord(a, h->stream);
+  for (int r = 0; r < rounds; ++r) launch();
+  cudaEventRecord(b, h->stream);
+  float ms = 1e30f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 1e30f;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms;
+}
+gabp_status tune_ctl(gabp_handle h, const double *b);  // (re)arms ctl_tune for a tuning run (b: any n-vector)
 
 // shared host helpers (defined in setup.cu / solve64.cu / solve32.cu)
 gabp_status read_ctl(gabp_handle h);  // copies ctl -> ctl_host and synchronises

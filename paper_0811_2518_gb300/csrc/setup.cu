@@ -129,6 +129,28 @@ static void free_graph(Graph &g) {
   g = Graph{};
 }
 
+__global__ void k_ctl_arm_tune(DevCtl *c, const double *b) {
+  c->round = 0;
+  c->done = 0;
+  c->status = GABP_NOT_CONVERGED;
+  c->max_iter = 0x7fffffff;
+  c->check_from = 1;
+  c->stable = 0;
+  c->tol2bb = -1.0;
+  c->arrive = 0;
+  c->edge_bad = 0;
+  c->b = b;
+  c->no_stop = 1;
+}
+
+gabp_status tune_ctl(gabp_handle h, const double *b) {
+  if (!h->ctl_tune) GABP_CUDA(cudaMalloc(&h->ctl_tune, sizeof(DevCtl)));
+  if (!h->ctl_tune) return GABP_ERR_NOMEM;
+  k_ctl_arm_tune<<<1, 1, 0, h->stream>>>(h->ctl_tune, b ? b : h->g.ad);
+  GABP_CUDA(cudaGetLastError());
+  return GABP_OK;
+}
+
 gabp_status read_ctl(gabp_handle h) {
   GABP_CUDA(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
   GABP_CUDA(cudaStreamSynchronize(h->stream));
@@ -153,6 +175,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   cudaFree(h->hb);
   cudaFree(h->hx);
   cudaFree(h->gamma);
+  cudaFree(h->ctl_tune);
   if (h->prof.e0) cudaEventDestroy(h->prof.e0);
   if (h->prof.e1) cudaEventDestroy(h->prof.e1);
   cudaSetDevice(cur);

@@ -31,6 +31,7 @@
 namespace gabp {
 
 constexpr int kPrecMaxRounds = 300;  // cap of the FP32 precision phase
+constexpr int kUnroll32 = 4;         // slots per lane whose loads are issued together
 
 struct Args32 {
   int n;
@@ -72,44 +73,59 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   const float *__restrict__ Pm2 = ring3(a.NP0, a.NP1, a.NP2, t + 1);
   float *__restrict__ Pt = ring3(a.NP0, a.NP1, a.NP2, t);
   constexpr int RPW = 32 / L;
+  constexpr int U = kUnroll32;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
   float rel = 0.f;
-  double bad = 0.0;
+  int bad = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     float acc = 0.f;
     if (i < a.n) {
       const float Pi2 = t >= 2 ? Pm2[i] : 0.f;
       const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + sl; e < e1; e += L) {
-        const int k = a.ci[e];
-        const float A = a.av[e];
-        const float A2 = A * A;
-        float Pout = 0.f;
-        if (t >= 2) {
-          const float d1 = Pi2 - Mc[e];
-          if (d1 == 0.f) bad += 1.0;
-          Pout = -A2 / d1;
+      for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+        // all loads of U slots first (memory-level parallelism), then the gathers
+        int k[U];
+        float A[U], Ps[U], Pp[U], Pk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) { k[u] = __ldcs(a.ci + e); A[u] = __ldcs(a.av + e); Ps[u] = __ldcs(Mc + e); Pp[u] = __ldcs(Mo + e); }
         }
-        const float d2 = Pm1[k] - Pout;
-        if (d2 == 0.f) bad += 1.0;
-        const float Pn = -A2 / d2;
-        const float prev = Mo[e];
-        Mc[e] = Pn;
-        acc += Pn;
-        rel = fmaxf(rel, fabsf(Pn - prev) / fabsf(Pn));
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (eb + u * L < e1) Pk[u] = Pm1[k[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            const float A2 = A[u] * A[u];
+            float Pout = 0.f;
+            if (t >= 2) {
+              const float d1 = Pi2 - Ps[u];
+              bad |= (d1 == 0.f);
+              Pout = -A2 / d1;
+            }
+            const float d2 = Pk[u] - Pout;
+            bad |= (d2 == 0.f);
+            const float Pn = -A2 / d2;
+            __stcs(Mc + e, Pn);
+            acc += Pn;
+            rel = fmaxf(rel, fabsf(Pn - Pp[u]) / fabsf(Pn));
+          }
+        }
       }
     }
     acc = sub_sum<L>(acc);
     if (i < a.n && sl == 0) {
       const float P = a.ad[i] + acc;
-      if (P == 0.f) bad += 1.0;
+      bad |= (P == 0.f);
       Pt[i] = P;
     }
   }
-  double vb[1] = {bad}, vr[1] = {(double)rel};
+  double vb[1] = {(double)bad}, vr[1] = {(double)rel};
   block_sum<1>(vb);
   block_max<1>(vr);
   double v[2] = {vb[0], vr[0]}, tot[2];
@@ -119,7 +135,9 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
     ctl->maxrel = tot[1];
     const bool stat = !(tot[1] > 9.5367431640625e-7);  // 2^-20; NaN counts as not stationary
     ctl->stable = stat ? ctl->stable + 1 : 0;
-    if (tot[0] > 0.0) {
+    if (ctl->no_stop) {
+      // autotuning run: no decision
+    } else if (tot[0] > 0.0) {
       ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     } else if (!isfinite(tot[1]) && t > 1) {
       ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
@@ -173,23 +191,39 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   const float *__restrict__ Hm2 = ring3(a.NH0, a.NH1, a.NH2, t + 1);
   float *__restrict__ Ht = ring3(a.NH0, a.NH1, a.NH2, t);
   constexpr int RPW = 32 / L;
+  constexpr int U = kUnroll32;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  double dxx = 0.0, xx = 0.0;
+  float dxx = 0.f, xx = 0.f;  // per-thread partial sums stay in FP32 (the FP64 pipe is narrow)
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     float acc = 0.f;
     if (i < a.n) {
       const float hi2 = t >= 2 ? Hm2[i] : 0.f;
       const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + sl; e < e1; e += L) {
-        const int k = a.ci[e];
-        const float2 cf = a.CF[e];
-        const float hout = t >= 2 ? cf.y * (hi2 - Hc[e]) : 0.f;
-        const float hn = cf.x * (Hm1[k] - hout);
-        Hc[e] = hn;
-        acc += hn;
+      for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+        int k[U];
+        float2 cf[U];
+        float hs[U], hk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) { k[u] = __ldcs(a.ci + e); cf[u] = __ldcs(a.CF + e); hs[u] = __ldcs(Hc + e); }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (eb + u * L < e1) hk[u] = Hm1[k[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            const float hout = t >= 2 ? cf[u].y * (hi2 - hs[u]) : 0.f;  // message i -> k at t-1
+            const float hn = cf[u].x * (hk[u] - hout);                  // message k -> i at t
+            __stcs(Hc + e, hn);
+            acc += hn;
+          }
+        }
       }
     }
     acc = sub_sum<L>(acc);
@@ -197,19 +231,21 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
       const float hnew = a.rhs[i] + acc;
       Ht[i] = hnew;
       const float ip = a.invP[i];
-      const double x = (double)(hnew * ip), dx = (double)((hnew - Hm1[i]) * ip);
-      dxx = fma(dx, dx, dxx);
-      xx = fma(x, x, xx);
+      const float x = hnew * ip, dx = (hnew - Hm1[i]) * ip;
+      dxx = fmaf(dx, dx, dxx);
+      xx = fmaf(x, x, xx);
     }
   }
-  double v[2] = {dxx, xx}, tot[2];
+  double v[2] = {(double)dxx, (double)xx}, tot[2];
   const int modes[2] = {0, 0};
   block_sum<2>(v);
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
     ctl->round = t;
     ctl->rr = tot[0];
     ctl->xx = tot[1];
-    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+    if (ctl->no_stop) {
+      // autotuning run: no decision
+    } else if (!isfinite(tot[0]) || !isfinite(tot[1])) {
       ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     } else if (t >= 2 && tot[0] <= ctl->tol2bb * tot[1]) {
       ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
@@ -295,6 +331,7 @@ __global__ void k_ctl_reset(DevCtl *c, int max_iter, double tol2) {
   c->maxrel = 0.0;
   c->arrive = 0;
   c->edge_bad = 0;
+  c->no_stop = 0;
 }
 
 // Diagonal loading of the convergence fix.  mode 1: Gamma_i = gamma A_ii (the
@@ -404,11 +441,16 @@ static Args32 args32(gabp_handle h) {
   return a;
 }
 
-static int lanes32(gabp_handle h) {
+static int lanes32(gabp_handle h, bool mean) {
   if (h->opt.lanes) return h->opt.lanes;
+  const int tuned = mean ? h->tuned_Lm32 : h->tuned_Lp32;
+  if (tuned) return tuned;
+  // One unrolled pass (kUnroll32 slots per lane) should cover a row of average
+  // degree: the widest sub-warp with L * kUnroll32 <= degree (degree 16: 4 lanes;
+  // degree 6: 1 lane -- the measured optimum on both workloads).
   double d = h->g.avg_deg;
   int L = 1;
-  while (L < 32 && L * 2 <= d) L *= 2;
+  while (L < 32 && (2 * L) * kUnroll32 <= d + 0.5) L *= 2;
   return L;
 }
 
@@ -424,10 +466,16 @@ static int lanes32(gabp_handle h) {
 
 // Run K-round graphs of one round kernel until the control block says done.
 template <typename LaunchFn>
-static gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, LaunchFn launch, int max_rounds, int phase) {
+static gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_key, int key, LaunchFn launch,
+                              int max_rounds, int phase) {
   const int K = h->opt.check_every;
   const bool use_graph = h->stream != nullptr;
+  if (use_graph && *cache && *cache_key != key) {
+    cudaGraphExecDestroy(*cache);
+    *cache = nullptr;
+  }
   if (use_graph && !*cache) {
+    *cache_key = key;
     cudaGraph_t graph;
     GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < K; ++k) launch();
@@ -460,28 +508,71 @@ static gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, LaunchFn la
 }
 
 // Precision phase + coefficient freeze on A (+ Gamma).
+// Autotuner of the sub-warp widths of the FP32 round kernels (see autotune64).
+static gabp_status autotune32(gabp_handle h, bool mean) {
+  if (h->opt.lanes || (mean ? h->tuned_Lm32 : h->tuned_Lp32)) return GABP_OK;
+  Graph &g = h->g;
+  gabp_status s0 = tune_ctl(h, nullptr);  // allocates the scratch control block on first use
+  if (s0 != GABP_OK) return s0;
+  Args32 a = args32(h);
+  a.ctl = h->ctl_tune;
+  const int cands[4] = {1, 2, 4, 8};
+  float best = 1e30f;
+  int bestL = 1;
+  gabp_status s;
+  for (int L : cands) {
+    if ((s = tune_ctl(h, nullptr)) != GABP_OK) return s;
+    float ms = 1e30f;
+    if (mean) {
+      GABP_DISPATCH_L(L, ms = time_launches(h, [&] {
+        k32_mean<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL>)), kBlock, 0, h->stream>>>(a);
+      }, 3));
+    } else {
+      GABP_DISPATCH_L(L, ms = time_launches(h, [&] {
+        k32_prec<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL>)), kBlock, 0, h->stream>>>(a);
+      }, 3));
+    }
+    if (ms < best) { best = ms; bestL = L; }
+  }
+  GABP_CUDA(cudaGetLastError());
+  (mean ? h->tuned_Lm32 : h->tuned_Lp32) = bestL;
+  return GABP_OK;
+}
+
 static gabp_status precision_phase(gabp_handle h, const double *gamma_diag) {
   Work32 &w = h->w32;
   Graph &g = h->g;
-  const int L = lanes32(h);
   size_t E = (size_t)(g.E > 0 ? g.E : 1);
   k_diag32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad, gamma_diag, g.ad32);
-  GABP_CUDA(cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, h->stream));
-  GABP_CUDA(cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, h->stream));
-  GABP_CUDA(cudaMemcpyAsync(w.NP[0], g.ad32, sizeof(float) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  // round-0 state: zero precision messages, P~ = diagonal
+  auto init = [&]() -> gabp_status {
+    GABP_CUDA(cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, h->stream));
+    GABP_CUDA(cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, h->stream));
+    GABP_CUDA(cudaMemcpyAsync(w.NP[0], g.ad32, sizeof(float) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+    return GABP_OK;
+  };
+  gabp_status st = init();
+  if (st != GABP_OK) return st;
+  if (!h->opt.lanes && !h->tuned_Lp32) {
+    if ((st = autotune32(h, false)) != GABP_OK) return st;
+    if ((st = init()) != GABP_OK) return st;
+  }
+  const int L = lanes32(h, false);
   k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, 0.0);
   h->prof.launches += 2;
   GABP_CUDA(cudaGetLastError());
   Args32 a = args32(h);
-  const int nb = blocks_for(g.n, kBlock / L, h->max_blocks);
   gabp_status s;
-  GABP_DISPATCH_L(L, s = run_rounds(h, &h->gP32, [&] { k32_prec<LL><<<nb, kBlock, 0, h->stream>>>(a); }, kPrecMaxRounds,
-                                  PH_PREC32));
+  GABP_DISPATCH_L(L, s = run_rounds(h, &h->gP32, &h->gP32_L, L, [&] {
+    const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL>));
+    k32_prec<LL><<<nb, kBlock, 0, h->stream>>>(a);
+  }, kPrecMaxRounds, PH_PREC32));
   if (s != GABP_OK) return s;
   const DevCtl c = *h->ctl_host;
   h->stats.rounds += c.round;
   if (c.status == GABP_BREAKDOWN || c.status == GABP_DIVERGED) return (gabp_status)c.status;
-  GABP_DISPATCH_L(L, (k32_coef<LL><<<nb, kBlock, 0, h->stream>>>(a, c.result_round)));
+  GABP_DISPATCH_L(L, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)), kBlock, 0,
+                                     h->stream>>>(a, c.result_round)));
   h->prof.launches += 1;
   GABP_CUDA(cudaGetLastError());
   w.prec_round = c.result_round;
@@ -505,12 +596,16 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     if ((s = precision_phase(h, gamma_diag)) != GABP_OK) return s;
     if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
   }
-  const int L = lanes32(h);
-  const int nbr = blocks_for(g.n, kBlock / L, h->max_blocks);
+  if ((s = autotune32(h, true)) != GABP_OK) return s;
+  const int L = lanes32(h, true);
+  // FP64 residual: narrow sub-warps (its per-row epilogue is FP64)
+  const int LR = h->opt.lanes ? h->opt.lanes : (g.avg_deg >= 12.0 ? 2 : 1);
+  int nbr = 1;
+  GABP_DISPATCH_L(LR, nbr = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k64_residual<LL>)));
   GABP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * g.n, h->stream));
   GABP_CUDA(cudaMemsetAsync(w.ctlR, 0, sizeof(DevCtl), h->stream));
-  GABP_DISPATCH_L(L, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
-                                                                         w.NH[0], w.ctlR, h->partials, 1)));
+  GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
+                                                                          w.NH[0], w.ctlR, h->partials, 1)));
   h->prof.launches += 1;
   GABP_CUDA(cudaGetLastError());
   DevCtl cr;
@@ -537,7 +632,10 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, itol * itol);
     h->prof.launches += 1;
     GABP_CUDA(cudaGetLastError());
-    GABP_DISPATCH_L(L, s = run_rounds(h, &h->gH32, [&] { k32_mean<LL><<<nbr, kBlock, 0, h->stream>>>(a); }, cap, PH_MEAN32));
+    GABP_DISPATCH_L(L, s = run_rounds(h, &h->gH32, &h->gH32_L, L, [&] {
+      const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL>));
+      k32_mean<LL><<<nb, kBlock, 0, h->stream>>>(a);
+    }, cap, PH_MEAN32));
     if (s != GABP_OK) return s;
     const DevCtl c = *h->ctl_host;
     total_inner += c.round;
@@ -546,8 +644,8 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     float *hT = c.result_round % 3 == 0 ? w.NH[0] : (c.result_round % 3 == 1 ? w.NH[1] : w.NH[2]);
     prof_begin(h);
     k64_update<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, X, hT, w.invP);
-    GABP_DISPATCH_L(L, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
-                                                                           w.NH[0], w.ctlR, h->partials, 0)));
+    GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
+                                                                            w.NH[0], w.ctlR, h->partials, 0)));
     prof_end(h);
     h->prof.launches += 2;
     GABP_CUDA(cudaGetLastError());

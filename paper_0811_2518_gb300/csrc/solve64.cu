@@ -38,7 +38,9 @@ struct Args64 {
 __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
   const int tchk = t - 1;
   ctl->round = t;
-  if (tchk >= ctl->check_from && isfinite(rr) && rr <= ctl->tol2bb) {
+  if (ctl->no_stop) {
+    ctl->rr = rr;
+  } else if (tchk >= ctl->check_from && isfinite(rr) && rr <= ctl->tol2bb) {
     ctl->status = GABP_OK;
     ctl->iters = tchk;
     ctl->result_round = tchk;
@@ -125,7 +127,8 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
   const int sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  double rr = 0.0, bad = 0.0;
+  double rr = 0.0;
+  int bad = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     double accP = 0.0, acch = 0.0, accr = 0.0;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
         const double2 rv = Min[a.rev[e]];  // message i -> k of round t-1
         const NodeRec64 nk = Nin[k];       // node k at round t-1
         const double den = nk.P - rv.x;    // cavity precision P_{k\i}
-        if (den == 0.0) bad += 1.0;
+        bad |= is_zero64(den);
         const double cin = -A * rcp64(den);
         const double2 m = make_double2(cin * A, cin * (nk.h - rv.y));
         Mout[e] = m;
@@ -152,13 +155,13 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
     if (i < a.n && sl == 0) {
       const double bi = b[i], d = a.ad[i];
       const double P = d + accP, h = bi + acch;
-      if (P == 0.0) bad += 1.0;
-      Nout[i] = NodeRec64{P, h, h / P, 0.0};
+      bad |= is_zero64(P);
+      Nout[i] = NodeRec64{P, h, h * rcp64(P), 0.0};
       const double r = bi - fma(d, Nin[i].x, accr);
       rr = fma(r, r, rr);
     }
   }
-  double v[2] = {rr, bad}, tot[2];
+  double v[2] = {rr, (double)bad}, tot[2];
   const int modes[2] = {0, 0};
   block_sum<2>(v);
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0)
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kBlock) k64_edge_msg(Args64 a, int E) {
     const double2 rv = Min[a.rev[e]];
     const NodeRec64 nk = Nin[k];
     const double den = nk.P - rv.x;
-    bad |= (den == 0.0);
+    bad |= is_zero64(den);
     const double cin = -A * rcp64(den);
     Mout[e] = make_double2(cin * A, cin * (nk.h - rv.y));
   }
@@ -205,7 +208,8 @@ __global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
   const int sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  double rr = 0.0, bad = 0.0;
+  double rr = 0.0;
+  int bad = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     double accP = 0.0, acch = 0.0, accr = 0.0;
@@ -224,13 +228,13 @@ __global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
     if (i < a.n && sl == 0) {
       const double bi = b[i], d = a.ad[i];
       const double P = d + accP, h = bi + acch;
-      if (P == 0.0) bad += 1.0;
-      Nout[i] = NodeRec64{P, h, h / P, 0.0};
+      bad |= is_zero64(P);
+      Nout[i] = NodeRec64{P, h, h * rcp64(P), 0.0};
       const double r = bi - fma(d, Nin[i].x, accr);
       rr = fma(r, r, rr);
     }
   }
-  double v[2] = {rr, bad}, tot[2];
+  double v[2] = {rr, (double)bad}, tot[2];
   const int modes[2] = {0, 0};
   block_sum<2>(v);
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
@@ -300,11 +304,13 @@ void free_w64(gabp_handle h) {
 
 static int pick_lanes(gabp_handle h) {
   if (h->opt.lanes) return h->opt.lanes;
-  // about two slots per lane; rows of degree ~16 get 8 lanes, grid rows 2-4
-  double d = h->g.avg_deg;
-  int L = 1;
-  while (L < 32 && L * 2 <= d) L *= 2;
-  return L;
+  if (h->tuned_L64) return h->tuned_L64;
+  // The FP64 round is bound by the FP64 pipe.  A row's epilogue (aggregate,
+  // x_i, residual) runs on one lane of its sub-warp while the others wait, and
+  // the sub-warp reduction adds FP64 adds, so narrow sub-warps win: 2 lanes for
+  // rows of average degree >= 12, else 1 (measured on the n = 2^20 random graph
+  // of degree 16 and on the 128^3 grid).
+  return h->g.avg_deg >= 12.0 ? 2 : 1;
 }
 
 static Args64 args64(gabp_handle h) {
@@ -327,12 +333,13 @@ static Args64 args64(gabp_handle h) {
 template <int L>
 static void launch_round_L(gabp_handle h, const Args64 &a) {
   const int rows_per_block = kBlock / L;
-  const int nb = blocks_for(h->g.n, rows_per_block, h->max_blocks);
   if (h->opt.variant == GABP_VARIANT_EDGE) {
-    const int eb = blocks_for(h->g.E, kBlock, h->max_blocks);
+    const int eb = blocks_for(h->g.E, kBlock, resident_grid(h->num_sms, k64_edge_msg));
+    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_edge_agg<L>));
     k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a, h->g.E);
     k64_edge_agg<L><<<nb, kBlock, 0, h->stream>>>(a);
   } else {
+    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L>));
     k64_node<L><<<nb, kBlock, 0, h->stream>>>(a);
   }
 }
@@ -346,6 +353,28 @@ static void launch_round(gabp_handle h, const Args64 &a, int L) {
     case 16: launch_round_L<16>(h, a); break;
     default: launch_round_L<32>(h, a); break;
   }
+}
+
+// Autotuner of the sub-warp width: a few rounds of each candidate, run from the
+// solve's round-0 state under a scratch control block that never stops; the
+// fastest width is kept for the life of the handle.
+static gabp_status autotune64(gabp_handle h, const double *b) {
+  if (h->opt.lanes || h->tuned_L64) return GABP_OK;
+  gabp_status s = tune_ctl(h, b);  // allocates the scratch control block on first use
+  if (s != GABP_OK) return s;
+  Args64 a = args64(h);
+  a.ctl = h->ctl_tune;
+  const int cands[3] = {1, 2, 4};
+  float best = 1e30f;
+  int bestL = 1;
+  for (int L : cands) {
+    if ((s = tune_ctl(h, b)) != GABP_OK) return s;
+    float ms = time_launches(h, [&] { launch_round(h, a, L); }, 3);
+    if (ms < best) { best = ms; bestL = L; }
+  }
+  GABP_CUDA(cudaGetLastError());
+  h->tuned_L64 = bestL;
+  return GABP_OK;
 }
 
 // K rounds as one CUDA graph (the round index lives in device memory, so the
@@ -379,16 +408,24 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   if (s != GABP_OK) return s;
   Graph &g = h->g;
   h->w64.valid = false;
-  // control block: zero, then point it at b
-  GABP_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(DevCtl), h->stream));
-  const double *bptr = b;
-  GABP_CUDA(cudaMemcpyAsync(&h->ctl->b, &bptr, sizeof(bptr), cudaMemcpyHostToDevice, h->stream));
-  // the pinned staging copy must stay alive until the copy ran: synchronise below
-  GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
   Args64 a = args64(h);
-  k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter);
-  GABP_CUDA(cudaGetLastError());
-  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  // round-0 state (Algorithm 1 step 1): control block pointed at b, zero messages
+  auto init = [&]() -> gabp_status {
+    GABP_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(DevCtl), h->stream));
+    const double *bptr = b;
+    GABP_CUDA(cudaMemcpyAsync(&h->ctl->b, &bptr, sizeof(bptr), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
+    k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter);
+    GABP_CUDA(cudaGetLastError());
+    GABP_CUDA(cudaStreamSynchronize(h->stream));  // also retires the pageable copy of bptr
+    return GABP_OK;
+  };
+  if ((s = init()) != GABP_OK) return s;
+  if (!h->opt.lanes && !h->tuned_L64) {
+    // tune on this solve's own round-0 state, then start it again from round 0
+    if ((s = autotune64(h, b)) != GABP_OK) return s;
+    if ((s = init()) != GABP_OK) return s;
+  }
 
   const int L = pick_lanes(h);
   const bool use_graph = h->stream != nullptr;
