@@ -280,6 +280,24 @@ class Solver:
             raise GaBPError(st, "gabp_solve_host")
         return st, it, rel
 
+    def solve_batched(self, B, tol=1e-10, max_iter=5000, X=None, check=True):
+        """Solve A X_r = B_r for every row r of the CUDA tensor B [R, n] (FP32 messages,
+        FP64 refinement, shared precision messages).  Returns (X, status, inner_rounds, relres[R])."""
+        import numpy as np
+        import torch
+
+        B = B.to(self.device, torch.float64).contiguous()
+        if B.dim() != 2 or B.shape[1] != self.n:
+            raise ValueError("B must be [R, n]")
+        if X is None:
+            X = torch.empty_like(B)
+        rel = np.zeros(B.shape[0])
+        st, it = gabp_solve_batched(self.handle, B.shape[0], B.data_ptr(), X.data_ptr(), self.n, tol, max_iter,
+                                    rel.ctypes.data)
+        if check and st < 0:
+            raise GaBPError(st, "gabp_solve_batched")
+        return X, st, it, rel
+
     def marginal_precisions(self):
         import torch
 

@@ -81,9 +81,19 @@ extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x
 
 extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
                                           double tol, int32_t max_iter, int32_t *iters_out, double *relres_out) {
-  (void)h; (void)nrhs; (void)B; (void)X; (void)ld; (void)tol; (void)max_iter; (void)iters_out; (void)relres_out;
-  set_last_error("gabp_solve_batched: not available in this build");
-  return GABP_ERR_INVALID;
+  if (!h || !B || !X || nrhs < 1 || ld < h->g.n || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  if (!is_device_ptr(B) || !is_device_ptr(X)) {
+    set_last_error("gabp_solve_batched: B and X must be device arrays");
+    return GABP_ERR_INVALID;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  int it = 0;
+  gabp_status s = solve_batched32(h, nrhs, B, X, ld, tol, max_iter, &it, relres_out);
+  if (cur != h->device) cudaSetDevice(cur);
+  if (s >= 0 && iters_out) *iters_out = it;
+  return s;
 }
 
 extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {

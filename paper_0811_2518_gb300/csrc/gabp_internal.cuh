@@ -88,6 +88,8 @@ struct Work32 {
   int *rhs_active = nullptr;
 };
 
+struct WorkB;  // batched multi-RHS work arrays (batched.cu)
+
 struct Stats {
   int64_t rounds = 0;
   int refine_steps = 0;
@@ -131,6 +133,7 @@ struct gabp_handle_s {
   int gP32_L = -1, gH32_L = -1;
   double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
   gabp::Prof prof;
+  gabp::WorkB *wb = nullptr;
 };
 
 namespace gabp {
@@ -206,8 +209,64 @@ inline float time_launches(gabp_handle h, F launch, int rounds) {
 }
 gabp_status tune_ctl(gabp_handle h, const double *b);  // (re)arms ctl_tune for a tuning run (b: any n-vector)
 
-// shared host helpers (defined in setup.cu / solve64.cu / solve32.cu)
 gabp_status read_ctl(gabp_handle h);  // copies ctl -> ctl_host and synchronises
+
+// Run K-round graphs of one round kernel (CUDA graph of K launches when the
+// stream can be captured) until the control block says done.
+#define GABP_DISPATCH_L(L, CALL) \
+  switch (L) {                   \
+    case 1: { constexpr int LL = 1; CALL; } break;  \
+    case 2: { constexpr int LL = 2; CALL; } break;  \
+    case 4: { constexpr int LL = 4; CALL; } break;  \
+    case 8: { constexpr int LL = 8; CALL; } break;  \
+    case 16: { constexpr int LL = 16; CALL; } break; \
+    default: { constexpr int LL = 32; CALL; } break; \
+  }
+
+template <typename LaunchFn>
+inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_key, int key, LaunchFn launch,
+                              int max_rounds, int phase) {
+  const int K = h->opt.check_every;
+  const bool use_graph = h->stream != nullptr;
+  if (use_graph && *cache && *cache_key != key) {
+    cudaGraphExecDestroy(*cache);
+    *cache = nullptr;
+  }
+  if (use_graph && !*cache) {
+    *cache_key = key;
+    cudaGraph_t graph;
+    GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < K; ++k) launch();
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "capture FP32 rounds");
+    e = cudaGraphInstantiate(cache, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate FP32 rounds");
+  }
+  const int64_t max_batches = (int64_t)max_rounds / K + 3;
+  int prev_round = 0;
+  for (int64_t bI = 0; bI < max_batches; ++bI) {
+    prof_begin(h);
+    if (use_graph) {
+      GABP_CUDA(cudaGraphLaunch(*cache, h->stream));
+    } else {
+      for (int k = 0; k < K; ++k) launch();
+      GABP_CUDA(cudaGetLastError());
+    }
+    prof_end(h);
+    h->prof.launches += K;
+    gabp_status s = read_ctl(h);
+    if (s != GABP_OK) return s;
+    prof_collect(h, phase, h->ctl_host->round - prev_round);
+    prev_round = h->ctl_host->round;
+    if (h->ctl_host->done) return GABP_OK;
+  }
+  set_last_error("FP32 rounds ended without a decision");
+  return GABP_ERR_CUDA;
+}
+
+
+// shared host helpers (defined in setup.cu / solve64.cu / solve32.cu)
 gabp_status ensure_w64(gabp_handle h);
 void free_w64(gabp_handle h);
 gabp_status ensure_w32(gabp_handle h, int R);
@@ -221,5 +280,9 @@ gabp_status marginals(gabp_handle h, double *Pi);
 gabp_status grad_values(gabp_handle h, const double *lam, const double *x, double *g);
 gabp_status make_gamma(gabp_handle h, double *out);
 gabp_status marginals32(gabp_handle h, double *Pi);
+gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
+void free_wb(gabp_handle h);
+gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
+                            int max_iter, int *iters, double *relres_host);
 
 }  // namespace gabp

@@ -168,6 +168,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   if (h->gH32) cudaGraphExecDestroy(h->gH32);
   free_w64(h);
   free_w32(h);
+  free_wb(h);
   free_graph(h->g);
   cudaFree(h->ctl);
   cudaFreeHost(h->ctl_host);

@@ -454,59 +454,6 @@ static int lanes32(gabp_handle h, bool mean) {
   return L;
 }
 
-#define GABP_DISPATCH_L(L, CALL) \
-  switch (L) {                   \
-    case 1: { constexpr int LL = 1; CALL; } break;  \
-    case 2: { constexpr int LL = 2; CALL; } break;  \
-    case 4: { constexpr int LL = 4; CALL; } break;  \
-    case 8: { constexpr int LL = 8; CALL; } break;  \
-    case 16: { constexpr int LL = 16; CALL; } break; \
-    default: { constexpr int LL = 32; CALL; } break; \
-  }
-
-// Run K-round graphs of one round kernel until the control block says done.
-template <typename LaunchFn>
-static gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_key, int key, LaunchFn launch,
-                              int max_rounds, int phase) {
-  const int K = h->opt.check_every;
-  const bool use_graph = h->stream != nullptr;
-  if (use_graph && *cache && *cache_key != key) {
-    cudaGraphExecDestroy(*cache);
-    *cache = nullptr;
-  }
-  if (use_graph && !*cache) {
-    *cache_key = key;
-    cudaGraph_t graph;
-    GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < K; ++k) launch();
-    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-    if (e != cudaSuccess) return cuda_fail(e, "capture FP32 rounds");
-    e = cudaGraphInstantiate(cache, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "instantiate FP32 rounds");
-  }
-  const int64_t max_batches = (int64_t)max_rounds / K + 3;
-  int prev_round = 0;
-  for (int64_t bI = 0; bI < max_batches; ++bI) {
-    prof_begin(h);
-    if (use_graph) {
-      GABP_CUDA(cudaGraphLaunch(*cache, h->stream));
-    } else {
-      for (int k = 0; k < K; ++k) launch();
-      GABP_CUDA(cudaGetLastError());
-    }
-    prof_end(h);
-    h->prof.launches += K;
-    gabp_status s = read_ctl(h);
-    if (s != GABP_OK) return s;
-    prof_collect(h, phase, h->ctl_host->round - prev_round);
-    prev_round = h->ctl_host->round;
-    if (h->ctl_host->done) return GABP_OK;
-  }
-  set_last_error("FP32 rounds ended without a decision");
-  return GABP_ERR_CUDA;
-}
-
 // Precision phase + coefficient freeze on A (+ Gamma).
 // Autotuner of the sub-warp widths of the FP32 round kernels (see autotune64).
 static gabp_status autotune32(gabp_handle h, bool mean) {
@@ -539,7 +486,7 @@ static gabp_status autotune32(gabp_handle h, bool mean) {
   return GABP_OK;
 }
 
-static gabp_status precision_phase(gabp_handle h, const double *gamma_diag) {
+gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
   Work32 &w = h->w32;
   Graph &g = h->g;
   size_t E = (size_t)(g.E > 0 ? g.E : 1);
@@ -593,7 +540,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   // the precision state is cached per handle when no loading is applied
   if (!w.coef_ready || gamma_diag || !h->opt.reuse_precisions) {
     w.coef_ready = false;
-    if ((s = precision_phase(h, gamma_diag)) != GABP_OK) return s;
+    if ((s = precision_phase32(h, gamma_diag)) != GABP_OK) return s;
     if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
   }
   if ((s = autotune32(h, true)) != GABP_OK) return s;
