@@ -39,6 +39,33 @@ WORKLOAD = (f"random sparse symmetric diagonally dominant A, n=2^20, {PICKS} uni
             f"values U(-1,1), diagonal {DIAG} x row abs-sum, b ~ N(0,1)")
 
 
+def _profiled_traffic(summary, source, scale_to=None):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current source of the kernel (the summary records the source's sha256)."""
+    import hashlib
+
+    ps, src = os.path.join(ROOT, "profiles", summary), os.path.join(ROOT, source)
+    if not (os.path.exists(ps) and os.path.exists(src)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = {}
+    for line in open(ps):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            v = v.strip().split()
+            if v:
+                vals[k.strip(" -*`")] = v[0].strip("`")
+    if vals.get("source_sha256") != sha:
+        return None
+    try:
+        traffic = float(vals["dram_bytes_per_launch"])
+        if scale_to is not None:  # captured on a smaller case: scale by the units processed
+            traffic *= scale_to / float(vals["algorithmic_bytes_captured"])
+        return traffic
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -137,7 +164,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="fp32,fp64,e2e",
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
+    ap.add_argument("--batched-grid", type=int, default=128,
+                    help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
+    ap.add_argument("--legs", default="fp32,fp64,e2e,batched",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
 
@@ -170,8 +201,8 @@ def main():
     b_dev = torch.from_numpy(b).to(dev)
     x_dev = torch.empty_like(b_dev)
 
-    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1)
-    s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1)
+    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1, lanes=args.lanes)
+    s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1, lanes=args.lanes)
 
     def step(s):
         _, st, it, rel = s.solve(b_dev, tol=TOL, max_iter=2000, x=x_dev)
@@ -251,6 +282,43 @@ def main():
         barrier()
         e2e_s = time.perf_counter() - t1
 
+    # ---- batched: 128^3 heterogeneous diffusion grid, 64 right-hand sides in one launch sequence
+    batched = None
+    if "batched" in legs:
+        s32.close()
+        s64.close()
+        mg = synth.grid3d(args.batched_grid, 1.05, 3)
+        Rb = 64
+        Bb = torch.from_numpy(synth.rhs_batch(mg.n, Rb, 3 + rank)).to(dev)
+        sb = gb.Solver.from_csr(mg, profile=1, reuse_precisions=0)
+        Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL)
+        sb.profile(reset=True)
+        barrier()
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eb0.record()
+        Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL, X=Xb)
+        eb1.record()
+        barrier()
+        msb = eb0.elapsed_time(eb1)
+        pb = sb.profile(reset=True)
+        stats_b = sb.stats()
+        Eg, ng = mg.num_edges, mg.n
+        mean_ms = pb["ms"]["mean32"] / max(pb["rounds"]["mean32"], 1)
+        bytes_b = Eg * (8 * Rb + 12) + ng * (16 * Rb + 4)
+        batched = {"workload": f"{args.batched_grid}^3 7-point grid, face coefficients LogNormal(0,1), diagonal 1.05 x "
+                               "row abs-sum, 64 right-hand sides N(0,1)", "n": ng, "edges": Eg, "rhs": Rb, "status": stb,
+                   "ms_per_solve": msb, "inner_rounds": itb, "refine_steps": stats_b["refine_steps"],
+                   "max_relres": float(np.max(relb)),
+                   "rhs_edge_updates_per_s": Eg * Rb * stats_b["rounds"] / (msb / 1e3),
+                   "ms_per_rhs": msb / Rb,
+                   "roofline": {"bound": "hbm", "kernel": "kb_mean", "achieved": bytes_b / (mean_ms / 1e3) / 1e9,
+                                "peak": peak, "unit": "GB/s", "frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak,
+                                "traffic": _profiled_traffic("kb_mean_grid3d_64_64rhs.md",
+                                                             "paper_0811_2518_gb300/csrc/batched.cu",
+                                                             scale_to=bytes_b),
+                                "bytes_per_launch": bytes_b, "launch_ms": mean_ms}}
+        sb.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(m, b, rounds=5)
@@ -266,7 +334,9 @@ def main():
                        "l2": "inputs larger than L2: 268 MB of edge state read and written per round",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": _profiled_traffic(f"{kname}_random_sym_n1048576.md",
+                                                      "paper_0811_2518_gb300/csrc/solve32.cu"),
                          "bytes_per_launch": bytes_launch, "launch_ms": dur_ms},
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
             "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},
@@ -283,6 +353,8 @@ def main():
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if batched is not None:
+            line["batched_grid3d_64rhs"] = batched
         print(json.dumps(line), flush=True)
     s32.close()
     s64.close()
