@@ -86,7 +86,9 @@ typedef struct {
   int reuse_precisions; /* FP32 path: 1 keeps the converged precision messages of A for later
                            solves (they do not depend on b); 0 re-runs the precision phase in every
                            solve.  Default 1 */
-  int reserved[6];
+  int multi_split;      /* gabp_solve_systems: systems with rows + off-diagonal entries >= this go to a
+                           thread-block cluster, smaller ones to one block; 0 = autotune.  Default 0 */
+  int reserved[5];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */
@@ -151,6 +153,25 @@ gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x, double to
 gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
                                double tol, int32_t max_iter, int32_t *iters_out, double *relres_out);
 
+/*
+ * gabp_solve_systems -- solve nsys independent systems in ONE persistent launch.
+ * The handle's A must be block diagonal: system s owns rows and columns
+ * [offsets[s], offsets[s+1]) (host array of nsys+1 ints, offsets[0] = 0,
+ * offsets[nsys] = n, strictly increasing); an entry coupling two systems gives
+ * GABP_ERR_INVALID.  b, x: device arrays of n doubles.  Every system runs its own
+ * FP32 precision phase, FP32 mean rounds and FP64 refinement to
+ * ||b_s - A_s x_s|| <= tol ||b_s|| (the batching direction of the paper's method:
+ * systems share nothing).  Large systems are solved by a thread-block cluster,
+ * small ones by a single thread block (a host scheduler balances the work; the
+ * size threshold between the two is autotuned on the handle's first call).
+ * status_out / iters_out / relres_out: nullable HOST arrays of nsys receiving each
+ * system's status, rounds (precision + inner) and final relative residual.
+ * Returns the worst status.
+ */
+gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offsets, const double *b, double *x,
+                               double tol, int32_t max_iter, int32_t *status_out, int32_t *iters_out,
+                               double *relres_out);
+
 /* Marginal precisions P_i = A_ii + sum_k P_ki of the last solve (Algorithm 1,
  * step 4), device array of n doubles.  Exact (= 1/(A^{-1})_ii) on trees; an
  * approximation on loopy graphs.  GABP_ERR_INVALID before the first solve. */
@@ -170,20 +191,25 @@ gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm);
  * dL/db is lambda itself.  Device arrays. */
 gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val);
 
-/* Rounds (edge-update passes) executed by the last solve, including
- * precision-phase and refinement inner rounds, and the directed-edge count E
- * (off-diagonal nnz).  edge-updates of the solve = rounds * E * nrhs. */
-gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int32_t *refine_steps);
+/* Statistics of the last solve (all outputs nullable): rounds executed
+ * (precision-phase plus inner mean rounds; for gabp_solve_systems the largest
+ * over the systems), the directed-edge count E (off-diagonal nnz), the number
+ * of edge-updates performed (one directed edge's messages recomputed in one
+ * round, summed over rounds, right-hand sides and systems), and refinement steps. */
+gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int64_t *edge_updates,
+                            int32_t *refine_steps);
 
 /* Per-phase device time of the solves since the last reset (options.profile = 1):
  * phase 0 FP64 GaBP rounds, 1 FP32 precision rounds, 2 FP32 mean rounds,
- * 3 FP64 refinement steps (residual + update).  ms: summed CUDA-event time
- * around the phase's launches on the handle's stream (it includes the few
- * rounds launched after a decision, which return at once); rounds: round
- * kernels that did work; launches: every kernel the library launched. */
+ * 3 FP64 refinement steps (residual + update), 4 the persistent multi-system
+ * kernel (always timed).  ms: summed CUDA-event time around the phase's
+ * launches on the handle's stream (it includes the few rounds launched after a
+ * decision, which return at once); rounds: round kernels that did work (phase
+ * 4: the largest per-system round count); launches: every kernel the library
+ * launched. */
 typedef struct {
-  double ms[4];
-  int64_t rounds[4];
+  double ms[5];
+  int64_t rounds[5];
   int64_t launches;
 } gabp_profile;
 gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);

@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -49,13 +49,14 @@ class Options(ctypes.Structure):
         ("lanes", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("reuse_precisions", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("multi_split", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
 class Profile(ctypes.Structure):
     """Mirror of ``gabp_profile``."""
-    _fields_ = [("ms", ctypes.c_double * 4), ("rounds", ctypes.c_int64 * 4), ("launches", ctypes.c_int64)]
+    _fields_ = [("ms", ctypes.c_double * 5), ("rounds", ctypes.c_int64 * 5), ("launches", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -75,7 +76,9 @@ _SIGNATURES = {
     "gabp_get_messages": ([_P, _P, _P], ctypes.c_int),
     "gabp_grad_values": ([_P, _P, _P, _P], ctypes.c_int),
     "gabp_last_stats": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
-                         ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_solve_systems": ([_P, ctypes.c_int32, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P],
+                           ctypes.c_int),
     "gabp_profile_read": ([_P, ctypes.POINTER(Profile), ctypes.c_int], ctypes.c_int),
     "gabp_solve_noalloc": ([ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32,
                             _P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -173,16 +176,23 @@ def gabp_grad_values(h, lam_ptr, x_ptr, g_ptr):
 
 
 def gabp_last_stats(h):
-    r, e, s = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
-    st = lib.gabp_last_stats(h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(s))
-    return st, r.value, e.value, s.value
+    """Returns (status, rounds, num_edges, edge_updates, refine_steps)."""
+    r, e, u, s = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    st = lib.gabp_last_stats(h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(u), ctypes.byref(s))
+    return st, r.value, e.value, u.value, s.value
+
+
+def gabp_solve_systems(h, nsys, offsets_host_ptr, b_ptr, x_ptr, tol, max_iter, status_ptr=None, iters_ptr=None,
+                       relres_ptr=None):
+    return lib.gabp_solve_systems(h, int(nsys), _P(offsets_host_ptr), _P(b_ptr), _P(x_ptr), float(tol),
+                                  int(max_iter), _P(status_ptr), _P(iters_ptr), _P(relres_ptr))
 
 
 def gabp_profile_read(h, reset=False):
     """Returns (status, dict) with per-phase ms / rounds and the launch count."""
     p = Profile()
     st = lib.gabp_profile_read(h, ctypes.byref(p), 1 if reset else 0)
-    names = ("fp64", "prec32", "mean32", "refine64")
+    names = ("fp64", "prec32", "mean32", "refine64", "multi")
     return st, {"ms": dict(zip(names, list(p.ms))), "rounds": dict(zip(names, list(p.rounds))),
                 "launches": p.launches}
 
@@ -328,8 +338,28 @@ class Solver:
         return g
 
     def stats(self):
-        st, rounds, E, steps = gabp_last_stats(self.handle)
-        return {"rounds": rounds, "edges": E, "refine_steps": steps}
+        st, rounds, E, eu, steps = gabp_last_stats(self.handle)
+        return {"rounds": rounds, "edges": E, "edge_updates": eu, "refine_steps": steps}
+
+    def solve_systems(self, b, offsets, tol=1e-10, max_iter=5000, x=None, check=True):
+        """Independent systems of a block-diagonal A (row offsets ``offsets``, host ints) in one
+        persistent launch.  Returns (x, worst status, per-system status, rounds, relres)."""
+        import numpy as np
+        import torch
+
+        b = b.to(self.device, torch.float64).contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        ns = off.size - 1
+        sts = np.zeros(ns, dtype=np.int32)
+        its = np.zeros(ns, dtype=np.int32)
+        rel = np.zeros(ns)
+        st = gabp_solve_systems(self.handle, ns, off.ctypes.data, b.data_ptr(), x.data_ptr(), tol, max_iter,
+                                sts.ctypes.data, its.ctypes.data, rel.ctypes.data)
+        if check and st < 0:
+            raise GaBPError(st, "gabp_solve_systems")
+        return x, st, sts, its, rel
 
     def profile(self, reset=False):
         st, p = gabp_profile_read(self.handle, reset)

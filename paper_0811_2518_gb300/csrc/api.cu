@@ -113,25 +113,44 @@ extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, con
   return grad_values(h, lambda, x, grad_val);
 }
 
-extern "C" gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int32_t *refine_steps) {
+extern "C" gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int64_t *edge_updates,
+                                       int32_t *refine_steps) {
   if (!h) return GABP_ERR_INVALID;
   if (rounds) *rounds = h->stats.rounds;
   if (num_edges) *num_edges = h->g.E;
+  if (edge_updates)
+    *edge_updates = h->stats.edge_updates >= 0 ? h->stats.edge_updates : h->stats.rounds * (int64_t)h->g.E;
   if (refine_steps) *refine_steps = h->stats.refine_steps;
   return GABP_OK;
+}
+
+extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offsets, const double *b,
+                                          double *x, double tol, int32_t max_iter, int32_t *status_out,
+                                          int32_t *iters_out, double *relres_out) {
+  if (!h || !offsets || !b || !x || nsys < 1 || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  if (!is_device_ptr(b) || !is_device_ptr(x)) {
+    set_last_error("gabp_solve_systems: b and x must be device arrays");
+    return GABP_ERR_INVALID;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  gabp_status s = solve_systems(h, nsys, offsets, b, x, tol, max_iter, status_out, iters_out, relres_out);
+  if (cur != h->device) cudaSetDevice(cur);
+  return s;
 }
 
 extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset) {
   if (!h) return GABP_ERR_INVALID;
   if (out) {
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < PH_COUNT; ++j) {
       out->ms[j] = h->prof.ms[j];
       out->rounds[j] = h->prof.rounds[j];
     }
     out->launches = h->prof.launches;
   }
   if (reset) {
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < PH_COUNT; ++j) {
       h->prof.ms[j] = 0.0;
       h->prof.rounds[j] = 0;
     }

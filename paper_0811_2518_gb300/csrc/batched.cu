@@ -419,6 +419,7 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
     const DevCtl c = *h->ctl_host;
     total_inner += c.round;
     h->stats.rounds += c.round;
+    h->stats.edge_updates += (int64_t)c.round * g.E * R;
     if (c.status == GABP_DIVERGED) { diverged = true; break; }
     float *hT = w.NH[c.result_round % 3];
     prof_begin(h);
@@ -460,10 +461,12 @@ gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X,
   gabp_status s = ensure_w32(h, 1);
   if (s != GABP_OK) return s;
   h->stats.rounds = 0;
+  h->stats.edge_updates = 0;
   h->stats.refine_steps = 0;
   if (!h->w32.coef_ready || !h->opt.reuse_precisions) {
     h->w32.coef_ready = false;
     if ((s = precision_phase32(h, nullptr)) != GABP_OK) return s;
+    h->stats.edge_updates += h->stats.rounds * (int64_t)h->g.E;  // precision rounds serve every column
   }
   int worst = GABP_OK, total = 0;
   for (int r0 = 0; r0 < nrhs; r0 += 128) {

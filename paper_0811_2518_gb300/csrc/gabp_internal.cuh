@@ -92,14 +92,16 @@ struct WorkB;  // batched multi-RHS work arrays (batched.cu)
 
 struct Stats {
   int64_t rounds = 0;
+  int64_t edge_updates = -1;  // set by paths whose systems differ in size (else rounds x E x nrhs)
   int refine_steps = 0;
+  int nrhs = 1;
 };
 
 // Phase timing (options.profile): CUDA events around each phase's launches.
-enum { PH_FP64 = 0, PH_PREC32 = 1, PH_MEAN32 = 2, PH_REFINE64 = 3 };
+enum { PH_FP64 = 0, PH_PREC32 = 1, PH_MEAN32 = 2, PH_REFINE64 = 3, PH_MULTI = 4, PH_COUNT = 5 };
 struct Prof {
-  double ms[4] = {0, 0, 0, 0};
-  int64_t rounds[4] = {0, 0, 0, 0};
+  double ms[PH_COUNT] = {0, 0, 0, 0, 0};
+  int64_t rounds[PH_COUNT] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -134,6 +136,7 @@ struct gabp_handle_s {
   double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
   gabp::Prof prof;
   gabp::WorkB *wb = nullptr;
+  long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
 };
 
 namespace gabp {
@@ -282,6 +285,8 @@ gabp_status make_gamma(gabp_handle h, double *out);
 gabp_status marginals32(gabp_handle h, double *Pi);
 gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
 void free_wb(gabp_handle h);
+gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
+                          int max_iter, int *status_host, int *iters_host, double *relres_host);
 gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
                             int max_iter, int *iters, double *relres_host);
 

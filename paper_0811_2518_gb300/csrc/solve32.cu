@@ -536,6 +536,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   Work32 &w = h->w32;
   Graph &g = h->g;
   h->stats.rounds = 0;
+  h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
   // the precision state is cached per handle when no loading is applied
   if (!w.coef_ready || gamma_diag || !h->opt.reuse_precisions) {

@@ -465,6 +465,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   h->w64.result_round = c.result_round;
   h->w64.valid = true;
   h->stats.rounds = c.round;
+  h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
   k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x);
   h->prof.launches += 1;

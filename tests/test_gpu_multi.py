@@ -1,0 +1,96 @@
+"""Many independent systems in one persistent launch (GPU, through the C ABI), against the
+FP64 oracle per system.  Refined tolerance: 1e-10 relative error per system."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0811_2518_gb300 as m
+
+    return m
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _check(gb, mats, split, zero_system=None):
+    big = synth.block_diag(mats)
+    off = big.meta["offsets"]
+    b = synth.rhs(big.n, 21)
+    if zero_system is not None:
+        b[off[zero_system]:off[zero_system + 1]] = 0.0
+    s = gb.Solver.from_csr(big, multi_split=split)
+    x, st, sts, its, rel = s.solve_systems(torch.from_numpy(b).cuda(), off, tol=1e-12)
+    s.close()
+    assert st == gb.GABP_OK and np.all(sts == 0) and np.all(rel <= 1e-12)
+    x = x.cpu().numpy()
+    for k, m in enumerate(mats):
+        xs, bs = x[off[k]:off[k + 1]], b[off[k]:off[k + 1]]
+        if not np.any(bs):
+            assert not np.any(xs)
+            continue
+        ref = oracle.gabp_broadcast(m, bs, max_iter=5000, tol=1e-13)
+        assert _relerr(xs, ref["x"]) <= 1e-10, k
+
+
+@pytest.mark.parametrize("split", [1, 1 << 30, 9000])
+def test_systems_cluster_single_and_mixed(gb, split):
+    """split 1: every system solved by a whole cluster; 2^30: every system by one block;
+    9000: mixed (systems of rows + entries >= 9000 on clusters)."""
+    mats = synth.rgg_batch(12, 1024, 8192, 2.0, 4)
+    _check(gb, mats, split, zero_system=3)
+
+
+def test_systems_autotuned_split(gb):
+    mats = synth.rgg_batch(20, 1024, 16384, 2.0, 5)
+    _check(gb, mats, 0)
+
+
+def test_systems_coupled_rejected(gb):
+    mats = synth.rgg_batch(2, 1024, 2048, 2.0, 6)
+    big = synth.block_diag(mats)
+    off = big.meta["offsets"].copy()
+    off[1] += 1  # the boundary now cuts through the first system's edges
+    s = gb.Solver.from_csr(big)
+    b = torch.zeros(big.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(gb.GaBPError) as ei:
+        s.solve_systems(b, off)
+    s.close()
+    assert ei.value.status == gb.GABP_ERR_INVALID
+
+
+def test_512_power_law_systems(gb):
+    """The benchmark batch: 512 random geometric graphs, sizes ~ n^-2 on [1024, 65536].
+    Every system's residual recomputed on the host meets the tolerance; 8 systems are
+    compared with the oracle."""
+    mats = synth.rgg_batch(512, 1024, 65536, 2.0, 4)
+    big = synth.block_diag(mats)
+    off = big.meta["offsets"]
+    b = synth.rhs(big.n, 4)
+    s = gb.Solver.from_csr(big)
+    x, st, sts, its, rel = s.solve_systems(torch.from_numpy(b).cuda(), off, tol=1e-10)
+    s.close()
+    assert st == gb.GABP_OK and np.all(sts == 0)
+    x = x.cpu().numpy()
+    rows = np.repeat(np.arange(big.n), np.diff(big.rowptr))
+    r = b - np.bincount(rows, big.val * x[big.col], minlength=big.n)
+    for k in range(len(mats)):
+        sl = slice(off[k], off[k + 1])
+        assert np.linalg.norm(r[sl]) <= 1.0001e-10 * np.linalg.norm(b[sl])
+    sizes = np.diff(off)
+    for k in list(np.argsort(sizes)[:4]) + list(np.argsort(sizes)[-4:]):
+        sl = slice(off[k], off[k + 1])
+        ref = oracle.gabp_broadcast(mats[k], b[sl], max_iter=5000, tol=1e-12)
+        assert _relerr(x[sl], ref["x"]) <= 1e-9
