@@ -168,7 +168,7 @@ def main():
                     help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
     ap.add_argument("--batched-grid", type=int, default=128,
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
-    ap.add_argument("--legs", default="fp32,fp64,e2e,batched",
+    ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
 
@@ -319,6 +319,66 @@ def main():
                                 "bytes_per_launch": bytes_b, "launch_ms": mean_ms}}
         sb.close()
 
+    # ---- 512 independent random-geometric-graph systems in one persistent launch
+    multi = None
+    if "multi" in legs:
+        mats = synth.rgg_batch(512, 1024, 65536, 2.0, 4)
+        bigm = synth.block_diag(mats)
+        offm = bigm.meta["offsets"]
+        bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
+        sm = gb.Solver.from_csr(bigm)
+        xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL)  # first call autotunes the split
+        sm.profile(reset=True)
+        barrier()
+        em0, em1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        em0.record()
+        xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL, x=xm)
+        em1.record()
+        barrier()
+        msm = em0.elapsed_time(em1)
+        pm = sm.profile(reset=True)
+        stm_ = sm.stats()
+        multi = {"workload": "512 random geometric graphs, sizes ~ n^-2 on [1024, 65536], radius for degree 6, "
+                             "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
+                 "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
+                 "ms_per_batch": msm, "kernel_ms": pm["ms"]["multi"], "edge_updates": stm_["edge_updates"],
+                 "edge_updates_per_s": stm_["edge_updates"] / (msm / 1e3),
+                 "rounds_per_system": {"min": int(itsm.min()), "median": int(np.median(itsm)), "max": int(itsm.max())},
+                 "max_relres": float(relm.max()), "launches_per_batch": 1}
+        sm.close()
+
+    # ---- differentiable solve: n = 2^22, degree ~6, forward + hand-written backward
+    grad = None
+    if "grad" in legs:
+        from paper_0811_2518_gb300 import autograd as ga
+
+        mc = synth.random_sym(1 << 22, 3, 1.2, 5)
+        rp_t = torch.from_numpy(mc.rowptr).to(dev)
+        cl_t = torch.from_numpy(mc.col).to(dev)
+        xs_t = torch.from_numpy(synth.rhs(mc.n, 105)).to(dev)
+        b_c = synth.rhs(mc.n, 5 + rank)
+
+        def fwd_bwd():
+            vals = torch.from_numpy(mc.val).to(dev).requires_grad_(True)
+            bt = torch.from_numpy(b_c).to(dev).requires_grad_(True)
+            xg = ga.gabp_solve_autograd(rp_t, cl_t, vals, bt, tol=TOL)
+            loss = 0.5 * torch.sum((xg - xs_t) ** 2)
+            loss.backward()
+            return vals.grad, bt.grad
+
+        fwd_bwd()
+        barrier()
+        eg0, eg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eg0.record()
+        fwd_bwd()
+        eg1.record()
+        barrier()
+        grad = {"workload": "random sparse symmetric A, n=2^22, 3 picks per row (degree ~6), U(-1,1), diagonal "
+                            "1.2 x row abs-sum; loss 0.5||x - x*||^2; FP32 messages + FP64 refinement",
+                "n": mc.n, "edges": mc.num_edges, "ms_forward_backward": eg0.elapsed_time(eg1),
+                "includes": "handle creation (validation, reverse index), forward solve, adjoint solve on the "
+                            "same precision state, dL/dA and dL/db"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(m, b, rounds=5)
@@ -355,6 +415,10 @@ def main():
             line["cpu_baseline"] = cpu
         if batched is not None:
             line["batched_grid3d_64rhs"] = batched
+        if multi is not None:
+            line["multi_rgg_512"] = multi
+        if grad is not None:
+            line["autograd_n4194304"] = grad
         print(json.dumps(line), flush=True)
     s32.close()
     s64.close()
