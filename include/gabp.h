@@ -75,7 +75,9 @@ typedef struct {
   int precision;        /* gabp_precision, default GABP_PREC_FP64 */
   int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16 */
   int freeze_precisions;/* reserved for the FP64 path (precisions co-iterate there), default 1 */
-  double inner_tol;     /* FP32 inner-solve relative residual target, default 1e-4 */
+  double inner_tol;     /* loosest target of an FP32 inner solve (relative change of its iterate); each
+                           inner solve aims at min(inner_tol, max(1e-6, 0.1 tol ||b|| / ||r||)),
+                           the reduction still needed.  Default 1e-4 */
   int inner_max_iter;   /* rounds per inner solve, default 400 */
   int max_refine;       /* refinement steps, default 30 */
   int gamma_mode;       /* convergence fix: 0 off, 1 Gamma = gamma * diag(A),
@@ -88,7 +90,9 @@ typedef struct {
                            solve.  Default 1 */
   int multi_split;      /* gabp_solve_systems: systems with rows + off-diagonal entries >= this go to a
                            thread-block cluster, smaller ones to one block; 0 = autotune.  Default 0 */
-  int reserved[5];
+  int prec_stop_log2;   /* FP32 precision phase stops at a max relative change <= 2^-prec_stop_log2 in
+                           two consecutive rounds (10..23).  Default 16 */
+  int reserved[4];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

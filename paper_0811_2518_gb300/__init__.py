@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("reuse_precisions", ctypes.c_int),
         ("multi_split", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("prec_stop_log2", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 

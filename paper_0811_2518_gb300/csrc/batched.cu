@@ -410,7 +410,11 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
   for (int step = 0; step < h->opt.max_refine && !all_done() && total_inner < max_iter; ++step) {
     GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E * RP, h->stream));
     const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
-    kb_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, itol * itol);
+    double worst_ratio = 0.0;  // the column furthest from its target sets the inner tolerance
+    for (int r = 0; r < R; ++r)
+      if (bb[r] > 0.0) worst_ratio = std::max(worst_ratio, rr[r] / bb[r]);
+    const double it_tol = inner_target(itol, tol, 1.0, worst_ratio);
+    kb_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
     h->prof.launches += 1;
     GABP_CUDA(cudaGetLastError());
     s = run_rounds(h, &w.graph, &w.graph_key, RP, [&] { kb_mean<VEC><<<nb_mean, kBlock, shmem, h->stream>>>(a); }, cap,

@@ -13,6 +13,8 @@
 #include <cstdint>
 #include <cstddef>
 #include <string>
+#include <algorithm>
+#include <cmath>
 
 #include "../../include/gabp.h"
 
@@ -213,6 +215,14 @@ inline float time_launches(gabp_handle h, F launch, int rounds) {
 gabp_status tune_ctl(gabp_handle h, const double *b);  // (re)arms ctl_tune for a tuning run (b: any n-vector)
 
 gabp_status read_ctl(gabp_handle h);  // copies ctl -> ctl_host and synchronises
+
+// Tolerance of one FP32 inner solve: only the reduction still needed to reach
+// tol (with a factor 10 of margin), never looser than the option's inner_tol,
+// never tighter than FP32 can deliver (1e-6) unless inner_tol itself asks for it.
+inline double inner_target(double inner_tol, double tol, double bb, double rr) {
+  const double need = rr > 0.0 ? 0.1 * tol * std::sqrt(bb / rr) : inner_tol;
+  return std::min(inner_tol, std::max(1e-6, need));
+}
 
 // Run K-round graphs of one round kernel (CUDA graph of K launches when the
 // stream can be captured) until the control block says done.

@@ -221,9 +221,11 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
       if (bb == 0.0 || rr <= a.tol * a.tol * bb) { status = GABP_OK; break; }
       if (!isfinite(rr)) { status = GABP_DIVERGED; break; }
       if (steps >= a.max_refine || inner_total >= a.max_iter) { status = GABP_NOT_CONVERGED; break; }
-      // inner FP32 mean iteration from zero messages
+      // inner FP32 mean iteration from zero messages, to the reduction still needed
       int Tm = 0;
       const int cap = min(a.inner_max, max(1, a.max_iter - inner_total));
+      const double need = 0.1 * a.tol * sqrt(bb / rr);
+      const double itol = fmin(a.inner_tol, fmax(1e-6, need));
       bool div = false;
       for (int t = 1; t <= cap; ++t) {
         float *Hc = (t & 1) ? a.H1 : a.H0;
@@ -267,7 +269,7 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
         team_reduce<2>(T, v2, md2, o2);
         Tm = t;
         if (!isfinite(o2[0]) || !isfinite(o2[1])) { div = true; break; }
-        if (t >= 2 && o2[0] <= a.inner_tol * a.inner_tol * o2[1]) break;
+        if (t >= 2 && o2[0] <= itol * itol * o2[1]) break;
       }
       inner_total += Tm;
       if (div) { status = GABP_DIVERGED; break; }

@@ -57,8 +57,9 @@ __device__ __forceinline__ float *ring3(float *a, float *b, float *c, int t) {
 
 // ---------------------------------------------------------------------------- precision phase
 // Round t of the precision-only iteration (eq_prec + eq_prec_message, Algorithm 2),
-// recompute form.  The run stops once max |P^(t) - P^(t-1)| / |P^(t)| <= 2^-20
-// (16 ulp of FP32) in two consecutive rounds, on a zero cavity, or at max_iter.
+// recompute form.  The run stops once max |P^(t) - P^(t-1)| / |P^(t)| <= 2^-s
+// (s = options.prec_stop_log2, default 16; kept in ctl->tol2bb)
+// in two consecutive rounds, on a zero cavity, or at max_iter.
 // FP32 rounding keeps some messages moving by a few ulp forever, so an exact
 // stationary point is not waited for: the outer FP64 refinement absorbs what
 // the frozen coefficients are off by.
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
     ctl->round = t;
     ctl->maxrel = tot[1];
-    const bool stat = !(tot[1] > 9.5367431640625e-7);  // 2^-20; NaN counts as not stationary
+    const bool stat = !(tot[1] > ctl->tol2bb);  // 2^-prec_stop_log2; NaN counts as not stationary
     ctl->stable = stat ? ctl->stable + 1 : 0;
     if (ctl->no_stop) {
       // autotuning run: no decision
@@ -505,7 +506,7 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
     if ((st = init()) != GABP_OK) return st;
   }
   const int L = lanes32(h, false);
-  k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, 0.0);
+  k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, std::ldexp(1.0, -h->opt.prec_stop_log2));
   h->prof.launches += 2;
   GABP_CUDA(cudaGetLastError());
   Args32 a = args32(h);
@@ -577,7 +578,8 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     // inner FP32 GaBP on A d = r (messages from zero, Algorithm 1 step 1)
     GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
     const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
-    k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, itol * itol);
+    const double it_tol = inner_target(itol, tol, bb, rr);
+    k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
     h->prof.launches += 1;
     GABP_CUDA(cudaGetLastError());
     GABP_DISPATCH_L(L, s = run_rounds(h, &h->gH32, &h->gH32_L, L, [&] {
