@@ -92,7 +92,9 @@ typedef struct {
                            thread-block cluster, smaller ones to one block; 0 = autotune.  Default 0 */
   int prec_stop_log2;   /* FP32 precision phase stops at a max relative change <= 2^-prec_stop_log2 in
                            two consecutive rounds (10..23).  Default 16 */
-  int reserved[4];
+  int multi_mode;       /* gabp_solve_systems kernel: 0 autotune, 1 grid-persistent (every round sweeps
+                           all running systems), 2 cluster / single-block teams.  Default 0 */
+  int reserved[3];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */
@@ -243,6 +245,13 @@ gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
 gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *b, double *x, double tol,
                                int32_t max_iter, void *stream, int32_t *iters_out, double *relres_out);
+
+/* The autotuner's choices for this handle (0 where not tuned yet; all outputs
+ * nullable): the FP64 round's lanes per row; the FP32 precision and mean
+ * rounds' shapes, packed as lanes | unroll << 8; the multi-system size split
+ * and kernel (1 grid-persistent, 2 teams). */
+gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int32_t *prec32_shape, int32_t *mean32_shape,
+                              int64_t *multi_split, int32_t *multi_mode);
 
 /* Free everything the handle owns.  NULL is accepted. */
 gabp_status gabp_destroy(gabp_handle h);

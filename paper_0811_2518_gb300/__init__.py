@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -51,7 +51,8 @@ class Options(ctypes.Structure):
         ("reuse_precisions", ctypes.c_int),
         ("multi_split", ctypes.c_int),
         ("prec_stop_log2", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("multi_mode", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -83,6 +84,9 @@ _SIGNATURES = {
     "gabp_profile_read": ([_P, ctypes.POINTER(Profile), ctypes.c_int], ctypes.c_int),
     "gabp_solve_noalloc": ([ctypes.c_int32, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32,
                             _P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gabp_tuned_shapes": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -205,6 +209,16 @@ def gabp_solve_noalloc(n, nnz, rowptr_ptr, col_ptr, val_ptr, b_ptr, x_ptr, tol, 
     st = lib.gabp_solve_noalloc(int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr), _P(b_ptr), _P(x_ptr),
                                 float(tol), int(max_iter), _P(stream_ptr), ctypes.byref(it), ctypes.byref(rel))
     return st, it.value, rel.value
+
+
+def gabp_tuned_shapes(h):
+    """Returns dict of the autotuner's choices: fp64 lanes, (lanes, unroll) of the FP32 kernels, multi-system
+    split and kernel (1 grid-persistent, 2 teams)."""
+    a, b, c, d, e = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    lib.gabp_tuned_shapes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d), ctypes.byref(e))
+    sh = lambda v: (v & 0xFF, v >> 8)
+    return {"fp64_lanes": a.value, "prec32": sh(b.value), "mean32": sh(c.value), "multi_split": d.value,
+            "multi_mode": e.value}
 
 
 def gabp_destroy(h):
@@ -361,6 +375,9 @@ class Solver:
         if check and st < 0:
             raise GaBPError(st, "gabp_solve_systems")
         return x, st, sts, its, rel
+
+    def tuned(self):
+        return gabp_tuned_shapes(self.handle)
 
     def profile(self, reset=False):
         st, p = gabp_profile_read(self.handle, reset)

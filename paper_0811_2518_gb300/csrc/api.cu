@@ -158,3 +158,14 @@ extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int r
   }
   return GABP_OK;
 }
+
+extern "C" gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int32_t *prec32_shape,
+                                         int32_t *mean32_shape, int64_t *multi_split, int32_t *multi_mode) {
+  if (!h) return GABP_ERR_INVALID;
+  if (fp64_lanes) *fp64_lanes = h->tuned_L64;
+  if (prec32_shape) *prec32_shape = h->tuned_Lp32;
+  if (mean32_shape) *mean32_shape = h->tuned_Lm32;
+  if (multi_split) *multi_split = h->multi_big;
+  if (multi_mode) *multi_mode = h->multi_mode;
+  return GABP_OK;
+}

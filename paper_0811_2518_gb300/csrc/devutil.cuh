@@ -64,6 +64,48 @@ __device__ __forceinline__ T sub_sum(T v) {
   return v;
 }
 
+// Block-wide sum of NV doubles over NT threads.  Result valid in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_nt(double (&v)[NV]) {
+  __shared__ double sh[NV][NT / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = warp_sum(v[j]);
+    if (l == 0) sh[j][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = l < NT / 32 ? sh[j][l] : 0.0;
+      v[j] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Block-wide max of NV doubles over NT threads.  Result valid in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_max_nt(double (&v)[NV]) {
+  __shared__ double sh[NV][NT / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double s = warp_max(v[j]);
+    if (l == 0) sh[j][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = l < NT / 32 ? sh[j][l] : -1.0;
+      v[j] = warp_max(s);
+    }
+  }
+  __syncthreads();
+}
+
 // Block-wide sum of NV doubles (kBlock threads).  Result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {

@@ -139,6 +139,8 @@ struct gabp_handle_s {
   gabp::Prof prof;
   gabp::WorkB *wb = nullptr;
   long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
+  int multi_nt = 0;                 // autotuned block size of the multi-system kernel
+  int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
 };
 
 namespace gabp {
@@ -297,6 +299,9 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
 void free_wb(gabp_handle h);
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host);
+gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
+                               int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
+                               float *ms_out);
 gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
                             int max_iter, int *iters, double *relres_host);
 

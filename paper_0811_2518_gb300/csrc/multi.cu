@@ -32,7 +32,7 @@ namespace gabp {
 namespace {
 
 constexpr int kCS = 8;         // CTAs per cluster (portable maximum)
-constexpr int kMU = 4;         // slots per thread whose loads are issued together
+constexpr int kMU = 2;         // slots per thread whose loads are issued together
 constexpr int kPrecCap = 300;  // precision-phase round cap per system
 
 struct MultiArgs {
@@ -80,14 +80,14 @@ __device__ __forceinline__ void team_sync(const Team &T) {
 
 // Sum (mode 0) or max (mode 1) of NV per-thread doubles over the team; every
 // thread of every CTA of the team receives the same totals (fixed order).
-template <int NV>
+template <int NV, int NT>
 __device__ void team_reduce(const Team &T, double (&v)[NV], const int (&mode)[NV], double (&out)[NV]) {
   __shared__ double part[NV];
   double s[NV], m[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) { s[j] = mode[j] ? 0.0 : v[j]; m[j] = mode[j] ? v[j] : -1.0; }
-  block_sum<NV>(s);
-  block_max<NV>(m);
+  block_sum_nt<NV, NT>(s);
+  block_max_nt<NV, NT>(m);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) part[j] = mode[j] ? m[j] : s[j];
@@ -114,7 +114,8 @@ __device__ void team_reduce(const Team &T, double (&v)[NV], const int (&mode)[NV
   cl.sync();  // every CTA has read the partials before they are overwritten
 }
 
-// One system, solved by team T.  Thread t of rank r handles rows lo + t, lo + t + 256, ...
+// One system, solved by team T.  Thread t of rank r handles rows lo + t, lo + t + NT, ...
+template <int NT>
 __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
   const int r0 = a.offsets[s], r1 = a.offsets[s + 1];
   const int nrow = r1 - r0;
@@ -177,10 +178,10 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
     }
     double v[2] = {(double)bad, (double)rel}, o[2];
     const int md[2] = {0, 1};
-    team_reduce<2>(T, v, md, o);  // also orders this round's writes before the next round's reads
+    team_reduce<2, NT>(T, v, md, o);  // also orders this round's writes before the next round's reads
     Tp = t;
     if (o[0] > 0.0) { status = GABP_BREAKDOWN; break; }
-    stable = !(o[1] > 9.5367431640625e-7) ? stable + 1 : 0;
+    stable = (o[1] <= 9.5367431640625e-7) ? stable + 1 : 0;  // a NaN is not stationary
     if (stable >= 2) break;
   }
   if (status == GABP_OK) {
@@ -215,7 +216,7 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
       }
       double v[1] = {acc_rr}, o[1];
       const int md[1] = {0};
-      team_reduce<1>(T, v, md, o);
+      team_reduce<1, NT>(T, v, md, o);
       rr = o[0];
       if (it == 0) bb = rr;
       if (bb == 0.0 || rr <= a.tol * a.tol * bb) { status = GABP_OK; break; }
@@ -266,7 +267,7 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
         }
         double v2[2] = {(double)dxx, (double)xx}, o2[2];
         const int md2[2] = {0, 0};
-        team_reduce<2>(T, v2, md2, o2);
+        team_reduce<2, NT>(T, v2, md2, o2);
         Tm = t;
         if (!isfinite(o2[0]) || !isfinite(o2[1])) { div = true; break; }
         if (t >= 2 && o2[0] <= itol * itol * o2[1]) break;
@@ -291,16 +292,20 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
   team_sync(T);
 }
 
-__global__ void __launch_bounds__(kBlock) km_solve(MultiArgs a) {
+// Register cap: 64 per thread (65536 / (NT * blocks)), so at least 1024 threads
+// per SM are resident -- the kernel is latency bound and needs warps in flight.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) km_solve(MultiArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank();
   const int cid = blockIdx.x / kCS;
   // 1) systems solved by the whole cluster, together
   Team tc{true, crank, kCS};
-  for (int q = 0; q < a.cl_count[cid]; ++q) solve_system(a, a.cl_jobs[a.cl_start[cid] + q], tc);
+  for (int q = 0; q < a.cl_count[cid]; ++q) solve_system<NT>(a, a.cl_jobs[a.cl_start[cid] + q], tc);
   // 2) systems solved by this CTA alone
   Team ts{false, 0, 1};
-  for (int q = 0; q < a.cta_count[blockIdx.x]; ++q) solve_system(a, a.cta_jobs[a.cta_start[blockIdx.x] + q], ts);
+  for (int q = 0; q < a.cta_count[blockIdx.x]; ++q)
+    solve_system<NT>(a, a.cta_jobs[a.cta_start[blockIdx.x] + q], ts);
 }
 
 __global__ void km_diag32(int n, const double *__restrict__ ad, float *__restrict__ d32) {
@@ -371,6 +376,10 @@ static MultiSched schedule(const std::vector<int> &rows, const std::vector<int> 
   return S;
 }
 
+static gabp_status collect_systems(gabp_handle h, int nsys, const std::vector<int> &slots, const int *d_res,
+                                   const double *d_rel, float ms, int *status_host, int *iters_host,
+                                   double *relres_host);
+
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host) {
   Graph &g = h->g;
@@ -416,25 +425,32 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
   km_diag32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad, g.ad32);
   GABP_CUDA(cudaGetLastError());
 
-  // one wave of clusters
-  cudaLaunchConfig_t cfg = {};
+  // launch configuration of one wave of clusters for a block size NT
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kCS;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = h->stream;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3(kCS);
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, km_solve, &cfg) != cudaSuccess || nclusters < 1) {
-    cudaGetLastError();
-    nclusters = std::max(1, h->num_sms / kCS);
-  }
-  cfg.gridDim = dim3(nclusters * kCS);
+  auto config = [&](int NT, int *nclusters) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kCS);
+    int nc = 0;
+    cudaError_t e = NT == 1024 ? cudaOccupancyMaxActiveClusters(&nc, km_solve<1024>, &cfg)
+                  : NT == 512  ? cudaOccupancyMaxActiveClusters(&nc, km_solve<512>, &cfg)
+                               : cudaOccupancyMaxActiveClusters(&nc, km_solve<256>, &cfg);
+    if (e != cudaSuccess || nc < 1) {
+      cudaGetLastError();
+      nc = std::max(1, h->num_sms / kCS);
+    }
+    cfg.gridDim = dim3(nc * kCS);
+    *nclusters = nc;
+    return cfg;
+  };
 
   MultiArgs a;
   a.offsets = d_off;
@@ -448,8 +464,10 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
   a.tol = tol; a.inner_tol = h->opt.inner_tol; a.inner_max = h->opt.inner_max_iter;
   a.max_refine = h->opt.max_refine; a.max_iter = max_iter;
 
-  // one run of the persistent kernel with a given cluster / single-CTA split
-  auto run = [&](long long big, float *ms) -> gabp_status {
+  // one run of the persistent kernel with a given block size and cluster / single-CTA split
+  auto run = [&](int NT, long long big, float *ms) -> gabp_status {
+    int nclusters = 1;
+    cudaLaunchConfig_t cfg = config(NT, &nclusters);
     MultiSched S = schedule(rows, slots, nclusters, big);
     std::vector<int> packed;
     auto put = [&](const std::vector<int> &v) {
@@ -469,7 +487,9 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
     GABP_CUDA(cudaEventCreate(&e0));
     GABP_CUDA(cudaEventCreate(&e1));
     cudaEventRecord(e0, h->stream);
-    cudaError_t le = cudaLaunchKernelEx(&cfg, km_solve, a);
+    cudaError_t le = NT == 1024 ? cudaLaunchKernelEx(&cfg, km_solve<1024>, a)
+                   : NT == 512  ? cudaLaunchKernelEx(&cfg, km_solve<512>, a)
+                                : cudaLaunchKernelEx(&cfg, km_solve<256>, a);
     cudaEventRecord(e1, h->stream);
     h->prof.launches += 1;
     if (le == cudaSuccess) le = cudaEventSynchronize(e1);
@@ -486,21 +506,57 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
     ~SchedFree() { if (*p) cudaFree(*p); }
   } sf{&d_sched};
   float ms = 0.f;
-  if (h->opt.multi_split > 0) h->multi_big = h->opt.multi_split;
-  if (!h->multi_big) {
-    // autotune the size above which a system gets a whole cluster: time the
-    // candidates once (each run is a complete solve), keep the fastest
-    const long long cands[4] = {1LL << 40, 60000, 20000, 6000};
-    float best = 1e30f;
-    long long bestc = cands[0];
-    for (long long c : cands) {
-      if ((st = run(c, &ms)) != GABP_OK) return st;
-      if (ms < best) { best = ms; bestc = c; }
-    }
-    h->multi_big = bestc;
+  auto finish = [&](float t) -> gabp_status {
+    return collect_systems(h, nsys, slots, d_res, d_rel, t, status_host, iters_host, relres_host);
+  };
+  auto run_grid = [&](float *t) {
+    return solve_systems_grid(h, nsys, d_off, b, x, tol, max_iter, d_res, d_res + nsys, d_res + 2 * nsys, d_rel, t);
+  };
+  // kernel choice: the options may force the grid-persistent kernel (mode 1) or
+  // teams (mode 2, or any fixed split); otherwise the first call on a handle
+  // times both and later calls reuse the faster one
+  const int mode = h->opt.multi_split > 0 ? 2 : h->opt.multi_mode ? h->opt.multi_mode : h->multi_mode;
+  if (mode == 1) {
+    if ((st = run_grid(&ms)) != GABP_OK) return st;
+    return finish(ms);
   }
-  if ((st = run(h->multi_big, &ms)) != GABP_OK) return st;
-  if (h->opt.multi_split > 0) h->multi_big = 0;  // a fixed split does not replace the tuned one
+  int NT = h->multi_nt ? h->multi_nt : 512;
+  if (h->opt.multi_split > 0 || (mode == 2 && h->multi_big)) {
+    if ((st = run(NT, h->opt.multi_split > 0 ? h->opt.multi_split : h->multi_big, &ms)) != GABP_OK) return st;
+    return finish(ms);
+  }
+  float grid_ms = 1e30f;
+  if (mode == 0 && (st = run_grid(&grid_ms)) != GABP_OK) return st;
+  // autotune block size, then the size above which a system gets a whole
+  // cluster: each candidate is one complete run; the fastest is kept
+  float best = 1e30f;
+  const int nts[3] = {256, 512, 1024};
+  for (int c : nts) {
+    if ((st = run(c, 20000, &ms)) != GABP_OK) return st;
+    if (ms < best) { best = ms; NT = c; }
+  }
+  const long long cands[3] = {1LL << 40, 60000, 6000};
+  long long split = 20000;
+  for (long long c : cands) {
+    if ((st = run(NT, c, &ms)) != GABP_OK) return st;
+    if (ms < best) { best = ms; split = c; }
+  }
+  h->multi_big = split;
+  h->multi_nt = NT;
+  if (best <= grid_ms) {
+    if (mode == 0) h->multi_mode = 2;
+    if ((st = run(NT, split, &ms)) != GABP_OK) return st;
+  } else {
+    h->multi_mode = 1;
+    if ((st = run_grid(&ms)) != GABP_OK) return st;
+  }
+  return finish(ms);
+}
+
+// per-system results of the last multi-system run (device arrays) back to the caller
+static gabp_status collect_systems(gabp_handle h, int nsys, const std::vector<int> &slots, const int *d_res,
+                                   const double *d_rel, float ms, int *status_host, int *iters_host,
+                                   double *relres_host) {
   h->prof.ms[PH_MULTI] += ms;
   std::vector<int> res(3 * nsys);
   std::vector<double> rel(nsys);

@@ -268,6 +268,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->reuse_precisions = 1;
   o->multi_split = 0;
   o->prec_stop_log2 = 16;
+  o->multi_mode = 0;
   return GABP_OK;
 }
 
@@ -279,7 +280,8 @@ static gabp_status check_options(const gabp_options *o) {
   if (o->gamma_mode < 0 || o->gamma_mode > 2 || !(o->gamma >= 0.0)) return GABP_ERR_INVALID;
   if (o->lanes != 0 && (o->lanes < 1 || o->lanes > 32 || (o->lanes & (o->lanes - 1)))) return GABP_ERR_INVALID;
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
-      o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23)
+      o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
+      o->multi_mode > 2)
     return GABP_ERR_INVALID;
   return GABP_OK;
 }

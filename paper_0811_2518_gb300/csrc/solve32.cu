@@ -27,11 +27,36 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace gabp {
 
 constexpr int kPrecMaxRounds = 300;  // cap of the FP32 precision phase
-constexpr int kUnroll32 = 4;         // slots per lane whose loads are issued together
+constexpr int kUnroll32 = 4;         // default slots per lane whose loads are issued together
+
+// Round-kernel shapes the autotuner chooses from: (lanes per row L, slots per
+// lane whose loads are issued together U), packed as L | U << 8.
+constexpr int shape_code(int L, int U) { return L | (U << 8); }
+constexpr int kShapes[] = {shape_code(1, 4), shape_code(2, 4), shape_code(4, 4), shape_code(8, 4),
+                           shape_code(1, 8), shape_code(2, 8), shape_code(4, 8),
+                           shape_code(2, 2), shape_code(4, 2), shape_code(8, 2)};
+template <int V> using IC = std::integral_constant<int, V>;
+// f(IC<L>, IC<U>) for a shape code (unknown codes map to (4, 4)).
+template <typename F>
+void with_shape(int code, F &&f) {
+  switch (code) {
+    case shape_code(1, 4): f(IC<1>{}, IC<4>{}); break;
+    case shape_code(2, 4): f(IC<2>{}, IC<4>{}); break;
+    case shape_code(8, 4): f(IC<8>{}, IC<4>{}); break;
+    case shape_code(1, 8): f(IC<1>{}, IC<8>{}); break;
+    case shape_code(2, 8): f(IC<2>{}, IC<8>{}); break;
+    case shape_code(4, 8): f(IC<4>{}, IC<8>{}); break;
+    case shape_code(2, 2): f(IC<2>{}, IC<2>{}); break;
+    case shape_code(4, 2): f(IC<4>{}, IC<2>{}); break;
+    case shape_code(8, 2): f(IC<8>{}, IC<2>{}); break;
+    default: f(IC<4>{}, IC<4>{}); break;
+  }
+}
 
 struct Args32 {
   int n;
@@ -63,7 +88,7 @@ __device__ __forceinline__ float *ring3(float *a, float *b, float *c, int t) {
 // FP32 rounding keeps some messages moving by a few ulp forever, so an exact
 // stationary point is not waited for: the outer FP64 refinement absorbs what
 // the frozen coefficients are off by.
-template <int L>
+template <int L, int U>
 __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -74,7 +99,6 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   const float *__restrict__ Pm2 = ring3(a.NP0, a.NP1, a.NP2, t + 1);
   float *__restrict__ Pt = ring3(a.NP0, a.NP1, a.NP2, t);
   constexpr int RPW = 32 / L;
-  constexpr int U = kUnroll32;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
@@ -134,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
     ctl->round = t;
     ctl->maxrel = tot[1];
-    const bool stat = !(tot[1] > ctl->tol2bb);  // 2^-prec_stop_log2; NaN counts as not stationary
+    const bool stat = tot[1] <= ctl->tol2bb;  // 2^-prec_stop_log2; a NaN is not stationary
     ctl->stable = stat ? ctl->stable + 1 : 0;
     if (ctl->no_stop) {
       // autotuning run: no decision
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T) {
 // Round t of the frozen-precision mean iteration (recompute form).  The inner
 // solve stops when ||x^(t) - x^(t-1)|| <= inner_tol ||x^(t)|| (node-local
 // quantities, no extra edge traffic) or at max_iter.
-template <int L>
+template <int L, int U>
 __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -192,7 +216,6 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   const float *__restrict__ Hm2 = ring3(a.NH0, a.NH1, a.NH2, t + 1);
   float *__restrict__ Ht = ring3(a.NH0, a.NH1, a.NH2, t);
   constexpr int RPW = 32 / L;
-  constexpr int U = kUnroll32;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
@@ -442,21 +465,21 @@ static Args32 args32(gabp_handle h) {
   return a;
 }
 
-static int lanes32(gabp_handle h, bool mean) {
-  if (h->opt.lanes) return h->opt.lanes;
+// Shape (lanes per row, unroll) of an FP32 round kernel: the option if set, else
+// the autotuned one, else a heuristic (one unrolled pass of 4 slots per lane
+// covers a row of average degree).
+static int shape32(gabp_handle h, bool mean) {
+  if (h->opt.lanes) return shape_code(h->opt.lanes, kUnroll32);
   const int tuned = mean ? h->tuned_Lm32 : h->tuned_Lp32;
   if (tuned) return tuned;
-  // One unrolled pass (kUnroll32 slots per lane) should cover a row of average
-  // degree: the widest sub-warp with L * kUnroll32 <= degree (degree 16: 4 lanes;
-  // degree 6: 1 lane -- the measured optimum on both workloads).
   double d = h->g.avg_deg;
   int L = 1;
-  while (L < 32 && (2 * L) * kUnroll32 <= d + 0.5) L *= 2;
-  return L;
+  while (L < 8 && (2 * L) * kUnroll32 <= d + 0.5) L *= 2;
+  return shape_code(L, kUnroll32);
 }
 
-// Precision phase + coefficient freeze on A (+ Gamma).
-// Autotuner of the sub-warp widths of the FP32 round kernels (see autotune64).
+// Autotuner of the FP32 round kernels' shapes (see autotune64): a few rounds of
+// every candidate (lanes, unroll) under a scratch control block, fastest kept.
 static gabp_status autotune32(gabp_handle h, bool mean) {
   if (h->opt.lanes || (mean ? h->tuned_Lm32 : h->tuned_Lp32)) return GABP_OK;
   Graph &g = h->g;
@@ -464,26 +487,29 @@ static gabp_status autotune32(gabp_handle h, bool mean) {
   if (s0 != GABP_OK) return s0;
   Args32 a = args32(h);
   a.ctl = h->ctl_tune;
-  const int cands[4] = {1, 2, 4, 8};
   float best = 1e30f;
-  int bestL = 1;
+  int bestS = kShapes[0];
   gabp_status s;
-  for (int L : cands) {
+  for (int sc : kShapes) {
     if ((s = tune_ctl(h, nullptr)) != GABP_OK) return s;
     float ms = 1e30f;
-    if (mean) {
-      GABP_DISPATCH_L(L, ms = time_launches(h, [&] {
-        k32_mean<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL>)), kBlock, 0, h->stream>>>(a);
-      }, 3));
-    } else {
-      GABP_DISPATCH_L(L, ms = time_launches(h, [&] {
-        k32_prec<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL>)), kBlock, 0, h->stream>>>(a);
-      }, 3));
-    }
-    if (ms < best) { best = ms; bestL = L; }
+    with_shape(sc, [&](auto Lc, auto Uc) {
+      constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+      if (mean)
+        ms = time_launches(h, [&] {
+          k32_mean<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>)), kBlock, 0,
+                             h->stream>>>(a);
+        }, 3);
+      else
+        ms = time_launches(h, [&] {
+          k32_prec<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL, UU>)), kBlock, 0,
+                             h->stream>>>(a);
+        }, 3);
+    });
+    if (ms < best) { best = ms; bestS = sc; }
   }
   GABP_CUDA(cudaGetLastError());
-  (mean ? h->tuned_Lm32 : h->tuned_Lp32) = bestL;
+  (mean ? h->tuned_Lm32 : h->tuned_Lp32) = bestS;
   return GABP_OK;
 }
 
@@ -505,22 +531,26 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
     if ((st = autotune32(h, false)) != GABP_OK) return st;
     if ((st = init()) != GABP_OK) return st;
   }
-  const int L = lanes32(h, false);
+  const int SH = shape32(h, false);
   k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, std::ldexp(1.0, -h->opt.prec_stop_log2));
   h->prof.launches += 2;
   GABP_CUDA(cudaGetLastError());
   Args32 a = args32(h);
   gabp_status s;
-  GABP_DISPATCH_L(L, s = run_rounds(h, &h->gP32, &h->gP32_L, L, [&] {
-    const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL>));
-    k32_prec<LL><<<nb, kBlock, 0, h->stream>>>(a);
-  }, kPrecMaxRounds, PH_PREC32));
+  with_shape(SH, [&](auto Lc, auto Uc) {
+    constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+    s = run_rounds(h, &h->gP32, &h->gP32_L, SH, [&] {
+      const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL, UU>));
+      k32_prec<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
+    }, kPrecMaxRounds, PH_PREC32);
+  });
   if (s != GABP_OK) return s;
   const DevCtl c = *h->ctl_host;
   h->stats.rounds += c.round;
   if (c.status == GABP_BREAKDOWN || c.status == GABP_DIVERGED) return (gabp_status)c.status;
-  GABP_DISPATCH_L(L, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)), kBlock, 0,
-                                     h->stream>>>(a, c.result_round)));
+  const int Lc = SH & 0xff;
+  GABP_DISPATCH_L(Lc, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)), kBlock, 0,
+                                      h->stream>>>(a, c.result_round)));
   h->prof.launches += 1;
   GABP_CUDA(cudaGetLastError());
   w.prec_round = c.result_round;
@@ -546,7 +576,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
   }
   if ((s = autotune32(h, true)) != GABP_OK) return s;
-  const int L = lanes32(h, true);
+  const int SH = shape32(h, true);
   // FP64 residual: narrow sub-warps (its per-row epilogue is FP64)
   const int LR = h->opt.lanes ? h->opt.lanes : (g.avg_deg >= 12.0 ? 2 : 1);
   int nbr = 1;
@@ -582,10 +612,13 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
     h->prof.launches += 1;
     GABP_CUDA(cudaGetLastError());
-    GABP_DISPATCH_L(L, s = run_rounds(h, &h->gH32, &h->gH32_L, L, [&] {
-      const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL>));
-      k32_mean<LL><<<nb, kBlock, 0, h->stream>>>(a);
-    }, cap, PH_MEAN32));
+    with_shape(SH, [&](auto Lc, auto Uc) {
+      constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+      s = run_rounds(h, &h->gH32, &h->gH32_L, SH, [&] {
+        const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
+        k32_mean<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
+      }, cap, PH_MEAN32);
+    });
     if (s != GABP_OK) return s;
     const DevCtl c = *h->ctl_host;
     total_inner += c.round;

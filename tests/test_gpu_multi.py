@@ -25,15 +25,20 @@ def _relerr(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def _check(gb, mats, split, zero_system=None):
+def _check(gb, mats, split, zero_system=None, mode=0):
     big = synth.block_diag(mats)
     off = big.meta["offsets"]
     b = synth.rhs(big.n, 21)
     if zero_system is not None:
         b[off[zero_system]:off[zero_system + 1]] = 0.0
-    s = gb.Solver.from_csr(big, multi_split=split)
+    s = gb.Solver.from_csr(big, multi_split=split, multi_mode=mode)
     x, st, sts, its, rel = s.solve_systems(torch.from_numpy(b).cuda(), off, tol=1e-12)
+    tuned = s.tuned()
     s.close()
+    if mode or split:
+        assert tuned["multi_mode"] == 0  # a forced kernel is not recorded as a tuning choice
+    else:
+        assert tuned["multi_mode"] in (1, 2)
     assert st == gb.GABP_OK and np.all(sts == 0) and np.all(rel <= 1e-12)
     x = x.cpu().numpy()
     for k, m in enumerate(mats):
@@ -56,6 +61,35 @@ def test_systems_cluster_single_and_mixed(gb, split):
 def test_systems_autotuned_split(gb):
     mats = synth.rgg_batch(20, 1024, 16384, 2.0, 5)
     _check(gb, mats, 0)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_systems_forced_kernel(gb, mode):
+    """mode 1: the grid-persistent kernel (one global round sweeps the rows of every running
+    system); mode 2: cluster / single-block teams with an autotuned split."""
+    mats = synth.rgg_batch(16, 1024, 16384, 2.0, 7)
+    _check(gb, mats, 0, zero_system=5, mode=mode)
+
+
+def test_systems_grid_breakdown_isolated(gb):
+    """One system whose precision recursion breaks down (a zero cavity precision) stops with
+    BREAKDOWN in the grid-persistent kernel while the others still converge."""
+    good = synth.rgg_batch(3, 1024, 2048, 2.0, 8)
+    star = synth.from_dense(np.array([[2.0, 1, 0, 0], [1, 3, 1, 1], [0, 1, 1, 0], [0, 1, 0, 0.5]]))
+    mats = [good[0], star, good[1], good[2]]
+    big = synth.block_diag(mats)
+    off = big.meta["offsets"]
+    b = synth.rhs(big.n, 3)
+    s = gb.Solver.from_csr(big, multi_mode=1)
+    x, st, sts, its, rel = s.solve_systems(torch.from_numpy(b).cuda(), off, tol=1e-12)
+    s.close()
+    assert st == gb.GABP_BREAKDOWN
+    assert sts[1] == gb.GABP_BREAKDOWN and sts[0] == sts[2] == sts[3] == gb.GABP_OK
+    x = x.cpu().numpy()
+    for k in (0, 2, 3):
+        sl = slice(off[k], off[k + 1])
+        ref = oracle.gabp_broadcast(mats[k], b[sl], max_iter=5000, tol=1e-13)
+        assert _relerr(x[sl], ref["x"]) <= 1e-10
 
 
 def test_systems_coupled_rejected(gb):
