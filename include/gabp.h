@@ -248,8 +248,9 @@ gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, co
 
 /* The autotuner's choices for this handle (0 where not tuned yet; all outputs
  * nullable): the FP64 round's lanes per row; the FP32 precision and mean
- * rounds' shapes, packed as lanes | unroll << 8; the multi-system size split
- * and kernel (1 grid-persistent, 2 teams). */
+ * rounds' shapes, packed as lanes | unroll << 8; the multi-system size split;
+ * the multi-system kernel (1 grid-persistent, 2 teams) | the grid-persistent
+ * kernel's shape << 8. */
 gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int32_t *prec32_shape, int32_t *mean32_shape,
                               int64_t *multi_split, int32_t *multi_mode);
 

@@ -218,7 +218,7 @@ def gabp_tuned_shapes(h):
     lib.gabp_tuned_shapes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d), ctypes.byref(e))
     sh = lambda v: (v & 0xFF, v >> 8)
     return {"fp64_lanes": a.value, "prec32": sh(b.value), "mean32": sh(c.value), "multi_split": d.value,
-            "multi_mode": e.value}
+            "multi_mode": e.value & 0xFF, "multi_grid": sh(e.value >> 8)}
 
 
 def gabp_destroy(h):

@@ -166,6 +166,6 @@ extern "C" gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int
   if (prec32_shape) *prec32_shape = h->tuned_Lp32;
   if (mean32_shape) *mean32_shape = h->tuned_Lm32;
   if (multi_split) *multi_split = h->multi_big;
-  if (multi_mode) *multi_mode = h->multi_mode;
+  if (multi_mode) *multi_mode = h->multi_mode | (h->multi_grid_shape << 8);
   return GABP_OK;
 }

@@ -48,10 +48,24 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// max that keeps a NaN from either side (fmax drops it): a NaN change or
+// residual must never read as "small".
+template <typename T>
+__device__ __forceinline__ T nan_max(T a, T b) {
+  return (a > b || a != a) ? a : b;
+}
+
+// |now - prev| / |now| with 0 for an unchanged value (an explicitly stored zero
+// coupling keeps a zero message: 0/0 must not read as a NaN change).
+__device__ __forceinline__ float rel_change(float now, float prev) {
+  const float d = fabsf(now - prev);
+  return d == 0.f ? 0.f : d / fabsf(now);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -174,7 +188,7 @@ __device__ __forceinline__ bool last_block_reduce(double (&v)[NV], const int (&m
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       double p = __ldcg(partials + j * gridDim.x + bI);
-      acc[j] = modes[j] ? fmax(acc[j], p) : acc[j] + p;
+      acc[j] = modes[j] ? nan_max(acc[j], p) : acc[j] + p;
     }
   }
   // deterministic: each thread's stripe is fixed; the block tree is fixed

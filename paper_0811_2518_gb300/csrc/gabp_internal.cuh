@@ -141,6 +141,7 @@ struct gabp_handle_s {
   long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
   int multi_nt = 0;                 // autotuned block size of the multi-system kernel
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
+  int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
 };
 
 namespace gabp {
@@ -299,9 +300,12 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
 void free_wb(gabp_handle h);
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host);
+// Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
+// multi-system kernel the autotuner chooses from.
+constexpr int kGridShapes[5] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8)};
 gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
                                int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
-                               float *ms_out);
+                               int shape, float *ms_out);
 gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
                             int max_iter, int *iters, double *relres_host);
 

@@ -107,7 +107,7 @@ __device__ void team_reduce(const Team &T, double (&v)[NV], const int (&mode)[NV
     double acc = mode[j] ? -1.0 : 0.0;
     for (int r = 0; r < T.size; ++r) {
       const double p = *cl.map_shared_rank(&part[j], r);
-      acc = mode[j] ? fmax(acc, p) : acc + p;
+      acc = mode[j] ? nan_max(acc, p) : acc + p;
     }
     out[j] = acc;
   }
@@ -168,7 +168,7 @@ __device__ void solve_system(const MultiArgs &a, int s, const Team &T) {
             const float Pn = -A2 / d2;
             Mc[eb + u] = Pn;
             acc += Pn;
-            rel = fmaxf(rel, fabsf(Pn - Pp[u]) / fabsf(Pn));
+            rel = nan_max(rel, rel_change(Pn, Pp[u]));
           }
         }
       }
@@ -509,8 +509,26 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
   auto finish = [&](float t) -> gabp_status {
     return collect_systems(h, nsys, slots, d_res, d_rel, t, status_host, iters_host, relres_host);
   };
-  auto run_grid = [&](float *t) {
-    return solve_systems_grid(h, nsys, d_off, b, x, tol, max_iter, d_res, d_res + nsys, d_res + 2 * nsys, d_rel, t);
+  auto run_grid_shape = [&](int shape, float *t) {
+    return solve_systems_grid(h, nsys, d_off, b, x, tol, max_iter, d_res, d_res + nsys, d_res + 2 * nsys, d_rel,
+                              shape, t);
+  };
+  // grid-kernel shape: the lanes option, else the tuned one, else tune it now
+  // (each candidate one complete run; the fastest is kept)
+  auto run_grid = [&](float *t) -> gabp_status {
+    int shape = 0;
+    if (h->opt.lanes >= 1 && h->opt.lanes <= 8) shape = h->opt.lanes | ((h->opt.lanes >= 4 ? 2 : 4) << 8);
+    else shape = h->multi_grid_shape;
+    if (shape) return run_grid_shape(shape, t);
+    float best = 1e30f;
+    for (int c : kGridShapes) {
+      float tc = 0.f;
+      gabp_status e = run_grid_shape(c, &tc);
+      if (e != GABP_OK) return e;
+      if (tc < best) { best = tc; shape = c; }
+    }
+    h->multi_grid_shape = shape;
+    return run_grid_shape(shape, t);
   };
   // kernel choice: the options may force the grid-persistent kernel (mode 1) or
   // teams (mode 2, or any fixed split); otherwise the first call on a handle

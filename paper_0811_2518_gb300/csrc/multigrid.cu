@@ -9,16 +9,18 @@
 //   INNER  one FP32 mean round of the inner solve of A d = r,
 //   UPDATE x += d (FP64),
 // and its row sums (max change of the precisions, the inner ||dx||^2 and
-// ||x||^2, the outer ||r||^2) are gathered per system; after a grid barrier one
-// thread per system takes that system's decision (stationary precisions, inner
-// tolerance reached -- with the adaptive target of solve32.cu -- outer
-// tolerance reached, breakdown, divergence, caps), then a second barrier opens
-// the next round.  Systems therefore converge independently, as if solved one
-// by one, while each round streams the rows of all running systems at once.
+// ||x||^2, the outer ||r||^2) are gathered per system.  Each round ends with
+// ONE grid barrier: the last block to arrive takes every system's decision
+// (stationary precisions, inner tolerance reached -- with the adaptive target
+// of solve32.cu -- outer tolerance reached, breakdown, divergence, caps) and
+// then releases the others.  Systems therefore converge independently, as if
+// solved one by one, while each round streams the rows of all running systems.
+// L lanes work on one row (coalesced slot loads), U slots per lane have their
+// loads issued together.
 //
-// The grid barrier spins on a generation counter with a clock-bounded wait:
-// all blocks are co-resident (cooperative launch), so it always completes; if
-// it ever did not within ~2 s, the kernel records GABP_TIMEOUT and returns.
+// The barrier spins on a generation counter with a clock-bounded wait: all
+// blocks are co-resident (cooperative launch), so it always completes; if it
+// ever did not within ~2 s, the kernel records GABP_TIMEOUT and returns.
 #include "gabp_internal.cuh"
 #include "devutil.cuh"
 
@@ -31,8 +33,8 @@ namespace gabp {
 namespace {
 
 enum : int { PH_PREC = 0, PH_COEF = 1, PH_RESID = 2, PH_INNER = 3, PH_UPDATE = 4, PH_DONE = 5 };
-constexpr int kGU = 4;                       // slots per thread whose loads are issued together
 constexpr int kGPrecCap = 300;               // precision-round cap per system
+constexpr int kGChunk = 8;                   // warp steps per chunk of contiguous rows
 constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles (~2 s) before a barrier gives up
 
 struct SysState {
@@ -71,68 +73,65 @@ __device__ __forceinline__ float *ring(float *a, float *b, float *c, int t) {
   return m == 0 ? a : (m == 1 ? b : c);
 }
 
-// Bounded grid barrier (all blocks co-resident).  Returns false if it gave up.
-__device__ bool grid_barrier(unsigned int *bar, int *err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int *gen = bar + 1;
-    const unsigned int g = *gen;
-    __threadfence();
-    int ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      bar[0] = 0;
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (*(volatile int *)err || clock64() - t0 > kBarrierLimit) { ok = 0; break; }
-        __nanosleep(64);
-      }
-    }
-    if (!ok) atomicExch(err, 1);
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
+// Per-warp running sums of one system (slot 0: sum; slot 1: sum, or max for
+// the precision rounds' relative change), flushed to the system's accumulators
+// in global memory only when the warp meets another system or ends its pass:
+// a warp reads contiguous chunks of rows, so most rows fold in registers and a
+// system's accumulator sees a few atomics per chunk, not one per row.  A NaN in
+// a max survives (it must not read as "stationary"); 0 is neutral for the max
+// too, the values being >= 0 or NaN.
+struct WarpAcc {
+  int s = -1;
+  bool max1 = false;
+  double r0 = 0.0, r1 = 0.0;
 
-// Accumulate a row's contribution into its system's sums (slot 0: sum; slot 1:
-// sum, or max when max1).  When the whole warp works for one system the warp
-// reduces first and lane 0 issues the atomics; otherwise each lane does.  A NaN
-// in a max survives (it must not read as "stationary").
-__device__ __forceinline__ void accumulate(double *acc, int s, double v0, double v1, bool max1, bool has) {
-  __syncwarp();
-  const int key = has ? s : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (peers == 0xffffffffu) {
-    if (key < 0) return;
-    double a0 = v0, a1 = v1;
+  __device__ __forceinline__ void flush(double *acc) {
+    if (s < 0) return;  // warp-uniform
+    double a0 = r0, a1 = r1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       const double b1 = __shfl_xor_sync(0xffffffffu, a1, o);
-      a1 = max1 ? ((a1 > b1 || a1 != a1) ? a1 : b1) : a1 + b1;
+      a1 = max1 ? nan_max(a1, b1) : a1 + b1;
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(acc + 4 * key, a0);
+      atomicAdd(acc + 4 * s, a0);
       if (max1)
-        atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * key + 1), (unsigned long long)__double_as_longlong(a1));
+        atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * s + 1), (unsigned long long)__double_as_longlong(a1));
       else
-        atomicAdd(acc + 4 * key + 1, a1);
+        atomicAdd(acc + 4 * s + 1, a1);
     }
-  } else if (has) {
-    atomicAdd(acc + 4 * s, v0);
-    if (max1)
-      atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * s + 1), (unsigned long long)__double_as_longlong(v1));
-    else
-      atomicAdd(acc + 4 * s + 1, v1);
+    s = -1;
+    r0 = r1 = 0.0;
   }
-}
 
-// A system's state as last written by its decision thread (possibly on another
+  // one row's values (lanes with has = false contribute nothing); all lanes call
+  __device__ __forceinline__ void add(double *acc, int sys, double v0, double v1, bool mx, bool has) {
+    const unsigned with = __ballot_sync(0xffffffffu, has);
+    if (!with) return;
+    const int src = __ffs(with) - 1;
+    const int s0 = __shfl_sync(0xffffffffu, sys, src);
+    if (__all_sync(0xffffffffu, !has || sys == s0)) {
+      if (s0 != s) {
+        flush(acc);
+        s = s0;
+        max1 = __shfl_sync(0xffffffffu, mx, src);
+      }
+      if (has) {
+        r0 += v0;
+        r1 = max1 ? nan_max(r1, v1) : r1 + v1;
+      }
+    } else if (has) {  // rows of several systems in this warp step: direct atomics
+      atomicAdd(acc + 4 * sys, v0);
+      if (mx)
+        atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * sys + 1), (unsigned long long)__double_as_longlong(v1));
+      else
+        atomicAdd(acc + 4 * sys + 1, v1);
+    }
+  }
+};
+
+// A system's state as last written by the deciding block (possibly on another
 // SM): read through L2.
 __device__ __forceinline__ SysState load_state(const SysState *p) {
   SysState S;
@@ -143,43 +142,152 @@ __device__ __forceinline__ SysState load_state(const SysState *p) {
   return S;
 }
 
-__global__ void __launch_bounds__(kBlock) kg_solve(GridArgs a) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  const int lane = threadIdx.x & 31, wid = tid >> 5, nw = nth >> 5;
+// One system's decision after a round (run by the deciding block).  Returns 1
+// while the system is still running.
+__device__ int decide(const GridArgs &a, int s) {
+  SysState S = load_state(a.st + s);
+  double *ac = a.acc + 4 * s;
+  const double v0 = __ldcg(ac), v1 = __ldcg(ac + 1);
+  ac[0] = 0.0;
+  ac[1] = 0.0;
+  switch (S.phase) {
+    case PH_PREC: {
+      S.stable = (v1 <= a.prec_thr) ? S.stable + 1 : 0;  // a NaN is not stationary
+      if (v0 > 0.0) { S.status = GABP_BREAKDOWN; S.phase = PH_DONE; S.Tp = S.t; }
+      else if (!(v1 <= 1e30)) { S.status = GABP_DIVERGED; S.phase = PH_DONE; S.Tp = S.t; }
+      else if (S.stable >= 2 || S.t >= kGPrecCap) { S.Tp = S.t; S.phase = PH_COEF; }
+      else S.t += 1;
+      break;
+    }
+    case PH_COEF: S.phase = PH_RESID; break;
+    case PH_RESID: {
+      S.rr = v0;
+      if (S.steps == 0) S.bb = v0;
+      if (S.bb == 0.0 || S.rr <= a.tol * a.tol * S.bb) { S.status = GABP_OK; S.phase = PH_DONE; }
+      else if (!isfinite(S.rr)) { S.status = GABP_DIVERGED; S.phase = PH_DONE; }
+      else if (S.steps >= a.max_refine || S.inner_total >= a.max_iter) { S.status = GABP_NOT_CONVERGED; S.phase = PH_DONE; }
+      else {
+        const double need = 0.1 * a.tol * sqrt(S.bb / S.rr);
+        S.itol = fmin(a.inner_tol, fmax(1e-6, need));
+        S.phase = PH_INNER;
+        S.t = 1;
+      }
+      break;
+    }
+    case PH_INNER: {
+      const int cap = min(a.inner_max, max(1, a.max_iter - S.inner_total));
+      if (!isfinite(v0) || !isfinite(v1)) { S.status = GABP_DIVERGED; S.phase = PH_DONE; S.inner_total += S.t; }
+      else if ((S.t >= 2 && v0 <= S.itol * S.itol * v1) || S.t >= cap) {
+        S.Tm = S.t;
+        S.inner_total += S.t;
+        S.phase = PH_UPDATE;
+      } else S.t += 1;
+      break;
+    }
+    case PH_UPDATE: S.steps += 1; S.phase = PH_RESID; break;
+    default: return 0;
+  }
+  a.st[s] = S;
+  return S.phase != PH_DONE;
+}
+
+// End of a round: bounded grid barrier whose last arriving block takes all
+// decisions before it releases the others.  Returns the number of systems still
+// running, or -1 if a wait gave up.
+__device__ int round_end(const GridArgs &a) {
+  __shared__ int s_last, s_act;
+  __shared__ unsigned s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned *)(a.bar + 1);
+    __threadfence();
+    s_last = atomicAdd(a.bar, 1u) == gridDim.x - 1;
+    s_gen = g;
+    s_act = 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    int mine = 0;
+    for (int s = threadIdx.x; s < a.nsys; s += blockDim.x) mine += decide(a, s);
+    if (mine) atomicAdd(&s_act, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *(volatile int *)a.active = s_act;
+      a.bar[0] = 0;
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    volatile unsigned *gen = a.bar + 1;
+    const long long t0 = clock64();
+    int ok = 1;
+    while (*gen == s_gen) {
+      if (*(volatile int *)a.err || clock64() - t0 > kBarrierLimit) { ok = 0; break; }
+      __nanosleep(64);
+    }
+    if (!ok) atomicExch(a.err, 1);
+    __threadfence();
+    s_act = ok ? *(volatile int *)a.active : -1;
+  }
+  __syncthreads();
+  return s_act;
+}
+
+template <int L, int U>
+__global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : 4) kg_solve(GridArgs a) {
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  constexpr int CR = RPW * kGChunk;  // rows per chunk
+  const int nchunks = (a.n + CR - 1) / CR;
   for (int round = 0; round < a.max_rounds; ++round) {
-    // ---------------------------------------------------------------- work pass
-    // warp-uniform loop: every lane of a warp runs every iteration (row i = base + lane)
-    for (int base = wid * 32; base < a.n; base += nw * 32) {
-      const int i = base + lane;
-      double c0 = 0.0, c1 = 0.0;
-      bool has = false, mx = false;
-      int s = -1;
+    WarpAcc wacc;
+    int sc = -1, phc = PH_DONE, tc = 0, Tc = 0;  // this lane's cached system state (fixed within a round)
+    // warp-uniform loops: every lane of a warp runs every iteration
+    for (int chunk = warp; chunk < nchunks; chunk += nwarps)
+    for (int base = chunk * CR; base < min(a.n, (chunk + 1) * CR); base += RPW) {
+      const int i = base + sw;
+      int s = -1, ph = PH_DONE, t = 0, T = 0;
       if (i < a.n) {
-      s = a.sys_of[i];
-      const SysState S = load_state(a.st + s);
-      if (S.phase == PH_PREC) {
-        const int t = S.t;
+        s = a.sys_of[i];
+        if (s != sc) {
+          const SysState S = load_state(a.st + s);
+          sc = s;
+          phc = S.phase;
+          tc = S.t;
+          Tc = S.phase == PH_COEF ? S.Tp : S.Tm;
+        }
+        ph = phc;
+        t = tc;
+        T = Tc;
+      }
+      // ---------------------------------------------------------- edge part, L lanes per row
+      float facc = 0.f, frel = 0.f;
+      double dacc = 0.0;
+      int bad = 0;
+      if (ph == PH_PREC) {
         float *Mc = (t & 1) ? a.MP1 : a.MP0;
         const float *Mo = (t & 1) ? a.MP0 : a.MP1;
         const float *Pm1 = ring(a.NP0, a.NP1, a.NP2, t + 2);
-        const float *Pm2 = ring(a.NP0, a.NP1, a.NP2, t + 1);
-        float *Pt = ring(a.NP0, a.NP1, a.NP2, t);
-        const float Pi2 = t >= 2 ? Pm2[i] : 0.f;
-        float acc = 0.f, rel = 0.f;
-        int bad = 0;
+        const float Pi2 = t >= 2 ? ring(a.NP0, a.NP1, a.NP2, t + 1)[i] : 0.f;
         const int e1 = a.rp[i + 1];
-        for (int eb = a.rp[i]; eb < e1; eb += kGU) {
-          int k[kGU];
-          float A[kGU], Ps[kGU], Pp[kGU], Pk[kGU];
+        for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+          int k[U];
+          float A[U], Ps[U], Pp[U], Pk[U];
 #pragma unroll
-          for (int u = 0; u < kGU; ++u)
-            if (eb + u < e1) { k[u] = a.ci[eb + u]; A[u] = a.av[eb + u]; Ps[u] = Mc[eb + u]; Pp[u] = Mo[eb + u]; }
+          for (int u = 0; u < U; ++u) {
+            const int e = eb + u * L;
+            if (e < e1) { k[u] = a.ci[e]; A[u] = a.av[e]; Ps[u] = Mc[e]; Pp[u] = Mo[e]; }
+          }
 #pragma unroll
-          for (int u = 0; u < kGU; ++u)
-            if (eb + u < e1) Pk[u] = __ldcg(Pm1 + k[u]);
+          for (int u = 0; u < U; ++u)
+            if (eb + u * L < e1) Pk[u] = __ldcg(Pm1 + k[u]);
 #pragma unroll
-          for (int u = 0; u < kGU; ++u) {
-            if (eb + u < e1) {
+          for (int u = 0; u < U; ++u) {
+            const int e = eb + u * L;
+            if (e < e1) {
               const float A2 = A[u] * A[u];
               float Pout = 0.f;
               if (t >= 2) {
@@ -190,136 +298,97 @@ __global__ void __launch_bounds__(kBlock) kg_solve(GridArgs a) {
               const float d2 = Pk[u] - Pout;
               bad |= (d2 == 0.f);
               const float Pn = -A2 / d2;
-              Mc[eb + u] = Pn;
-              acc += Pn;
-              rel = fmaxf(rel, fabsf(Pn - Pp[u]) / fabsf(Pn));
+              Mc[e] = Pn;
+              facc += Pn;
+              frel = nan_max(frel, rel_change(Pn, Pp[u]));
             }
           }
         }
-        const float P = a.ad[i] + acc;
-        bad |= (P == 0.f);
-        Pt[i] = P;
-        c0 = (double)bad;
-        c1 = (double)rel;
-        has = true;
-        mx = true;
-      } else if (S.phase == PH_COEF) {
-        const int T = S.Tp;
+      } else if (ph == PH_COEF) {
         const float *Ms = (T & 1) ? a.MP1 : a.MP0;
         const float *PT = ring(a.NP0, a.NP1, a.NP2, T);
         const float Pi = PT[i];
-        for (int e = a.rp[i]; e < a.rp[i + 1]; ++e) {
+        for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) {
           const float A = a.av[e];
           const float cout = -A / (Pi - Ms[e]);
           const float cin = -A / (__ldcg(PT + a.ci[e]) - cout * A);
           a.CF[e] = make_float2(cin, cout);
         }
-        a.invP[i] = 1.f / Pi;
-        a.x[i] = 0.0;
-      } else if (S.phase == PH_RESID) {
-        double ax = 0.0;
-        for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) ax = fma(a.val[p], __ldcg(a.x + a.col[p]), ax);
-        const double r = a.b[i] - ax;
-        a.rhs[i] = (float)r;
-        a.NH0[i] = (float)r;
-        for (int e = a.rp[i]; e < a.rp[i + 1]; ++e) a.H0[e] = 0.f;
-        c0 = r * r;
-        has = true;
-      } else if (S.phase == PH_INNER) {
-        const int t = S.t;
+      } else if (ph == PH_RESID) {
+        for (int p = a.rowptr[i] + sl; p < a.rowptr[i + 1]; p += L) dacc = fma(a.val[p], __ldcg(a.x + a.col[p]), dacc);
+        for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) a.H0[e] = 0.f;
+      } else if (ph == PH_INNER) {
         float *Hc = (t & 1) ? a.H1 : a.H0;
         const float *Hm1 = ring(a.NH0, a.NH1, a.NH2, t + 2);
-        const float *Hm2 = ring(a.NH0, a.NH1, a.NH2, t + 1);
-        float *Ht = ring(a.NH0, a.NH1, a.NH2, t);
-        const float hi2 = t >= 2 ? Hm2[i] : 0.f;
-        float acc = 0.f;
+        const float hi2 = t >= 2 ? ring(a.NH0, a.NH1, a.NH2, t + 1)[i] : 0.f;
         const int e1 = a.rp[i + 1];
-        for (int eb = a.rp[i]; eb < e1; eb += kGU) {
-          int k[kGU];
-          float2 cf[kGU];
-          float hs[kGU], hk[kGU];
+        for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+          int k[U];
+          float2 cf[U];
+          float hs[U], hk[U];
 #pragma unroll
-          for (int u = 0; u < kGU; ++u)
-            if (eb + u < e1) { k[u] = a.ci[eb + u]; cf[u] = a.CF[eb + u]; hs[u] = Hc[eb + u]; }
+          for (int u = 0; u < U; ++u) {
+            const int e = eb + u * L;
+            if (e < e1) { k[u] = a.ci[e]; cf[u] = a.CF[e]; hs[u] = Hc[e]; }
+          }
 #pragma unroll
-          for (int u = 0; u < kGU; ++u)
-            if (eb + u < e1) hk[u] = __ldcg(Hm1 + k[u]);
+          for (int u = 0; u < U; ++u)
+            if (eb + u * L < e1) hk[u] = __ldcg(Hm1 + k[u]);
 #pragma unroll
-          for (int u = 0; u < kGU; ++u) {
-            if (eb + u < e1) {
+          for (int u = 0; u < U; ++u) {
+            const int e = eb + u * L;
+            if (e < e1) {
               const float hout = t >= 2 ? cf[u].y * (hi2 - hs[u]) : 0.f;
               const float hn = cf[u].x * (hk[u] - hout);
-              Hc[eb + u] = hn;
-              acc += hn;
+              Hc[e] = hn;
+              facc += hn;
             }
           }
         }
-        const float hnew = a.rhs[i] + acc;
-        Ht[i] = hnew;
-        const float ip = a.invP[i];
-        const float xi = hnew * ip, dx = (hnew - Hm1[i]) * ip;
-        c0 = (double)(dx * dx);
-        c1 = (double)(xi * xi);
-        has = true;
-      } else if (S.phase == PH_UPDATE) {
-        const float *hT = ring(a.NH0, a.NH1, a.NH2, S.Tm);
-        a.x[i] += (double)(hT[i] * a.invP[i]);
       }
+      // ---------------------------------------------------------- row sums over the L lanes
+      facc = sub_sum<L>(facc);
+      dacc = sub_sum<L>(dacc);
+      bad = sub_sum<L>(bad);
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) frel = nan_max(frel, __shfl_xor_sync(0xffffffffu, frel, o, L));
+      // ---------------------------------------------------------- node part, one lane per row
+      double c0 = 0.0, c1 = 0.0;
+      bool has = false;
+      if (sl == 0 && ph != PH_DONE) {
+        if (ph == PH_PREC) {
+          const float P = a.ad[i] + facc;
+          bad |= (P == 0.f);
+          ring(a.NP0, a.NP1, a.NP2, t)[i] = P;
+          c0 = (double)bad;
+          c1 = (double)frel;
+          has = true;
+        } else if (ph == PH_COEF) {
+          a.invP[i] = 1.f / ring(a.NP0, a.NP1, a.NP2, T)[i];
+          a.x[i] = 0.0;
+        } else if (ph == PH_RESID) {
+          const double r = a.b[i] - dacc;
+          a.rhs[i] = (float)r;
+          a.NH0[i] = (float)r;
+          c0 = r * r;
+          has = true;
+        } else if (ph == PH_INNER) {
+          const float hnew = a.rhs[i] + facc;
+          ring(a.NH0, a.NH1, a.NH2, t)[i] = hnew;
+          const float ip = a.invP[i];
+          const float xi = hnew * ip, dx = (hnew - ring(a.NH0, a.NH1, a.NH2, t + 2)[i]) * ip;
+          c0 = (double)(dx * dx);
+          c1 = (double)(xi * xi);
+          has = true;
+        } else if (ph == PH_UPDATE) {
+          a.x[i] += (double)(ring(a.NH0, a.NH1, a.NH2, T)[i] * a.invP[i]);
+        }
       }
-      accumulate(a.acc, s, c0, c1, mx, has);
+      wacc.add(a.acc, s, c0, c1, ph == PH_PREC, has);
     }
-    if (!grid_barrier(a.bar, a.err)) return;
-    // ---------------------------------------------------------------- decisions, one thread per system
-    for (int s = tid; s < a.nsys; s += nth) {
-      SysState S = load_state(a.st + s);
-      double *ac = a.acc + 4 * s;
-      const double v0 = __ldcg(ac), v1 = __ldcg(ac + 1);
-      ac[0] = 0.0;
-      ac[1] = 0.0;
-      switch (S.phase) {
-        case PH_PREC: {
-          S.stable = (v1 <= a.prec_thr) ? S.stable + 1 : 0;  // a NaN is not stationary
-          if (v0 > 0.0) { S.status = GABP_BREAKDOWN; S.phase = PH_DONE; S.Tp = S.t; }
-          else if (S.stable >= 2 || S.t >= kGPrecCap) { S.Tp = S.t; S.phase = PH_COEF; }
-          else S.t += 1;
-          break;
-        }
-        case PH_COEF: S.phase = PH_RESID; break;
-        case PH_RESID: {
-          S.rr = v0;
-          if (S.steps == 0) S.bb = v0;
-          if (S.bb == 0.0 || S.rr <= a.tol * a.tol * S.bb) { S.status = GABP_OK; S.phase = PH_DONE; }
-          else if (!isfinite(S.rr)) { S.status = GABP_DIVERGED; S.phase = PH_DONE; }
-          else if (S.steps >= a.max_refine || S.inner_total >= a.max_iter) { S.status = GABP_NOT_CONVERGED; S.phase = PH_DONE; }
-          else {
-            const double need = 0.1 * a.tol * sqrt(S.bb / S.rr);
-            S.itol = fmin(a.inner_tol, fmax(1e-6, need));
-            S.phase = PH_INNER;
-            S.t = 1;
-          }
-          break;
-        }
-        case PH_INNER: {
-          const int cap = min(a.inner_max, max(1, a.max_iter - S.inner_total));
-          if (!isfinite(v0) || !isfinite(v1)) { S.status = GABP_DIVERGED; S.phase = PH_DONE; S.inner_total += S.t; }
-          else if ((S.t >= 2 && v0 <= S.itol * S.itol * v1) || S.t >= cap) {
-            S.Tm = S.t;
-            S.inner_total += S.t;
-            S.phase = PH_UPDATE;
-          } else S.t += 1;
-          break;
-        }
-        case PH_UPDATE: S.steps += 1; S.phase = PH_RESID; break;
-        default: break;
-      }
-      a.st[s] = S;
-      if (S.phase != PH_DONE) atomicAdd(a.active, 1);
-    }
-    if (!grid_barrier(a.bar, a.err)) return;
-    const int act = *(volatile int *)a.active;
-    if (!grid_barrier(a.bar, a.err)) return;  // everyone has read the count before it is reset
-    if (tid == 0) *a.active = 0;
-    if (act == 0) return;
+    wacc.flush(a.acc);
+    const int act = round_end(a);
+    if (act <= 0) return;
   }
 }
 
@@ -349,11 +418,22 @@ __global__ void kg_rows_init(int n, const int *__restrict__ rp, const double *__
   }
 }
 
+// kernel for a shape code L | U << 8 (unknown codes: (4, 2))
+void (*grid_kernel(int code))(GridArgs) {
+  switch (code) {
+    case kGridShapes[0]: return kg_solve<1, 4>;
+    case kGridShapes[1]: return kg_solve<2, 4>;
+    case kGridShapes[3]: return kg_solve<4, 4>;
+    case kGridShapes[4]: return kg_solve<8, 2>;
+    default: return kg_solve<4, 2>;
+  }
+}
+
 }  // namespace
 
 gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
                                int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
-                               float *ms_out) {
+                               int shape, float *ms_out) {
   Graph &g = h->g;
   Work32 &w = h->w32;
   struct Free {
@@ -393,8 +473,9 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
   const long long bound = (long long)kGPrecCap + 2 +
                           (long long)h->opt.max_refine * (std::min(h->opt.inner_max_iter, std::max(1, max_iter)) + 2) + 1;
   a.max_rounds = (int)std::min<long long>(bound, 0x7fffffff);
+  void (*kern)(GridArgs) = grid_kernel(shape);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kg_solve, kBlock, 0) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
@@ -404,7 +485,7 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
   GABP_CUDA(cudaEventCreate(&e1));
   cudaEventRecord(e0, h->stream);
   void *args[] = {&a};
-  cudaError_t le = cudaLaunchCooperativeKernel((void *)kg_solve, dim3(grid), dim3(kBlock), args, 0, h->stream);
+  cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(grid), dim3(kBlock), args, 0, h->stream);
   cudaEventRecord(e1, h->stream);
   h->prof.launches += 3;
   if (le == cudaSuccess) le = cudaEventSynchronize(e1);

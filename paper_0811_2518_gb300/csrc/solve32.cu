@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
             const float Pn = -A2 / d2;
             __stcs(Mc + e, Pn);
             acc += Pn;
-            rel = fmaxf(rel, fabsf(Pn - Pp[u]) / fabsf(Pn));
+            rel = nan_max(rel, rel_change(Pn, Pp[u]));
           }
         }
       }

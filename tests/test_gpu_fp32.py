@@ -102,3 +102,17 @@ def test_dd_loading_mode(gb):
     g = _solve(gb, m, b, 1e-10, max_iter=100000, gamma_mode=2, gamma=0.05, max_refine=2000)
     assert g["status"] == gb.GABP_OK
     assert _relerr(g["x"], oracle.dense_solve(oracle.to_dense(m), b)) <= 1e-8
+
+
+def test_stored_zero_coupling_rejected(gb):
+    """A stored zero off the diagonal is not an edge of the graph (the graph of Section 2.1 has an
+    edge exactly where A_ij != 0): gabp_create rejects it instead of carrying a zero message."""
+    m = synth.grid2d(8, -1.0, 4.5)
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    p = int(np.flatnonzero(rows < m.col)[5])
+    i, j = rows[p], m.col[p]
+    q = m.rowptr[j] + np.flatnonzero(m.col[m.rowptr[j]:m.rowptr[j + 1]] == i)[0]
+    m.val[p] = m.val[q] = 0.0
+    with pytest.raises(gb.GaBPError) as ei:
+        gb.Solver.from_csr(m)
+    assert ei.value.status == gb.GABP_ERR_INVALID
