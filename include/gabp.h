@@ -94,7 +94,11 @@ typedef struct {
                            two consecutive rounds (10..23).  Default 16 */
   int multi_mode;       /* gabp_solve_systems kernel: 0 autotune, 1 grid-persistent (every round sweeps
                            all running systems), 2 cluster / single-block teams.  Default 0 */
-  int reserved[3];
+  int overlap_precision; /* FP32_REFINE, one right-hand side: 1 = while the precisions converge, the
+                           rounds update precision AND mean messages (Algorithm 2's full round), so
+                           the first inner solve starts with the precision phase; 0 = precision-only
+                           rounds first.  Default 1 */
+  int reserved[2];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
         ("multi_split", ctypes.c_int),
         ("prec_stop_log2", ctypes.c_int),
         ("multi_mode", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("overlap_precision", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 

@@ -88,6 +88,7 @@ struct Work32 {
   double *colnorm = nullptr;                      // per-RHS reductions [4][R]
   DevCtl *ctlR = nullptr;                         // per-RHS control (refinement)
   int *rhs_active = nullptr;
+  float2 *NQ[3] = {nullptr, nullptr, nullptr};    // [n] {P~, h~} ring of the joint rounds
 };
 
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
@@ -129,6 +130,9 @@ struct gabp_handle_s {
   int g64_key = -1;
   cudaGraphExec_t gP32 = nullptr;
   cudaGraphExec_t gH32 = nullptr;
+  cudaGraphExec_t gJ32 = nullptr;   // joint precision + mean rounds
+  int gJ32_L = -1;
+  int tuned_Lj32 = 0;               // autotuned shape of the joint round
   int gH32_R = -1;
   int last_path = -1;               // 0 FP64, 1 FP32 refinement (for gabp_marginal_precisions)
   // autotuned sub-warp widths (0 = not tuned yet) and the scratch control block the tuner uses
@@ -241,7 +245,7 @@ inline double inner_target(double inner_tol, double tol, double bb, double rr) {
 
 template <typename LaunchFn>
 inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_key, int key, LaunchFn launch,
-                              int max_rounds, int phase) {
+                              int max_rounds, int phase, int round0 = 0) {
   const int K = h->opt.check_every;
   const bool use_graph = h->stream != nullptr;
   if (use_graph && *cache && *cache_key != key) {
@@ -260,7 +264,7 @@ inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_
     if (e != cudaSuccess) return cuda_fail(e, "instantiate FP32 rounds");
   }
   const int64_t max_batches = (int64_t)max_rounds / K + 3;
-  int prev_round = 0;
+  int prev_round = round0;
   for (int64_t bI = 0; bI < max_batches; ++bI) {
     prof_begin(h);
     if (use_graph) {

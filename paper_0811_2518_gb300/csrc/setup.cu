@@ -166,6 +166,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   if (h->g64) cudaGraphExecDestroy(h->g64);
   if (h->gP32) cudaGraphExecDestroy(h->gP32);
   if (h->gH32) cudaGraphExecDestroy(h->gH32);
+  if (h->gJ32) cudaGraphExecDestroy(h->gJ32);
   free_w64(h);
   free_w32(h);
   free_wb(h);
@@ -269,6 +270,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->multi_split = 0;
   o->prec_stop_log2 = 16;
   o->multi_mode = 0;
+  o->overlap_precision = 1;
   return GABP_OK;
 }
 
@@ -281,7 +283,7 @@ static gabp_status check_options(const gabp_options *o) {
   if (o->lanes != 0 && (o->lanes < 1 || o->lanes > 32 || (o->lanes & (o->lanes - 1)))) return GABP_ERR_INVALID;
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
-      o->multi_mode > 2)
+      o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1)
     return GABP_ERR_INVALID;
   return GABP_OK;
 }
@@ -347,6 +349,8 @@ extern "C" gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt) 
     h->gP32 = nullptr;
     if (h->gH32) cudaGraphExecDestroy(h->gH32);
     h->gH32 = nullptr;
+    if (h->gJ32) cudaGraphExecDestroy(h->gJ32);
+    h->gJ32 = nullptr;
     h->gH32_R = -1;
   }
   return GABP_OK;

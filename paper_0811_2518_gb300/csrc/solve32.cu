@@ -71,11 +71,16 @@ struct Args32 {
   float *H0, *H1;                 // mean chains
   float *NH0, *NH1, *NH2;         // h~ ring
   const float *rhs;               // FP32 right-hand side of the inner solve
+  float2 *NQ0, *NQ1, *NQ2;        // {P~, h~} ring of the joint rounds
   DevCtl *ctl;
   double *partials;
 };
 
 __device__ __forceinline__ float *ring3(float *a, float *b, float *c, int t) {
+  int m = t % 3;
+  return m == 0 ? a : (m == 1 ? b : c);
+}
+__device__ __forceinline__ float2 *ring3(float2 *a, float2 *b, float2 *c, int t) {
   int m = t % 3;
   return m == 0 ? a : (m == 1 ? b : c);
 }
@@ -173,6 +178,131 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
     }
     ctl->arrive = 0;
     __threadfence();
+  }
+}
+
+// ---------------------------------------------------------------------------- joint rounds
+// Round t of the full FP32 iteration (Algorithm 2: eq_prec_message and
+// eq_mean_message for every directed edge, in information form), recompute form
+// for both messages.  Slot e = (i, k) keeps the in-messages P_ki, h_ki; the
+// reverse messages of round t-1 are recomputed from row i's own round t-2 state:
+//   P_ik = -A^2 / (P~_i - P_ki),  h_ik = -A (h~_i - h_ki) / (P~_i - P_ki),
+// then  P_ki^t = -A^2 / (P~_k - P_ik),  h_ki^t = -A (h~_k - h_ik) / (P~_k - P_ik)
+// with the sender's round t-1 aggregates {P~_k, h~_k} fetched as ONE 8-byte
+// gather.  The node aggregates go to the {P~, h~} ring and to the P~ and h~ rings
+// the precision-only and frozen-coefficient kernels read, so the run can freeze
+// the coefficients at any round T and continue with k32_mean from round T + 1.
+// Stop rule: the precision phase's (relative change <= 2^-s in two consecutive
+// rounds, zero cavity, max_iter).
+template <int L, int U>
+__global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  float *__restrict__ Mc = (t & 1) ? a.MP1 : a.MP0;        // P chain: holds t-2, becomes t
+  const float *__restrict__ Mo = (t & 1) ? a.MP0 : a.MP1;  // P at t-1
+  float *__restrict__ Hc = (t & 1) ? a.H1 : a.H0;          // h chain: holds t-2, becomes t
+  const float2 *__restrict__ Qm1 = ring3(a.NQ0, a.NQ1, a.NQ2, t + 2);
+  const float2 *__restrict__ Qm2 = ring3(a.NQ0, a.NQ1, a.NQ2, t + 1);
+  float2 *__restrict__ Qt = ring3(a.NQ0, a.NQ1, a.NQ2, t);
+  float *__restrict__ Pt = ring3(a.NP0, a.NP1, a.NP2, t);
+  float *__restrict__ Ht = ring3(a.NH0, a.NH1, a.NH2, t);
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  float rel = 0.f;
+  int bad = 0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    float accP = 0.f, accH = 0.f;
+    if (i < a.n) {
+      const float2 q2 = t >= 2 ? Qm2[i] : make_float2(0.f, 0.f);
+      const int e1 = a.rp[i + 1];
+      for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+        int k[U];
+        float A[U], Ps[U], Pp[U], hs[U];
+        float2 qk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            k[u] = __ldcs(a.ci + e); A[u] = __ldcs(a.av + e);
+            Ps[u] = __ldcs(Mc + e); Pp[u] = __ldcs(Mo + e); hs[u] = __ldcs(Hc + e);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (eb + u * L < e1) qk[u] = Qm1[k[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            float Pout = 0.f, hout = 0.f;
+            if (t >= 2) {  // message i -> k of round t-1
+              const float d1 = q2.x - Ps[u];
+              bad |= (d1 == 0.f);
+              const float r1 = 1.f / d1;
+              Pout = -A[u] * A[u] * r1;
+              hout = -A[u] * (q2.y - hs[u]) * r1;
+            }
+            const float d2 = qk[u].x - Pout;  // message k -> i of round t
+            bad |= (d2 == 0.f);
+            const float r2 = 1.f / d2;
+            const float Pn = -A[u] * A[u] * r2;
+            const float hn = -A[u] * (qk[u].y - hout) * r2;
+            __stcs(Mc + e, Pn);
+            __stcs(Hc + e, hn);
+            accP += Pn;
+            accH += hn;
+            rel = nan_max(rel, rel_change(Pn, Pp[u]));
+          }
+        }
+      }
+    }
+    accP = sub_sum<L>(accP);
+    accH = sub_sum<L>(accH);
+    if (i < a.n && sl == 0) {
+      const float P = a.ad[i] + accP, hh = a.rhs[i] + accH;
+      bad |= (P == 0.f);
+      Qt[i] = make_float2(P, hh);
+      Pt[i] = P;
+      Ht[i] = hh;
+    }
+  }
+  double vb[1] = {(double)bad}, vr[1] = {(double)rel};
+  block_sum<1>(vb);
+  block_max<1>(vr);
+  double v[2] = {vb[0], vr[0]}, tot[2];
+  const int modes[2] = {0, 1};
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    ctl->round = t;
+    ctl->maxrel = tot[1];
+    const bool stat = tot[1] <= ctl->tol2bb;  // 2^-prec_stop_log2; a NaN is not stationary
+    ctl->stable = stat ? ctl->stable + 1 : 0;
+    if (ctl->no_stop) {
+      // autotuning run: no decision
+    } else if (tot[0] > 0.0) {
+      ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (!isfinite(tot[1]) && t > 1) {
+      ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (ctl->stable >= 2) {
+      ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= ctl->max_iter) {
+      ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    }
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
+// round-0 state of the joint rounds: zero messages, {P~, h~} = {A_ii (+ Gamma_ii), r}
+__global__ void k32_joint_init(int n, const float *__restrict__ ad, const float *__restrict__ rhs, float2 *nq0,
+                               float *np0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    nq0[i] = make_float2(ad[i], rhs[i]);
+    np0[i] = ad[i];
   }
 }
 
@@ -340,8 +470,8 @@ __global__ void k_diag32(int n, const double *__restrict__ ad, const double *__r
   if (i < n) d32[i] = (float)(ad[i] + (gam ? gam[i] : 0.0));
 }
 
-__global__ void k_ctl_reset(DevCtl *c, int max_iter, double tol2) {
-  c->round = 0;
+__global__ void k_ctl_reset(DevCtl *c, int max_iter, double tol2, int round0 = 0) {
+  c->round = round0;
   c->done = 0;
   c->status = GABP_NOT_CONVERGED;
   c->iters = 0;
@@ -415,6 +545,7 @@ gabp_status ensure_w32(gabp_handle h, int R) {
     GABP_CUDA(cudaMalloc(&g.ad32, sizeof(float) * n));
     GABP_CUDA(cudaMalloc(&w.ctlR, sizeof(DevCtl)));
     GABP_CUDA(cudaMemsetAsync(w.ctlR, 0, sizeof(DevCtl), h->stream));
+    for (int j = 0; j < 3; ++j) GABP_CUDA(cudaMalloc(&w.NQ[j], sizeof(float2) * n));
     k_to_f32<<<(int)((E + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>((int64_t)g.E, g.av, g.av32);
     GABP_CUDA(cudaGetLastError());
   }
@@ -442,7 +573,7 @@ gabp_status ensure_w32(gabp_handle h, int R) {
 void free_w32(gabp_handle h) {
   Work32 &w = h->w32;
   cudaFree(w.MP[0]); cudaFree(w.MP[1]);
-  for (int j = 0; j < 3; ++j) { cudaFree(w.NP[j]); cudaFree(w.NH[j]); }
+  for (int j = 0; j < 3; ++j) { cudaFree(w.NP[j]); cudaFree(w.NH[j]); cudaFree(w.NQ[j]); }
   cudaFree(w.CF); cudaFree(w.invP); cudaFree(w.H[0]); cudaFree(w.H[1]);
   cudaFree(w.rhs32); cudaFree(w.X); cudaFree(w.Rs); cudaFree(w.Bt); cudaFree(w.colnorm);
   cudaFree(w.ctlR); cudaFree(w.rhs_active);
@@ -460,6 +591,7 @@ static Args32 args32(gabp_handle h) {
   a.H0 = w.H[0]; a.H1 = w.H[1];
   a.NH0 = w.NH[0]; a.NH1 = w.NH[1]; a.NH2 = w.NH[2];
   a.rhs = w.rhs32;
+  a.NQ0 = w.NQ[0]; a.NQ1 = w.NQ[1]; a.NQ2 = w.NQ[2];
   a.ctl = h->ctl;
   a.partials = h->partials;
   return a;
@@ -468,9 +600,13 @@ static Args32 args32(gabp_handle h) {
 // Shape (lanes per row, unroll) of an FP32 round kernel: the option if set, else
 // the autotuned one, else a heuristic (one unrolled pass of 4 slots per lane
 // covers a row of average degree).
-static int shape32(gabp_handle h, bool mean) {
+enum { K32_PREC = 0, K32_MEAN = 1, K32_JOINT = 2 };
+static int &tuned32(gabp_handle h, int kind) {
+  return kind == K32_MEAN ? h->tuned_Lm32 : kind == K32_JOINT ? h->tuned_Lj32 : h->tuned_Lp32;
+}
+static int shape32(gabp_handle h, int kind) {
   if (h->opt.lanes) return shape_code(h->opt.lanes, kUnroll32);
-  const int tuned = mean ? h->tuned_Lm32 : h->tuned_Lp32;
+  const int tuned = tuned32(h, kind);
   if (tuned) return tuned;
   double d = h->g.avg_deg;
   int L = 1;
@@ -480,8 +616,8 @@ static int shape32(gabp_handle h, bool mean) {
 
 // Autotuner of the FP32 round kernels' shapes (see autotune64): a few rounds of
 // every candidate (lanes, unroll) under a scratch control block, fastest kept.
-static gabp_status autotune32(gabp_handle h, bool mean) {
-  if (h->opt.lanes || (mean ? h->tuned_Lm32 : h->tuned_Lp32)) return GABP_OK;
+static gabp_status autotune32(gabp_handle h, int kind) {
+  if (h->opt.lanes || tuned32(h, kind)) return GABP_OK;
   Graph &g = h->g;
   gabp_status s0 = tune_ctl(h, nullptr);  // allocates the scratch control block on first use
   if (s0 != GABP_OK) return s0;
@@ -495,10 +631,15 @@ static gabp_status autotune32(gabp_handle h, bool mean) {
     float ms = 1e30f;
     with_shape(sc, [&](auto Lc, auto Uc) {
       constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
-      if (mean)
+      if (kind == K32_MEAN)
         ms = time_launches(h, [&] {
           k32_mean<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>)), kBlock, 0,
                              h->stream>>>(a);
+        }, 3);
+      else if (kind == K32_JOINT)
+        ms = time_launches(h, [&] {
+          k32_joint<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_joint<LL, UU>)), kBlock, 0,
+                              h->stream>>>(a);
         }, 3);
       else
         ms = time_launches(h, [&] {
@@ -509,7 +650,7 @@ static gabp_status autotune32(gabp_handle h, bool mean) {
     if (ms < best) { best = ms; bestS = sc; }
   }
   GABP_CUDA(cudaGetLastError());
-  (mean ? h->tuned_Lm32 : h->tuned_Lp32) = bestS;
+  tuned32(h, kind) = bestS;
   return GABP_OK;
 }
 
@@ -528,10 +669,10 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
   gabp_status st = init();
   if (st != GABP_OK) return st;
   if (!h->opt.lanes && !h->tuned_Lp32) {
-    if ((st = autotune32(h, false)) != GABP_OK) return st;
+    if ((st = autotune32(h, K32_PREC)) != GABP_OK) return st;
     if ((st = init()) != GABP_OK) return st;
   }
-  const int SH = shape32(h, false);
+  const int SH = shape32(h, K32_PREC);
   k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, kPrecMaxRounds, std::ldexp(1.0, -h->opt.prec_stop_log2));
   h->prof.launches += 2;
   GABP_CUDA(cudaGetLastError());
@@ -558,6 +699,57 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
   return GABP_OK;
 }
 
+// Joint rounds (precision and mean messages together) from zero messages until
+// the precisions are stationary or `cap` rounds, then the coefficient freeze at
+// that round T.  The mean state of round T is the start of the first inner
+// solve's frozen-coefficient rounds.  Needs rhs32 / NH[0] = r (k64_residual).
+static gabp_status joint_phase32(gabp_handle h, const double *gamma_diag, int cap, int *T_out) {
+  Work32 &w = h->w32;
+  Graph &g = h->g;
+  size_t E = (size_t)(g.E > 0 ? g.E : 1);
+  k_diag32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad, gamma_diag, g.ad32);
+  auto init = [&]() -> gabp_status {
+    GABP_CUDA(cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, h->stream));
+    GABP_CUDA(cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, h->stream));
+    GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
+    k32_joint_init<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad32, w.rhs32, w.NQ[0], w.NP[0]);
+    GABP_CUDA(cudaGetLastError());
+    return GABP_OK;
+  };
+  gabp_status st = init();
+  if (st != GABP_OK) return st;
+  if (!h->opt.lanes && !h->tuned_Lj32) {
+    if ((st = autotune32(h, K32_JOINT)) != GABP_OK) return st;
+    if ((st = init()) != GABP_OK) return st;
+  }
+  const int SH = shape32(h, K32_JOINT);
+  const int rounds = std::max(1, std::min(kPrecMaxRounds, cap));
+  k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, rounds, std::ldexp(1.0, -h->opt.prec_stop_log2));
+  h->prof.launches += 3;
+  GABP_CUDA(cudaGetLastError());
+  Args32 a = args32(h);
+  gabp_status s;
+  with_shape(SH, [&](auto Lc, auto Uc) {
+    constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+    s = run_rounds(h, &h->gJ32, &h->gJ32_L, SH, [&] {
+      const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_joint<LL, UU>));
+      k32_joint<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
+    }, rounds, PH_PREC32);
+  });
+  if (s != GABP_OK) return s;
+  const DevCtl c = *h->ctl_host;
+  if (c.status == GABP_BREAKDOWN || c.status == GABP_DIVERGED) return (gabp_status)c.status;
+  const int Lc = SH & 0xff;
+  GABP_DISPATCH_L(Lc, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)), kBlock, 0,
+                                      h->stream>>>(a, c.result_round)));
+  h->prof.launches += 1;
+  GABP_CUDA(cudaGetLastError());
+  w.prec_round = c.result_round;
+  w.coef_ready = true;
+  *T_out = c.result_round;
+  return GABP_OK;
+}
+
 gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int64_t ld, double tol,
                            int max_iter, const double *gamma_diag, int *iters, double *relres) {
   if (R != 1) return GABP_ERR_INVALID;  // batched path: gabp_solve_batched
@@ -569,14 +761,20 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   h->stats.rounds = 0;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
-  // the precision state is cached per handle when no loading is applied
+  // the precision state is cached per handle when no loading is applied; when it
+  // has to be computed, it is either computed first (precision-only rounds) or
+  // together with the first inner solve (joint rounds, overlap_precision)
+  bool joint = false;
   if (!w.coef_ready || gamma_diag || !h->opt.reuse_precisions) {
     w.coef_ready = false;
-    if ((s = precision_phase32(h, gamma_diag)) != GABP_OK) return s;
-    if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
+    joint = h->opt.overlap_precision != 0;
+    if (!joint) {
+      if ((s = precision_phase32(h, gamma_diag)) != GABP_OK) return s;
+      if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
+    }
   }
-  if ((s = autotune32(h, true)) != GABP_OK) return s;
-  const int SH = shape32(h, true);
+  if ((s = autotune32(h, K32_MEAN)) != GABP_OK) return s;
+  const int SH = shape32(h, K32_MEAN);
   // FP64 residual: narrow sub-warps (its per-row epilogue is FP64)
   const int LR = h->opt.lanes ? h->opt.lanes : (g.avg_deg >= 12.0 ? 2 : 1);
   int nbr = 1;
@@ -595,6 +793,9 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   int total_inner = 0;
   gabp_status result = GABP_NOT_CONVERGED;
   if (bb == 0.0) {
+    // x = 0; the precision state is still made available (marginal precisions)
+    if (joint && (s = precision_phase32(h, gamma_diag)) != GABP_OK) return s;
+    if (gamma_diag) w.coef_ready = false;
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
     return GABP_OK;
@@ -605,26 +806,45 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   for (int step = 0; step < h->opt.max_refine; ++step) {
     if (rr <= tol * tol * bb) { result = GABP_OK; break; }
     if (total_inner >= max_iter) break;
-    // inner FP32 GaBP on A d = r (messages from zero, Algorithm 1 step 1)
-    GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
+    // inner FP32 GaBP on A d = r (messages from zero, Algorithm 1 step 1); the
+    // first one may start with the joint rounds, which leave round T's mean state
     const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
     const double it_tol = inner_target(itol, tol, bb, rr);
-    k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
-    h->prof.launches += 1;
-    GABP_CUDA(cudaGetLastError());
-    with_shape(SH, [&](auto Lc, auto Uc) {
-      constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
-      s = run_rounds(h, &h->gH32, &h->gH32_L, SH, [&] {
-        const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
-        k32_mean<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
-      }, cap, PH_MEAN32);
-    });
-    if (s != GABP_OK) return s;
-    const DevCtl c = *h->ctl_host;
-    total_inner += c.round;
-    h->stats.rounds += c.round;
-    if (c.status == GABP_DIVERGED) { result = GABP_DIVERGED; break; }
-    float *hT = c.result_round % 3 == 0 ? w.NH[0] : (c.result_round % 3 == 1 ? w.NH[1] : w.NH[2]);
+    int T = 0;
+    if (step == 0 && joint) {
+      if ((s = joint_phase32(h, gamma_diag, cap, &T)) != GABP_OK) {
+        if (gamma_diag) w.coef_ready = false;
+        return s;
+      }
+      if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
+    } else {
+      GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
+    }
+    int result_round = T;
+    if (T < cap) {
+      k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol, T);
+      h->prof.launches += 1;
+      GABP_CUDA(cudaGetLastError());
+      with_shape(SH, [&](auto Lc, auto Uc) {
+        constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+        s = run_rounds(h, &h->gH32, &h->gH32_L, SH, [&] {
+          const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
+          k32_mean<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
+        }, cap - T, PH_MEAN32, T);
+      });
+      if (s != GABP_OK) return s;
+      const DevCtl c = *h->ctl_host;
+      result_round = c.result_round;
+      if (c.status == GABP_DIVERGED) {
+        total_inner += c.round;
+        h->stats.rounds += c.round;
+        result = GABP_DIVERGED;
+        break;
+      }
+    }
+    total_inner += result_round;
+    h->stats.rounds += result_round;
+    float *hT = result_round % 3 == 0 ? w.NH[0] : (result_round % 3 == 1 ? w.NH[1] : w.NH[2]);
     prof_begin(h);
     k64_update<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, X, hT, w.invP);
     GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,

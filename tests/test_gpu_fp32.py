@@ -37,27 +37,36 @@ def _solve(gb, m, b, tol, max_iter=5000, **opts):
     return out
 
 
+@pytest.mark.parametrize("overlap", [0, 1])
 @pytest.mark.parametrize("make", [
     lambda: synth.grid2d(32, -1.0, 4.5),
     lambda: synth.random_sym(20011, 8, 1.1, 2),
     lambda: synth.grid3d(16, 1.05, 3),
 ])
-def test_refined_matches_fp64_oracle(gb, make):
+def test_refined_matches_fp64_oracle(gb, make, overlap):
+    """overlap 0: precision-only rounds, then frozen-coefficient mean rounds; overlap 1: the
+    first inner solve starts with joint precision + mean rounds (Algorithm 2's full round)."""
     m = make()
     b = synth.rhs(m.n, 5)
     ref = oracle.gabp_broadcast(m, b, max_iter=5000, tol=1e-13)
-    g = _solve(gb, m, b, 1e-12, precision=gb.GABP_PREC_FP32_REFINE)
+    g = _solve(gb, m, b, 1e-12, precision=gb.GABP_PREC_FP32_REFINE, overlap_precision=overlap)
     assert g["status"] == gb.GABP_OK and g["relres"] <= 1e-12
     assert _relerr(g["x"], ref["x"]) <= 1e-10
     assert g["stats"]["refine_steps"] >= 1
+    # the frozen FP32 precisions are the oracle's marginal precisions to FP32 stationarity
+    assert np.allclose(g["P"], ref["P"], rtol=1e-3)
 
 
-def test_unrefined_within_1e5(gb):
+@pytest.mark.parametrize("overlap", [0, 1])
+def test_unrefined_within_1e5(gb, overlap):
+    """One inner solve, no refinement: FP32 GaBP run to its fixed point (with overlap 1 its
+    first rounds are joint precision + mean rounds) is within 1e-5 of the FP64 oracle."""
     m = synth.random_sym(20011, 8, 1.1, 2)
     b = synth.rhs(m.n, 5)
     ref = oracle.gabp_broadcast(m, b, max_iter=5000, tol=1e-13)
     g = _solve(gb, m, b, 1e-12, precision=gb.GABP_PREC_FP32_REFINE, max_refine=1, inner_tol=1e-7,
-               inner_max_iter=200, prec_stop_log2=22)
+               inner_max_iter=200, prec_stop_log2=22, overlap_precision=overlap)
+    assert g["stats"]["refine_steps"] == 1
     assert _relerr(g["x"], ref["x"]) <= 1e-5
     # FP32 marginal precisions, run to a 2^-22 stationary point, agree with the FP64 oracle's
     assert np.allclose(g["P"], ref["P"], rtol=1e-5)
