@@ -98,7 +98,11 @@ typedef struct {
                            rounds update precision AND mean messages (Algorithm 2's full round), so
                            the first inner solve starts with the precision phase; 0 = precision-only
                            rounds first.  Default 1 */
-  int reserved[2];
+  int device_loop;      /* FP32_REFINE, one right-hand side, no loading, profile 0: 1 = the whole
+                           refinement loop (rounds, stop decisions, residuals, updates) runs as ONE
+                           CUDA graph with conditional while/if nodes, no host round trip until the
+                           result; 0 = host-driven batches of check_every rounds.  Default 1 */
+  int reserved[1];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

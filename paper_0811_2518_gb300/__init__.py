@@ -53,7 +53,8 @@ class Options(ctypes.Structure):
         ("prec_stop_log2", ctypes.c_int),
         ("multi_mode", ctypes.c_int),
         ("overlap_precision", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("device_loop", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 

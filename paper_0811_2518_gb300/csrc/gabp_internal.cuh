@@ -89,6 +89,9 @@ struct Work32 {
   DevCtl *ctlR = nullptr;                         // per-RHS control (refinement)
   int *rhs_active = nullptr;
   float2 *NQ[3] = {nullptr, nullptr, nullptr};    // [n] {P~, h~} ring of the joint rounds
+  struct RefineCtl *rc = nullptr;                 // device-resident refinement loop state
+  struct RefineCtl *rc_host = nullptr;            // pinned copy read after a device-loop solve
+  double *Bd = nullptr;                           // [n] right-hand side staged for the device loop
 };
 
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
@@ -131,6 +134,9 @@ struct gabp_handle_s {
   cudaGraphExec_t gP32 = nullptr;
   cudaGraphExec_t gH32 = nullptr;
   cudaGraphExec_t gJ32 = nullptr;   // joint precision + mean rounds
+  cudaGraph_t gRefG = nullptr;      // whole FP32 refinement loop (conditional nodes) and its instance
+  cudaGraphExec_t gRef = nullptr;
+  long long gRef_key = -1;
   int gJ32_L = -1;
   int tuned_Lj32 = 0;               // autotuned shape of the joint round
   int gH32_R = -1;
@@ -226,9 +232,9 @@ gabp_status read_ctl(gabp_handle h);  // copies ctl -> ctl_host and synchronises
 // Tolerance of one FP32 inner solve: only the reduction still needed to reach
 // tol (with a factor 10 of margin), never looser than the option's inner_tol,
 // never tighter than FP32 can deliver (1e-6) unless inner_tol itself asks for it.
-inline double inner_target(double inner_tol, double tol, double bb, double rr) {
-  const double need = rr > 0.0 ? 0.1 * tol * std::sqrt(bb / rr) : inner_tol;
-  return std::min(inner_tol, std::max(1e-6, need));
+__host__ __device__ inline double inner_target(double inner_tol, double tol, double bb, double rr) {
+  const double need = rr > 0.0 ? 0.1 * tol * sqrt(bb / rr) : inner_tol;
+  return fmin(inner_tol, fmax(1e-6, need));
 }
 
 // Run K-round graphs of one round kernel (CUDA graph of K launches when the

@@ -167,6 +167,8 @@ static gabp_status destroy_impl(gabp_handle h) {
   if (h->gP32) cudaGraphExecDestroy(h->gP32);
   if (h->gH32) cudaGraphExecDestroy(h->gH32);
   if (h->gJ32) cudaGraphExecDestroy(h->gJ32);
+  if (h->gRef) cudaGraphExecDestroy(h->gRef);
+  if (h->gRefG) cudaGraphDestroy(h->gRefG);
   free_w64(h);
   free_w32(h);
   free_wb(h);
@@ -271,6 +273,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->prec_stop_log2 = 16;
   o->multi_mode = 0;
   o->overlap_precision = 1;
+  o->device_loop = 1;
   return GABP_OK;
 }
 
@@ -283,7 +286,8 @@ static gabp_status check_options(const gabp_options *o) {
   if (o->lanes != 0 && (o->lanes < 1 || o->lanes > 32 || (o->lanes & (o->lanes - 1)))) return GABP_ERR_INVALID;
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
-      o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1)
+      o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
+      o->device_loop < 0 || o->device_loop > 1)
     return GABP_ERR_INVALID;
   return GABP_OK;
 }
@@ -351,6 +355,11 @@ extern "C" gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt) 
     h->gH32 = nullptr;
     if (h->gJ32) cudaGraphExecDestroy(h->gJ32);
     h->gJ32 = nullptr;
+    if (h->gRef) cudaGraphExecDestroy(h->gRef);
+    if (h->gRefG) cudaGraphDestroy(h->gRefG);
+    h->gRef = nullptr;
+    h->gRefG = nullptr;
+    h->gRef_key = -1;
     h->gH32_R = -1;
   }
   return GABP_OK;

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 namespace gabp {
 
@@ -74,6 +75,8 @@ struct Args32 {
   float2 *NQ0, *NQ1, *NQ2;        // {P~, h~} ring of the joint rounds
   DevCtl *ctl;
   double *partials;
+  cudaGraphConditionalHandle cond;  // while-node condition cleared when the run is decided
+  int use_cond;                     // (only inside the device-loop graph)
 };
 
 __device__ __forceinline__ float *ring3(float *a, float *b, float *c, int t) {
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
     } else if (t >= ctl->max_iter) {
       ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     }
+    if (a.use_cond && ctl->done) cudaGraphSetConditional(a.cond, 0);
     ctl->arrive = 0;
     __threadfence();
   }
@@ -309,7 +313,8 @@ __global__ void k32_joint_init(int n, const float *__restrict__ ad, const float 
 // Freeze: c_out = c_ik = -A / (P~_i - P_ki), P_ik = c_out A, c_in = c_ki = -A / (P~_k - P_ik),
 // 1/P~_i.  Uses round T's precision state.
 template <int L>
-__global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T) {
+__global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T, const DevCtl *tctl = nullptr) {
+  if (tctl) T = tctl->result_round;  // device-loop graph: the round the joint phase stopped at
   const float *__restrict__ Ms = (T & 1) ? a.MP1 : a.MP0;
   const float *__restrict__ PT = ring3(a.NP0, a.NP1, a.NP2, T);
   constexpr int RPW = 32 / L;
@@ -406,6 +411,7 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
     } else if (t >= ctl->max_iter) {
       ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     }
+    if (a.use_cond && ctl->done) cudaGraphSetConditional(a.cond, 0);
     ctl->arrive = 0;
     __threadfence();
   }
@@ -419,7 +425,9 @@ __global__ void __launch_bounds__(kBlock) k64_residual(int n, const int *__restr
                                                        const int *__restrict__ col, const double *__restrict__ val,
                                                        const double *__restrict__ b, const double *__restrict__ x,
                                                        float *__restrict__ rhs32, float *__restrict__ nh0,
-                                                       DevCtl *ctl, double *partials, int set_bb) {
+                                                       DevCtl *ctl, double *partials, int set_bb,
+                                                       const int *skip = nullptr) {
+  if (skip && *skip) return;  // device-loop graph: the loop already stopped
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -566,6 +574,11 @@ gabp_status ensure_w32(gabp_handle h, int R) {
     if (h->gH32) cudaGraphExecDestroy(h->gH32);
     h->gH32 = nullptr;
     h->gH32_R = -1;
+    if (h->gRef) cudaGraphExecDestroy(h->gRef);  // holds the old buffers
+    if (h->gRefG) cudaGraphDestroy(h->gRefG);
+    h->gRef = nullptr;
+    h->gRefG = nullptr;
+    h->gRef_key = -1;
   }
   return GABP_OK;
 }
@@ -576,7 +589,8 @@ void free_w32(gabp_handle h) {
   for (int j = 0; j < 3; ++j) { cudaFree(w.NP[j]); cudaFree(w.NH[j]); cudaFree(w.NQ[j]); }
   cudaFree(w.CF); cudaFree(w.invP); cudaFree(w.H[0]); cudaFree(w.H[1]);
   cudaFree(w.rhs32); cudaFree(w.X); cudaFree(w.Rs); cudaFree(w.Bt); cudaFree(w.colnorm);
-  cudaFree(w.ctlR); cudaFree(w.rhs_active);
+  cudaFree(w.ctlR); cudaFree(w.rhs_active); cudaFree(w.rc); cudaFree(w.Bd);
+  if (w.rc_host) cudaFreeHost(w.rc_host);
   w = Work32{};
 }
 
@@ -592,6 +606,8 @@ static Args32 args32(gabp_handle h) {
   a.NH0 = w.NH[0]; a.NH1 = w.NH[1]; a.NH2 = w.NH[2];
   a.rhs = w.rhs32;
   a.NQ0 = w.NQ[0]; a.NQ1 = w.NQ[1]; a.NQ2 = w.NQ[2];
+  a.cond = 0;
+  a.use_cond = 0;
   a.ctl = h->ctl;
   a.partials = h->partials;
   return a;
@@ -750,6 +766,362 @@ static gabp_status joint_phase32(gabp_handle h, const double *gamma_diag, int ca
   return GABP_OK;
 }
 
+// ---------------------------------------------------------------------------- device-driven refinement loop
+// The whole FP32 + FP64-refinement solve of one right-hand side as ONE CUDA
+// graph: the stop decisions that the host loop of solve32_refine takes after
+// each batch of rounds and after each residual are taken by single-thread
+// kernels that set the conditions of while / if nodes (cudaGraphSetConditional),
+// so the host only launches the graph and reads the result:
+//
+//   r = b - A x (x = 0), decide
+//   while (refining) {
+//     zero the inner messages
+//     if (precisions not computed yet) { joint rounds while not stationary; freeze; continue at T }
+//     while (inner not decided) { K frozen-coefficient mean rounds }
+//     x += d; r = b - A x; decide
+//   }
+//
+// Same arithmetic, same kernels, same decisions as the host-driven loop.
+struct RefineCtl {
+  // parameters of the call
+  double tol, tol2, inner_tol, prec_thr;
+  int max_refine, max_iter, inner_max, prec_cap;
+  // loop state
+  double rr, bb, it2;
+  int steps, total_inner, status, skip, joint_pending, prec_round, cap, pad;
+};
+
+struct RefineParams {
+  double tol, inner_tol, prec_thr;
+  int max_refine, max_iter, inner_max, prec_cap, joint;
+};
+
+__device__ void ctl_arm(DevCtl *c, int round0, int max_iter, double tol2) {
+  c->round = round0;
+  c->done = round0 >= max_iter;
+  c->status = GABP_NOT_CONVERGED;
+  c->iters = round0;
+  c->result_round = round0;
+  c->max_iter = max_iter;
+  c->check_from = 1;
+  c->stable = 0;
+  c->tol2bb = tol2;
+  c->rr = 0.0;
+  c->xx = 0.0;
+  c->maxrel = 0.0;
+  c->arrive = 0;
+  c->edge_bad = 0;
+  c->no_stop = 0;
+}
+
+__global__ void k_ref_setup(RefineCtl *rc, RefineParams p) {
+  RefineCtl r = {};
+  r.tol = p.tol;
+  r.tol2 = p.tol * p.tol;
+  r.inner_tol = p.inner_tol;
+  r.prec_thr = p.prec_thr;
+  r.max_refine = p.max_refine;
+  r.max_iter = p.max_iter;
+  r.inner_max = p.inner_max;
+  r.prec_cap = p.prec_cap;
+  r.status = GABP_NOT_CONVERGED;
+  r.joint_pending = p.joint;
+  r.prec_round = -1;
+  *rc = r;
+}
+
+// After a residual: stop (converged / diverged / caps) or arm the next inner solve.
+__global__ void k_ref_decide(RefineCtl *rc, const DevCtl *ctlR, DevCtl *ctl, int first,
+                             cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_joint,
+                             cudaGraphConditionalHandle h_inner) {
+  int go = 0;
+  if (!rc->skip) {
+    if (!first) rc->steps += 1;
+    const double rr = ctlR->rr, bb = ctlR->bb;
+    rc->rr = rr;
+    rc->bb = bb;
+    if (!isfinite(rr)) rc->status = GABP_DIVERGED;
+    else if (bb == 0.0 || rr <= rc->tol2 * bb) rc->status = GABP_OK;
+    else if (rc->steps >= rc->max_refine || rc->total_inner >= rc->max_iter) rc->status = GABP_NOT_CONVERGED;
+    else {
+      go = 1;
+      rc->cap = min(rc->inner_max, max(1, rc->max_iter - rc->total_inner));
+      const double it = inner_target(rc->inner_tol, rc->tol, bb, rr);
+      rc->it2 = it * it;
+      ctl_arm(ctl, 0, rc->cap, rc->it2);
+    }
+  }
+  cudaGraphSetConditional(h_outer, go);
+  cudaGraphSetConditional(h_joint, go && rc->joint_pending);
+  cudaGraphSetConditional(h_inner, go);
+}
+
+__global__ void k_joint_prep(RefineCtl *rc, DevCtl *ctl, cudaGraphConditionalHandle h_jw) {
+  ctl_arm(ctl, 0, max(1, min(rc->prec_cap, rc->cap)), rc->prec_thr);
+  cudaGraphSetConditional(h_jw, 1);
+}
+
+// After the joint rounds (and the freeze at their last round T): stop on a
+// breakdown, else continue the first inner solve's rounds from T.
+__global__ void k_joint_after(RefineCtl *rc, DevCtl *ctl, cudaGraphConditionalHandle h_inner) {
+  const int T = ctl->result_round, st = ctl->status;
+  rc->joint_pending = 0;
+  if (st == GABP_BREAKDOWN || st == GABP_DIVERGED) {
+    rc->status = st;
+    rc->skip = 1;
+    cudaGraphSetConditional(h_inner, 0);
+    return;
+  }
+  rc->prec_round = T;
+  ctl_arm(ctl, T, rc->cap, rc->it2);
+  cudaGraphSetConditional(h_inner, T < rc->cap);
+}
+
+__global__ void k_ref_after_inner(RefineCtl *rc, const DevCtl *ctl) {
+  if (rc->skip) return;
+  rc->total_inner += ctl->result_round;
+  if (ctl->status == GABP_DIVERGED) {
+    rc->status = GABP_DIVERGED;
+    rc->skip = 1;
+  }
+}
+
+// x <- x + d with d from the inner solve's final round (read on the device)
+__global__ void k64_update_ctl(int n, double *__restrict__ x, const float *NH0, const float *NH1, const float *NH2,
+                               const float *__restrict__ invP, const DevCtl *ctl, const int *skip) {
+  if (*skip) return;
+  const int m = ctl->result_round % 3;
+  const float *__restrict__ hT = m == 0 ? NH0 : (m == 1 ? NH1 : NH2);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += (double)(hT[i] * invP[i]);
+}
+
+constexpr int kLoopK = 2;  // round kernels per while-body iteration (later ones exit at once when decided)
+
+// A graph under construction: nodes are appended in sequence after `last`.
+struct SeqGraph {
+  cudaGraph_t g;
+  cudaGraphNode_t last;
+};
+
+// Append the launches `f` makes on `stream`, captured, after seq.last.
+template <typename F>
+static cudaError_t seq_capture(SeqGraph &seq, cudaStream_t stream, F &&f) {
+  cudaError_t e = cudaStreamBeginCaptureToGraph(stream, seq.g, seq.last ? &seq.last : nullptr, nullptr,
+                                                seq.last ? 1 : 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  f();
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  e = cudaStreamGetCaptureInfo(stream, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+  std::vector<cudaGraphNode_t> frontier(deps, deps + (e == cudaSuccess ? nd : 0));
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(stream, &out);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  if (frontier.size() == 1) {
+    seq.last = frontier[0];
+  } else if (frontier.size() > 1) {
+    cudaGraphNode_t join;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeEmpty;
+    e = cudaGraphAddNode(&join, seq.g, frontier.data(), nullptr, frontier.size(), &p);
+    if (e != cudaSuccess) return e;
+    seq.last = join;
+  }
+  return cudaSuccess;
+}
+
+// Append a while / if node on `handle`; returns its body as a new sequence.
+static cudaError_t seq_conditional(SeqGraph &seq, cudaGraphConditionalHandle handle, cudaGraphConditionalNodeType type,
+                                   SeqGraph *body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = handle;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddNode(&node, seq.g, seq.last ? &seq.last : nullptr, nullptr, seq.last ? 1 : 0, &p);
+  if (e != cudaSuccess) return e;
+  seq.last = node;
+  body->g = p.conditional.phGraph_out[0];
+  body->last = nullptr;
+  return cudaSuccess;
+}
+
+static gabp_status build_refine_graph(gabp_handle h, int SHm, int SHj, int LR) {
+  Graph &g = h->g;
+  Work32 &w = h->w32;
+  const size_t E = (size_t)(g.E > 0 ? g.E : 1);
+  cudaStream_t st = h->stream;
+  cudaGraph_t root;
+  GABP_CUDA(cudaGraphCreate(&root, 0));
+  struct Guard {
+    cudaGraph_t *g;
+    ~Guard() { if (*g) cudaGraphDestroy(*g); }
+  } guard{&root};
+  cudaGraphConditionalHandle h_outer, h_joint, h_jw, h_inner;
+  GABP_CUDA(cudaGraphConditionalHandleCreate(&h_outer, root, 0, cudaGraphCondAssignDefault));
+  GABP_CUDA(cudaGraphConditionalHandleCreate(&h_joint, root, 0, cudaGraphCondAssignDefault));
+  GABP_CUDA(cudaGraphConditionalHandleCreate(&h_jw, root, 0, cudaGraphCondAssignDefault));
+  GABP_CUDA(cudaGraphConditionalHandleCreate(&h_inner, root, 0, cudaGraphCondAssignDefault));
+  Args32 a = args32(h);
+  int nbr = 1;
+  GABP_DISPATCH_L(LR, nbr = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k64_residual<LL>)));
+  RefineCtl *rc = w.rc;
+  const int nb1 = (g.n + kBlock - 1) / kBlock;
+  auto residual = [&](int set_bb) {
+    GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, st>>>(g.n, g.rowptr, g.col, g.val, w.Bd, w.X, w.rhs32,
+                                                                    w.NH[0], w.ctlR, h->partials, set_bb,
+                                                                    &rc->skip)));
+  };
+  SeqGraph top{root, nullptr};
+  cudaError_t e = seq_capture(top, st, [&] {
+    cudaMemsetAsync(w.X, 0, sizeof(double) * g.n, st);
+    residual(1);
+    k_ref_decide<<<1, 1, 0, st>>>(rc, w.ctlR, h->ctl, 1, h_outer, h_joint, h_inner);
+  });
+  SeqGraph outer{}, joint{}, jw{}, inner{};
+  if (e == cudaSuccess) e = seq_conditional(top, h_outer, cudaGraphCondTypeWhile, &outer);
+  if (e == cudaSuccess)
+    e = seq_capture(outer, st, [&] { cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, st); });
+  // precision state computed together with the first inner solve
+  if (e == cudaSuccess) e = seq_conditional(outer, h_joint, cudaGraphCondTypeIf, &joint);
+  if (e == cudaSuccess)
+    e = seq_capture(joint, st, [&] {
+      cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, st);
+      cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, st);
+      k32_joint_init<<<nb1, kBlock, 0, st>>>(g.n, g.ad32, w.rhs32, w.NQ[0], w.NP[0]);
+      k_joint_prep<<<1, 1, 0, st>>>(rc, h->ctl, h_jw);
+    });
+  if (e == cudaSuccess) e = seq_conditional(joint, h_jw, cudaGraphCondTypeWhile, &jw);
+  if (e == cudaSuccess)
+    e = seq_capture(jw, st, [&] {
+      Args32 aj = a;
+      aj.cond = h_jw;
+      aj.use_cond = 1;
+      with_shape(SHj, [&](auto Lc, auto Uc) {
+        constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+        const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_joint<LL, UU>));
+        for (int k = 0; k < kLoopK; ++k) k32_joint<LL, UU><<<nb, kBlock, 0, st>>>(aj);
+      });
+    });
+  if (e == cudaSuccess)
+    e = seq_capture(joint, st, [&] {
+      const int Lc = SHj & 0xff;
+      GABP_DISPATCH_L(Lc, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)),
+                                          kBlock, 0, st>>>(a, 0, h->ctl)));
+      k_joint_after<<<1, 1, 0, st>>>(rc, h->ctl, h_inner);
+    });
+  // the inner solve's frozen-coefficient rounds
+  if (e == cudaSuccess) e = seq_conditional(outer, h_inner, cudaGraphCondTypeWhile, &inner);
+  if (e == cudaSuccess)
+    e = seq_capture(inner, st, [&] {
+      Args32 am = a;
+      am.cond = h_inner;
+      am.use_cond = 1;
+      with_shape(SHm, [&](auto Lc, auto Uc) {
+        constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+        const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
+        for (int k = 0; k < kLoopK; ++k) k32_mean<LL, UU><<<nb, kBlock, 0, st>>>(am);
+      });
+    });
+  if (e == cudaSuccess)
+    e = seq_capture(outer, st, [&] {
+      k_ref_after_inner<<<1, 1, 0, st>>>(rc, h->ctl);
+      k64_update_ctl<<<nb1, kBlock, 0, st>>>(g.n, w.X, w.NH[0], w.NH[1], w.NH[2], w.invP, h->ctl, &rc->skip);
+      residual(0);
+      k_ref_decide<<<1, 1, 0, st>>>(rc, w.ctlR, h->ctl, 0, h_outer, h_joint, h_inner);
+    });
+  if (e != cudaSuccess) return cuda_fail(e, "build the refinement-loop graph");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, root, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "instantiate the refinement-loop graph");
+  if (h->gRef) cudaGraphExecDestroy(h->gRef);
+  if (h->gRefG) cudaGraphDestroy(h->gRefG);
+  h->gRef = exec;
+  h->gRefG = root;
+  root = nullptr;
+  return GABP_OK;
+}
+
+// solve32_refine for one right-hand side without loading, as one graph launch.
+static gabp_status solve32_device_loop(gabp_handle h, const double *B, double *X, double tol, int max_iter,
+                                       int *iters, double *relres) {
+  Work32 &w = h->w32;
+  Graph &g = h->g;
+  if (!w.rc) {
+    GABP_CUDA(cudaMalloc(&w.rc, sizeof(RefineCtl)));
+    GABP_CUDA(cudaMallocHost(&w.rc_host, sizeof(RefineCtl)));
+    GABP_CUDA(cudaMalloc(&w.Bd, sizeof(double) * (size_t)g.n));
+  }
+  const bool joint = !w.coef_ready || !h->opt.reuse_precisions;
+  if (joint) {
+    w.coef_ready = false;
+    if (!h->opt.overlap_precision) {
+      gabp_status s = precision_phase32(h, nullptr);
+      if (s != GABP_OK) return s;
+    } else {
+      k_diag32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad, nullptr, g.ad32);
+      GABP_CUDA(cudaGetLastError());
+      if (!h->opt.lanes && !h->tuned_Lj32) {
+        // the autotuner runs a few joint rounds on scratch state (re-initialised by the graph)
+        const size_t E = (size_t)(g.E > 0 ? g.E : 1);
+        GABP_CUDA(cudaMemsetAsync(w.rhs32, 0, sizeof(float) * g.n, h->stream));
+        GABP_CUDA(cudaMemsetAsync(w.MP[0], 0, sizeof(float) * E, h->stream));
+        GABP_CUDA(cudaMemsetAsync(w.MP[1], 0, sizeof(float) * E, h->stream));
+        GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
+        k32_joint_init<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.ad32, w.rhs32, w.NQ[0], w.NP[0]);
+        gabp_status s = autotune32(h, K32_JOINT);
+        if (s != GABP_OK) return s;
+      }
+    }
+  }
+  const bool run_joint = joint && h->opt.overlap_precision;
+  gabp_status s = autotune32(h, K32_MEAN);
+  if (s != GABP_OK) return s;
+  const int SHm = shape32(h, K32_MEAN), SHj = shape32(h, K32_JOINT);
+  const int LR = h->opt.lanes ? h->opt.lanes : (g.avg_deg >= 12.0 ? 2 : 1);
+  const long long key = (long long)SHm | ((long long)SHj << 16) | ((long long)LR << 32);
+  if (!h->gRef || h->gRef_key != key) {
+    if ((s = build_refine_graph(h, SHm, SHj, LR)) != GABP_OK) return s;
+    h->gRef_key = key;
+  }
+  RefineParams p;
+  p.tol = tol;
+  p.inner_tol = h->opt.inner_tol;
+  p.prec_thr = std::ldexp(1.0, -h->opt.prec_stop_log2);
+  p.max_refine = h->opt.max_refine;
+  p.max_iter = max_iter;
+  p.inner_max = h->opt.inner_max_iter;
+  p.prec_cap = kPrecMaxRounds;
+  p.joint = run_joint ? 1 : 0;
+  GABP_CUDA(cudaMemcpyAsync(w.Bd, B, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  k_ref_setup<<<1, 1, 0, h->stream>>>(w.rc, p);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaGraphLaunch(h->gRef, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(X, w.X, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(w.rc_host, w.rc, sizeof(RefineCtl), cudaMemcpyDeviceToHost, h->stream));
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  const RefineCtl r = *w.rc_host;
+  h->prof.launches += 4 + 2 * (int64_t)r.total_inner + 4 * (int64_t)r.steps;
+  if (run_joint) {
+    if (r.prec_round >= 0) {
+      w.prec_round = r.prec_round;
+      w.coef_ready = true;
+    } else if (r.status != GABP_BREAKDOWN && r.status != GABP_DIVERGED) {
+      // stopped before any inner solve (b = 0): the precision state is still provided
+      if ((s = precision_phase32(h, nullptr)) != GABP_OK) return s;
+    }
+  }
+  h->stats.rounds += r.total_inner;
+  h->stats.refine_steps = r.steps;
+  if (iters) *iters = r.total_inner;
+  if (relres) *relres = r.bb > 0.0 ? sqrt(r.rr / r.bb) : 0.0;
+  return (gabp_status)r.status;
+}
+
 gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int64_t ld, double tol,
                            int max_iter, const double *gamma_diag, int *iters, double *relres) {
   if (R != 1) return GABP_ERR_INVALID;  // batched path: gabp_solve_batched
@@ -761,6 +1133,8 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   h->stats.rounds = 0;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
+  if (h->opt.device_loop && !gamma_diag && !h->opt.profile && h->stream)
+    return solve32_device_loop(h, B, X, tol, max_iter, iters, relres);
   // the precision state is cached per handle when no loading is applied; when it
   // has to be computed, it is either computed first (precision-only rounds) or
   // together with the first inner solve (joint rounds, overlap_precision)

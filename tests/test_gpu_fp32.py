@@ -58,6 +58,53 @@ def test_refined_matches_fp64_oracle(gb, make, overlap):
 
 
 @pytest.mark.parametrize("overlap", [0, 1])
+@pytest.mark.parametrize("make", [
+    lambda: synth.random_sym(20011, 8, 1.1, 2),
+    lambda: synth.grid3d(16, 1.05, 3),
+])
+def test_device_loop_equals_host_loop(gb, make, overlap):
+    """The refinement loop run as one CUDA graph with conditional nodes takes the same
+    decisions on the same kernels as the host-driven loop: bitwise the same x, the same
+    round and step counts (kernel shapes fixed, so that no autotuner choice differs)."""
+    m = make()
+    b = synth.rhs(m.n, 8)
+    outs = [_solve(gb, m, b, 1e-11, precision=gb.GABP_PREC_FP32_REFINE, overlap_precision=overlap, device_loop=d,
+                   lanes=4) for d in (0, 1)]
+    for o in outs:
+        assert o["status"] == gb.GABP_OK and o["relres"] <= 1e-11
+    assert np.array_equal(outs[0]["x"], outs[1]["x"])
+    assert np.array_equal(outs[0]["P"], outs[1]["P"])
+    assert outs[0]["iters"] == outs[1]["iters"]
+    assert outs[0]["stats"]["refine_steps"] == outs[1]["stats"]["refine_steps"]
+
+
+def test_device_loop_repeated_and_zero_rhs(gb):
+    """One handle, the cached graph relaunched: reused precisions, a new right-hand side,
+    b = 0 (x = 0 at once, precisions still available), and a max_iter cap."""
+    m = synth.random_sym(4099, 8, 1.1, 9)
+    s = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE)
+    ref = oracle.dense_solve(oracle.to_dense(m), synth.rhs(m.n, 1))
+    for seed in (1, 2, 1):
+        b = synth.rhs(m.n, seed)
+        x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-10)
+        assert st == gb.GABP_OK and rel <= 1e-10
+        if seed == 1:
+            assert _relerr(x.cpu().numpy(), ref) <= 1e-8
+    x, st, it, rel = s.solve(torch.zeros(m.n, dtype=torch.float64, device="cuda"), tol=1e-10)
+    assert st == gb.GABP_OK and it == 0 and not torch.any(x)
+    x, st, it, rel = s.solve(torch.from_numpy(synth.rhs(m.n, 3)).cuda(), tol=1e-14, max_iter=5)
+    assert st == gb.GABP_NOT_CONVERGED and it <= 5  # the cap bounds the inner rounds
+    s.close()
+    z = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE)
+    x, st, it, rel = z.solve(torch.zeros(m.n, dtype=torch.float64, device="cuda"), tol=1e-10)
+    assert st == gb.GABP_OK and it == 0
+    P = z.marginal_precisions().cpu().numpy()
+    r = oracle.gabp_broadcast(m, synth.rhs(m.n, 1), max_iter=5000, tol=1e-13)
+    assert np.allclose(P, r["P"], rtol=1e-3)
+    z.close()
+
+
+@pytest.mark.parametrize("overlap", [0, 1])
 def test_unrefined_within_1e5(gb, overlap):
     """One inner solve, no refinement: FP32 GaBP run to its fixed point (with overlap 1 its
     first rounds are joint precision + mean rounds) is within 1e-5 of the FP64 oracle."""
