@@ -1,8 +1,9 @@
 """Benchmark: GaBP edge-updates/s on the random sparse symmetric workload (n = 2^20).
 
 One step = one complete solve of A x = b to relative residual 1e-10 through the
-C ABI: FP32 precision phase, frozen coefficients, FP32 mean rounds and FP64
-iterative refinement (the precision phase is re-run every step, nothing is
+C ABI: FP32 joint rounds (precision and mean messages together until the
+precisions are stationary), frozen coefficients, FP32 mean rounds and FP64
+iterative refinement (the precision state is recomputed every step, nothing is
 cached between steps).  value = directed edges x rounds of all steps / device
 time.  The plain FP64 GaBP solve of the same system is timed beside it.
 
@@ -243,11 +244,12 @@ def main():
     ph = max(("mean32", "prec32"), key=lambda k: prof["ms"][k])
     n = m.n
     # algorithmic bytes per launch: mean round 20 B/slot (c_in,c_out 8, col 4, h read 4, h write 4)
-    # + 24 B/node; precision round 20 B/slot (A 4, col 4, P read 4, previous-round P 4, P write 4) + 16 B/node
-    bytes_launch = (20 * E + 24 * n) if ph == "mean32" else (20 * E + 16 * n)
+    # + 24 B/node; joint round (the "prec32" phase of a solve with overlap_precision) 28 B/slot (A 4,
+    # col 4, P read 4, previous-round P 4, h read 4, P and h writes 8) + 36 B/node
+    bytes_launch = (20 * E + 24 * n) if ph == "mean32" else (28 * E + 36 * n)
     dur_ms = prof["ms"][ph] / max(prof["rounds"][ph], 1)
     achieved = bytes_launch / (dur_ms / 1e3) / 1e9
-    kname = "k32_mean" if ph == "mean32" else "k32_prec"
+    kname = "k32_mean" if ph == "mean32" else "k32_joint"
 
     legs = set(args.legs.split(","))
     ms64, r64, k64, p64 = None, 0, 1, {"ms": {"fp64": 0.0}}
@@ -269,18 +271,24 @@ def main():
         p64 = s64.profile(reset=True)
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    # (default options: the refinement loop runs as one CUDA graph, no per-phase timing events)
     e2e_rounds, e2e_s = 0, None
     if "e2e" in legs:
+        se = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes)
         bh = torch.from_numpy(b).pin_memory().numpy()
         xh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
-        s32.solve_host(bh, xh, tol=TOL, max_iter=2000)
+        for _ in range(max(1, args.warmup)):
+            se.solve_host(bh, xh, tol=TOL, max_iter=2000)
         barrier()
         t1 = time.perf_counter()
         for _ in range(args.steps):
-            st, it, rr = s32.solve_host(bh, xh, tol=TOL, max_iter=2000)
-            e2e_rounds += s32.stats()["rounds"]
+            st, it, rr = se.solve_host(bh, xh, tol=TOL, max_iter=2000)
+            if st != gb.GABP_OK:
+                raise RuntimeError(f"e2e solve status {st}")
+            e2e_rounds += se.stats()["rounds"]
         barrier()
         e2e_s = time.perf_counter() - t1
+        se.close()
 
     # ---- batched: 128^3 heterogeneous diffusion grid, 64 right-hand sides in one launch sequence
     batched = None
@@ -358,26 +366,41 @@ def main():
         xs_t = torch.from_numpy(synth.rhs(mc.n, 105)).to(dev)
         b_c = synth.rhs(mc.n, 5 + rank)
 
-        def fwd_bwd():
-            vals = torch.from_numpy(mc.val).to(dev).requires_grad_(True)
-            bt = torch.from_numpy(b_c).to(dev).requires_grad_(True)
-            xg = ga.gabp_solve_autograd(rp_t, cl_t, vals, bt, tol=TOL)
+        vals0 = torch.from_numpy(mc.val).to(dev)
+        b0 = torch.from_numpy(b_c).to(dev)
+
+        def fwd_bwd(solver=None):
+            vals = vals0.detach().clone().requires_grad_(True)
+            bt = b0.detach().clone().requires_grad_(True)
+            xg = ga.gabp_solve_autograd(rp_t, cl_t, vals, bt, tol=TOL, solver=solver)
             loss = 0.5 * torch.sum((xg - xs_t) ** 2)
             loss.backward()
             return vals.grad, bt.grad
 
-        fwd_bwd()
-        barrier()
-        eg0, eg1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        eg0.record()
-        fwd_bwd()
-        eg1.record()
-        barrier()
+        def timed(f, reps=3):
+            f()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f()
+            e1.record()
+            barrier()
+            return e0.elapsed_time(e1) / reps
+
+        ms_fresh = timed(fwd_bwd)
+        shared = gb.Solver(mc.n, rp_t, cl_t, vals0, precision=gb.GABP_PREC_FP32_REFINE)
+        ms_shared = timed(lambda: fwd_bwd(shared))
+        shared.close()
         grad = {"workload": "random sparse symmetric A, n=2^22, 3 picks per row (degree ~6), U(-1,1), diagonal "
                             "1.2 x row abs-sum; loss 0.5||x - x*||^2; FP32 messages + FP64 refinement",
-                "n": mc.n, "edges": mc.num_edges, "ms_forward_backward": eg0.elapsed_time(eg1),
-                "includes": "handle creation (validation, reverse index), forward solve, adjoint solve on the "
-                            "same precision state, dL/dA and dL/db"}
+                "n": mc.n, "edges": mc.num_edges, "ms_forward_backward": ms_fresh,
+                "includes": "handle creation (validation, reverse index), forward solve (precision state "
+                            "recomputed), adjoint solve on the same precision state, dL/dA and dL/db; inputs "
+                            "already on the device",
+                "ms_forward_backward_shared_solver": ms_shared,
+                "shared_solver": "one handle for the pattern, new values set each step (gabp_set_values) "
+                                 "instead of a new handle"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

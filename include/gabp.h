@@ -129,6 +129,16 @@ gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t 
                         const int32_t *col, const double *val, int mem_space, void *stream,
                         const gabp_options *opt);
 
+/* New values for the same sparsity pattern (the full symmetric CSR values in
+ * the order of the rowptr/col given to gabp_create, host (mem_space 0) or
+ * device (1)), e.g. the matrix of a learning step.  The reverse-edge index,
+ * the layout and the autotuner's choices are kept; the precision state is
+ * recomputed by the next solve (eq_prec depends on A only, Section 2.2).
+ * Checked like gabp_create's values (finite, nonzero diagonal and
+ * off-diagonals, A_ij == A_ji bit for bit); on GABP_ERR_INVALID the handle
+ * holds no valid matrix and every solve fails until a valid call. */
+gabp_status gabp_set_values(gabp_handle h, const double *val, int mem_space);
+
 /* Replace the handle's options (validated) / stream. */
 gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt);
 gabp_status gabp_set_stream(gabp_handle h, void *stream);
@@ -258,7 +268,9 @@ gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, co
  * nullable): the FP64 round's lanes per row; the FP32 precision and mean
  * rounds' shapes, packed as lanes | unroll << 8; the multi-system size split;
  * the multi-system kernel (1 grid-persistent, 2 teams) | the grid-persistent
- * kernel's shape << 8. */
+ * kernel's shape << 8.  The FP64 and FP32 choices are remembered for the
+ * process per (device, n, directed-edge count): a later handle of a matrix of
+ * that size starts with them instead of tuning again. */
 gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int32_t *prec32_shape, int32_t *mean32_shape,
                               int64_t *multi_split, int32_t *multi_mode);
 

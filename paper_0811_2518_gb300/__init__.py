@@ -19,7 +19,7 @@ __all__ = [
     "GABP_ERR_INVALID", "GABP_ERR_CUDA", "GABP_ERR_NOMEM",
     "GABP_PREC_FP64", "GABP_PREC_FP32_REFINE", "GABP_VARIANT_NODE", "GABP_VARIANT_EDGE",
     "Options", "lib", "library_path", "exported_symbols",
-    "gabp_options_default", "gabp_create", "gabp_set_options", "gabp_set_stream", "gabp_solve",
+    "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
     "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
@@ -68,6 +68,7 @@ _SIGNATURES = {
     "gabp_options_default": ([ctypes.POINTER(Options)], ctypes.c_int),
     "gabp_create": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64, _P, _P, _P, ctypes.c_int, _P,
                      ctypes.POINTER(Options)], ctypes.c_int),
+    "gabp_set_values": ([_P, _P, ctypes.c_int], ctypes.c_int),
     "gabp_set_options": ([_P, ctypes.POINTER(Options)], ctypes.c_int),
     "gabp_set_stream": ([_P, _P], ctypes.c_int),
     "gabp_solve": ([_P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
@@ -137,6 +138,11 @@ def gabp_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, mem_space, stream_ptr, opt
     st = lib.gabp_create(ctypes.byref(h), int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
                          int(mem_space), _P(stream_ptr), ctypes.byref(options) if options is not None else None)
     return st, h
+
+
+def gabp_set_values(h, val_ptr, mem_space):
+    """New values on the handle's sparsity pattern (pointer to nnz doubles; mem_space 0 host, 1 device)."""
+    return lib.gabp_set_values(h, val_ptr, mem_space)
 
 
 def gabp_set_options(h, options):
@@ -280,6 +286,22 @@ class Solver:
     @classmethod
     def from_csr(cls, m, **kw):
         return cls(m.n, m.rowptr, m.col, m.val, **kw)
+
+    def set_values(self, val):
+        """New values (full CSR order, diagonal included) on the same pattern: a numpy array or a
+        CUDA float64 tensor.  Raises GaBPError (and leaves the solver unusable) if they are invalid."""
+        import numpy as np
+        import torch
+
+        if isinstance(val, torch.Tensor):
+            v = val.detach().to(self.device, torch.float64).contiguous()
+            st = gabp_set_values(self.handle, v.data_ptr(), 1)
+        else:
+            v = np.ascontiguousarray(val, dtype=np.float64)
+            st = gabp_set_values(self.handle, v.ctypes.data, 0)
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_set_values")
+        self.values_version = getattr(self, "values_version", 0) + 1
 
     def set_options(self, **opts):
         for k, v in opts.items():

@@ -14,6 +14,11 @@ refinement).  Backward, for an upstream gradient g = dL/dx:
 
 With ``save_x=False`` the forward result is not kept for backward; x is
 recomputed by a third solve (the memory-saving mode for large batches).
+
+``solver``: a Solver created once for the sparsity pattern and reused across
+calls (a training loop whose parameters are A's values): the forward sets the
+new values on it (gabp_set_values) instead of building a handle, and the
+backward puts them back first if another forward changed them meanwhile.
 """
 from __future__ import annotations
 
@@ -26,12 +31,19 @@ __all__ = ["GaBPSolve", "gabp_solve_autograd"]
 
 class GaBPSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, vals, b, rowptr, col, tol, max_iter, precision, save_x):
+    def forward(ctx, vals, b, rowptr, col, tol, max_iter, precision, save_x, solver=None):
         n = b.shape[0]
-        solver = Solver(n, rowptr, col, vals.detach(), precision=precision, reuse_precisions=1)
+        ctx.own = solver is None
+        if ctx.own:
+            solver = Solver(n, rowptr, col, vals.detach(), precision=precision, reuse_precisions=1)
+        else:
+            solver.set_values(vals)
+            ctx.vals = vals.detach()
+            ctx.version = solver.values_version
         x, st, it, rel = solver.solve(b.detach(), tol=tol, max_iter=max_iter)
         if st != GABP_OK:
-            solver.close()
+            if ctx.own:
+                solver.close()
             raise GaBPError(st, "GaBPSolve.forward")
         ctx.solver = solver
         ctx.tol, ctx.max_iter, ctx.save_x = tol, max_iter, save_x
@@ -44,6 +56,8 @@ class GaBPSolve(torch.autograd.Function):
     def backward(ctx, gx):
         solver = ctx.solver
         try:
+            if not ctx.own and solver.values_version != ctx.version:
+                solver.set_values(ctx.vals)  # another forward used the solver since
             gx = gx.contiguous().to(torch.float64)
             lam, st, it, rel = solver.solve(gx, tol=ctx.tol, max_iter=ctx.max_iter)
             if st != GABP_OK:
@@ -56,15 +70,18 @@ class GaBPSolve(torch.autograd.Function):
             gvals = solver.grad_values(lam, x) if ctx.needs_input_grad[0] else None
             gb = lam if ctx.needs_input_grad[1] else None
         finally:
-            solver.close()
+            if ctx.own:
+                solver.close()
             ctx.solver = None
             ctx.x = None
-        return gvals, gb, None, None, None, None, None, None
+            ctx.vals = None
+        return gvals, gb, None, None, None, None, None, None, None
 
 
 def gabp_solve_autograd(rowptr, col, vals, b, tol=1e-10, max_iter=5000, precision=GABP_PREC_FP32_REFINE,
-                        save_x=True):
+                        save_x=True, solver=None):
     """x = A^{-1} b, differentiable in ``vals`` (the full symmetric CSR values,
     diagonal included) and ``b``.  ``rowptr``/``col`` are int32 CUDA tensors,
-    ``vals``/``b`` float64 CUDA tensors."""
-    return GaBPSolve.apply(vals, b, rowptr, col, tol, max_iter, precision, save_x)
+    ``vals``/``b`` float64 CUDA tensors; ``solver`` an optional Solver of the
+    same pattern reused across calls."""
+    return GaBPSolve.apply(vals, b, rowptr, col, tol, max_iter, precision, save_x, solver)

@@ -17,9 +17,16 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// a handle whose last gabp_set_values was rejected holds no valid matrix
+bool values_usable(gabp_handle h) {
+  if (h->values_ok) return true;
+  set_last_error("the handle's values were rejected by gabp_set_values; set valid values first");
+  return false;
+}
+
 gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                            int32_t *iters_out, double *relres_out) {
-  if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || !values_usable(h)) return GABP_ERR_INVALID;
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
@@ -81,7 +88,8 @@ extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x
 
 extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const double *B, double *X, int64_t ld,
                                           double tol, int32_t max_iter, int32_t *iters_out, double *relres_out) {
-  if (!h || !B || !X || nrhs < 1 || ld < h->g.n || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  if (!h || !B || !X || nrhs < 1 || ld < h->g.n || !(tol >= 0.0) || max_iter < 0 || !values_usable(h))
+    return GABP_ERR_INVALID;
   if (!is_device_ptr(B) || !is_device_ptr(X)) {
     set_last_error("gabp_solve_batched: B and X must be device arrays");
     return GABP_ERR_INVALID;
@@ -109,7 +117,7 @@ extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
 }
 
 extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val) {
-  if (!h || !lambda || !x || !grad_val) return GABP_ERR_INVALID;
+  if (!h || !lambda || !x || !grad_val || !values_usable(h)) return GABP_ERR_INVALID;
   return grad_values(h, lambda, x, grad_val);
 }
 
@@ -127,7 +135,8 @@ extern "C" gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *
 extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offsets, const double *b,
                                           double *x, double tol, int32_t max_iter, int32_t *status_out,
                                           int32_t *iters_out, double *relres_out) {
-  if (!h || !offsets || !b || !x || nsys < 1 || !(tol >= 0.0) || max_iter < 0) return GABP_ERR_INVALID;
+  if (!h || !offsets || !b || !x || nsys < 1 || !(tol >= 0.0) || max_iter < 0 || !values_usable(h))
+    return GABP_ERR_INVALID;
   if (!is_device_ptr(b) || !is_device_ptr(x)) {
     set_last_error("gabp_solve_systems: b and x must be device arrays");
     return GABP_ERR_INVALID;

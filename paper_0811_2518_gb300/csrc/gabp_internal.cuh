@@ -150,6 +150,7 @@ struct gabp_handle_s {
   gabp::WorkB *wb = nullptr;
   long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
   int multi_nt = 0;                 // autotuned block size of the multi-system kernel
+  bool values_ok = true;            // false after a rejected gabp_set_values
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
 };
@@ -293,6 +294,11 @@ inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_
 
 
 // shared host helpers (defined in setup.cu / solve64.cu / solve32.cu)
+// Process-wide memory of the autotuner's kernel shapes, keyed by (device, n,
+// directed edges): a handle created for a matrix of the same size (typically the
+// same pattern with new values, e.g. one handle per training step) starts tuned.
+void tune_cache_load(gabp_handle h);
+void tune_cache_store(gabp_handle h);
 gabp_status ensure_w64(gabp_handle h);
 void free_w64(gabp_handle h);
 gabp_status ensure_w32(gabp_handle h, int R);

@@ -11,7 +11,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 namespace gabp {
 
@@ -93,6 +96,17 @@ __global__ void k_compact(int n, const int *__restrict__ rowptr, const int *__re
     ci[e] = col[a + q];
     av[e] = val[a + q];
   }
+}
+
+// New values on the existing pattern: A_ik == A_ki bit for bit through rev[].
+__global__ void k_values_to_f32(int64_t E, const double *__restrict__ s, float *__restrict__ d) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < E) d[e] = (float)s[e];
+}
+
+__global__ void k_check_sym(int64_t E, const double *__restrict__ av, const int *__restrict__ rev, int *flag) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < E && __double_as_longlong(av[e]) != __double_as_longlong(av[rev[e]])) atomicOr(flag, (int)BAD_VALUE);
 }
 
 // rev[e] for slot e = (row i, column k): binary search of i among row k's columns.
@@ -292,6 +306,33 @@ static gabp_status check_options(const gabp_options *o) {
   return GABP_OK;
 }
 
+namespace {
+struct TunedShapes {
+  int L64 = 0, Lp32 = 0, Lm32 = 0, Lj32 = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int64_t>, TunedShapes> g_tune;
+}  // namespace
+
+void gabp::tune_cache_load(gabp_handle h) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(h->device, h->g.n, (int64_t)h->g.E));
+  if (it == g_tune.end()) return;
+  h->tuned_L64 = it->second.L64;
+  h->tuned_Lp32 = it->second.Lp32;
+  h->tuned_Lm32 = it->second.Lm32;
+  h->tuned_Lj32 = it->second.Lj32;
+}
+
+void gabp::tune_cache_store(gabp_handle h) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TunedShapes &t = g_tune[std::make_tuple(h->device, h->g.n, (int64_t)h->g.E)];
+  if (h->tuned_L64) t.L64 = h->tuned_L64;
+  if (h->tuned_Lp32) t.Lp32 = h->tuned_Lp32;
+  if (h->tuned_Lm32) t.Lm32 = h->tuned_Lm32;
+  if (h->tuned_Lj32) t.Lj32 = h->tuned_Lj32;
+}
+
 extern "C" gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t *rowptr,
                                    const int32_t *col, const double *val, int mem_space, void *stream,
                                    const gabp_options *opt) {
@@ -337,7 +378,57 @@ extern "C" gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, con
     destroy_impl(h);
     return s;
   }
+  tune_cache_load(h);
   *out = h;
+  return GABP_OK;
+}
+
+extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem_space) {
+  if (!h || !val || (mem_space != 0 && mem_space != 1)) return GABP_ERR_INVALID;
+  Graph &g = h->g;
+  h->values_ok = false;  // until the new values pass every check
+  h->last_path = -1;     // marginals / messages of the old values are gone
+  h->w32.coef_ready = false;
+  h->w32.prec_round = -1;
+  int *dflag = nullptr;
+  GABP_CUDA(cudaMalloc(&dflag, sizeof(int)));
+  struct F {
+    int *p;
+    ~F() { cudaFree(p); }
+  } fr{dflag};
+  int hflag = 0;
+  auto read_flag = [&]() -> gabp_status {
+    cudaError_t e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "validation read-back");
+    return GABP_OK;
+  };
+  GABP_CUDA(cudaMemcpyAsync(g.val, val, sizeof(double) * g.nnz,
+                            mem_space == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+  GABP_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), h->stream));
+  const int nb = (g.n + kBlock - 1) / kBlock;
+  k_check_rows<<<nb, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, g.dpos, dflag);
+  gabp_status s = read_flag();
+  if (s != GABP_OK) return s;
+  if (hflag) {
+    set_last_error(hflag & BAD_DIAG ? "gabp_set_values: a diagonal entry is zero or non-finite"
+                                    : "gabp_set_values: zero or non-finite off-diagonal entry");
+    return GABP_ERR_INVALID;
+  }
+  k_compact<<<(g.n + 1 + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, g.dpos, g.rp,
+                                                                        g.ci, g.av, g.ad);
+  if (g.E > 0)
+    k_check_sym<<<(int)(((int64_t)g.E + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(g.E, g.av, g.rev, dflag);
+  if ((s = read_flag()) != GABP_OK) return s;
+  if (hflag) {
+    set_last_error("gabp_set_values: A_ij != A_ji");
+    return GABP_ERR_INVALID;
+  }
+  if (g.av32 && g.E > 0) {
+    k_values_to_f32<<<(int)(((int64_t)g.E + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(g.E, g.av, g.av32);
+    GABP_CUDA(cudaGetLastError());
+  }
+  h->values_ok = true;
   return GABP_OK;
 }
 

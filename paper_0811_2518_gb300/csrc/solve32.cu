@@ -667,6 +667,7 @@ static gabp_status autotune32(gabp_handle h, int kind) {
   }
   GABP_CUDA(cudaGetLastError());
   tuned32(h, kind) = bestS;
+  tune_cache_store(h);
   return GABP_OK;
 }
 

@@ -374,6 +374,7 @@ static gabp_status autotune64(gabp_handle h, const double *b) {
   }
   GABP_CUDA(cudaGetLastError());
   h->tuned_L64 = bestL;
+  tune_cache_store(h);
   return GABP_OK;
 }
 

@@ -130,3 +130,69 @@ def test_full_size_gradient_properties(ag):
     want = np.where(i == j, -lam[i] * x[i], -0.5 * (lam[i] * x[j] + lam[j] * x[i]))
     scale = np.abs(lam[i] * x[j]) + np.abs(lam[j] * x[i])  # rounding of the two products and the sum
     assert np.all(np.abs(gv[idx] - want) <= 1e-15 * scale + 1e-300)
+
+
+def test_shared_solver_training_loop(ag):
+    """One Solver reused across steps whose parameters are A's values (gabp_set_values): each
+    step's gradients equal those of a fresh handle, also when a second forward changes the
+    values before the first backward runs (the backward puts its values back)."""
+    gb, autograd = ag
+    m, b, xs = _setup(n=2048, seed=7)
+    rp = torch.from_numpy(m.rowptr).cuda()
+    cl = torch.from_numpy(m.col).cuda()
+    xst = torch.from_numpy(xs).cuda()
+    shared = gb.Solver(m.n, rp, cl, torch.from_numpy(m.val).cuda(), precision=1)
+    rng = np.random.default_rng(3)
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    vals_steps = []
+    for step in range(3):
+        v = m.val.copy()
+        off = rows != m.col
+        v[off] *= 1.0 + 0.05 * step  # stays symmetric: the same factor on (i,j) and (j,i)
+        v[~off] *= 1.0 + 0.08 * step + 0.01 * rng.random()
+        vals_steps.append(v)
+
+    def run(v, solver):
+        vt = torch.from_numpy(v).cuda().requires_grad_(True)
+        bt = torch.from_numpy(b).cuda().requires_grad_(True)
+        x = autograd.gabp_solve_autograd(rp, cl, vt, bt, tol=1e-12, solver=solver)
+        return vt, bt, 0.5 * torch.sum((x - xst) ** 2)
+
+    for v in vals_steps:
+        vt, bt, loss = run(v, shared)
+        loss.backward()
+        vf, bf, lf = run(v, None)
+        lf.backward()
+        assert torch.allclose(vt.grad, vf.grad, rtol=1e-9, atol=1e-14)
+        assert torch.allclose(bt.grad, bf.grad, rtol=1e-9, atol=1e-14)
+    # interleaved: forward(v0), forward(v2), backward(v0), backward(v2)
+    v0t, b0t, l0 = run(vals_steps[0], shared)
+    v2t, b2t, l2 = run(vals_steps[2], shared)
+    l0.backward()
+    l2.backward()
+    for v, vt in ((vals_steps[0], v0t), (vals_steps[2], v2t)):
+        A = oracle.to_dense(synth.CSR(m.n, m.rowptr, m.col, v, {}))
+        x0, lam, G = oracle.dense_gradient(A, b, xs)
+        assert _relerr(vt.grad.cpu().numpy(), G[np.repeat(np.arange(m.n), np.diff(m.rowptr)), m.col]) <= 1e-8
+    shared.close()
+
+
+def test_set_values_rejects_and_recovers(ag):
+    gb, _ = ag
+    m = synth.random_sym(512, 3, 1.2, 4)
+    s = gb.Solver.from_csr(m, precision=1)
+    b = torch.from_numpy(synth.rhs(m.n, 1)).cuda()
+    bad = m.val.copy()
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    p = int(np.flatnonzero(rows != m.col)[0])
+    bad[p] *= 1.5  # A_ij != A_ji
+    with pytest.raises(gb.GaBPError):
+        s.set_values(bad)
+    x, st, it, rel = s.solve(b, tol=1e-10, check=False)
+    assert st == gb.GABP_ERR_INVALID
+    s.set_values(m.val)
+    x, st, it, rel = s.solve(b, tol=1e-10)
+    assert st == gb.GABP_OK
+    ref = oracle.dense_solve(oracle.to_dense(m), synth.rhs(m.n, 1))
+    assert _relerr(x.cpu().numpy(), ref) <= 1e-8
+    s.close()
