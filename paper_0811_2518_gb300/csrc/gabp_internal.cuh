@@ -43,7 +43,7 @@ struct DevCtl {
   double bb;         // ||b||^2
   double tol2bb;     // tol^2 ||b||^2
   double rr;         // squared residual (or squared update) of the latest checked iterate
-  double maxrel;     // max relative change of the precision messages in the latest round
+  double maxrel;     // FP32 precision rounds: messages that moved by more than 2^-s in the latest round
   double xx;         // squared norm of the latest iterate (FP32 inner solves)
   unsigned int arrive;
   int edge_bad;      // breakdown flag raised by an edge kernel, consumed by the round's last block

@@ -90,9 +90,13 @@ __device__ __forceinline__ float2 *ring3(float2 *a, float2 *b, float2 *c, int t)
 
 // ---------------------------------------------------------------------------- precision phase
 // Round t of the precision-only iteration (eq_prec + eq_prec_message, Algorithm 2),
-// recompute form.  The run stops once max |P^(t) - P^(t-1)| / |P^(t)| <= 2^-s
-// (s = options.prec_stop_log2, default 16; kept in ctl->tol2bb)
-// in two consecutive rounds, on a zero cavity, or at max_iter.
+// recompute form.  The run stops once every message has |P^(t) - P^(t-1)| <=
+// 2^-s |P^(t)| (s = options.prec_stop_log2, default 16; kept in ctl->tol2bb)
+// in two consecutive rounds, on a zero cavity, or at max_iter; a non-finite
+// message after round 1 stops it as diverged.  The reciprocals use the fast
+// FP32 division (__fdividef, about 2 ulp): the FP32 precision state only has to
+// be FP32-accurate, the FP64 refinement absorbs what the frozen coefficients are
+// off by (|divisor| >= 2^126 would give 0; such precisions are outside FP32's use).
 // FP32 rounding keeps some messages moving by a few ulp forever, so an exact
 // stationary point is not waited for: the outer FP64 refinement absorbs what
 // the frozen coefficients are off by.
@@ -110,8 +114,8 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  float rel = 0.f;
-  int bad = 0;
+  const float thr = (float)ctl->tol2bb;  // 2^-prec_stop_log2
+  int bad = 0, moving = 0, nonfinite = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     float acc = 0.f;
@@ -139,14 +143,15 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
             if (t >= 2) {
               const float d1 = Pi2 - Ps[u];
               bad |= (d1 == 0.f);
-              Pout = -A2 / d1;
+              Pout = -A2 * __fdividef(1.f, d1);
             }
             const float d2 = Pk[u] - Pout;
             bad |= (d2 == 0.f);
-            const float Pn = -A2 / d2;
+            const float Pn = -A2 * __fdividef(1.f, d2);
             __stcs(Mc + e, Pn);
             acc += Pn;
-            rel = nan_max(rel, rel_change(Pn, Pp[u]));
+            moving |= !(fabsf(Pn - Pp[u]) <= thr * fabsf(Pn));  // a NaN counts as moving
+            nonfinite |= !isfinite(Pn);
           }
         }
       }
@@ -158,21 +163,18 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
       Pt[i] = P;
     }
   }
-  double vb[1] = {(double)bad}, vr[1] = {(double)rel};
-  block_sum<1>(vb);
-  block_max<1>(vr);
-  double v[2] = {vb[0], vr[0]}, tot[2];
-  const int modes[2] = {0, 1};
-  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+  double v[3] = {(double)bad, (double)moving, (double)nonfinite}, tot[3];
+  block_sum<3>(v);
+  const int modes[3] = {0, 0, 0};
+  if (last_block_reduce<3>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
     ctl->round = t;
-    ctl->maxrel = tot[1];
-    const bool stat = tot[1] <= ctl->tol2bb;  // 2^-prec_stop_log2; a NaN is not stationary
-    ctl->stable = stat ? ctl->stable + 1 : 0;
+    ctl->maxrel = tot[1];                      // messages that moved by more than 2^-s
+    ctl->stable = tot[1] == 0.0 ? ctl->stable + 1 : 0;
     if (ctl->no_stop) {
       // autotuning run: no decision
     } else if (tot[0] > 0.0) {
       ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
-    } else if (!isfinite(tot[1]) && t > 1) {
+    } else if (tot[2] > 0.0 && t > 1) {
       ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     } else if (ctl->stable >= 2) {
       ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) k32_prec(Args32 a) {
 // Stop rule: the precision phase's (relative change <= 2^-s in two consecutive
 // rounds, zero cavity, max_iter).
 template <int L, int U>
-__global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
+__global__ void __launch_bounds__(kBlock, 4) k32_joint(Args32 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int t = ctl->round + 1;
@@ -214,8 +216,8 @@ __global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  float rel = 0.f;
-  int bad = 0;
+  const float thr = (float)ctl->tol2bb;  // 2^-prec_stop_log2
+  int bad = 0, moving = 0, nonfinite = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
     float accP = 0.f, accH = 0.f;
@@ -245,20 +247,21 @@ __global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
             if (t >= 2) {  // message i -> k of round t-1
               const float d1 = q2.x - Ps[u];
               bad |= (d1 == 0.f);
-              const float r1 = 1.f / d1;
+              const float r1 = __fdividef(1.f, d1);
               Pout = -A[u] * A[u] * r1;
               hout = -A[u] * (q2.y - hs[u]) * r1;
             }
             const float d2 = qk[u].x - Pout;  // message k -> i of round t
             bad |= (d2 == 0.f);
-            const float r2 = 1.f / d2;
+            const float r2 = __fdividef(1.f, d2);
             const float Pn = -A[u] * A[u] * r2;
             const float hn = -A[u] * (qk[u].y - hout) * r2;
             __stcs(Mc + e, Pn);
             __stcs(Hc + e, hn);
             accP += Pn;
             accH += hn;
-            rel = nan_max(rel, rel_change(Pn, Pp[u]));
+            moving |= !(fabsf(Pn - Pp[u]) <= thr * fabsf(Pn));  // a NaN counts as moving
+            nonfinite |= !isfinite(Pn);
           }
         }
       }
@@ -273,21 +276,18 @@ __global__ void __launch_bounds__(kBlock) k32_joint(Args32 a) {
       Ht[i] = hh;
     }
   }
-  double vb[1] = {(double)bad}, vr[1] = {(double)rel};
-  block_sum<1>(vb);
-  block_max<1>(vr);
-  double v[2] = {vb[0], vr[0]}, tot[2];
-  const int modes[2] = {0, 1};
-  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+  double v[3] = {(double)bad, (double)moving, (double)nonfinite}, tot[3];
+  block_sum<3>(v);
+  const int modes[3] = {0, 0, 0};
+  if (last_block_reduce<3>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
     ctl->round = t;
-    ctl->maxrel = tot[1];
-    const bool stat = tot[1] <= ctl->tol2bb;  // 2^-prec_stop_log2; a NaN is not stationary
-    ctl->stable = stat ? ctl->stable + 1 : 0;
+    ctl->maxrel = tot[1];                      // messages that moved by more than 2^-s
+    ctl->stable = tot[1] == 0.0 ? ctl->stable + 1 : 0;
     if (ctl->no_stop) {
       // autotuning run: no decision
     } else if (tot[0] > 0.0) {
       ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
-    } else if (!isfinite(tot[1]) && t > 1) {
+    } else if (tot[2] > 0.0 && t > 1) {
       ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     } else if (ctl->stable >= 2) {
       ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
