@@ -40,15 +40,35 @@ WORKLOAD = (f"random sparse symmetric diagonally dominant A, n=2^20, {PICKS} uni
             f"values U(-1,1), diagonal {DIAG} x row abs-sum, b ~ N(0,1)")
 
 
-def _profiled_traffic(summary, source, scale_to=None):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current source of the kernel (the summary records the source's sha256)."""
+def kernel_source_sha(source, kernel):
+    """sha256 of a kernel's own definition (from its template / __global__ line to
+    the closing brace in column 0) plus the shared device helpers (devutil.cuh):
+    a committed ncu summary stays valid while neither changes."""
     import hashlib
 
+    import re
+
+    lines = open(os.path.join(ROOT, source)).read().split("\n")
+    pat = re.compile(r"__global__.*\b" + re.escape(kernel) + r"\s*\(")
+    start = next(i for i, l in enumerate(lines) if pat.search(l))
+    if start > 0 and lines[start - 1].startswith("template"):
+        start -= 1
+    end = next(i for i in range(start + 1, len(lines)) if lines[i] == "}")
+    body = "\n".join(lines[start:end + 1])
+    helpers = open(os.path.join(ROOT, "paper_0811_2518_gb300", "csrc", "devutil.cuh")).read()
+    return hashlib.sha256((body + "\n" + helpers).encode()).hexdigest()
+
+
+def _profiled_traffic(summary, source, kernel, scale_to=None):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current source of the kernel (the summary records kernel_source_sha)."""
     ps, src = os.path.join(ROOT, "profiles", summary), os.path.join(ROOT, source)
     if not (os.path.exists(ps) and os.path.exists(src)):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    try:
+        sha = kernel_source_sha(source, kernel)
+    except StopIteration:
+        return None
     vals = {}
     for line in open(ps):
         if ":" in line:
@@ -56,7 +76,7 @@ def _profiled_traffic(summary, source, scale_to=None):
             v = v.strip().split()
             if v:
                 vals[k.strip(" -*`")] = v[0].strip("`")
-    if vals.get("source_sha256") != sha:
+    if vals.get("kernel_source_sha256") != sha:
         return None
     try:
         traffic = float(vals["dram_bytes_per_launch"])
@@ -322,7 +342,7 @@ def main():
                    "roofline": {"bound": "hbm", "kernel": "kb_mean", "achieved": bytes_b / (mean_ms / 1e3) / 1e9,
                                 "peak": peak, "unit": "GB/s", "frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak,
                                 "traffic": _profiled_traffic("kb_mean_grid3d_64_64rhs.md",
-                                                             "paper_0811_2518_gb300/csrc/batched.cu",
+                                                             "paper_0811_2518_gb300/csrc/batched.cu", "kb_mean",
                                                              scale_to=bytes_b),
                                 "bytes_per_launch": bytes_b, "launch_ms": mean_ms}}
         sb.close()
@@ -419,7 +439,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _profiled_traffic(f"{kname}_random_sym_n1048576.md",
-                                                      "paper_0811_2518_gb300/csrc/solve32.cu"),
+                                                      "paper_0811_2518_gb300/csrc/solve32.cu", kname),
                          "bytes_per_launch": bytes_launch, "launch_ms": dur_ms},
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
             "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},

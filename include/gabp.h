@@ -224,16 +224,18 @@ gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, 
                             int32_t *refine_steps);
 
 /* Per-phase device time of the solves since the last reset (options.profile = 1):
- * phase 0 FP64 GaBP rounds, 1 FP32 precision rounds, 2 FP32 mean rounds,
- * 3 FP64 refinement steps (residual + update), 4 the persistent multi-system
- * kernel (always timed).  ms: summed CUDA-event time around the phase's
+ * phase 0 FP64 GaBP rounds, 1 FP32 precision rounds (joint precision + mean
+ * rounds with overlap_precision), 2 FP32 mean rounds, 3 FP64 refinement steps
+ * (residual + update), 4 the persistent multi-system kernel (always timed),
+ * 5 the coefficient freeze (with overlap_precision: the first mean round,
+ * which also computes the frozen coefficients).  ms: summed CUDA-event time around the phase's
  * launches on the handle's stream (it includes the few rounds launched after a
  * decision, which return at once); rounds: round kernels that did work (phase
  * 4: the largest per-system round count); launches: every kernel the library
  * launched. */
 typedef struct {
-  double ms[5];
-  int64_t rounds[5];
+  double ms[6];
+  int64_t rounds[6];
   int64_t launches;
 } gabp_profile;
 gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);

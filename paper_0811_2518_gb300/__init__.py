@@ -60,7 +60,7 @@ class Options(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     """Mirror of ``gabp_profile``."""
-    _fields_ = [("ms", ctypes.c_double * 5), ("rounds", ctypes.c_int64 * 5), ("launches", ctypes.c_int64)]
+    _fields_ = [("ms", ctypes.c_double * 6), ("rounds", ctypes.c_int64 * 6), ("launches", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -205,7 +205,7 @@ def gabp_profile_read(h, reset=False):
     """Returns (status, dict) with per-phase ms / rounds and the launch count."""
     p = Profile()
     st = lib.gabp_profile_read(h, ctypes.byref(p), 1 if reset else 0)
-    names = ("fp64", "prec32", "mean32", "refine64", "multi")
+    names = ("fp64", "prec32", "mean32", "refine64", "multi", "freeze32")
     return st, {"ms": dict(zip(names, list(p.ms))), "rounds": dict(zip(names, list(p.rounds))),
                 "launches": p.launches}
 

@@ -104,10 +104,10 @@ struct Stats {
 };
 
 // Phase timing (options.profile): CUDA events around each phase's launches.
-enum { PH_FP64 = 0, PH_PREC32 = 1, PH_MEAN32 = 2, PH_REFINE64 = 3, PH_MULTI = 4, PH_COUNT = 5 };
+enum { PH_FP64 = 0, PH_PREC32 = 1, PH_MEAN32 = 2, PH_REFINE64 = 3, PH_MULTI = 4, PH_FREEZE32 = 5, PH_COUNT = 6 };
 struct Prof {
-  double ms[PH_COUNT] = {0, 0, 0, 0, 0};
-  int64_t rounds[PH_COUNT] = {0, 0, 0, 0, 0};
+  double ms[PH_COUNT] = {0, 0, 0, 0, 0, 0};
+  int64_t rounds[PH_COUNT] = {0, 0, 0, 0, 0, 0};
   int64_t launches = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
@@ -198,6 +198,7 @@ inline void prof_end(gabp_handle h) {
 inline void prof_collect(gabp_handle h, int phase, int64_t rounds) {
   h->prof.rounds[phase] += rounds;
   if (!h->opt.profile) return;
+  cudaEventSynchronize(h->prof.e1);  // profiling mode only: wait for the phase's end
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, h->prof.e0, h->prof.e1) == cudaSuccess) h->prof.ms[phase] += ms;
   else cudaGetLastError();

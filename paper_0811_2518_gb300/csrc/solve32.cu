@@ -313,8 +313,7 @@ __global__ void k32_joint_init(int n, const float *__restrict__ ad, const float 
 // Freeze: c_out = c_ik = -A / (P~_i - P_ki), P_ik = c_out A, c_in = c_ki = -A / (P~_k - P_ik),
 // 1/P~_i.  Uses round T's precision state.
 template <int L>
-__global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T, const DevCtl *tctl = nullptr) {
-  if (tctl) T = tctl->result_round;  // device-loop graph: the round the joint phase stopped at
+__global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T) {
   const float *__restrict__ Ms = (T & 1) ? a.MP1 : a.MP0;
   const float *__restrict__ PT = ring3(a.NP0, a.NP1, a.NP2, T);
   constexpr int RPW = 32 / L;
@@ -417,6 +416,102 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   }
 }
 
+// ---------------------------------------------------------------------------- coefficient freeze
+// The first frozen-coefficient mean round after the joint rounds, fused with the
+// freeze: from round T's precision state ({P~, h~} ring and P chain) it writes
+//   c_out = c_ik = -A / (P~_i - P_ki),  c_in = c_ki = -A / (P~_k - c_out A),  1/P~_i
+// and uses them at once for mean round T + 1, the sender's {P~_k, h~_k} coming
+// from ONE 8-byte gather (the separate freeze pass would re-read every slot and
+// gather P~_k).  Same arithmetic as k32_coef followed by k32_mean.  If the mean
+// solve is already decided (T reached the inner cap) only the coefficients and
+// 1/P~ are written.
+template <int L, int U>
+__global__ void __launch_bounds__(kBlock) k32_freeze(Args32 a) {
+  DevCtl *ctl = a.ctl;
+  const bool coef_only = ctl->done;
+  const int T = ctl->round, t = T + 1;
+  const float *__restrict__ Ms = (T & 1) ? a.MP1 : a.MP0;  // P_ki of round T
+  const float2 *__restrict__ QT = ring3(a.NQ0, a.NQ1, a.NQ2, T);
+  float *__restrict__ Hc = (t & 1) ? a.H1 : a.H0;  // holds t-2, becomes t
+  const float *__restrict__ Hm2 = ring3(a.NH0, a.NH1, a.NH2, t + 1);
+  float *__restrict__ Ht = ring3(a.NH0, a.NH1, a.NH2, t);
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  float dxx = 0.f, xx = 0.f;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    float acc = 0.f;
+    float2 qi = make_float2(1.f, 0.f);
+    if (i < a.n) {
+      qi = QT[i];
+      const float hi2 = t >= 2 ? Hm2[i] : 0.f;
+      const int e1 = a.rp[i + 1];
+      for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+        int k[U];
+        float A[U], Ps[U], hs[U];
+        float2 qk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) { k[u] = __ldcs(a.ci + e); A[u] = __ldcs(a.av + e); Ps[u] = __ldcs(Ms + e); hs[u] = __ldcs(Hc + e); }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (eb + u * L < e1) qk[u] = QT[k[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            const float cout = -A[u] / (qi.x - Ps[u]);
+            const float Pout = cout * A[u];
+            const float cin = -A[u] / (qk[u].x - Pout);
+            a.CF[e] = make_float2(cin, cout);
+            if (!coef_only) {
+              const float hout = t >= 2 ? cout * (hi2 - hs[u]) : 0.f;  // message i -> k at t-1
+              const float hn = cin * (qk[u].y - hout);                 // message k -> i at t
+              __stcs(Hc + e, hn);
+              acc += hn;
+            }
+          }
+        }
+      }
+    }
+    acc = sub_sum<L>(acc);
+    if (i < a.n && sl == 0) {
+      const float ip = 1.f / qi.x;
+      a.invP[i] = ip;
+      if (!coef_only) {
+        const float hnew = a.rhs[i] + acc;
+        Ht[i] = hnew;
+        const float x = hnew * ip, dx = (hnew - qi.y) * ip;
+        dxx = fmaf(dx, dx, dxx);
+        xx = fmaf(x, x, xx);
+      }
+    }
+  }
+  if (coef_only) return;
+  double v[2] = {(double)dxx, (double)xx}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    ctl->round = t;
+    ctl->rr = tot[0];
+    ctl->xx = tot[1];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= 2 && tot[0] <= ctl->tol2bb * tot[1]) {
+      ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    } else if (t >= ctl->max_iter) {
+      ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+    }
+    if (a.use_cond && ctl->done) cudaGraphSetConditional(a.cond, 0);
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
 // ---------------------------------------------------------------------------- FP64 outer steps
 // r = b - A x over the full CSR (diagonal included), in FP64; the FP32 copy of r
 // seeds the next inner solve (its round-0 aggregate h~^(0) = r and its RHS).
@@ -426,7 +521,7 @@ __global__ void __launch_bounds__(kBlock) k64_residual(int n, const int *__restr
                                                        const double *__restrict__ b, const double *__restrict__ x,
                                                        float *__restrict__ rhs32, float *__restrict__ nh0,
                                                        DevCtl *ctl, double *partials, int set_bb,
-                                                       const int *skip = nullptr) {
+                                                       const int *skip = nullptr, int x_zero = 0) {
   if (skip && *skip) return;  // device-loop graph: the loop already stopped
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
@@ -436,7 +531,7 @@ __global__ void __launch_bounds__(kBlock) k64_residual(int n, const int *__restr
   for (int base = warp * RPW; base < n; base += nwarps * RPW) {
     const int i = base + sw;
     double ax = 0.0;
-    if (i < n)
+    if (i < n && !x_zero)  // x = 0 (the first residual): r = b exactly, no product needed
       for (int p = rowptr[i] + sl; p < rowptr[i + 1]; p += L) ax = fma(val[p], x[col[p]], ax);
     ax = sub_sum<L>(ax);
     if (i < n && sl == 0) {
@@ -480,10 +575,10 @@ __global__ void k_diag32(int n, const double *__restrict__ ad, const double *__r
 
 __global__ void k_ctl_reset(DevCtl *c, int max_iter, double tol2, int round0 = 0) {
   c->round = round0;
-  c->done = 0;
+  c->done = round0 > 0 && round0 >= max_iter;
   c->status = GABP_NOT_CONVERGED;
-  c->iters = 0;
-  c->result_round = 0;
+  c->iters = round0;
+  c->result_round = round0;
   c->max_iter = max_iter;
   c->check_from = 1;
   c->stable = 0;
@@ -717,9 +812,9 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
 }
 
 // Joint rounds (precision and mean messages together) from zero messages until
-// the precisions are stationary or `cap` rounds, then the coefficient freeze at
-// that round T.  The mean state of round T is the start of the first inner
-// solve's frozen-coefficient rounds.  Needs rhs32 / NH[0] = r (k64_residual).
+// the precisions are stationary or `cap` rounds; returns that round T, whose
+// state freeze32 freezes.  The mean state of round T is the start of the first
+// inner solve's frozen-coefficient rounds.  Needs rhs32 / NH[0] = r (k64_residual).
 static gabp_status joint_phase32(gabp_handle h, const double *gamma_diag, int cap, int *T_out) {
   Work32 &w = h->w32;
   Graph &g = h->g;
@@ -756,14 +851,29 @@ static gabp_status joint_phase32(gabp_handle h, const double *gamma_diag, int ca
   if (s != GABP_OK) return s;
   const DevCtl c = *h->ctl_host;
   if (c.status == GABP_BREAKDOWN || c.status == GABP_DIVERGED) return (gabp_status)c.status;
-  const int Lc = SH & 0xff;
-  GABP_DISPATCH_L(Lc, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)), kBlock, 0,
-                                      h->stream>>>(a, c.result_round)));
-  h->prof.launches += 1;
-  GABP_CUDA(cudaGetLastError());
-  w.prec_round = c.result_round;
-  w.coef_ready = true;
   *T_out = c.result_round;
+  return GABP_OK;
+}
+
+// The coefficient freeze at the joint rounds' last round T fused with mean round
+// T + 1 (k32_freeze), on the control block armed for the inner solve from T.
+static gabp_status freeze32(gabp_handle h, int T) {
+  Graph &g = h->g;
+  Work32 &w = h->w32;
+  Args32 a = args32(h);
+  const int SH = shape32(h, K32_JOINT);
+  prof_begin(h);
+  with_shape(SH, [&](auto Lc, auto Uc) {
+    constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+    k32_freeze<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_freeze<LL, UU>)), kBlock, 0,
+                         h->stream>>>(a);
+  });
+  prof_end(h);
+  GABP_CUDA(cudaGetLastError());
+  prof_collect(h, PH_FREEZE32, 1);
+  h->prof.launches += 1;
+  w.prec_round = T;
+  w.coef_ready = true;
   return GABP_OK;
 }
 
@@ -972,10 +1082,10 @@ static gabp_status build_refine_graph(gabp_handle h, int SHm, int SHj, int LR) {
   GABP_DISPATCH_L(LR, nbr = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k64_residual<LL>)));
   RefineCtl *rc = w.rc;
   const int nb1 = (g.n + kBlock - 1) / kBlock;
-  auto residual = [&](int set_bb) {
+  auto residual = [&](int first) {
     GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, st>>>(g.n, g.rowptr, g.col, g.val, w.Bd, w.X, w.rhs32,
-                                                                    w.NH[0], w.ctlR, h->partials, set_bb,
-                                                                    &rc->skip)));
+                                                                    w.NH[0], w.ctlR, h->partials, first,
+                                                                    &rc->skip, first)));
   };
   SeqGraph top{root, nullptr};
   cudaError_t e = seq_capture(top, st, [&] {
@@ -1010,10 +1120,16 @@ static gabp_status build_refine_graph(gabp_handle h, int SHm, int SHj, int LR) {
     });
   if (e == cudaSuccess)
     e = seq_capture(joint, st, [&] {
-      const int Lc = SHj & 0xff;
-      GABP_DISPATCH_L(Lc, (k32_coef<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_coef<LL>)),
-                                          kBlock, 0, st>>>(a, 0, h->ctl)));
       k_joint_after<<<1, 1, 0, st>>>(rc, h->ctl, h_inner);
+      // freeze at T fused with round T + 1 (only the freeze if the inner cap is reached)
+      Args32 af = a;
+      af.cond = h_inner;
+      af.use_cond = 1;
+      with_shape(SHj, [&](auto Lc, auto Uc) {
+        constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+        k32_freeze<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_freeze<LL, UU>)), kBlock, 0,
+                             st>>>(af);
+      });
     });
   // the inner solve's frozen-coefficient rounds
   if (e == cudaSuccess) e = seq_conditional(outer, h_inner, cudaGraphCondTypeWhile, &inner);
@@ -1157,7 +1273,8 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   GABP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * g.n, h->stream));
   GABP_CUDA(cudaMemsetAsync(w.ctlR, 0, sizeof(DevCtl), h->stream));
   GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
-                                                                          w.NH[0], w.ctlR, h->partials, 1)));
+                                                                          w.NH[0], w.ctlR, h->partials, 1, nullptr,
+                                                                          1)));
   h->prof.launches += 1;
   GABP_CUDA(cudaGetLastError());
   DevCtl cr;
@@ -1187,25 +1304,28 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     const double it_tol = inner_target(itol, tol, bb, rr);
     int T = 0;
     if (step == 0 && joint) {
-      if ((s = joint_phase32(h, gamma_diag, cap, &T)) != GABP_OK) {
-        if (gamma_diag) w.coef_ready = false;
-        return s;
-      }
+      if ((s = joint_phase32(h, gamma_diag, cap, &T)) != GABP_OK) return s;
+      // freeze at T fused with the first frozen-coefficient round T + 1
+      k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol, T);
+      h->prof.launches += 1;
+      if ((s = freeze32(h, T)) != GABP_OK) return s;
       if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
     } else {
       GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E, h->stream));
     }
     int result_round = T;
     if (T < cap) {
-      k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol, T);
-      h->prof.launches += 1;
+      if (T == 0) {
+        k_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol, 0);
+        h->prof.launches += 1;
+      }
       GABP_CUDA(cudaGetLastError());
       with_shape(SH, [&](auto Lc, auto Uc) {
         constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
         s = run_rounds(h, &h->gH32, &h->gH32_L, SH, [&] {
           const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
           k32_mean<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
-        }, cap - T, PH_MEAN32, T);
+        }, cap - T, PH_MEAN32, T > 0 ? T + 1 : 0);
       });
       if (s != GABP_OK) return s;
       const DevCtl c = *h->ctl_host;
