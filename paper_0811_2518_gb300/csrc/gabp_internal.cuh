@@ -209,23 +209,31 @@ inline void prof_collect(gabp_handle h, int phase, int64_t rounds) {
 // with no_stop set, so the launches do real work whatever the buffers hold.
 template <typename F>
 inline float time_launches(gabp_handle h, F launch, int rounds) {
+  // the fastest single launch (x rounds): robust to a neighbour's interference
   launch();
-  cudaEvent_t a, b;
-  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-    cudaGetLastError();
-    return 1e30f;
+  constexpr int kMaxEv = 16;
+  rounds = rounds < 1 ? 1 : (rounds > kMaxEv - 1 ? kMaxEv - 1 : rounds);
+  cudaEvent_t ev[kMaxEv];
+  int made = 0;
+  for (; made <= rounds; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  float best = 1e30f;
+  if (made == rounds + 1) {
+    cudaEventRecord(ev[0], h->stream);
+    for (int r = 0; r < rounds; ++r) {
+      launch();
+      cudaEventRecord(ev[r + 1], h->stream);
+    }
+    if (cudaEventSynchronize(ev[rounds]) == cudaSuccess) {
+      for (int r = 0; r < rounds; ++r) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[r], ev[r + 1]) == cudaSuccess && ms < best) best = ms;
+      }
+    }
   }
-  cudaEventRecord(a, h->stream);
-  for (int r = 0; r < rounds; ++r) launch();
-  cudaEventRecord(b, h->stream);
-  float ms = 1e30f;
-  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-    cudaGetLastError();
-    ms = 1e30f;
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  return ms;
+  cudaGetLastError();
+  for (int j = 0; j < made; ++j) cudaEventDestroy(ev[j]);
+  return best < 1e30f ? best * rounds : 1e30f;
 }
 gabp_status tune_ctl(gabp_handle h, const double *b);  // (re)arms ctl_tune for a tuning run (b: any n-vector)
 

@@ -746,17 +746,17 @@ static gabp_status autotune32(gabp_handle h, int kind) {
         ms = time_launches(h, [&] {
           k32_mean<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>)), kBlock, 0,
                              h->stream>>>(a);
-        }, 3);
+        }, 5);
       else if (kind == K32_JOINT)
         ms = time_launches(h, [&] {
           k32_joint<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_joint<LL, UU>)), kBlock, 0,
                               h->stream>>>(a);
-        }, 3);
+        }, 5);
       else
         ms = time_launches(h, [&] {
           k32_prec<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_prec<LL, UU>)), kBlock, 0,
                              h->stream>>>(a);
-        }, 3);
+        }, 5);
     });
     if (ms < best) { best = ms; bestS = sc; }
   }
