@@ -97,43 +97,63 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 100 ms, one streaming process) of SM clock and throttle
+    reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
         self.index = index
         self.samples = []
-        self._stop = threading.Event()
+        self._proc = None
         self._th = None
+        self._t_begin = 0.0
 
     def start(self):
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+
         def run():
-            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap")
-            while not self._stop.is_set():
-                try:
-                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                         timeout=5).stdout.strip()
-                    if out:
-                        self.samples.append([v.strip() for v in out.split(",")])
-                except Exception:
-                    return
-                self._stop.wait(0.2)
+            for line in self._proc.stdout:
+                v = [x.strip() for x in line.split(",")]
+                if len(v) >= 7:
+                    self.samples.append((time.perf_counter(), v))
 
         self._th = threading.Thread(target=run, daemon=True)
         self._th.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 2.0:  # the sampler is running
+            time.sleep(0.01)
+        self._t_begin = time.perf_counter()
 
     def stop(self):
-        self._stop.set()
+        t_end = time.perf_counter()
+        time.sleep(0.15)  # the sample that covers the end of the region
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._th:
-            self._th.join(timeout=10)
+            self._th.join(timeout=5)
+        window = [v for t, v in self.samples if self._t_begin <= t <= t_end + 0.1]
+        if not window and self.samples:  # region shorter than the sampling period: the nearest sample
+            window = [min(self.samples, key=lambda tv: abs(tv[0] - t_end))[1]]
+        self.samples = window
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
         mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[j] for s in self.samples for j in range(4) if len(s) > 3 + j and s[3 + j] == "Active"})
+        reasons = sorted({names[j] for s in self.samples for j in range(4) if s[3 + j] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
 
@@ -181,7 +201,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
