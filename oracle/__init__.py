@@ -10,6 +10,11 @@ Contents and the passage each follows:
 
 * :func:`gabp_naive`      -- Algorithm 1, parallel (synchronous) schedule, in C.
 * :func:`gabp_broadcast`  -- Algorithm 2 (broadcast variant), in C.
+* :func:`gabp_serial`     -- Algorithm 1's rules under the serial schedule (one
+  message store updated in place; Sec. "The Gaussian BP Algorithm", the
+  paragraph on parallel vs serial scheduling), nodes firing colour by colour, in C.
+* :func:`colour_greedy`   -- the colouring of those sweeps (index order, smallest
+  colour unused by lower-indexed neighbours), in C.
 * :func:`dense_solve`     -- x* = A^{-1} b by LU (Proposition "linear system =
   inference": the GaBP fixed point is the marginal-mean vector A^{-1} b).
 * :func:`marginal_precisions_exact` -- 1/(A^{-1})_ii, the exact marginal
@@ -62,7 +67,9 @@ def _load():
         if _lib is None:
             build()
             lib = ctypes.CDLL(_LIB_PATH)
-            for name in ("orc_gabp_naive", "orc_gabp_broadcast"):
+            lib.orc_colour_greedy.restype = ctypes.c_int
+            lib.orc_colour_greedy.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            for name in ("orc_gabp_naive", "orc_gabp_broadcast", "orc_gabp_serial"):
                 f = getattr(lib, name)
                 f.restype = ctypes.c_int
                 f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -117,6 +124,24 @@ def gabp_naive(m, b, max_iter=1000, tol=1e-12, stop_rule="residual", messages=Fa
 def gabp_broadcast(m, b, max_iter=1000, tol=1e-12, stop_rule="residual", messages=False):
     """Algorithm 2 (broadcast GaBP), synchronous schedule, FP64; same interface as :func:`gabp_naive`."""
     return _run("orc_gabp_broadcast", m, b, max_iter, tol, 0 if stop_rule == "residual" else 1, messages)
+
+
+def gabp_serial(m, b, max_iter=1000, tol=1e-12, stop_rule="residual", messages=False):
+    """Algorithm 1's message rules, serial schedule (one store, in place): each sweep fires the
+    nodes of colour 0, then colour 1, ... (:func:`colour_greedy`); ``iters`` counts sweeps.
+    Same interface as :func:`gabp_naive`."""
+    return _run("orc_gabp_serial", m, b, max_iter, tol, 0 if stop_rule == "residual" else 1, messages)
+
+
+def colour_greedy(m):
+    """(colour[n], number of colours): nodes in index order, each taking the smallest colour
+    not used by a lower-indexed neighbour."""
+    lib = _load()
+    rowptr = np.ascontiguousarray(m.rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(m.col, dtype=np.int32)
+    colour = np.zeros(m.n, dtype=np.int32)
+    nc = lib.orc_colour_greedy(m.n, _ptr(rowptr), _ptr(col), _ptr(colour))
+    return colour, nc
 
 
 # --------------------------------------------------------------------------- dense references

@@ -21,6 +21,17 @@
  *                       its aggregate P~_i, mu~_i over all of N(i); each message
  *                       then subtracts the reverse message j->i
  *                       (Sec. "GaBP Broadcast Variant").
+ *   orc_gabp_serial     Algorithm 1's message rules under the serial schedule
+ *                       (same paragraph: ONE message store, so messages sent
+ *                       earlier in a sweep are seen by the nodes that fire later).
+ *                       A sweep fires the nodes colour by colour (colour 0 first)
+ *                       and, within a colour, in index order; nodes of one colour
+ *                       share no edge, so this is one sequential order.  Firing
+ *                       node i rebuilds every message i -> j from the current
+ *                       messages into i.
+ *   orc_colour_greedy   the colouring used by the serial sweeps: nodes in index
+ *                       order, each taking the smallest colour not used by a
+ *                       lower-indexed neighbour.
  *
  * Message storage: the input is the FULL symmetric CSR (diagonal included,
  * columns sorted within rows).  For row i, the slot p with col[p] = k != i holds
@@ -186,12 +197,68 @@ static int round_broadcast(int n, const int *rowptr, const int *col, const doubl
   return ORC_OK;
 }
 
+/* Greedy colouring in index order; returns the number of colours. */
+int orc_colour_greedy(int n, const int *rowptr, const int *col, int *colour) {
+  int ncol = 0;
+  int *used = calloc((size_t)n + 1, sizeof(int)); /* used[c] == i + 1: colour c taken by a lower neighbour of i */
+  if (!used) return -1;
+  for (int i = 0; i < n; ++i) {
+    for (long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      int k = col[p];
+      if (k < i) used[colour[k]] = i + 1;
+    }
+    int c = 0;
+    while (used[c] == i + 1) ++c;
+    colour[i] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+  }
+  free(used);
+  return ncol;
+}
+
+/* One serial sweep: nodes fire colour by colour, each node rebuilding its
+ * outgoing messages (Algorithm 1's rules, cavity sums over N(i)\j) from the
+ * CURRENT store, which it updates in place. */
+static int sweep_serial(int n, const int *rowptr, const int *col, const double *val, const double *b,
+                        const int *colour, int ncol, double *Pm, double *Mm) {
+  for (int c = 0; c < ncol; ++c) {
+    for (int i = 0; i < n; ++i) {
+      if (colour[i] != c) continue;
+      double Pii = diag_entry(rowptr, col, val, i);
+      double muii = b[i] / Pii;
+      for (long q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        int j = col[q];
+        if (j == i) continue;
+        double Pcav = Pii, hcav = Pii * muii;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+          int k = col[p];
+          if (k == i || k == j) continue;
+          Pcav += Pm[p];
+          hcav += Pm[p] * Mm[p];
+        }
+        if (Pcav == 0.0) return ORC_BREAKDOWN;
+        double Aij = val[q];
+        long dst = slot_of(rowptr, col, j, i); /* row j's slot that receives i -> j */
+        Pm[dst] = -Aij * Aij / Pcav;
+        Mm[dst] = hcav / Aij;
+      }
+    }
+  }
+  return ORC_OK;
+}
+
 static int run(int variant, int n, const int *rowptr, const int *col, const double *val, const double *b,
                int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
                double *relres, double *Pmsg, double *Mmsg) {
   int rc = check_input(n, rowptr, col, val);
   if (rc != ORC_OK) return rc;
   long nnz = rowptr[n];
+  int *colour = NULL, ncol = 0;
+  if (variant == 2) {
+    colour = calloc((size_t)n + 1, sizeof(int));
+    if (!colour) return ORC_INVALID;
+    ncol = orc_colour_greedy(n, rowptr, col, colour);
+  }
   double *Po = calloc(nnz + 1, sizeof(double)), *Mo = calloc(nnz + 1, sizeof(double));
   double *Pn = calloc(nnz + 1, sizeof(double)), *Mn = calloc(nnz + 1, sizeof(double));
   double *Pt = calloc(n + 1, sizeof(double)), *Mt = calloc(n + 1, sizeof(double));
@@ -213,8 +280,15 @@ static int run(int variant, int n, const int *rowptr, const int *col, const doub
   *relres = rn / bn;
   rc = ORC_NOT_CONVERGED;
   for (int t = 1; t <= max_iter; ++t) {
-    int r = variant == 0 ? round_naive(n, rowptr, col, val, b, Po, Mo, Pn, Mn)
-                         : round_broadcast(n, rowptr, col, val, b, Po, Mo, Pn, Mn, Pt, Mt);
+    int r;
+    if (variant == 2) { /* serial: Pn/Mn keep the previous sweep for the change test */
+      memcpy(Pn, Po, nnz * sizeof(double));
+      memcpy(Mn, Mo, nnz * sizeof(double));
+      r = sweep_serial(n, rowptr, col, val, b, colour, ncol, Pn, Mn);
+    } else {
+      r = variant == 0 ? round_naive(n, rowptr, col, val, b, Po, Mo, Pn, Mn)
+                       : round_broadcast(n, rowptr, col, val, b, Po, Mo, Pn, Mn, Pt, Mt);
+    }
     if (r != ORC_OK) { rc = r; *iters = t; break; }
     double maxchange = 0.0;
     for (long p = 0; p < nnz; ++p) {
@@ -236,7 +310,7 @@ static int run(int variant, int n, const int *rowptr, const int *col, const doub
   if (Pmsg) memcpy(Pmsg, Po, nnz * sizeof(double));
   if (Mmsg) memcpy(Mmsg, Mo, nnz * sizeof(double));
 done:
-  free(Po); free(Mo); free(Pn); free(Mn); free(Pt); free(Mt);
+  free(Po); free(Mo); free(Pn); free(Mn); free(Pt); free(Mt); free(colour);
   return rc;
 }
 
@@ -255,4 +329,11 @@ int orc_gabp_broadcast(int n, const int *rowptr, const int *col, const double *v
                        double *relres, double *Pmsg, double *Mmsg) {
   *relres = NAN;
   return run(1, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg);
+}
+
+int orc_gabp_serial(int n, const int *rowptr, const int *col, const double *val, const double *b,
+                    int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
+                    double *relres, double *Pmsg, double *Mmsg) {
+  *relres = NAN;
+  return run(2, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg);
 }

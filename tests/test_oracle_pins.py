@@ -345,3 +345,101 @@ def test_dense_gradient_against_finite_differences():
         E[i, i] = h
         fd = (loss(A + E, b) - loss(A - E, b)) / (2 * h)
         assert abs(fd - G[i, i]) <= 1e-7 * max(1.0, abs(fd))
+
+
+# ----------------------------------------------------------------------------- serial schedule
+def test_colour_greedy_facts():
+    """The colouring of the serial sweeps: proper; on a grid in index order the red-black
+    pattern (x + y) mod 2; on a path alternating; on a complete graph one colour per node in
+    index order; never more than max degree + 1 colours."""
+    m = synth.grid2d(7, -1.0, 4.5)
+    colour, nc = oracle.colour_greedy(m)
+    xy = np.arange(m.n)
+    assert nc == 2 and np.array_equal(colour, (xy // 7 + xy % 7) % 2)
+    n = 6
+    A = 4.0 * np.eye(n)
+    for i in range(n - 1):
+        A[i, i + 1] = A[i + 1, i] = -1.0
+    colour, nc = oracle.colour_greedy(synth.from_dense(A))
+    assert nc == 2 and np.array_equal(colour, np.arange(n) % 2)
+    K = np.full((5, 5), 0.1) + 5.0 * np.eye(5)
+    colour, nc = oracle.colour_greedy(synth.from_dense(K))
+    assert nc == 5 and np.array_equal(colour, np.arange(5))
+    for seed in (1, 2, 3):
+        m = synth.random_sym(300, 4, 1.1, seed)
+        colour, nc = oracle.colour_greedy(m)
+        rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+        off = rows != m.col
+        assert not np.any(colour[rows[off]] == colour[m.col[off]])  # proper
+        assert nc == colour.max() + 1 <= np.diff(m.rowptr).max()  # <= (max degree + 1), diagonal stored
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_serial_tree_exact(seed):
+    """On a tree the serial schedule is exact too (Sec. "Convergence and Exactness"): after at
+    most diameter sweeps x = A^{-1} b and P_i = 1 / (A^{-1})_ii."""
+    m = synth.random_tree(40, seed)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, seed)
+    r = oracle.gabp_serial(m, b, max_iter=40, tol=0.0)
+    assert np.allclose(r["x"], np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    assert np.allclose(r["P"], oracle.marginal_precisions_exact(A), rtol=1e-10)
+
+
+@pytest.mark.parametrize("make", [lambda: synth.grid2d(20, -1.0, 4.5), lambda: synth.random_sym(500, 4, 1.1, 3)])
+def test_serial_fixed_point_and_fewer_sweeps(make):
+    """The serial schedule converges to A^{-1} b on diagonally dominant A, in fewer sweeps than
+    the parallel schedule needs rounds (the paper's observation in every table)."""
+    m = make()
+    b = synth.rhs(m.n, 4)
+    x0 = np.linalg.solve(oracle.to_dense(m), b)
+    s = oracle.gabp_serial(m, b, max_iter=2000, tol=1e-12)
+    p = oracle.gabp_naive(m, b, max_iter=2000, tol=1e-12)
+    assert s["status"] == oracle.OK and np.allclose(s["x"], x0, rtol=1e-9, atol=1e-12)
+    assert s["iters"] < p["iters"]
+
+
+def test_serial_soft_counts():
+    """Tables tab_nonPSD and tab_2D_Poisson, serial GaBP (paper: 25 and 73 iterations)."""
+    g = read_golden("iteration_counts.txt")
+    A, b = synth.nonpsd3x3()
+    r = oracle.gabp_serial(synth.from_dense(A), b, max_iter=1000, tol=1e-6, stop_rule="message")
+    assert r["status"] == oracle.OK and _soft(r["iters"], g["nonpsd3x3_serial"][0])
+    p = 10
+    m = synth.poisson2d(p)
+    r = oracle.gabp_serial(m, np.full(m.n, (1.0 / (p + 1)) ** 2), max_iter=1000, tol=1e-6, stop_rule="message")
+    assert r["status"] == oracle.OK and _soft(r["iters"], g["poisson10_serial"][0])
+
+
+def test_serial_matches_sequential_broadcast_form():
+    """A second, independent form of the serial schedule: nodes fire one at a time in colour
+    order, each forming its aggregate over ALL of N(i) and subtracting the reverse message
+    (the broadcast form of Algorithm 2, in the information form), messages in a dict.  After
+    4 sweeps every message agrees with the C oracle's cavity-sum form."""
+    m = synth.random_sym(30, 3, 1.2, 8)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 8)
+    colour, nc = oracle.colour_greedy(m)
+    nbr = [np.flatnonzero((A[i] != 0) & (np.arange(m.n) != i)) for i in range(m.n)]
+    P, h = {}, {}  # (k, i): message k -> i
+    for i in range(m.n):
+        for k in nbr[i]:
+            P[(k, i)] = h[(k, i)] = 0.0
+    order = [i for c in range(nc) for i in range(m.n) if colour[i] == c]
+    for _ in range(4):
+        for i in order:
+            Pt = A[i, i] + sum(P[(k, i)] for k in nbr[i])
+            ht = b[i] + sum(h[(k, i)] for k in nbr[i])
+            for j in nbr[i]:
+                Pc, hc = Pt - P[(j, i)], ht - h[(j, i)]
+                P[(i, j)] = -A[i, j] ** 2 / Pc
+                h[(i, j)] = -A[i, j] * hc / Pc
+    r = oracle.gabp_serial(m, b, max_iter=4, tol=0.0, messages=True)
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    for p in range(m.nnz):
+        i, k = rows[p], m.col[p]
+        if i == k:
+            continue
+        assert abs(r["Pmsg"][p] - P[(k, i)]) <= 1e-13 * abs(P[(k, i)])
+        hm = r["Pmsg"][p] * r["mumsg"][p]  # information form h = P mu
+        assert abs(hm - h[(k, i)]) <= 1e-12 * (abs(h[(k, i)]) + 1e-12)
