@@ -102,7 +102,11 @@ typedef struct {
                            refinement loop (rounds, stop decisions, residuals, updates) runs as ONE
                            CUDA graph with conditional while/if nodes, no host round trip until the
                            result; 0 = host-driven batches of check_every rounds.  Default 1 */
-  int reserved[1];
+  int schedule;         /* message schedule (Sec. "The Gaussian BP Algorithm", parallel vs serial):
+                           0 parallel (synchronous, two stores); 1 serial (one store updated in place,
+                           nodes firing colour by colour in a greedy index-order colouring; rounds then
+                           count sweeps).  gabp_solve, FP64 and FP32_REFINE without loading.  Default 0 */
+  int reserved[4];
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */
@@ -196,12 +200,19 @@ gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offse
                                double tol, int32_t max_iter, int32_t *status_out, int32_t *iters_out,
                                double *relres_out);
 
+/* The colouring of the serial schedule (options.schedule = 1): nodes in index
+ * order, each taking the smallest colour not used by a lower-indexed
+ * neighbour; a sweep fires colour 0, then colour 1, ...  colour: device array
+ * of n int32 (nullable); *ncolours (nullable) the number of colours.  Computed
+ * once per handle (on the device) and kept. */
+gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolours);
+
 /* Marginal precisions P_i = A_ii + sum_k P_ki of the last solve (Algorithm 1,
  * step 4), device array of n doubles.  Exact (= 1/(A^{-1})_ii) on trees; an
  * approximation on loopy graphs.  GABP_ERR_INVALID before the first solve. */
 gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi);
 
-/* Messages of the last FP64 solve at its returned round, in the receiver
+/* Messages of the last FP64 solve at its returned round (or sweep), in the receiver
  * layout of the input CSR: for slot p of row i with col[p] = k != i,
  * P[p] = P_ki and hm[p] = P_ki * mu_ki (the information-form mean message);
  * diagonal slots get 0.  Device arrays of nnz doubles. */

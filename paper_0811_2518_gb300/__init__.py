@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -54,7 +54,8 @@ class Options(ctypes.Structure):
         ("multi_mode", ctypes.c_int),
         ("overlap_precision", ctypes.c_int),
         ("device_loop", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("schedule", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -90,6 +91,7 @@ _SIGNATURES = {
     "gabp_tuned_shapes": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_serial_colours": ([_P, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -138,6 +140,14 @@ def gabp_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, mem_space, stream_ptr, opt
     st = lib.gabp_create(ctypes.byref(h), int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
                          int(mem_space), _P(stream_ptr), ctypes.byref(options) if options is not None else None)
     return st, h
+
+
+def gabp_serial_colours(h, colour_ptr):
+    """Colouring of the serial schedule into a device int32[n] array (pointer or None);
+    returns (status, number of colours)."""
+    nc = ctypes.c_int32(0)
+    st = lib.gabp_serial_colours(h, colour_ptr, ctypes.byref(nc))
+    return st, nc.value
 
 
 def gabp_set_values(h, val_ptr, mem_space):
@@ -286,6 +296,16 @@ class Solver:
     @classmethod
     def from_csr(cls, m, **kw):
         return cls(m.n, m.rowptr, m.col, m.val, **kw)
+
+    def serial_colours(self):
+        """(colour tensor int32[n] on the device, number of colours) of the serial schedule."""
+        import torch
+
+        c = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        st, nc = gabp_serial_colours(self.handle, c.data_ptr())
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_serial_colours")
+        return c, nc
 
     def set_values(self, val):
         """New values (full CSR order, diagonal included) on the same pattern: a numpy array or a

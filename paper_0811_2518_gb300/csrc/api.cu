@@ -45,6 +45,9 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
   } else if (h->opt.precision == GABP_PREC_FP32_REFINE) {
     s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, nullptr, &it, &rel);
     h->last_path = 1;
+  } else if (h->opt.schedule == 1) {
+    s = solve64_serial(h, b, x, tol, max_iter, &it, &rel);
+    h->last_path = 2;
   } else {
     s = solve64(h, b, x, tol, max_iter, &it, &rel);
     h->last_path = 0;
@@ -108,12 +111,29 @@ extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
   if (!h || !Pi) return GABP_ERR_INVALID;
   if (h->last_path == 0) return marginals(h, Pi);
   if (h->last_path == 1) return marginals32(h, Pi);
+  if (h->last_path == 2) return serial_marginals64(h, Pi);
   return GABP_ERR_INVALID;
 }
 
 extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
-  if (!h || !P || !hm || h->last_path != 0) return GABP_ERR_INVALID;
-  return messages64(h, P, hm);
+  if (!h || !P || !hm) return GABP_ERR_INVALID;
+  if (h->last_path == 0) return messages64(h, P, hm);
+  if (h->last_path != 2) return GABP_ERR_INVALID;
+  double2 *M = nullptr;  // serial messages back in the input layout
+  GABP_CUDA(cudaMalloc(&M, sizeof(double2) * (size_t)(h->g.E > 0 ? h->g.E : 1)));
+  gabp_status s = serial_messages64(h, M);
+  if (s == GABP_OK) s = messages64_from(h, M, P, hm);
+  cudaFree(M);
+  return s;
+}
+
+extern "C" gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolours) {
+  if (!h || !values_usable(h)) return GABP_ERR_INVALID;
+  if (colour && !is_device_ptr(colour)) {
+    set_last_error("gabp_serial_colours: colour must be a device array");
+    return GABP_ERR_INVALID;
+  }
+  return serial_colours(h, colour, ncolours);
 }
 
 extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val) {

@@ -94,6 +94,26 @@ struct Work32 {
   double *Bd = nullptr;                           // [n] right-hand side staged for the device loop
 };
 
+// Serial schedule (serial.cu): colouring, colour-sorted slot layout, state.
+struct WorkS {
+  bool ready = false;
+  int C = 0;                   // number of colours
+  int *colour = nullptr;       // [n]
+  int *co = nullptr;           // [(C+1) x n] segment bounds per colour
+  int *sperm = nullptr;        // [E] serial slot -> input-layout slot
+  int *sci = nullptr;          // [E] sender of a serial slot
+  int *srev = nullptr;         // [E] serial slot of the reverse edge
+  double *sav = nullptr;       // [E] A values in serial order
+  double2 *SM = nullptr;       // [E] FP64 messages {P, h}
+  double2 *fire = nullptr;     // [n] FP64 firing aggregates
+  double *Pm = nullptr;        // [n] marginal precisions of the last FP64 sweep
+  bool valid = false;
+  int result_round = 0;
+  float2 *sCF = nullptr;       // [E] frozen coefficients in serial order
+  float *sH = nullptr;         // [E] FP32 mean messages
+  float *hfire = nullptr;      // [n] FP32 firing aggregates h~
+};
+
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
 
 struct Stats {
@@ -134,6 +154,9 @@ struct gabp_handle_s {
   cudaGraphExec_t gP32 = nullptr;
   cudaGraphExec_t gH32 = nullptr;
   cudaGraphExec_t gJ32 = nullptr;   // joint precision + mean rounds
+  gabp::WorkS ws;                   // serial schedule
+  cudaGraphExec_t gS64 = nullptr, gS32 = nullptr;  // serial sweeps (FP64, FP32 mean)
+  int gS64_key = -1, gS32_key = -1;
   cudaGraph_t gRefG = nullptr;      // whole FP32 refinement loop (conditional nodes) and its instance
   cudaGraphExec_t gRef = nullptr;
   long long gRef_key = -1;
@@ -325,6 +348,18 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
 void free_wb(gabp_handle h);
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host);
+// serial schedule (serial.cu)
+void free_ws(gabp_handle h);
+gabp_status serial_prepare(gabp_handle h);
+gabp_status serial_colours(gabp_handle h, int *colour_dev, int *ncolours);
+gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
+                           double *relres);
+gabp_status serial_messages64(gabp_handle h, double2 *M_input_layout);
+gabp_status serial_marginals64(gabp_handle h, double *Pi);
+gabp_status serial_freeze32(gabp_handle h, const float2 *CF);
+gabp_status serial_inner32(gabp_handle h, const float *rhs, const float *invP, int cap, double itol, int *sweeps,
+                           int *status);
+gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.
 constexpr int kGridShapes[5] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8)};

@@ -186,6 +186,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   free_w64(h);
   free_w32(h);
   free_wb(h);
+  free_ws(h);
   free_graph(h->g);
   cudaFree(h->ctl);
   cudaFreeHost(h->ctl_host);
@@ -301,7 +302,7 @@ static gabp_status check_options(const gabp_options *o) {
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
-      o->device_loop < 0 || o->device_loop > 1)
+      o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1)
     return GABP_ERR_INVALID;
   return GABP_OK;
 }

@@ -1250,7 +1250,8 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   h->stats.rounds = 0;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
-  if (h->opt.device_loop && !gamma_diag && !h->opt.profile && h->stream)
+  const bool serial = h->opt.schedule == 1 && !gamma_diag;
+  if (h->opt.device_loop && !gamma_diag && !h->opt.profile && h->stream && !serial)
     return solve32_device_loop(h, B, X, tol, max_iter, iters, relres);
   // the precision state is cached per handle when no loading is applied; when it
   // has to be computed, it is either computed first (precision-only rounds) or
@@ -1258,13 +1259,14 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   bool joint = false;
   if (!w.coef_ready || gamma_diag || !h->opt.reuse_precisions) {
     w.coef_ready = false;
-    joint = h->opt.overlap_precision != 0;
+    joint = h->opt.overlap_precision != 0 && !serial;
     if (!joint) {
       if ((s = precision_phase32(h, gamma_diag)) != GABP_OK) return s;
       if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
     }
   }
-  if ((s = autotune32(h, K32_MEAN)) != GABP_OK) return s;
+  if (serial && (s = serial_freeze32(h, w.CF)) != GABP_OK) return s;  // coefficients in the serial slot order
+  if (!serial && (s = autotune32(h, K32_MEAN)) != GABP_OK) return s;
   const int SH = shape32(h, K32_MEAN);
   // FP64 residual: narrow sub-warps (its per-row epilogue is FP64)
   const int LR = h->opt.lanes ? h->opt.lanes : (g.avg_deg >= 12.0 ? 2 : 1);
@@ -1302,6 +1304,27 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     // first one may start with the joint rounds, which leave round T's mean state
     const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
     const double it_tol = inner_target(itol, tol, bb, rr);
+    if (serial) {  // serial frozen-coefficient sweeps (serial.cu)
+      int sweeps = 0, ist = 0;
+      if ((s = serial_inner32(h, w.rhs32, w.invP, cap, it_tol, &sweeps, &ist)) != GABP_OK) return s;
+      total_inner += sweeps;
+      h->stats.rounds += sweeps;
+      if (ist == GABP_DIVERGED) { result = GABP_DIVERGED; break; }
+      prof_begin(h);
+      k64_update<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, X, h->ws.hfire, w.invP);
+      GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
+                                                                              w.NH[0], w.ctlR, h->partials, 0)));
+      prof_end(h);
+      h->prof.launches += 2;
+      GABP_CUDA(cudaGetLastError());
+      GABP_CUDA(cudaMemcpyAsync(&cr, w.ctlR, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
+      GABP_CUDA(cudaStreamSynchronize(h->stream));
+      prof_collect(h, PH_REFINE64, 1);
+      h->stats.refine_steps = step + 1;
+      if (!std::isfinite(cr.rr)) { result = GABP_DIVERGED; rr = cr.rr; break; }
+      rr = cr.rr;
+      continue;
+    }
     int T = 0;
     if (step == 0 && joint) {
       if ((s = joint_phase32(h, gamma_diag, cap, &T)) != GABP_OK) return s;

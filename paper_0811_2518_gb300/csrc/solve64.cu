@@ -487,6 +487,14 @@ gabp_status messages64(gabp_handle h, double *P, double *hm) {
   return GABP_OK;
 }
 
+gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm) {
+  Graph &g = h->g;
+  k64_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp, M, P, hm);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
 gabp_status marginals(gabp_handle h, double *Pi) {
   if (!h->w64.valid) return GABP_ERR_INVALID;
   Graph &g = h->g;
