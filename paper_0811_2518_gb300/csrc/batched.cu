@@ -298,6 +298,178 @@ __global__ void kb_scatter_cols(int n, int R, int RP, const double *__restrict__
   }
 }
 
+// ---------------------------------------------------------------------------- serial schedule, R right-hand sides
+// Pass c of a serial frozen-coefficient mean sweep for RP columns (one warp per
+// new row, lane l owns columns [l*VEC, l*VEC+VEC)); the layout, the order and
+// the recompute identity are those of serial.cu.  Per-column sums of the pass
+// go to acc[2][RP]; after the last pass every column with a nonzero iterate must
+// have its estimated error (step x q/(1-q), q the step ratio of the last two
+// sweeps, taken between 1 and 4 steps) within itol ||x_r||.
+struct ArgsBS {
+  int n, C, RP;
+  const int *__restrict__ co;
+  const int *__restrict__ sci;
+  const int *__restrict__ scol;
+  const int *__restrict__ srp;
+  const float2 *__restrict__ sCF;
+  const float *__restrict__ sinvP;
+  const float *__restrict__ srhs;  // [n][RP] new order
+  float *sH;                       // [E][RP] serial slot order
+  float *hfire;                    // [n][RP] new order
+  DevCtl *ctl;
+  double *red;
+  double *col;                     // [2][RP] pass sums, then [2][RP] sweep sums, [RP] previous step
+};
+
+template <int VEC>
+__global__ void __launch_bounds__(kBlock) kbs_pass(ArgsBS a, int c, int skip0, int skipn) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int RP = a.RP;
+  const int cn = c + 1 == a.C ? 0 : c + 1;
+  const int nv = a.n - skipn;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  const int c0 = lane * VEC;
+  float acc2[2][VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) acc2[0][v] = acc2[1][v] = 0.f;
+  for (int vr = warp; vr < nv; vr += nwarps) {
+    const int j = vr < skip0 ? vr : vr + skipn;
+    float hj[VEC], acc[VEC];
+    ldv<VEC>(a.hfire + (size_t)j * RP + c0, hj);
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+    const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
+    for (int e = s0; e < s1; ++e) {
+      const int k = a.sci[e];
+      const float2 cf = a.sCF[e];
+      float hs[VEC], hk[VEC], hn[VEC];
+      ldv_cs<VEC>(a.sH + (size_t)e * RP + c0, hs);
+      ldv<VEC>(a.hfire + (size_t)k * RP + c0, hk);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const float hout = cf.y * (hj[v] - hs[v]);  // message j -> k when j last fired
+        hn[v] = cf.x * (hk[v] - hout);              // message k -> j, k firing now
+        acc[v] += hn[v];
+      }
+      stv_cs<VEC>(a.sH + (size_t)e * RP + c0, hn);
+    }
+    if (a.scol[j] == cn) {  // j fires next: its aggregate over the whole row
+      for (int e = a.srp[j]; e < s0; ++e) {
+        float hs[VEC];
+        ldv<VEC>(a.sH + (size_t)e * RP + c0, hs);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += hs[v];
+      }
+      for (int e = s1; e < a.srp[j + 1]; ++e) {
+        float hs[VEC];
+        ldv<VEC>(a.sH + (size_t)e * RP + c0, hs);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += hs[v];
+      }
+      float rh[VEC], hnew[VEC];
+      ldv<VEC>(a.srhs + (size_t)j * RP + c0, rh);
+      const float ip = a.sinvP[j];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        hnew[v] = rh[v] + acc[v];
+        const float x = hnew[v] * ip, dx = (hnew[v] - hj[v]) * ip;
+        acc2[0][v] = fmaf(dx, dx, acc2[0][v]);
+        acc2[1][v] = fmaf(x, x, acc2[1][v]);
+      }
+      stv<VEC>(a.hfire + (size_t)j * RP + c0, hnew);
+    }
+  }
+  double accd[2][VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    accd[0][v] = (double)acc2[0][v];
+    accd[1][v] = (double)acc2[1][v];
+  }
+  if (col_reduce<VEC, 2>(accd, RP, a.red, a.col, &ctl->arrive)) {
+    // the last block: add the pass to the sweep's per-column sums
+    double *sw = a.col + 2 * RP, *prev = a.col + 4 * RP;
+    for (int r = threadIdx.x; r < 2 * RP; r += kBlock) sw[r] += a.col[r];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (c == a.C - 1) {  // the sweep is complete: per-column decision
+        const int t = ctl->round + 1;
+        ctl->round = t;
+        int notdone = 0;
+        bool finite = true;
+        for (int r = 0; r < RP; ++r) {
+          const double dd = sw[r], xx = sw[RP + r], pv = prev[r];
+          if (!isfinite(dd) || !isfinite(xx)) finite = false;
+          double f2 = 1.0;
+          if (t >= 3 && pv > 0.0) {
+            const double q = sqrt(dd / pv);
+            f2 = q < 0.8 ? fmax(1.0, (q / (1.0 - q)) * (q / (1.0 - q))) : 16.0;
+          }
+          if (xx > 0.0 && !(dd * f2 <= ctl->tol2bb * xx)) ++notdone;
+          prev[r] = dd;
+          sw[r] = 0.0;
+          sw[RP + r] = 0.0;
+        }
+        ctl->rr = (double)notdone;
+        if (!finite) {
+          ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+        } else if (t >= 2 && notdone == 0) {
+          ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+        } else if (t >= ctl->max_iter) {
+          ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+        }
+      }
+      ctl->arrive = 0;
+      __threadfence();
+    }
+  }
+}
+
+// new-order rows of an [n][RP] FP32 array from the input order; the inner
+// solve starts with h~ = r
+__global__ void kbs_init(int n, int RP, const int *__restrict__ oid, const float *__restrict__ rhs,
+                         float *__restrict__ srhs, float *__restrict__ hfire) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < n; j += nwarps) {
+    const size_t src = (size_t)oid[j] * RP, dst = (size_t)j * RP;
+    for (int r = lane; r < RP; r += 32) {
+      const float v = rhs[src + r];
+      srhs[dst + r] = v;
+      hfire[dst + r] = v;
+    }
+  }
+}
+
+// X[oid[j]][r] += h~_j^fire[r] / P~_j
+__global__ void kbs_update(int n, int RP, const int *__restrict__ oid, const float *__restrict__ hfire,
+                           const float *__restrict__ sinvP, double *__restrict__ X) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = warp; j < n; j += nwarps) {
+    const float ip = sinvP[j];
+    const size_t src = (size_t)j * RP, dst = (size_t)oid[j] * RP;
+    for (int r = lane; r < RP; r += 32) X[dst + r] += (double)(hfire[src + r] * ip);
+  }
+}
+
+__global__ void kbs_ctl_reset(DevCtl *c, int max_iter, double tol2, double *col, int RP) {
+  c->round = 0;
+  c->done = 0;
+  c->status = GABP_NOT_CONVERGED;
+  c->iters = 0;
+  c->result_round = 0;
+  c->max_iter = max_iter;
+  c->tol2bb = tol2;
+  c->arrive = 0;
+  c->no_stop = 0;
+  for (int r = 2 * RP; r < 5 * RP; ++r) col[r] = 0.0;  // sweep sums and previous steps
+}
+
 __global__ void kb_ctl_reset(DevCtl *c, int max_iter, double tol2) {
   c->round = 0;
   c->done = 0;
@@ -324,6 +496,9 @@ struct WorkB {
   unsigned int *arrive = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_key = -1;
+  float *sH = nullptr, *hfire = nullptr, *srhs = nullptr;  // serial schedule: [E][RP], [n][RP], [n][RP]
+  cudaGraphExec_t sgraph = nullptr;
+  int sgraph_key = -1;
 };
 
 void free_wb(gabp_handle h) {
@@ -332,7 +507,9 @@ void free_wb(gabp_handle h) {
   cudaFree(w->H[0]); cudaFree(w->H[1]);
   for (int j = 0; j < 3; ++j) cudaFree(w->NH[j]);
   cudaFree(w->rhs); cudaFree(w->X); cudaFree(w->Bt); cudaFree(w->red); cudaFree(w->col); cudaFree(w->arrive);
+  cudaFree(w->sH); cudaFree(w->hfire); cudaFree(w->srhs);
   if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->sgraph) cudaGraphExecDestroy(w->sgraph);
   delete w;
   h->wb = nullptr;
 }
@@ -350,7 +527,7 @@ static gabp_status ensure_wb(gabp_handle h, int RP) {
   GABP_CUDA(cudaMalloc(&w->X, sizeof(double) * n * RP));
   GABP_CUDA(cudaMalloc(&w->Bt, sizeof(double) * n * RP));
   GABP_CUDA(cudaMalloc(&w->red, sizeof(double) * 2 * (size_t)h->max_blocks * RP));
-  GABP_CUDA(cudaMalloc(&w->col, sizeof(double) * 4 * RP));
+  GABP_CUDA(cudaMalloc(&w->col, sizeof(double) * 5 * RP));
   GABP_CUDA(cudaMalloc(&w->arrive, sizeof(unsigned int)));
   GABP_CUDA(cudaMemsetAsync(w->arrive, 0, sizeof(unsigned int), h->stream));
   w->RP = RP;
@@ -400,6 +577,22 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
   a.H0 = w.H[0]; a.H1 = w.H[1]; a.NH0 = w.NH[0]; a.NH1 = w.NH[1]; a.NH2 = w.NH[2];
   a.rhs = w.rhs; a.ctl = h->ctl; a.red = w.red; a.col = w.col;
   const double itol = h->opt.inner_tol;
+  const bool serial = h->opt.schedule == 1;
+  ArgsBS as;
+  int nb_ser = 1;
+  if (serial) {
+    if ((s = serial_freeze32(h, w32.CF, w32.invP)) != GABP_OK) return s;
+    WorkS &ws = h->ws;
+    if (!w.sH) {
+      GABP_CUDA(cudaMalloc(&w.sH, sizeof(float) * E * RP));
+      GABP_CUDA(cudaMalloc(&w.hfire, sizeof(float) * g.n * RP));
+      GABP_CUDA(cudaMalloc(&w.srhs, sizeof(float) * g.n * RP));
+    }
+    as.n = g.n; as.C = ws.C; as.RP = RP; as.co = ws.co; as.sci = ws.sci; as.scol = ws.scol; as.srp = ws.srp;
+    as.sCF = ws.sCF; as.sinvP = ws.sinvP; as.srhs = w.srhs; as.sH = w.sH; as.hfire = w.hfire;
+    as.ctl = h->ctl; as.red = w.red; as.col = w.col;
+    nb_ser = grid_of(kbs_pass<VEC>);
+  }
   int total_inner = 0;
   auto all_done = [&]() {
     for (int r = 0; r < R; ++r)
@@ -408,17 +601,29 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
   };
   bool diverged = false;
   for (int step = 0; step < h->opt.max_refine && !all_done() && total_inner < max_iter; ++step) {
-    GABP_CUDA(cudaMemsetAsync(w.H[0], 0, sizeof(float) * E * RP, h->stream));
+    GABP_CUDA(cudaMemsetAsync(serial ? w.sH : w.H[0], 0, sizeof(float) * E * RP, h->stream));
     const int cap = std::min(h->opt.inner_max_iter, std::max(1, max_iter - total_inner));
     double worst_ratio = 0.0;  // the column furthest from its target sets the inner tolerance
     for (int r = 0; r < R; ++r)
       if (bb[r] > 0.0) worst_ratio = std::max(worst_ratio, rr[r] / bb[r]);
     const double it_tol = inner_target(itol, tol, 1.0, worst_ratio);
-    kb_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
-    h->prof.launches += 1;
-    GABP_CUDA(cudaGetLastError());
-    s = run_rounds(h, &w.graph, &w.graph_key, RP, [&] { kb_mean<VEC><<<nb_mean, kBlock, shmem, h->stream>>>(a); }, cap,
-                   PH_MEAN32);
+    if (serial) {
+      WorkS &ws = h->ws;
+      kbs_init<<<std::max(1, (g.n + 7) / 8), kBlock, 0, h->stream>>>(g.n, RP, ws.oid, w.rhs, w.srhs, w.hfire);
+      kbs_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol, w.col, RP);
+      h->prof.launches += 2;
+      GABP_CUDA(cudaGetLastError());
+      s = run_rounds(h, &w.sgraph, &w.sgraph_key, RP | (ws.C << 16), [&] {
+        for (int c = 0; c < ws.C; ++c)
+          kbs_pass<VEC><<<nb_ser, kBlock, shmem, h->stream>>>(as, c, ws.cstart[c], ws.cstart[c + 1] - ws.cstart[c]);
+      }, cap, PH_MEAN32);
+    } else {
+      kb_ctl_reset<<<1, 1, 0, h->stream>>>(h->ctl, cap, it_tol * it_tol);
+      h->prof.launches += 1;
+      GABP_CUDA(cudaGetLastError());
+      s = run_rounds(h, &w.graph, &w.graph_key, RP, [&] { kb_mean<VEC><<<nb_mean, kBlock, shmem, h->stream>>>(a); },
+                     cap, PH_MEAN32);
+    }
     if (s != GABP_OK) return s;
     const DevCtl c = *h->ctl_host;
     total_inner += c.round;
@@ -427,7 +632,10 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
     if (c.status == GABP_DIVERGED) { diverged = true; break; }
     float *hT = w.NH[c.result_round % 3];
     prof_begin(h);
-    kb_update<VEC><<<std::max(1, (g.n + 7) / 8), kBlock, 0, h->stream>>>(g.n, RP, w.X, hT, w32.invP);
+    if (serial)
+      kbs_update<<<std::max(1, (g.n + 7) / 8), kBlock, 0, h->stream>>>(g.n, RP, h->ws.oid, w.hfire, h->ws.sinvP, w.X);
+    else
+      kb_update<VEC><<<std::max(1, (g.n + 7) / 8), kBlock, 0, h->stream>>>(g.n, RP, w.X, hT, w32.invP);
     kb_residual<VEC><<<nb_res, kBlock, shmem, h->stream>>>(g.n, RP, g.rowptr, g.col, g.val, w.Bt, w.X, w.rhs,
                                                            w.NH[0], w.red, w.col, w.arrive);
     prof_end(h);

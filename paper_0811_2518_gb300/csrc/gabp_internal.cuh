@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <cstddef>
 #include <string>
+#include <vector>
 #include <algorithm>
 #include <cmath>
 
@@ -94,24 +95,35 @@ struct Work32 {
   double *Bd = nullptr;                           // [n] right-hand side staged for the device loop
 };
 
-// Serial schedule (serial.cu): colouring, colour-sorted slot layout, state.
+// Serial schedule (serial.cu): colouring, colour-grouped relabelling,
+// colour-sorted slot layout, state.
 struct WorkS {
   bool ready = false;
   int C = 0;                   // number of colours
-  int *colour = nullptr;       // [n]
+  std::vector<int> cstart;     // [C+1] first new label of each colour class (host)
+  int *colour = nullptr;       // [n] colour of each node (input labels)
+  int *oid = nullptr;          // [n] new label -> input label
+  int *nid = nullptr;          // [n] input label -> new label
+  int *srp = nullptr;          // [n+1] row pointer of the new rows
+  int *scol = nullptr;         // [n] colour of each new row
   int *co = nullptr;           // [(C+1) x n] segment bounds per colour
   int *sperm = nullptr;        // [E] serial slot -> input-layout slot
-  int *sci = nullptr;          // [E] sender of a serial slot
+  int *sci = nullptr;          // [E] sender (new label) of a serial slot
   int *srev = nullptr;         // [E] serial slot of the reverse edge
   double *sav = nullptr;       // [E] A values in serial order
+  double *sad = nullptr;       // [n] A_jj in the new order
+  double *sb = nullptr;        // [n] b in the new order (FP64 sweeps)
+  double *bin = nullptr, *xin = nullptr;  // [n] staged b and iterate (input order) of the FP64 sweeps
   double2 *SM = nullptr;       // [E] FP64 messages {P, h}
   double2 *fire = nullptr;     // [n] FP64 firing aggregates
-  double *Pm = nullptr;        // [n] marginal precisions of the last FP64 sweep
+  double *sPm = nullptr;       // [n] marginal precisions of the last FP64 sweep (new order)
   bool valid = false;
   int result_round = 0;
   float2 *sCF = nullptr;       // [E] frozen coefficients in serial order
   float *sH = nullptr;         // [E] FP32 mean messages
   float *hfire = nullptr;      // [n] FP32 firing aggregates h~
+  float *srhs = nullptr;       // [n] inner right-hand side (new order)
+  float *sinvP = nullptr;      // [n] 1 / P~ (new order)
 };
 
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
@@ -356,9 +368,9 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
                            double *relres);
 gabp_status serial_messages64(gabp_handle h, double2 *M_input_layout);
 gabp_status serial_marginals64(gabp_handle h, double *Pi);
-gabp_status serial_freeze32(gabp_handle h, const float2 *CF);
-gabp_status serial_inner32(gabp_handle h, const float *rhs, const float *invP, int cap, double itol, int *sweeps,
-                           int *status);
+gabp_status serial_freeze32(gabp_handle h, const float2 *CF, const float *invP);
+gabp_status serial_inner32(gabp_handle h, const float *rhs, int cap, double itol, int *sweeps, int *status);
+gabp_status serial_update32(gabp_handle h, double *X);
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.

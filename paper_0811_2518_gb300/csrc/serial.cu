@@ -12,10 +12,13 @@
 // priority is the index, which reproduces the sequential greedy colouring
 // exactly.
 //
-// Layout.  Every row's off-diagonal slots are re-sorted by the sender's colour
-// (then index): the slots of row i whose sender has colour c form the segment
-// [co[c][i], co[c+1][i]).  Pass c updates, in every row, the segment of colour
-// c: these are exactly the messages sent by the nodes that fire in pass c.
+// Layout.  The nodes are relabelled so that every colour class is one
+// contiguous range (colour order, index order inside a colour), and every
+// row's off-diagonal slots are sorted by the new sender label, so that the
+// slots of row j whose sender has colour c form the segment [co[c][j],
+// co[c+1][j]).  Pass c updates, in every row outside colour c's range, the
+// segment of colour c: exactly the messages sent by the nodes that fire in pass
+// c.  Right-hand sides, iterates and marginals are permuted at the boundary.
 //
 // Pull form.  The message k -> i sent when k fires is computed by row i's
 // thread from k's firing aggregate (one gather) and the reverse message i -> k
@@ -32,6 +35,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace gabp {
@@ -73,45 +77,43 @@ __global__ void ks_colour(int n, const int *__restrict__ rp, const int *__restri
   if (mine) atomicAdd(left, mine);
 }
 
-// Slots of row i in (sender colour, sender) order: sperm[rp[i] + rank] = e.
-__global__ void ks_sort(int n, const int *__restrict__ rp, const int *__restrict__ ci, const int *__restrict__ colour,
-                        int *__restrict__ sperm) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int e0 = rp[i], e1 = rp[i + 1];
+// Slots of new row j (old row oid[j]) in new-sender order: sperm[srp[j] + rank] = e
+// (e an off-diagonal slot of the input layout).
+__global__ void ks_sort(int n, const int *__restrict__ srp, const int *__restrict__ oid, const int *__restrict__ rp,
+                        const int *__restrict__ ci, const int *__restrict__ nid, int *__restrict__ sperm) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int i = oid[j], e0 = rp[i], e1 = rp[i + 1], p0 = srp[j];
     for (int e = e0; e < e1; ++e) {
-      const long long ke = ((long long)colour[ci[e]] << 32) | (unsigned)ci[e];
+      const int ke = nid[ci[e]];
       int rank = 0;
-      for (int f = e0; f < e1; ++f) {
-        const long long kf = ((long long)colour[ci[f]] << 32) | (unsigned)ci[f];
-        rank += kf < ke;
-      }
-      sperm[e0 + rank] = e;
+      for (int f = e0; f < e1; ++f) rank += nid[ci[f]] < ke;
+      sperm[p0 + rank] = e;
     }
   }
 }
 
-// Segment bounds co[c * n + i] (c = 0..C) and the permuted slot arrays.
-__global__ void ks_offsets(int n, int C, const int *__restrict__ rp, const int *__restrict__ ci,
-                           const int *__restrict__ colour, const int *__restrict__ sperm, int *__restrict__ co) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int p = rp[i];
-    const int e1 = rp[i + 1];
-    for (int c = 0; c <= C; ++c) {
-      while (p < e1 && colour[ci[sperm[p]]] < c) ++p;
-      co[(size_t)c * n + i] = p;
-    }
-  }
-}
-
-__global__ void ks_gather(int E, const int *__restrict__ sperm, const int *__restrict__ ci,
+__global__ void ks_gather(int E, const int *__restrict__ sperm, const int *__restrict__ ci, const int *__restrict__ nid,
                           const double *__restrict__ av, int *__restrict__ sci, double *__restrict__ sav,
                           int *__restrict__ inv) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < E) {
     const int e = sperm[p];
-    sci[p] = ci[e];
+    sci[p] = nid[ci[e]];
     sav[p] = av[e];
     inv[e] = p;
+  }
+}
+
+// Segment bounds co[c * n + j] (c = 0..C) of new row j.
+__global__ void ks_offsets(int n, int C, const int *__restrict__ srp, const int *__restrict__ sci,
+                           const int *__restrict__ scol, int *__restrict__ co) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int p = srp[j];
+    const int p1 = srp[j + 1];
+    for (int c = 0; c <= C; ++c) {
+      while (p < p1 && scol[sci[p]] < c) ++p;
+      co[(size_t)c * n + j] = p;
+    }
   }
 }
 
@@ -121,65 +123,89 @@ __global__ void ks_rev(int E, const int *__restrict__ sperm, const int *__restri
   if (p < E) srev[p] = inv[rev[sperm[p]]];
 }
 
+// out[j] = in[oid[j]] (old order -> new order), FP64 / FP32
+__global__ void ks_perm64(int n, const int *__restrict__ oid, const double *__restrict__ in, double *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = in[oid[j]];
+}
+__global__ void ks_perm32(int n, const int *__restrict__ oid, const float *__restrict__ in, float *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = in[oid[j]];
+}
+// out[oid[j]] = in[j] (new order -> old order)
+__global__ void ks_unperm64(int n, const int *__restrict__ oid, const double *__restrict__ in, double *__restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[oid[j]] = in[j];
+}
+
+// Row j of the v-th row of a pass that skips the rows [skip0, skip0 + skipn) of
+// the colour that fires (they have no segment of their own colour).
+__device__ __forceinline__ int pass_row(int v, int skip0, int skipn) { return v < skip0 ? v : v + skipn; }
+
 // ---------------------------------------------------------------------------- FP64 serial sweeps
 struct ArgsS64 {
   int n, C;
   const int *__restrict__ co;
   const int *__restrict__ sci;
   const int *__restrict__ srev;
-  const int *__restrict__ colour;
-  const int *__restrict__ rp;
+  const int *__restrict__ scol;
+  const int *__restrict__ srp;
+  const int *__restrict__ oid;
   const double *__restrict__ sav;
-  const double *__restrict__ ad;
-  const double *__restrict__ b;
+  const double *__restrict__ sad;  // A_jj in the new order
+  const double *__restrict__ sb;   // b in the new order
+  const double *__restrict__ b;    // b in the input order (residual)
   const int *__restrict__ rowptr;
   const int *__restrict__ col;
   const double *__restrict__ val;
   double2 *SM;    // {P, h} per serial slot (message sender -> row)
-  double2 *fire;  // {P~, h~} firing aggregate per node
-  double *x, *Pm;
+  double2 *fire;  // {P~, h~} firing aggregate per node (new order)
+  double *x;      // iterate in the input order
+  double *sPm;    // marginal precisions in the new order
   DevCtl *ctl;
   double *partials;
 };
 
 __global__ void ks64_init(ArgsS64 a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.n) a.fire[i] = make_double2(a.ad[i], a.b[i]);  // no message yet: P~ = A_ii, h~ = b_i
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < a.n) a.fire[j] = make_double2(a.sad[j], a.sb[j]);  // no message yet: P~ = A_jj, h~ = b_j
 }
 
-// Pass c: the nodes of colour c fire (every row updates its colour-c segment),
-// then the rows of colour c + 1 form their firing aggregates.
+// Pass c: the nodes of colour c fire (every other row updates its colour-c
+// segment), then the rows of colour c + 1 form their firing aggregates.
 template <int L>
-__global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c) {
+__global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0, int skipn) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int cn = c + 1 == a.C ? 0 : c + 1;
+  const int nv = a.n - skipn;
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
   int bad = 0;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
+  for (int base = warp * RPW; base < nv; base += nwarps * RPW) {
+    const int v = base + sw;
+    const int j = pass_row(v, skip0, skipn);
     double P = 0.0, h = 0.0;
     bool fires_next = false;
-    if (i < a.n) {
-      const int s0 = a.co[(size_t)c * a.n + i], s1 = a.co[(size_t)(c + 1) * a.n + i];
+    if (v < nv) {
+      const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
       for (int e = s0 + sl; e < s1; e += L) {
         const int k = a.sci[e];
         const double A = a.sav[e];
         const double2 fk = a.fire[k];         // k's aggregate when it fires
-        const double2 rv = a.SM[a.srev[e]];   // message i -> k as k holds it
-        const double d = fk.x - rv.x;         // P_{k\i}
+        const double2 rv = a.SM[a.srev[e]];   // message j -> k as k holds it
+        const double d = fk.x - rv.x;         // P_{k\j}
         bad |= is_zero64(d);
         const double r = rcp64(d);
         a.SM[e] = make_double2(-A * A * r, -A * (fk.y - rv.y) * r);
       }
-      fires_next = a.colour[i] == cn;
+      fires_next = a.scol[j] == cn;
     }
     __syncwarp();
     if (fires_next) {
-      for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) {
+      for (int e = a.srp[j] + sl; e < a.srp[j + 1]; e += L) {
         const double2 m = a.SM[e];
         P += m.x;
         h += m.y;
@@ -187,12 +213,13 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c) {
     }
     P = sub_sum<L>(P);
     h = sub_sum<L>(h);
-    if (fires_next && sl == 0) a.fire[i] = make_double2(a.ad[i] + P, a.b[i] + h);
+    if (fires_next && sl == 0) a.fire[j] = make_double2(a.sad[j] + P, a.sb[j] + h);
   }
   if (bad) atomicOr(&ctl->edge_bad, 1);
 }
 
-// After a sweep: x_i = h~_i / P~_i and P_i from every current message into i.
+// After a sweep: x = h~ / P~ and P from every current message (Algorithm 1
+// step 4), x written in the input order.
 template <int L>
 __global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
   DevCtl *ctl = a.ctl;
@@ -203,29 +230,29 @@ __global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
   const int nwarps = (gridDim.x * kBlock) >> 5;
   int bad = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
+    const int j = base + sw;
     double P = 0.0, h = 0.0;
-    if (i < a.n)
-      for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) {
+    if (j < a.n)
+      for (int e = a.srp[j] + sl; e < a.srp[j + 1]; e += L) {
         const double2 m = a.SM[e];
         P += m.x;
         h += m.y;
       }
     P = sub_sum<L>(P);
     h = sub_sum<L>(h);
-    if (i < a.n && sl == 0) {
-      P += a.ad[i];
-      h += a.b[i];
+    if (j < a.n && sl == 0) {
+      P += a.sad[j];
+      h += a.sb[j];
       bad |= is_zero64(P);
-      a.Pm[i] = P;
-      a.x[i] = h / P;
+      a.sPm[j] = P;
+      a.x[a.oid[j]] = h / P;
     }
   }
   if (bad) atomicOr(&ctl->edge_bad, 2);
 }
 
-// ||b - A x||^2 of the sweep's x and the decision (Algorithm 1 step 3 with the
-// residual rule): breakdown, divergence, convergence, max_iter.
+// ||b - A x||^2 of the sweep's x (input order) and the decision (Algorithm 1
+// step 3 with the residual rule): breakdown, divergence, convergence, max_iter.
 template <int L>
 __global__ void __launch_bounds__(kBlock) ks64_decide(ArgsS64 a) {
   DevCtl *ctl = a.ctl;
@@ -278,6 +305,7 @@ __global__ void ks64_ctl(DevCtl *c, int max_iter, double bb, double tol2) {
   c->tol2bb = tol2 * bb;
   c->rr = 0.0;
   c->xx = 0.0;
+  c->maxrel = 0.0;
   c->arrive = 0;
   c->edge_bad = 0;
   c->no_stop = 0;
@@ -297,7 +325,7 @@ __global__ void ks_bb(int n, const double *__restrict__ b, DevCtl *ctl, double *
   }
 }
 
-// serial slot -> input-layout slot (messages read-back, gradient-free marginals)
+// serial slot -> input-layout slot (messages read-back)
 __global__ void ks_unpermute(int E, const int *__restrict__ sperm, const double2 *__restrict__ SM, double2 *M) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < E) M[sperm[p]] = SM[p];
@@ -308,62 +336,90 @@ struct ArgsS32 {
   int n, C;
   const int *__restrict__ co;
   const int *__restrict__ sci;
-  const int *__restrict__ colour;
-  const int *__restrict__ rp;
+  const int *__restrict__ scol;
+  const int *__restrict__ srp;
   const float2 *__restrict__ sCF;  // {c_in, c_out} in the serial slot order
-  const float *__restrict__ rhs;
-  const float *__restrict__ invP;
+  const float *__restrict__ srhs;  // inner right-hand side, new order
+  const float *__restrict__ sinvP; // 1 / P~, new order
   float *sH;     // mean message per serial slot
-  float *hfire;  // h~_i at i's last firing
+  float *hfire;  // h~_j at j's last firing (new order)
   DevCtl *ctl;
   double *partials;
 };
 
-__global__ void ks32_init(int n, const float *__restrict__ rhs, float *hfire) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) hfire[i] = rhs[i];  // no message yet: h~_i = r_i
+__global__ void ks32_init(int n, const int *__restrict__ oid, const float *__restrict__ rhs, float *__restrict__ srhs,
+                          float *__restrict__ hfire) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    const float r = rhs[oid[j]];
+    srhs[j] = r;
+    hfire[j] = r;  // no message yet: h~_j = r_j
+  }
 }
 
-// Pass c of a frozen-coefficient mean sweep.  The sweep's stop test adds
-// ||x^fire_new - x^fire_old||^2 and ||x^fire_new||^2 over the rows that form a
-// new firing aggregate in this pass (every row once per sweep) and decides
-// after the last pass: ||dx|| <= itol ||x|| (from the second sweep), a
+// Pass c of a frozen-coefficient mean sweep (L lanes per row, U slots per lane
+// with their loads issued together).  The sweep's stop test adds
+// ||x^fire_new - x^fire_old||^2 and ||x^fire_new||^2 over the rows forming a new
+// firing aggregate in this pass (every row once per sweep) and decides after
+// the last pass: estimated error <= itol ||x|| (from the second sweep), a
 // non-finite value, or max_iter sweeps.
-template <int L>
-__global__ void __launch_bounds__(kBlock) ks32_pass(ArgsS32 a, int c) {
+template <int L, int U>
+__global__ void __launch_bounds__(kBlock) ks32_pass(ArgsS32 a, int c, int skip0, int skipn) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int cn = c + 1 == a.C ? 0 : c + 1;
+  const int nv = a.n - skipn;
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
   float dxx = 0.f, xx = 0.f;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
-    float h = 0.f;
+  for (int base = warp * RPW; base < nv; base += nwarps * RPW) {
+    const int v = base + sw;
+    const int j = pass_row(v, skip0, skipn);
     bool fires_next = false;
-    if (i < a.n) {
-      const float hi = a.hfire[i];
-      const int s0 = a.co[(size_t)c * a.n + i], s1 = a.co[(size_t)(c + 1) * a.n + i];
-      for (int e = s0 + sl; e < s1; e += L) {
-        const int k = a.sci[e];
-        const float2 cf = __ldcs(a.sCF + e);
-        const float hout = cf.y * (hi - a.sH[e]);  // message i -> k when i last fired
-        a.sH[e] = cf.x * (a.hfire[k] - hout);      // message k -> i, k firing now
+    float h = 0.f;  // this lane's share of the new aggregate
+    int s0 = 0, s1 = 0;
+    if (v < nv) {
+      const float hj = a.hfire[j];
+      s0 = a.co[(size_t)c * a.n + j];
+      s1 = a.co[(size_t)(c + 1) * a.n + j];
+      for (int eb = s0 + sl; eb < s1; eb += L * U) {
+        int k[U];
+        float2 cf[U];
+        float hs[U], hk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < s1) { k[u] = __ldcs(a.sci + e); cf[u] = __ldcs(a.sCF + e); hs[u] = a.sH[e]; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (eb + u * L < s1) hk[u] = a.hfire[k[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = eb + u * L;
+          if (e < s1) {
+            const float hout = cf[u].y * (hj - hs[u]);  // message j -> k when j last fired
+            const float hn = cf[u].x * (hk[u] - hout);  // message k -> j, k firing now
+            a.sH[e] = hn;
+            h += hn;
+          }
+        }
       }
-      fires_next = a.colour[i] == cn;
+      fires_next = a.scol[j] == cn;
     }
-    __syncwarp();
-    if (fires_next)
-      for (int e = a.rp[i] + sl; e < a.rp[i + 1]; e += L) h += a.sH[e];
+    if (fires_next) {  // the rest of the row (the segment's new messages are in h already)
+      for (int e = a.srp[j] + sl; e < s0; e += L) h += a.sH[e];
+      for (int e = s1 + sl; e < a.srp[j + 1]; e += L) h += a.sH[e];
+    }
     h = sub_sum<L>(h);
     if (fires_next && sl == 0) {
-      const float hn = a.rhs[i] + h, ip = a.invP[i];
-      const float dx = (hn - a.hfire[i]) * ip, xn = hn * ip;
+      const float hn = a.srhs[j] + h, ip = a.sinvP[j];
+      const float dx = (hn - a.hfire[j]) * ip, xn = hn * ip;
       dxx = fmaf(dx, dx, dxx);
       xx = fmaf(xn, xn, xx);
-      a.hfire[i] = hn;
+      a.hfire[j] = hn;
     }
   }
   double v[2] = {(double)dxx, (double)xx}, tot[2];
@@ -375,10 +431,20 @@ __global__ void __launch_bounds__(kBlock) ks32_pass(ArgsS32 a, int c) {
     if (c == a.C - 1) {  // the sweep is complete
       const int t = ctl->round + 1;
       ctl->round = t;
-      const double dd = ctl->rr, x2 = ctl->xx;
+      const double dd = ctl->rr, x2 = ctl->xx, prev = ctl->maxrel;
+      ctl->maxrel = dd;
+      // a serial sweep contracts without the sign alternation of the parallel
+      // rounds, so the step underestimates the error: error ~ step q / (1 - q)
+      // with q = ||dx_t|| / ||dx_{t-1}||, taken between 1 and 4 steps (a ratio
+      // near 1 is FP32 noise at the end of the solve, not slow convergence)
+      double f2 = 1.0;
+      if (t >= 3 && prev > 0.0) {
+        const double q = sqrt(dd / prev);
+        f2 = q < 0.8 ? fmax(1.0, (q / (1.0 - q)) * (q / (1.0 - q))) : 16.0;
+      }
       if (!isfinite(dd) || !isfinite(x2)) {
         ctl->status = GABP_DIVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
-      } else if (t >= 2 && dd <= ctl->tol2bb * x2) {
+      } else if (t >= 2 && dd * f2 <= ctl->tol2bb * x2) {
         ctl->status = GABP_OK; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
       } else if (t >= ctl->max_iter) {
         ctl->status = GABP_NOT_CONVERGED; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
@@ -391,26 +457,36 @@ __global__ void __launch_bounds__(kBlock) ks32_pass(ArgsS32 a, int c) {
   }
 }
 
+// x (input order) += d, d_j = h~_j^fire / P~_j
+__global__ void ks32_update(int n, const int *__restrict__ oid, const float *__restrict__ hfire,
+                            const float *__restrict__ sinvP, double *__restrict__ x) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) x[oid[j]] += (double)(hfire[j] * sinvP[j]);
+}
+
 __global__ void ks32_permute_cf(int E, const int *__restrict__ sperm, const float2 *__restrict__ CF, float2 *sCF) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < E) sCF[p] = CF[sperm[p]];
 }
 
-int serial_lanes(const Graph &g) { return g.avg_deg >= 24.0 ? 4 : (g.avg_deg >= 8.0 ? 2 : 1); }
+int serial_lanes64(const Graph &g) { return g.avg_deg >= 24.0 ? 4 : (g.avg_deg >= 8.0 ? 2 : 1); }
 
 }  // namespace
 
 void free_ws(gabp_handle h) {
   WorkS &s = h->ws;
   cudaFree(s.colour); cudaFree(s.co); cudaFree(s.sperm); cudaFree(s.sci); cudaFree(s.srev); cudaFree(s.sav);
-  cudaFree(s.SM); cudaFree(s.fire); cudaFree(s.sCF); cudaFree(s.sH); cudaFree(s.hfire);
+  cudaFree(s.oid); cudaFree(s.nid); cudaFree(s.srp); cudaFree(s.scol); cudaFree(s.sad); cudaFree(s.sb);
+  cudaFree(s.SM); cudaFree(s.fire); cudaFree(s.sPm); cudaFree(s.sCF); cudaFree(s.sH); cudaFree(s.hfire);
+  cudaFree(s.srhs); cudaFree(s.sinvP); cudaFree(s.bin); cudaFree(s.xin);
   if (h->gS64) cudaGraphExecDestroy(h->gS64);
   if (h->gS32) cudaGraphExecDestroy(h->gS32);
   h->gS64 = h->gS32 = nullptr;
   s = WorkS{};
 }
 
-// Colouring and the colour-sorted layout (once per handle).
+// Colouring, the colour-grouped relabelling and the colour-sorted slot layout
+// (once per handle).
 gabp_status serial_prepare(gabp_handle h) {
   WorkS &s = h->ws;
   if (s.ready) return GABP_OK;
@@ -429,7 +505,7 @@ gabp_status serial_prepare(gabp_handle h) {
   const int nb = blocks_for(n, kBlock, h->max_blocks);
   // every pass colours at least the lowest uncoloured node, so n passes always suffice
   int hm[2] = {1, 0};
-  for (long long done_passes = 0; hm[0] > 0; ) {
+  for (long long done_passes = 0; hm[0] > 0;) {
     if (done_passes > n) {
       set_last_error("serial colouring did not finish");
       return GABP_ERR_CUDA;
@@ -443,6 +519,34 @@ gabp_status serial_prepare(gabp_handle h) {
     GABP_CUDA(cudaStreamSynchronize(h->stream));
   }
   s.C = hm[1] + 1;
+  // relabelling: colour classes contiguous, index order inside (a stable counting sort)
+  std::vector<int> col(n), rp(n + 1), oid(n), nid(n), srp(n + 1), scol(n);
+  GABP_CUDA(cudaMemcpyAsync(col.data(), s.colour, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(rp.data(), g.rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  s.cstart.assign(s.C + 1, 0);
+  for (int i = 0; i < n; ++i) ++s.cstart[col[i] + 1];
+  for (int c = 0; c < s.C; ++c) s.cstart[c + 1] += s.cstart[c];
+  std::vector<int> fill(s.cstart.begin(), s.cstart.end() - 1);
+  for (int i = 0; i < n; ++i) {
+    const int j = fill[col[i]]++;
+    oid[j] = i;
+    nid[i] = j;
+  }
+  srp[0] = 0;
+  for (int j = 0; j < n; ++j) {
+    srp[j + 1] = srp[j] + (rp[oid[j] + 1] - rp[oid[j]]);
+    scol[j] = col[oid[j]];
+  }
+  GABP_CUDA(cudaMalloc(&s.oid, sizeof(int) * n));
+  GABP_CUDA(cudaMalloc(&s.nid, sizeof(int) * n));
+  GABP_CUDA(cudaMalloc(&s.srp, sizeof(int) * (n + 1)));
+  GABP_CUDA(cudaMalloc(&s.scol, sizeof(int) * n));
+  GABP_CUDA(cudaMalloc(&s.sad, sizeof(double) * n));
+  GABP_CUDA(cudaMemcpyAsync(s.oid, oid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(s.nid, nid.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(s.srp, srp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, h->stream));
+  GABP_CUDA(cudaMemcpyAsync(s.scol, scol.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
   GABP_CUDA(cudaMalloc(&s.co, sizeof(int) * (size_t)(s.C + 1) * n));
   GABP_CUDA(cudaMalloc(&s.sperm, sizeof(int) * Ea));
   GABP_CUDA(cudaMalloc(&s.sci, sizeof(int) * Ea));
@@ -454,13 +558,14 @@ gabp_status serial_prepare(gabp_handle h) {
     int *p;
     ~F2() { cudaFree(p); }
   } fr2{inv};
-  ks_sort<<<nb, kBlock, 0, h->stream>>>(n, g.rp, g.ci, s.colour, s.sperm);
-  ks_offsets<<<nb, kBlock, 0, h->stream>>>(n, s.C, g.rp, g.ci, s.colour, s.sperm, s.co);
+  ks_sort<<<nb, kBlock, 0, h->stream>>>(n, s.srp, s.oid, g.rp, g.ci, s.nid, s.sperm);
   if (E > 0) {
     const int eb = (E + kBlock - 1) / kBlock;
-    ks_gather<<<eb, kBlock, 0, h->stream>>>(E, s.sperm, g.ci, g.av, s.sci, s.sav, inv);
+    ks_gather<<<eb, kBlock, 0, h->stream>>>(E, s.sperm, g.ci, s.nid, g.av, s.sci, s.sav, inv);
     ks_rev<<<eb, kBlock, 0, h->stream>>>(E, s.sperm, g.rev, inv, s.srev);
   }
+  ks_offsets<<<nb, kBlock, 0, h->stream>>>(n, s.C, s.srp, s.sci, s.scol, s.co);
+  ks_perm64<<<(n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(n, s.oid, g.ad, s.sad);
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   s.ready = true;
@@ -481,9 +586,9 @@ static ArgsS64 args_s64(gabp_handle h, const double *b, double *x) {
   Graph &g = h->g;
   WorkS &s = h->ws;
   ArgsS64 a;
-  a.n = g.n; a.C = s.C; a.co = s.co; a.sci = s.sci; a.srev = s.srev; a.colour = s.colour; a.rp = g.rp;
-  a.sav = s.sav; a.ad = g.ad; a.b = b; a.rowptr = g.rowptr; a.col = g.col; a.val = g.val;
-  a.SM = s.SM; a.fire = s.fire; a.x = x; a.Pm = s.Pm;
+  a.n = g.n; a.C = s.C; a.co = s.co; a.sci = s.sci; a.srev = s.srev; a.scol = s.scol; a.srp = s.srp; a.oid = s.oid;
+  a.sav = s.sav; a.sad = s.sad; a.sb = s.sb; a.b = b; a.rowptr = g.rowptr; a.col = g.col; a.val = g.val;
+  a.SM = s.SM; a.fire = s.fire; a.x = x; a.sPm = s.sPm;
   a.ctl = h->ctl; a.partials = h->partials;
   return a;
 }
@@ -500,12 +605,19 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   if (!s.SM) {
     GABP_CUDA(cudaMalloc(&s.SM, sizeof(double2) * Ea));
     GABP_CUDA(cudaMalloc(&s.fire, sizeof(double2) * g.n));
-    GABP_CUDA(cudaMalloc(&s.Pm, sizeof(double) * g.n));
+    GABP_CUDA(cudaMalloc(&s.sPm, sizeof(double) * g.n));
+    GABP_CUDA(cudaMalloc(&s.sb, sizeof(double) * g.n));
+    GABP_CUDA(cudaMalloc(&s.bin, sizeof(double) * g.n));
+    GABP_CUDA(cudaMalloc(&s.xin, sizeof(double) * g.n));
   }
-  ArgsS64 a = args_s64(h, b, x);
+  // the captured sweeps read and write only the handle's arrays: b and x are staged
+  GABP_CUDA(cudaMemcpyAsync(s.bin, b, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  ArgsS64 a = args_s64(h, s.bin, s.xin);
+  const int n1 = (g.n + kBlock - 1) / kBlock;
+  ks_perm64<<<n1, kBlock, 0, h->stream>>>(g.n, s.oid, s.bin, s.sb);
   GABP_CUDA(cudaMemsetAsync(s.SM, 0, sizeof(double2) * Ea, h->stream));
-  GABP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.n, h->stream));
-  ks64_init<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(a);
+  GABP_CUDA(cudaMemsetAsync(s.xin, 0, sizeof(double) * g.n, h->stream));
+  ks64_init<<<n1, kBlock, 0, h->stream>>>(a);
   ks_bb<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(g.n, b, h->ctl, h->partials);
   GABP_CUDA(cudaGetLastError());
   if ((st = read_ctl(h)) != GABP_OK) return st;
@@ -515,12 +627,13 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   h->stats.refine_steps = 0;
   s.valid = true;
   s.result_round = 0;
+  const int L = serial_lanes64(g);
   if (bb == 0.0) {  // x = 0 after zero sweeps; P from the zero messages
     ks64_ctl<<<1, 1, 0, h->stream>>>(h->ctl, 1, 1.0, 0.0);
-    const int L = serial_lanes(g);
     GABP_DISPATCH_L(L, (ks64_final<LL><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_final<LL>)),
                                          kBlock, 0, h->stream>>>(a)));
     GABP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.n, h->stream));
+    GABP_CUDA(cudaMemsetAsync(s.xin, 0, sizeof(double) * g.n, h->stream));
     GABP_CUDA(cudaStreamSynchronize(h->stream));
     if (iters) *iters = 0;
     if (relres) *relres = 0.0;
@@ -528,18 +641,20 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   }
   ks64_ctl<<<1, 1, 0, h->stream>>>(h->ctl, std::max(1, max_iter), bb, tol * tol);
   GABP_CUDA(cudaGetLastError());
-  const int L = serial_lanes(g);
   const int key = L | (s.C << 8);
   gabp_status rs = GABP_OK;
   GABP_DISPATCH_L(L, {
     const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_pass<LL>));
     rs = run_rounds(h, &h->gS64, &h->gS64_key, key, [&] {
-      for (int c = 0; c < s.C; ++c) ks64_pass<LL><<<nb, kBlock, 0, h->stream>>>(a, c);
+      for (int c = 0; c < s.C; ++c)
+        ks64_pass<LL><<<nb, kBlock, 0, h->stream>>>(a, c, s.cstart[c], s.cstart[c + 1] - s.cstart[c]);
       ks64_final<LL><<<nb, kBlock, 0, h->stream>>>(a);
       ks64_decide<LL><<<nb, kBlock, 0, h->stream>>>(a);
     }, std::max(1, max_iter), PH_FP64);
   });
   if (rs != GABP_OK) return rs;
+  GABP_CUDA(cudaMemcpyAsync(x, s.xin, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
   const DevCtl c = *h->ctl_host;
   h->stats.rounds = c.round;
   s.result_round = c.round;
@@ -559,15 +674,16 @@ gabp_status serial_messages64(gabp_handle h, double2 *M_input_layout) {
 
 gabp_status serial_marginals64(gabp_handle h, double *Pi) {
   WorkS &s = h->ws;
-  if (!s.valid || !s.Pm) return GABP_ERR_INVALID;
-  GABP_CUDA(cudaMemcpyAsync(Pi, s.Pm, sizeof(double) * h->g.n, cudaMemcpyDeviceToDevice, h->stream));
+  if (!s.valid || !s.sPm) return GABP_ERR_INVALID;
+  ks_unperm64<<<(h->g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(h->g.n, s.oid, s.sPm, Pi);
+  GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   return GABP_OK;
 }
 
 // ---------------------------------------------------------------------------- FP32 serial inner solve
-// Frozen coefficients in the serial slot order (after every freeze).
-gabp_status serial_freeze32(gabp_handle h, const float2 *CF) {
+// Frozen coefficients and 1/P~ in the serial order (after every freeze).
+gabp_status serial_freeze32(gabp_handle h, const float2 *CF, const float *invP) {
   gabp_status st = serial_prepare(h);
   if (st != GABP_OK) return st;
   Graph &g = h->g;
@@ -577,41 +693,64 @@ gabp_status serial_freeze32(gabp_handle h, const float2 *CF) {
     GABP_CUDA(cudaMalloc(&s.sCF, sizeof(float2) * Ea));
     GABP_CUDA(cudaMalloc(&s.sH, sizeof(float) * Ea));
     GABP_CUDA(cudaMalloc(&s.hfire, sizeof(float) * g.n));
+    GABP_CUDA(cudaMalloc(&s.srhs, sizeof(float) * g.n));
+    GABP_CUDA(cudaMalloc(&s.sinvP, sizeof(float) * g.n));
   }
   if (g.E > 0) ks32_permute_cf<<<(g.E + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.E, s.sperm, CF, s.sCF);
+  ks_perm32<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, s.oid, invP, s.sinvP);
   GABP_CUDA(cudaGetLastError());
   return GABP_OK;
 }
 
-// One inner solve A d = r (rhs32) with serial frozen-coefficient sweeps until
-// ||dx|| <= itol ||x|| or cap sweeps; d_i = h~_i^fire / P~_i is left in hfire
-// (times invP).  *sweeps receives the sweep count.
-gabp_status serial_inner32(gabp_handle h, const float *rhs, const float *invP, int cap, double itol, int *sweeps,
-                           int *status) {
+// Shape (lanes per row, slots per lane) of the FP32 serial pass from the mean
+// length of a colour segment.
+static int serial_shape32(const Graph &g, int C) {
+  const double seg = C > 1 ? g.avg_deg / (C - 1) : 0.0;
+  return seg >= 12.0 ? (4 | (2 << 8)) : seg >= 4.0 ? (2 | (4 << 8)) : (1 | (4 << 8));
+}
+
+// One inner solve A d = r with serial frozen-coefficient sweeps until
+// ||dx|| <= itol ||x|| or cap sweeps.  *sweeps receives the sweep count.
+gabp_status serial_inner32(gabp_handle h, const float *rhs, int cap, double itol, int *sweeps, int *status) {
   Graph &g = h->g;
   WorkS &s = h->ws;
   const size_t Ea = (size_t)(g.E > 0 ? g.E : 1);
   ArgsS32 a;
-  a.n = g.n; a.C = s.C; a.co = s.co; a.sci = s.sci; a.colour = s.colour; a.rp = g.rp;
-  a.sCF = s.sCF; a.rhs = rhs; a.invP = invP; a.sH = s.sH; a.hfire = s.hfire;
+  a.n = g.n; a.C = s.C; a.co = s.co; a.sci = s.sci; a.scol = s.scol; a.srp = s.srp;
+  a.sCF = s.sCF; a.srhs = s.srhs; a.sinvP = s.sinvP; a.sH = s.sH; a.hfire = s.hfire;
   a.ctl = h->ctl; a.partials = h->partials;
   GABP_CUDA(cudaMemsetAsync(s.sH, 0, sizeof(float) * Ea, h->stream));
-  ks32_init<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, rhs, s.hfire);
+  ks32_init<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, s.oid, rhs, s.srhs, s.hfire);
   ks64_ctl<<<1, 1, 0, h->stream>>>(h->ctl, cap, 1.0, itol * itol);
   GABP_CUDA(cudaGetLastError());
-  const int L = serial_lanes(g);
-  const int key = L | (s.C << 8);
+  const int SH = serial_shape32(g, s.C);
+  const int key = SH | (s.C << 16);
   gabp_status rs = GABP_OK;
-  GABP_DISPATCH_L(L, {
-    const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks32_pass<LL>));
+  auto run = [&](auto Lc, auto Uc) {
+    constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
+    const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks32_pass<LL, UU>));
     rs = run_rounds(h, &h->gS32, &h->gS32_key, key, [&] {
-      for (int c = 0; c < s.C; ++c) ks32_pass<LL><<<nb, kBlock, 0, h->stream>>>(a, c);
+      for (int c = 0; c < s.C; ++c)
+        ks32_pass<LL, UU><<<nb, kBlock, 0, h->stream>>>(a, c, s.cstart[c], s.cstart[c + 1] - s.cstart[c]);
     }, cap, PH_MEAN32);
-  });
+  };
+  switch (SH) {
+    case 4 | (2 << 8): run(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{}); break;
+    case 2 | (4 << 8): run(std::integral_constant<int, 2>{}, std::integral_constant<int, 4>{}); break;
+    default: run(std::integral_constant<int, 1>{}, std::integral_constant<int, 4>{}); break;
+  }
   if (rs != GABP_OK) return rs;
   const DevCtl c = *h->ctl_host;
   *sweeps = c.round;
   *status = c.status;
+  return GABP_OK;
+}
+
+// x (input order) += d of the last serial inner solve
+gabp_status serial_update32(gabp_handle h, double *X) {
+  WorkS &s = h->ws;
+  ks32_update<<<(h->g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(h->g.n, s.oid, s.hfire, s.sinvP, X);
+  GABP_CUDA(cudaGetLastError());
   return GABP_OK;
 }
 

@@ -1265,7 +1265,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
       if (gamma_diag) w.coef_ready = false;  // do not reuse a loaded state for a plain solve
     }
   }
-  if (serial && (s = serial_freeze32(h, w.CF)) != GABP_OK) return s;  // coefficients in the serial slot order
+  if (serial && (s = serial_freeze32(h, w.CF, w.invP)) != GABP_OK) return s;  // coefficients in the serial order
   if (!serial && (s = autotune32(h, K32_MEAN)) != GABP_OK) return s;
   const int SH = shape32(h, K32_MEAN);
   // FP64 residual: narrow sub-warps (its per-row epilogue is FP64)
@@ -1306,12 +1306,12 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
     const double it_tol = inner_target(itol, tol, bb, rr);
     if (serial) {  // serial frozen-coefficient sweeps (serial.cu)
       int sweeps = 0, ist = 0;
-      if ((s = serial_inner32(h, w.rhs32, w.invP, cap, it_tol, &sweeps, &ist)) != GABP_OK) return s;
+      if ((s = serial_inner32(h, w.rhs32, cap, it_tol, &sweeps, &ist)) != GABP_OK) return s;
       total_inner += sweeps;
       h->stats.rounds += sweeps;
       if (ist == GABP_DIVERGED) { result = GABP_DIVERGED; break; }
       prof_begin(h);
-      k64_update<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, X, h->ws.hfire, w.invP);
+      if ((s = serial_update32(h, X)) != GABP_OK) return s;
       GABP_DISPATCH_L(LR, (k64_residual<LL><<<nbr, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.col, g.val, B, X, w.rhs32,
                                                                               w.NH[0], w.ctlR, h->partials, 0)));
       prof_end(h);

@@ -162,3 +162,38 @@ def test_fp32_serial_unrefined_within_1e5(gb):
     assert s.stats()["refine_steps"] == 1
     s.close()
     assert _relerr(x.cpu().numpy(), ref["x"]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeated_solves_one_handle(gb, precision):
+    """The captured serial sweeps are replayed for new right-hand sides and new output arrays."""
+    m = MATS["grid3d"]()
+    s = gb.Solver.from_csr(m, schedule=1, precision=precision)
+    A = oracle.to_dense(m)
+    for seed in (1, 2, 3):
+        b = synth.rhs(m.n, seed)
+        x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-11, max_iter=5000)
+        assert st == gb.GABP_OK
+        assert _relerr(x.cpu().numpy(), np.linalg.solve(A, b)) <= 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("R", [5, 64, 130])
+def test_batched_serial_refined(gb, R):
+    """R right-hand sides with serial sweeps (warp per row, lanes over right-hand sides):
+    every column within 1e-10 of the dense solution, fewer sweeps than parallel rounds."""
+    m = MATS["grid3d"]()
+    B = synth.rhs_batch(m.n, R, 9)  # [R, n]
+    A = oracle.to_dense(m)
+    X0 = np.linalg.solve(A, B.T).T
+    its = {}
+    for sched in (0, 1):
+        s = gb.Solver.from_csr(m, schedule=sched)
+        X, st, it, rel = s.solve_batched(torch.from_numpy(B).cuda(), tol=1e-11)
+        its[sched] = it
+        s.close()
+        assert st == gb.GABP_OK and np.all(rel <= 1e-11)
+        Xh = X.cpu().numpy()
+        for r in range(R):
+            assert _relerr(Xh[r], X0[r]) <= 1e-9, r
+    assert its[1] < its[0]
