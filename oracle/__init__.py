@@ -26,6 +26,8 @@ Contents and the passage each follows:
 * :func:`diagonal_loading` / :func:`convergence_fix` -- Chapter "Fixing
   convergence of GaBP": J' = J + Gamma and the double loop
   x^(t+1) = (J + Gamma)^{-1} (h + Gamma x^(t)) whose inner solve is GaBP.
+* :func:`convergence_fix_single_loop` -- the same chapter's single-loop form: one
+  GaBP round per outer step with the damped potential update (numpy, FP64).
 * :func:`dense_gradient`  -- gradients of 0.5 ||x - x*||^2 for x = A^{-1} b,
   written from the adjoint identity (no counterpart in the paper; it pins the
   differentiable solve).
@@ -239,6 +241,60 @@ def convergence_fix(m, b, Gamma, tol=1e-10, inner_tol=1e-12, max_outer=500, inne
             status = OK
             break
     return {"x": x, "outer": t, "inner_total": inner_total, "status": status, "history": hist}
+
+
+def convergence_fix_single_loop(m, b, Gamma, s=0.5, tol=1e-10, max_iter=100000, history=False):
+    """Chapter "Fixing convergence of GaBP", the single-loop form: ONE GaBP round (Algorithm 2,
+    information form, parallel schedule) on J' = A + Gamma per outer step, the node potentials
+    moved by the damped update h^(t+1) = (1 - s) h^(t) + s (b + Gamma x^(t)); x^(0) = 0, so the
+    first round runs with h^(1) = b.  The messages are never restarted.  Stops when
+    ||b - A x^(t)|| <= tol ||b||.  Returns dict(x, iters, status[, xs: x^(t) per round]).
+    """
+    Gamma = np.asarray(Gamma, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = m.n
+    rows = np.repeat(np.arange(n), np.diff(m.rowptr))
+    off = rows != m.col
+    r, c, a = rows[off], m.col[off], m.val[off]
+    diag1 = np.zeros(n)
+    diag1[rows[~off]] = m.val[~off]
+    diag1 = diag1 + Gamma
+    key = r.astype(np.int64) * n + c
+    order = np.argsort(key)
+    rev = order[np.searchsorted(key[order], c.astype(np.int64) * n + r)]  # slot of the reverse edge
+    P = np.zeros(len(a))  # slot e = (i, k): message k -> i
+    H = np.zeros(len(a))
+    hpot = b.copy()
+    x = np.zeros(n)
+    bn = np.linalg.norm(b)
+    xs = []
+    status = NOT_CONVERGED
+    t = 0
+    if bn == 0.0:
+        return {"x": x, "iters": 0, "status": OK, "xs": xs}
+    for t in range(1, max_iter + 1):
+        # one GaBP round on J' with the potentials h^(t): sender aggregates minus the reverse message
+        Pt = diag1 + np.bincount(r, P, minlength=n)
+        Ht = hpot + np.bincount(r, H, minlength=n)
+        d = Pt[c] - P[rev]
+        if np.any(d == 0.0):
+            status = BREAKDOWN
+            break
+        P, H = -a * a / d, -a * (Ht[c] - H[rev]) / d
+        Pt = diag1 + np.bincount(r, P, minlength=n)
+        Ht = hpot + np.bincount(r, H, minlength=n)
+        x = Ht / Pt
+        if history:
+            xs.append(x.copy())
+        if not np.all(np.isfinite(x)):
+            status = DIVERGED
+            break
+        hpot = (1.0 - s) * hpot + s * (b + Gamma * x)  # the damped potential of the next round
+        ax = np.bincount(rows, m.val * x[m.col], minlength=n)
+        if np.linalg.norm(b - ax) <= tol * bn:
+            status = OK
+            break
+    return {"x": x, "iters": t, "status": status, "xs": xs}
 
 
 def dense_gradient(A, b, xstar):

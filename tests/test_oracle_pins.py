@@ -443,3 +443,28 @@ def test_serial_matches_sequential_broadcast_form():
         assert abs(r["Pmsg"][p] - P[(k, i)]) <= 1e-13 * abs(P[(k, i)])
         hm = r["Pmsg"][p] * r["mumsg"][p]  # information form h = P mu
         assert abs(hm - h[(k, i)]) <= 1e-12 * (abs(h[(k, i)]) + 1e-12)
+
+
+# ----------------------------------------------------------------------------- single-loop convergence fix
+def test_single_loop_reduces_to_plain_gabp():
+    """With Gamma = 0 and s = 1 the potentials never move (h^(t) = b): the single loop is plain
+    GaBP, round for round equal to the C oracle's Algorithm 2."""
+    m = synth.random_sym(300, 4, 1.1, 4)
+    b = synth.rhs(m.n, 4)
+    sl = oracle.convergence_fix_single_loop(m, b, np.zeros(m.n), s=1.0, tol=0.0, max_iter=6, history=True)
+    for t in (1, 3, 6):
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0)
+        assert np.allclose(sl["xs"][t - 1], r["x"], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("s", [0.5, 0.25])
+def test_single_loop_converges_where_plain_fails(s):
+    """The non-walk-summable SPD case on which plain GaBP fails (n = 1024, diagonal 0.8 x row
+    abs-sum): the single loop with uniform loading reaches A^{-1} b."""
+    m = synth.random_sym(1024, 3, 0.8, 7)
+    A = oracle.to_dense(m)
+    b = synth.rhs(m.n, 5)
+    assert oracle.gabp_broadcast(m, b, max_iter=300, tol=1e-10)["status"] != oracle.OK
+    g = oracle.convergence_fix_single_loop(m, b, oracle.diagonal_loading(A, "uniform", 0.3), s=s, tol=1e-10)
+    assert g["status"] == oracle.OK
+    assert np.linalg.norm(g["x"] - np.linalg.solve(A, b)) <= 1e-8 * np.linalg.norm(np.linalg.solve(A, b))
