@@ -106,7 +106,12 @@ typedef struct {
                            0 parallel (synchronous, two stores); 1 serial (one store updated in place,
                            nodes firing colour by colour in a greedy index-order colouring; rounds then
                            count sweeps).  gabp_solve, FP64 and FP32_REFINE without loading.  Default 0 */
-  int reserved[4];
+  int fix_single_loop;  /* convergence fix (gamma_mode != 0): 0 the double loop (inner GaBP solves on
+                           A + Gamma, FP32 messages, FP64 outer steps); 1 the single loop of the same
+                           chapter: one FP64 GaBP round on A + Gamma per outer step, the node potentials
+                           moved by h <- (1 - s) h + s (b + Gamma x).  Default 0 */
+  int reserved[3];
+  double fix_step;      /* the single loop's step s in (0, 1], default 0.5 */
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

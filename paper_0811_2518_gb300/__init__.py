@@ -55,7 +55,9 @@ class Options(ctypes.Structure):
         ("overlap_precision", ctypes.c_int),
         ("device_loop", ctypes.c_int),
         ("schedule", ctypes.c_int),
-        ("reserved", ctypes.c_int * 4),
+        ("fix_single_loop", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
+        ("fix_step", ctypes.c_double),
     ]
 
 

@@ -40,8 +40,13 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
       if (e != cudaSuccess) return cuda_fail(e, "gamma");
     }
     s = make_gamma(h, h->gamma);
-    if (s == GABP_OK) s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, h->gamma, &it, &rel);
-    h->last_path = 1;
+    if (h->opt.fix_single_loop) {
+      if (s == GABP_OK) s = solve_fix_single(h, b, x, tol, max_iter, h->gamma, &it, &rel);
+      h->last_path = -1;  // the messages are those of A + Gamma: no marginals of A to report
+    } else {
+      if (s == GABP_OK) s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, h->gamma, &it, &rel);
+      h->last_path = 1;
+    }
   } else if (h->opt.precision == GABP_PREC_FP32_REFINE) {
     s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, nullptr, &it, &rel);
     h->last_path = 1;

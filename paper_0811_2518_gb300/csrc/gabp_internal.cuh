@@ -126,6 +126,13 @@ struct WorkS {
   float *sinvP = nullptr;      // [n] 1 / P~ (new order)
 };
 
+// Single-loop convergence fix (fixloop.cu)
+struct WorkF {
+  double2 *M[2] = {nullptr, nullptr};
+  double2 *N[2] = {nullptr, nullptr};
+  double *hpot = nullptr, *bin = nullptr, *xin = nullptr;
+};
+
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
 
 struct Stats {
@@ -167,6 +174,9 @@ struct gabp_handle_s {
   cudaGraphExec_t gH32 = nullptr;
   cudaGraphExec_t gJ32 = nullptr;   // joint precision + mean rounds
   gabp::WorkS ws;                   // serial schedule
+  gabp::WorkF wf;                   // single-loop convergence fix
+  cudaGraphExec_t gSL = nullptr;
+  int gSL_key = -1;
   cudaGraphExec_t gS64 = nullptr, gS32 = nullptr;  // serial sweeps (FP64, FP32 mean)
   int gS64_key = -1, gS32_key = -1;
   cudaGraph_t gRefG = nullptr;      // whole FP32 refinement loop (conditional nodes) and its instance
@@ -360,6 +370,10 @@ gabp_status precision_phase32(gabp_handle h, const double *gamma_diag);
 void free_wb(gabp_handle h);
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host);
+// single-loop convergence fix (fixloop.cu)
+void free_wf(gabp_handle h);
+gabp_status solve_fix_single(gabp_handle h, const double *b, double *x, double tol, int max_iter,
+                             const double *gamma_diag, int *iters, double *relres);
 // serial schedule (serial.cu)
 void free_ws(gabp_handle h);
 gabp_status serial_prepare(gabp_handle h);

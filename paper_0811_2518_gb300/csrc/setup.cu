@@ -187,6 +187,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   free_w32(h);
   free_wb(h);
   free_ws(h);
+  free_wf(h);
   free_graph(h->g);
   cudaFree(h->ctl);
   cudaFreeHost(h->ctl_host);
@@ -289,6 +290,8 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->multi_mode = 0;
   o->overlap_precision = 1;
   o->device_loop = 1;
+  o->fix_single_loop = 0;
+  o->fix_step = 0.5;
   return GABP_OK;
 }
 
@@ -302,7 +305,8 @@ static gabp_status check_options(const gabp_options *o) {
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
-      o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1)
+      o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0))
     return GABP_ERR_INVALID;
   return GABP_OK;
 }
