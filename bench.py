@@ -209,7 +209,7 @@ def main():
                     help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
     ap.add_argument("--batched-grid", type=int, default=128,
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
-    ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad",
+    ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad,fix",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
 
@@ -452,6 +452,27 @@ def main():
                 "shared_solver": "one handle for the pattern, new values set each step (gabp_set_values) "
                                  "instead of a new handle"}
 
+    # ---- convergence fix on a non-walk-summable SPD matrix (n = 4096, diagonal 0.9 x row abs-sum):
+    # the double loop (FP32 inner GaBP solves on A + Gamma) and the single loop (one FP64 round per step)
+    fix = None
+    if "fix" in legs:
+        mf = synth.random_sym(4096, 3, 0.9, 5)
+        bf = torch.from_numpy(synth.rhs(mf.n, 5)).to(dev)
+        fix = {"workload": "random sparse symmetric A, n=4096, 3 picks per row, diagonal 0.9 x row abs-sum "
+                           "(SPD, rho(|R|) = 1/0.9 > 1), uniform loading Gamma = 0.25 diag(A), to 1e-10"}
+        for name, kw in (("double_loop", {}), ("single_loop", {"fix_single_loop": 1, "fix_step": 0.5})):
+            sf = gb.Solver.from_csr(mf, gamma_mode=1, gamma=0.25, max_refine=2000, **kw)
+            sf.solve(bf, tol=TOL, max_iter=200000)
+            barrier()
+            ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ef0.record()
+            xf, stf, itf, relf = sf.solve(bf, tol=TOL, max_iter=200000)
+            ef1.record()
+            barrier()
+            fix[name] = {"ms": ef0.elapsed_time(ef1), "status": int(stf), "gabp_rounds": int(itf),
+                         "outer_steps": sf.stats()["refine_steps"] if not kw else int(itf), "relres": relf}
+            sf.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(m, b, rounds=5)
@@ -492,6 +513,8 @@ def main():
             line["multi_rgg_512"] = multi
         if grad is not None:
             line["autograd_n4194304"] = grad
+        if fix is not None:
+            line["convergence_fix_n4096"] = fix
         print(json.dumps(line), flush=True)
     s32.close()
     s64.close()
