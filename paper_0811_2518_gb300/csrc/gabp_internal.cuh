@@ -388,7 +388,8 @@ gabp_status serial_update32(gabp_handle h, double *X);
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.
-constexpr int kGridShapes[5] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8)};
+constexpr int kGridShapes[9] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8),
+                                 1 | (2 << 8), 2 | (2 << 8), 1 | (1 << 8), 2 | (1 << 8)};
 gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
                                int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
                                int shape, float *ms_out);

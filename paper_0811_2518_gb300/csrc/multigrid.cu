@@ -34,7 +34,7 @@ namespace {
 
 enum : int { PH_PREC = 0, PH_COEF = 1, PH_RESID = 2, PH_INNER = 3, PH_UPDATE = 4, PH_DONE = 5 };
 constexpr int kGPrecCap = 300;               // precision-round cap per system
-constexpr int kGChunk = 8;                   // warp steps per chunk of contiguous rows
+constexpr int kGChunkMax = 8;                // warp steps per chunk of contiguous rows (at most)
 constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles (~2 s) before a barrier gives up
 
 struct SysState {
@@ -44,6 +44,7 @@ struct SysState {
 
 struct GridArgs {
   int n, nsys;
+  int chunk;                        // warp steps per chunk (enough chunks per warp to balance the round)
   const int *__restrict__ sys_of;   // row -> system
   const int *__restrict__ rp;
   const int *__restrict__ ci;
@@ -235,12 +236,12 @@ __device__ int round_end(const GridArgs &a) {
 }
 
 template <int L, int U>
-__global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : 4) kg_solve(GridArgs a) {
+__global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solve(GridArgs a) {
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  constexpr int CR = RPW * kGChunk;  // rows per chunk
+  const int CR = RPW * a.chunk;  // rows per chunk
   const int nchunks = (a.n + CR - 1) / CR;
   for (int round = 0; round < a.max_rounds; ++round) {
     WarpAcc wacc;
@@ -425,6 +426,10 @@ void (*grid_kernel(int code))(GridArgs) {
     case kGridShapes[1]: return kg_solve<2, 4>;
     case kGridShapes[3]: return kg_solve<4, 4>;
     case kGridShapes[4]: return kg_solve<8, 2>;
+    case kGridShapes[5]: return kg_solve<1, 2>;
+    case kGridShapes[6]: return kg_solve<2, 2>;
+    case kGridShapes[7]: return kg_solve<1, 1>;
+    case kGridShapes[8]: return kg_solve<2, 1>;
     default: return kg_solve<4, 2>;
   }
 }
@@ -480,6 +485,14 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
     per_sm = 1;
   }
   const int grid = per_sm * h->num_sms;
+  {
+    // about four chunks per warp or more, so that the round's slowest warp has little more work
+    // than the average one; longer chunks (fewer accumulator flushes) when the rows allow
+    const int lanes = shape & 0xff;
+    const long long warps = (long long)grid * (kBlock / 32);
+    const long long steps_per_warp = ((long long)g.n * lanes + 32LL * warps - 1) / (32LL * warps);
+    a.chunk = (int)std::max(1LL, std::min<long long>(kGChunkMax, steps_per_warp / 4));
+  }
   cudaEvent_t e0, e1;
   GABP_CUDA(cudaEventCreate(&e0));
   GABP_CUDA(cudaEventCreate(&e1));
