@@ -209,6 +209,8 @@ def main():
                     help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
     ap.add_argument("--batched-grid", type=int, default=128,
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
+    ap.add_argument("--multi-systems", type=int, default=512,
+                    help="number of random geometric graphs of the independent-systems leg (512 = the workload)")
     ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad,fix",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
@@ -380,7 +382,7 @@ def main():
     # ---- 512 independent random-geometric-graph systems in one persistent launch
     multi = None
     if "multi" in legs:
-        mats = synth.rgg_batch(512, 1024, 65536, 2.0, 4)
+        mats = synth.rgg_batch(args.multi_systems, 1024, 65536, 2.0, 4)
         bigm = synth.block_diag(mats)
         offm = bigm.meta["offsets"]
         bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
@@ -396,7 +398,8 @@ def main():
         msm = em0.elapsed_time(em1)
         pm = sm.profile(reset=True)
         stm_ = sm.stats()
-        multi = {"workload": "512 random geometric graphs, sizes ~ n^-2 on [1024, 65536], radius for degree 6, "
+        multi = {"workload": f"{args.multi_systems} random geometric graphs, sizes ~ n^-2 on [1024, 65536], "
+                             "radius for degree 6, "
                              "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
                  "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
                  "ms_per_batch": msm, "kernel_ms": pm["ms"]["multi"], "edge_updates": stm_["edge_updates"],
@@ -510,7 +513,7 @@ def main():
         if batched is not None:
             line["batched_grid3d_64rhs"] = batched
         if multi is not None:
-            line["multi_rgg_512"] = multi
+            line[f"multi_rgg_{args.multi_systems}"] = multi
         if grad is not None:
             line["autograd_n4194304"] = grad
         if fix is not None:
