@@ -142,7 +142,7 @@ gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t 
  * the order of the rowptr/col given to gabp_create, host (mem_space 0) or
  * device (1)), e.g. the matrix of a learning step.  The reverse-edge index,
  * the layout and the autotuner's choices are kept; the precision state is
- * recomputed by the next solve (eq_prec depends on A only, Section 2.2).
+ * recomputed by the next solve (eq_prec depends on A only, Sec. "The Gaussian BP Algorithm").
  * Checked like gabp_create's values (finite, nonzero diagonal and
  * off-diagonals, A_ij == A_ji bit for bit); on GABP_ERR_INVALID the handle
  * holds no valid matrix and every solve fails until a valid call. */
