@@ -110,7 +110,14 @@ typedef struct {
                            A + Gamma, FP32 messages, FP64 outer steps); 1 the single loop of the same
                            chapter: one FP64 GaBP round on A + Gamma per outer step, the node potentials
                            moved by h <- (1 - s) h + s (b + Gamma x).  Default 0 */
-  int reserved[3];
+  int accel;            /* FP64, parallel schedule, node variant: 1 = Aitken's method (Sec.
+                           "Convergence Acceleration") on the marginal means -- every node
+                           extrapolates its last three iterates, y = x0 - (x1 - x0)^2 /
+                           (x2 - 2 x1 + x0); the stop rule and the answer use y; the GaBP
+                           iteration is unchanged.  Pays on smooth problems (the paper's Poisson
+                           example: 25 rounds instead of 134), not on rough right-hand sides.
+                           Default 0 */
+  int reserved[2];
   double fix_step;      /* the single loop's step s in (0, 1], default 0.5 */
 } gabp_options;
 

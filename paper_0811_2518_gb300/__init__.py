@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
         ("device_loop", ctypes.c_int),
         ("schedule", ctypes.c_int),
         ("fix_single_loop", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("accel", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
         ("fix_step", ctypes.c_double),
     ]
 

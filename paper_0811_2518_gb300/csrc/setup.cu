@@ -292,6 +292,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->device_loop = 1;
   o->fix_single_loop = 0;
   o->fix_step = 0.5;
+  o->accel = 0;
   return GABP_OK;
 }
 
@@ -306,7 +307,8 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0))
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 ||
+      (o->accel && o->variant != GABP_VARIANT_NODE))
     return GABP_ERR_INVALID;
   return GABP_OK;
 }
@@ -439,7 +441,8 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
 
 extern "C" gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt) {
   if (!h || !opt || check_options(opt) != GABP_OK) return GABP_ERR_INVALID;
-  bool rebuild = opt->variant != h->opt.variant || opt->lanes != h->opt.lanes || opt->check_every != h->opt.check_every;
+  bool rebuild = opt->variant != h->opt.variant || opt->lanes != h->opt.lanes || opt->check_every != h->opt.check_every ||
+                 opt->accel != h->opt.accel;
   h->opt = *opt;
   if (rebuild) {
     if (h->g64) cudaGraphExecDestroy(h->g64);

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max
   double bb = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) {
     double bi = b[i], d = a.ad[i];
-    a.N0[i] = NodeRec64{d, bi, bi / d, 0.0};
+    a.N0[i] = NodeRec64{d, bi, bi / d, bi / d};  // y^(0) = x^(0)
     bb = fma(bi, bi, bb);
   }
   double v[1] = {bb}, tot[1];
@@ -110,8 +110,22 @@ __global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max
   }
 }
 
+// Aitken's extrapolation (Sec. "Convergence Acceleration") of one node's last
+// three marginal means x0 = x^(t-2), x1 = x^(t-1), x2 = x^(t):
+// y = x0 - (x1 - x0)^2 / (x2 - 2 x1 + x0), or x2 where the second difference is
+// negligible (|D| <= 1e-14 |x2|: the node has stopped moving).
+__device__ __forceinline__ double aitken64(double x0, double x1, double x2) {
+  const double D = x2 - 2.0 * x1 + x0;
+  if (!(fabs(D) > 1e-14 * fabs(x2))) return x2;
+  const double d = x1 - x0;
+  return x0 - d * d / D;
+}
+
 // Fused node-centric round (GABP_VARIANT_NODE): a sub-warp of L lanes per row.
-template <int L>
+// With AIT, every node also forms y^(t) = aitken(x^(t-2), x^(t-1), x^(t)) into
+// its record's spare slot (x^(t-2) is the record being overwritten), and the
+// fused stop rule takes the residual of y^(t-1) instead of x^(t-1).
+template <int L, bool AIT>
 __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -146,7 +160,7 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
         Mout[e] = m;
         accP += m.x;
         acch += m.y;
-        accr = fma(A, nk.x, accr);
+        accr = fma(A, AIT ? nk.pad : nk.x, accr);
       }
     }
     accP = sub_sum<L>(accP);
@@ -156,8 +170,12 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
       const double bi = b[i], d = a.ad[i];
       const double P = d + accP, h = bi + acch;
       bad |= is_zero64(P);
-      Nout[i] = NodeRec64{P, h, h * rcp64(P), 0.0};
-      const double r = bi - fma(d, Nin[i].x, accr);
+      const NodeRec64 own = Nin[i];
+      const double xt = h * rcp64(P);
+      double yt = xt;
+      if (AIT && t >= 2) yt = aitken64(Nout[i].x, own.x, xt);
+      Nout[i] = NodeRec64{P, h, xt, yt};
+      const double r = bi - fma(d, AIT ? own.pad : own.x, accr);
       rr = fma(r, r, rr);
     }
   }
@@ -244,9 +262,9 @@ __global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
   }
 }
 
-__global__ void k64_finalize(int n, const NodeRec64 *__restrict__ N, double *__restrict__ x) {
+__global__ void k64_finalize(int n, const NodeRec64 *__restrict__ N, double *__restrict__ x, int aitken) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = N[i].x;
+  if (i < n) x[i] = aitken ? N[i].pad : N[i].x;
 }
 
 // Messages of the returned round in the layout of the input CSR.
@@ -339,8 +357,13 @@ static void launch_round_L(gabp_handle h, const Args64 &a) {
     k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a, h->g.E);
     k64_edge_agg<L><<<nb, kBlock, 0, h->stream>>>(a);
   } else {
-    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L>));
-    k64_node<L><<<nb, kBlock, 0, h->stream>>>(a);
+    if (h->opt.accel) {
+      const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, true>));
+      k64_node<L, true><<<nb, kBlock, 0, h->stream>>>(a);
+    } else {
+      const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, false>));
+      k64_node<L, false><<<nb, kBlock, 0, h->stream>>>(a);
+    }
   }
 }
 
@@ -468,7 +491,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   h->stats.rounds = c.round;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
-  k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x);
+  k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x,
+                                                                     h->opt.accel);
   h->prof.launches += 1;
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));

@@ -1,0 +1,72 @@
+"""Aitken's acceleration (Sec. "Convergence Acceleration") in the FP64 round kernel against the
+oracle's accelerated Algorithm 2, through the C ABI: the extrapolated iterates after a fixed
+number of rounds, the round count at convergence, and the paper's Poisson example where the
+acceleration cuts the rounds several-fold."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0811_2518_gb300 as m
+
+    return m
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _solve(gb, m, b, tol, max_iter, accel=1):
+    s = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, accel=accel)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=tol, max_iter=max_iter)
+    s.close()
+    return x.cpu().numpy(), st, it
+
+
+def _poisson():
+    p = 10
+    m = synth.poisson2d(p)
+    return m, np.full(m.n, (1.0 / (p + 1)) ** 2)
+
+
+@pytest.mark.parametrize("rounds", [3, 8, 20])
+def test_iterates_match_oracle(gb, rounds):
+    m, b = _poisson()
+    r = oracle.gabp_aitken(m, b, max_iter=rounds, tol=0.0)
+    x, st, it = _solve(gb, m, b, 0.0, rounds)
+    assert it == rounds
+    assert _relerr(x, r["x"]) <= 1e-11
+
+
+@pytest.mark.parametrize("make", [lambda: _poisson(), lambda: (synth.grid2d(32, -1.0, 4.5), synth.rhs(1024, 2)),
+                                  lambda: (synth.random_sym(5000, 4, 1.1, 6), synth.rhs(5000, 6))])
+def test_converged_equal_rounds(gb, make):
+    m, b = make()
+    r = oracle.gabp_aitken(m, b, max_iter=3000, tol=1e-12)
+    x, st, it = _solve(gb, m, b, 1e-12, 3000)
+    assert st == gb.GABP_OK and r["status"] == oracle.OK
+    # near convergence the second differences are rounding-sized and the extrapolation amplifies
+    # the last bits in which the GPU's x^(t) and the oracle's differ (x = h / P by a Newton
+    # reciprocal vs IEEE division): the residual of y then reaches 1e-12 a few rounds apart
+    assert abs(it - r["iters"]) <= max(2, 0.1 * r["iters"])
+    assert _relerr(x, np.linalg.solve(oracle.to_dense(m), b)) <= 1e-10
+
+
+def test_poisson_fewer_rounds(gb):
+    """The paper's example: the accelerated solve needs a fraction of the plain rounds."""
+    m, b = _poisson()
+    _, st0, it0 = _solve(gb, m, b, 1e-10, 3000, accel=0)
+    _, st1, it1 = _solve(gb, m, b, 1e-10, 3000, accel=1)
+    assert st0 == st1 == gb.GABP_OK
+    assert it1 < 0.5 * it0
