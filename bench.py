@@ -294,6 +294,31 @@ def main():
     kname = "k32_mean" if ph == "mean32" else "k32_joint"
 
     legs = set(args.legs.split(","))
+
+    # the random-gather ceiling the mean round meets on this graph: one 4-byte load per slot from a
+    # random row of an n-float array (torch's index_select over the round's own sender indices),
+    # timed like the round (CUDA events, L2-resident source, E indices streamed)
+    gather = None
+    if "fp32" in legs:
+        src = torch.randn(n, device=dev, dtype=torch.float32)
+        idx = torch.from_numpy(m.col[m.col != np.repeat(np.arange(n), np.diff(m.rowptr))].astype(np.int64)).to(dev)
+        out = torch.empty(idx.numel(), device=dev, dtype=torch.float32)
+        for _ in range(3):
+            torch.index_select(src, 0, idx, out=out)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(20):
+            torch.index_select(src, 0, idx, out=out)
+        g1.record()
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / 20
+        gather = {"what": "index_select of the E sender indices of the benchmark graph from an n-float array "
+                          "(4-byte random gathers, 8-byte indices streamed): the gather part of a mean round alone",
+                  "ms": gms, "gathers_per_s": idx.numel() / (gms / 1e3),
+                  "mean_round_ms": dur_ms if ph == "mean32" else None,
+                  "mean_round_vs_gather_only": (dur_ms / gms) if ph == "mean32" else None}
+        del src, idx, out
+
     ms64, r64, k64, p64 = None, 0, 1, {"ms": {"fp64": 0.0}}
     # ---- plain FP64 GaBP on the same system (time to 1e-10)
     for _ in range(max(1, args.warmup) if "fp64" in legs else 0):
@@ -494,7 +519,8 @@ def main():
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": _profiled_traffic(f"{kname}_random_sym_n1048576.md",
                                                       "paper_0811_2518_gb300/csrc/solve32.cu", kname),
-                         "bytes_per_launch": bytes_launch, "launch_ms": dur_ms},
+                         "bytes_per_launch": bytes_launch, "launch_ms": dur_ms,
+                         "random_gather_reference": gather},
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
             "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},
             "gpu_launches": prof["launches"],
