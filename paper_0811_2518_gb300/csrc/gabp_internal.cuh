@@ -378,6 +378,7 @@ gabp_status solve_fix_single(gabp_handle h, const double *b, double *x, double t
 void free_ws(gabp_handle h);
 gabp_status serial_prepare(gabp_handle h);
 gabp_status serial_colours(gabp_handle h, int *colour_dev, int *ncolours);
+gabp_status serial_refresh_values(gabp_handle h);
 gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
                            double *relres);
 gabp_status serial_messages64(gabp_handle h, double2 *M_input_layout);

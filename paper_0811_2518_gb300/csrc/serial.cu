@@ -117,6 +117,12 @@ __global__ void ks_offsets(int n, int C, const int *__restrict__ srp, const int 
   }
 }
 
+__global__ void ks_refresh(int E, const int *__restrict__ sperm, const double *__restrict__ av,
+                           double *__restrict__ sav) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < E) sav[p] = av[sperm[p]];
+}
+
 __global__ void ks_rev(int E, const int *__restrict__ sperm, const int *__restrict__ rev, const int *__restrict__ inv,
                        int *__restrict__ srev) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -569,6 +575,19 @@ gabp_status serial_prepare(gabp_handle h) {
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   s.ready = true;
+  return GABP_OK;
+}
+
+// New values on the same pattern (gabp_set_values): the serial-order copies of
+// A's values follow; the colouring and the layout depend on the pattern only.
+gabp_status serial_refresh_values(gabp_handle h) {
+  WorkS &s = h->ws;
+  if (!s.ready) return GABP_OK;
+  Graph &g = h->g;
+  if (g.E > 0)
+    ks_refresh<<<(g.E + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.E, s.sperm, g.av, s.sav);
+  ks_perm64<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, s.oid, g.ad, s.sad);
+  GABP_CUDA(cudaGetLastError());
   return GABP_OK;
 }
 

@@ -435,6 +435,7 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
     k_values_to_f32<<<(int)(((int64_t)g.E + kBlock - 1) / kBlock), kBlock, 0, h->stream>>>(g.E, g.av, g.av32);
     GABP_CUDA(cudaGetLastError());
   }
+  if ((s = serial_refresh_values(h)) != GABP_OK) return s;
   h->values_ok = true;
   return GABP_OK;
 }
