@@ -130,7 +130,7 @@ __device__ bool col_reduce(const double (&acc)[NV][VEC], int RP, double *red, do
 // Round t of the batched frozen-precision mean iteration (one warp per row).
 // Stops when every column with a nonzero iterate has ||dx_r|| <= inner_tol ||x_r||.
 template <int VEC>
-__global__ void __launch_bounds__(kBlock) kb_mean(ArgsB a) {
+__global__ void __launch_bounds__(kBlock, 6) kb_mean(ArgsB a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int t = ctl->round + 1;
@@ -152,7 +152,28 @@ __global__ void __launch_bounds__(kBlock) kb_mean(ArgsB a) {
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
     const int e0 = a.rp[i], e1 = a.rp[i + 1];
-    for (int e = e0; e < e1; ++e) {
+    int e = e0;
+    for (; e + 1 < e1; e += 2) {  // two slots with their loads issued together
+      const int k0 = a.ci[e], k1 = a.ci[e + 1];
+      const float2 cf0 = a.CF[e], cf1 = a.CF[e + 1];
+      float hs0[VEC], hs1[VEC], hk0[VEC], hk1[VEC], hn0[VEC], hn1[VEC];
+      ldv_cs<VEC>(Hc + (size_t)e * RP + c0, hs0);
+      ldv_cs<VEC>(Hc + (size_t)(e + 1) * RP + c0, hs1);
+      ldv<VEC>(Hm1 + (size_t)k0 * RP + c0, hk0);
+      ldv<VEC>(Hm1 + (size_t)k1 * RP + c0, hk1);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const float ho0 = t >= 2 ? cf0.y * (hi2[v] - hs0[v]) : 0.f;  // messages i -> k at t-1
+        const float ho1 = t >= 2 ? cf1.y * (hi2[v] - hs1[v]) : 0.f;
+        hn0[v] = cf0.x * (hk0[v] - ho0);                             // messages k -> i at t
+        hn1[v] = cf1.x * (hk1[v] - ho1);
+        acc[v] += hn0[v];
+        acc[v] += hn1[v];
+      }
+      stv_cs<VEC>(Hc + (size_t)e * RP + c0, hn0);
+      stv_cs<VEC>(Hc + (size_t)(e + 1) * RP + c0, hn1);
+    }
+    if (e < e1) {
       const int k = a.ci[e];
       const float2 cf = a.CF[e];
       float hs[VEC], hk[VEC];
@@ -322,7 +343,7 @@ struct ArgsBS {
 };
 
 template <int VEC>
-__global__ void __launch_bounds__(kBlock) kbs_pass(ArgsBS a, int c, int skip0, int skipn) {
+__global__ void __launch_bounds__(kBlock, 6) kbs_pass(ArgsBS a, int c, int skip0, int skipn) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int RP = a.RP;
@@ -342,7 +363,26 @@ __global__ void __launch_bounds__(kBlock) kbs_pass(ArgsBS a, int c, int skip0, i
 #pragma unroll
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
     const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
-    for (int e = s0; e < s1; ++e) {
+    int e = s0;
+    for (; e + 1 < s1; e += 2) {  // two slots with their loads issued together
+      const int k0 = a.sci[e], k1 = a.sci[e + 1];
+      const float2 cf0 = a.sCF[e], cf1 = a.sCF[e + 1];
+      float hs0[VEC], hs1[VEC], hk0[VEC], hk1[VEC], hn0[VEC], hn1[VEC];
+      ldv_cs<VEC>(a.sH + (size_t)e * RP + c0, hs0);
+      ldv_cs<VEC>(a.sH + (size_t)(e + 1) * RP + c0, hs1);
+      ldv<VEC>(a.hfire + (size_t)k0 * RP + c0, hk0);
+      ldv<VEC>(a.hfire + (size_t)k1 * RP + c0, hk1);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        hn0[v] = cf0.x * (hk0[v] - cf0.y * (hj[v] - hs0[v]));  // message k -> j, k firing now
+        hn1[v] = cf1.x * (hk1[v] - cf1.y * (hj[v] - hs1[v]));  // (reverse message recomputed)
+        acc[v] += hn0[v];
+        acc[v] += hn1[v];
+      }
+      stv_cs<VEC>(a.sH + (size_t)e * RP + c0, hn0);
+      stv_cs<VEC>(a.sH + (size_t)(e + 1) * RP + c0, hn1);
+    }
+    if (e < s1) {
       const int k = a.sci[e];
       const float2 cf = a.sCF[e];
       float hs[VEC], hk[VEC], hn[VEC];
