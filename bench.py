@@ -224,18 +224,14 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    import paper_0811_2518_gb300 as gb
+    from paper_0811_2518_gb300.replicas import Replicas
 
-        dist.init_process_group("nccl")
+    reps = Replicas()  # one replica per GPU (weak scaling); the group only times and counts
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        reps.barrier()
         torch.cuda.synchronize()
-
-    import paper_0811_2518_gb300 as gb
 
     m = synth.random_sym(N_NODES, PICKS, DIAG, SEED)
     b = synth.rhs(m.n, SEED + rank)
@@ -272,14 +268,12 @@ def main():
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
+    ms_local = ev0.elapsed_time(ev1)
     prof = s32.profile(reset=True)
-    if dist is not None:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    # whole job: every rank's edge-updates over the slowest rank's time
+    ms_total = reps.max(ms_local, device=dev)
+    value = reps.job_rate(E * rounds, ms_local / 1e3, device=dev)
     ms_step = ms_total / args.steps
-    value = E * rounds * world / (ms_total / 1e3)
 
     # roofline of the dominant kernel (largest phase time in the timed region)
     peak, peak_kind = _peaks()
@@ -547,8 +541,7 @@ def main():
         print(json.dumps(line), flush=True)
     s32.close()
     s64.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
