@@ -11,9 +11,14 @@
  *     message mu_ij (eq_prec_message, eq_mean_message; Algorithm 1);
  *   - each message is node i's aggregate minus the reverse message j->i, the
  *     broadcast form (Algorithm 2, Sec. "GaBP Broadcast Variant");
- *   - all messages of a round are computed from the previous round's
- *     messages (parallel / synchronous schedule, Sec. "The Gaussian BP
- *     Algorithm", scheduling paragraph);
+ *   - by default all messages of a round are computed from the previous
+ *     round's messages (parallel / synchronous schedule); the serial schedule
+ *     (one store updated in place, nodes firing colour by colour) is an
+ *     option (Sec. "The Gaussian BP Algorithm", scheduling paragraph);
+ *   - options add Aitken's method on the marginal means (Sec. "Convergence
+ *     Acceleration") and the convergence fix for non-walk-summable A, as a
+ *     double loop or a damped single loop (Chapter "Fixing convergence of
+ *     GaBP");
  *   - the answer is the marginal mean vector and, optionally, the marginal
  *     precisions (Algorithm 1, steps 4-5).
  *
