@@ -535,10 +535,10 @@ struct WorkB {
   double *red = nullptr, *col = nullptr;
   unsigned int *arrive = nullptr;
   cudaGraphExec_t graph = nullptr;
-  int graph_key = -1;
+  long long graph_key = -1;
   float *sH = nullptr, *hfire = nullptr, *srhs = nullptr;  // serial schedule: [E][RP], [n][RP], [n][RP]
   cudaGraphExec_t sgraph = nullptr;
-  int sgraph_key = -1;
+  long long sgraph_key = -1;
 };
 
 void free_wb(gabp_handle h) {

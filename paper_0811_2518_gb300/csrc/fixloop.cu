@@ -190,7 +190,7 @@ gabp_status solve_fix_single(gabp_handle h, const double *b, double *x, double t
     GABP_CUDA(cudaMalloc(&f.bin, sizeof(double) * g.n));
     GABP_CUDA(cudaMalloc(&f.xin, sizeof(double) * g.n));
   }
-  // the captured rounds read and write only the handle's arrays: b, Gamma and x are staged
+  // the captured rounds read and write only handle-owned arrays (Gamma is the handle's; b and x are staged)
   GABP_CUDA(cudaMemcpyAsync(f.bin, b, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
   ArgsSL a;
   a.n = g.n; a.rp = g.rp; a.ci = g.ci; a.rev = g.rev; a.av = g.av; a.ad = g.ad; a.gam = gamma_diag; a.b = f.bin;
@@ -210,7 +210,13 @@ gabp_status solve_fix_single(gabp_handle h, const double *b, double *x, double t
   h->stats.refine_steps = 0;
   if (bb > 0.0) {
     const int L = g.avg_deg >= 12.0 ? 2 : 1;
-    const int key = L | (h->opt.check_every << 8);
+    // the damping step s is baked into the captured rounds' arguments
+    if (h->gSL && h->wf.step != h->opt.fix_step) {
+      cudaGraphExecDestroy(h->gSL);
+      h->gSL = nullptr;
+    }
+    h->wf.step = h->opt.fix_step;
+    const int key = L;
     gabp_status rs = GABP_OK;
     GABP_DISPATCH_L(L, {
       const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ksl_round<LL>));

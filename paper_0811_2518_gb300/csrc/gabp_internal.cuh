@@ -131,6 +131,7 @@ struct WorkF {
   double2 *M[2] = {nullptr, nullptr};
   double2 *N[2] = {nullptr, nullptr};
   double *hpot = nullptr, *bin = nullptr, *xin = nullptr;
+  double step = 0.0;  // damping step the cached round graph was captured with
 };
 
 struct WorkB;  // batched multi-RHS work arrays (batched.cu)
@@ -176,20 +177,20 @@ struct gabp_handle_s {
   gabp::WorkS ws;                   // serial schedule
   gabp::WorkF wf;                   // single-loop convergence fix
   cudaGraphExec_t gSL = nullptr;
-  int gSL_key = -1;
+  long long gSL_key = -1;
   cudaGraphExec_t gS64 = nullptr, gS32 = nullptr;  // serial sweeps (FP64, FP32 mean)
-  int gS64_key = -1, gS32_key = -1;
+  long long gS64_key = -1, gS32_key = -1;
   cudaGraph_t gRefG = nullptr;      // whole FP32 refinement loop (conditional nodes) and its instance
   cudaGraphExec_t gRef = nullptr;
   long long gRef_key = -1;
-  int gJ32_L = -1;
+  long long gJ32_L = -1;
   int tuned_Lj32 = 0;               // autotuned shape of the joint round
   int gH32_R = -1;
   int last_path = -1;               // 0 FP64, 1 FP32 refinement (for gabp_marginal_precisions)
   // autotuned sub-warp widths (0 = not tuned yet) and the scratch control block the tuner uses
   int tuned_L64 = 0, tuned_Lp32 = 0, tuned_Lm32 = 0;
   gabp::DevCtl *ctl_tune = nullptr;
-  int gP32_L = -1, gH32_L = -1;
+  long long gP32_L = -1, gH32_L = -1;
   double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
   gabp::Prof prof;
   gabp::WorkB *wb = nullptr;
@@ -305,16 +306,18 @@ __host__ __device__ inline double inner_target(double inner_tol, double tol, dou
   }
 
 template <typename LaunchFn>
-inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, int *cache_key, int key, LaunchFn launch,
+inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, long long *cache_key, int key, LaunchFn launch,
                               int max_rounds, int phase, int round0 = 0) {
   const int K = h->opt.check_every;
   const bool use_graph = h->stream != nullptr;
-  if (use_graph && *cache && *cache_key != key) {
+  // a cached graph holds K rounds of one launch shape: both are part of its key
+  const long long full_key = ((long long)K << 32) | (unsigned)key;
+  if (use_graph && *cache && *cache_key != full_key) {
     cudaGraphExecDestroy(*cache);
     *cache = nullptr;
   }
   if (use_graph && !*cache) {
-    *cache_key = key;
+    *cache_key = full_key;
     cudaGraph_t graph;
     GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < K; ++k) launch();

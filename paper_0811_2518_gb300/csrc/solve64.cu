@@ -405,7 +405,7 @@ static gabp_status autotune64(gabp_handle h, const double *b) {
 // same graph serves every replay and every solve on this handle).
 static gabp_status get_graph64(gabp_handle h, int L, cudaGraphExec_t *out) {
   const int K = h->opt.check_every;
-  const int key = (L << 16) ^ (h->opt.variant << 12) ^ K;
+  const int key = (L << 16) ^ (h->opt.variant << 12) ^ (h->opt.accel << 24) ^ K;
   if (h->g64 && h->g64_key == key) {
     *out = h->g64;
     return GABP_OK;

@@ -1,0 +1,101 @@
+"""Changing options on a live handle (gabp_set_options) between solves.
+
+A handle caches captured CUDA graphs of its rounds; a cached graph holds
+`check_every` rounds and, for the single-loop convergence fix, the damping step.
+After the options change, a solve on the old handle must give what a fresh handle
+with the new options gives: the same status and round count and the same iterate.
+The sequence raises `check_every` from 1 to 64 so that a graph holding the old,
+shorter round count would run out of host polls before the stop rule fires.  The
+fresh handle also solves twice: a second solve reuses the converged precision
+messages of the first (reuse_precisions), so only second solves compare."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_0811_2518_gb300 as m
+
+    return m
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+PATHS = {
+    "fp64_parallel": dict(),
+    "fp64_serial": dict(schedule=1),
+    "fp64_aitken": dict(accel=1),
+    "fp32_parallel": dict(precision=1),
+    "fp32_serial": dict(precision=1, schedule=1),
+    "fix_single_loop": dict(gamma_mode=1, gamma=0.25, fix_single_loop=1),
+}
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_check_every_change(gb, path):
+    # n = 4096, 3-D grid with a weak diagonal: 73 FP64 rounds to 1e-10; max_iter = 1000
+    # with a stale 1-round graph would give up after 1000 // 64 + 3 polls
+    m = synth.grid3d(16, 1.15, 3)
+    b = torch.from_numpy(synth.rhs(m.n, 4)).cuda()
+    opts = PATHS[path]
+    s = gb.Solver.from_csr(m, check_every=1, **opts)
+    s.solve(b, tol=1e-10, max_iter=1000)
+    s.set_options(check_every=64)
+    x, st, it, rel = s.solve(b, tol=1e-10, max_iter=1000)
+    x = x.cpu().numpy()
+    s.close()
+    f = gb.Solver.from_csr(m, check_every=64, **opts)
+    f.solve(b, tol=1e-10, max_iter=1000)
+    xf, stf, itf, relf = f.solve(b, tol=1e-10, max_iter=1000)
+    f.close()
+    assert st == stf == gb.GABP_OK, (st, stf)
+    assert it == itf
+    assert _relerr(x, xf.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_check_every_change_batched(gb, schedule):
+    m = synth.grid3d(16, 1.15, 3)
+    B = torch.from_numpy(synth.rhs_batch(m.n, 5, 6)).cuda()
+    s = gb.Solver.from_csr(m, check_every=1, schedule=schedule)
+    s.solve_batched(B, tol=1e-10, max_iter=1000)
+    s.set_options(check_every=64)
+    X, st, it, rel = s.solve_batched(B, tol=1e-10, max_iter=1000)
+    X = X.cpu().numpy()
+    s.close()
+    f = gb.Solver.from_csr(m, check_every=64, schedule=schedule)
+    f.solve_batched(B, tol=1e-10, max_iter=1000)
+    Xf, stf, itf, relf = f.solve_batched(B, tol=1e-10, max_iter=1000)
+    f.close()
+    assert st == stf == gb.GABP_OK
+    assert it == itf
+    assert _relerr(X, Xf.cpu().numpy()) <= 1e-12
+
+
+def test_fix_step_change(gb):
+    """The single loop's damping step is an argument of its captured rounds."""
+    m = synth.random_sym(1024, 3, 0.8, 7)
+    b = torch.from_numpy(synth.rhs(m.n, 5)).cuda()
+    s = gb.Solver.from_csr(m, gamma_mode=1, gamma=0.3, fix_single_loop=1, fix_step=0.5)
+    x1, st1, it1, _ = s.solve(b, tol=1e-10, max_iter=20000)
+    s.set_options(fix_step=0.25)
+    x2, st2, it2, _ = s.solve(b, tol=1e-10, max_iter=20000)
+    s.close()
+    f = gb.Solver.from_csr(m, gamma_mode=1, gamma=0.3, fix_single_loop=1, fix_step=0.25)
+    f.solve(b, tol=1e-10, max_iter=20000)
+    xf, stf, itf, _ = f.solve(b, tol=1e-10, max_iter=20000)
+    f.close()
+    assert st1 == st2 == stf == gb.GABP_OK
+    assert it2 == itf and it2 != it1
+    assert _relerr(x2.cpu().numpy(), xf.cpu().numpy()) <= 1e-12
