@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=0,
                     help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
+    ap.add_argument("--unroll", type=int, default=0,
+                    help="with --lanes: slots per lane of the FP32 round kernels (0 = the library default)")
     ap.add_argument("--batched-grid", type=int, default=128,
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
     ap.add_argument("--multi-systems", type=int, default=512,
@@ -240,7 +242,8 @@ def main():
     b_dev = torch.from_numpy(b).to(dev)
     x_dev = torch.empty_like(b_dev)
 
-    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1, lanes=args.lanes)
+    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1, lanes=args.lanes,
+                             unroll=args.unroll if args.lanes else 0)
     s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1, lanes=args.lanes)
 
     def step(s):
@@ -286,6 +289,11 @@ def main():
     dur_ms = prof["ms"][ph] / max(prof["rounds"][ph], 1)
     achieved = bytes_launch / (dur_ms / 1e3) / 1e9
     kname = "k32_mean" if ph == "mean32" else "k32_joint"
+    _ts = s32.tuned()
+    tuned = {"k32_mean": _ts["mean32"], "k32_joint": _ts["prec32"]}  # (lanes per row, slots per lane)
+    if args.lanes:  # pinned: the library's mapping of (lanes, unroll)
+        _L = min(args.lanes, 16)
+        tuned = {k: (_L, args.unroll or (1 if _L >= 16 else 4)) for k in tuned}
 
     legs = set(args.legs.split(","))
 
@@ -335,7 +343,8 @@ def main():
     # (default options: the refinement loop runs as one CUDA graph, no per-phase timing events)
     e2e_rounds, e2e_s = 0, None
     if "e2e" in legs:
-        se = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes)
+        se = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes,
+                                unroll=args.unroll if args.lanes else 0)
         bh = torch.from_numpy(b).pin_memory().numpy()
         xh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
         for _ in range(max(1, args.warmup)):
@@ -514,6 +523,7 @@ def main():
                          "traffic": _profiled_traffic(f"{kname}_random_sym_n1048576.md",
                                                       "paper_0811_2518_gb300/csrc/solve32.cu", kname),
                          "bytes_per_launch": bytes_launch, "launch_ms": dur_ms,
+                         "shape": {"lanes_per_row": tuned[kname][0], "slots_per_lane": tuned[kname][1]},
                          "random_gather_reference": gather},
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
             "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},

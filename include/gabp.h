@@ -88,7 +88,8 @@ typedef struct {
   int gamma_mode;       /* convergence fix: 0 off, 1 Gamma = gamma * diag(A),
                            2 Gamma_ii = max(0, sum_j |A_ij| - A_ii) + gamma * A_ii; default 0 */
   double gamma;         /* loading parameter for gamma_mode, default 0.25 */
-  int lanes;            /* lanes per row for R = 1 kernels (1..32, power of two); 0 = autotune */
+  int lanes;            /* lanes per row for R = 1 kernels (1..32, power of two; the FP32 round
+                           kernels use at most 16); 0 = autotune */
   int profile;          /* 1: time every phase with CUDA events (read with gabp_profile_read), default 0 */
   int reuse_precisions; /* FP32 path: 1 keeps the converged precision messages of A for later
                            solves (they do not depend on b); 0 re-runs the precision phase in every
@@ -122,7 +123,12 @@ typedef struct {
                            iteration is unchanged.  Pays on smooth problems (the paper's Poisson
                            example: 25 rounds instead of 134), not on rough right-hand sides.
                            Default 0 */
-  int reserved[2];
+  int unroll;           /* FP32 R = 1 round kernels with lanes pinned: slots per lane whose loads are
+                           issued together (1, 2, 4 or 8); 0 = 4 (1 at 16 lanes).  The pinned
+                           (lanes, unroll) pair must be one the library is built with: (1|2|4|8, 4),
+                           (1|2|4, 8), (2|4|8, 2), (16, 1), (16, 2); others give GABP_ERR_INVALID.
+                           Ignored when lanes = 0 (autotuned).  Default 0 */
+  int reserved;
   double fix_step;      /* the single loop's step s in (0, 1], default 0.5 */
 } gabp_options;
 
@@ -295,8 +301,10 @@ gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, co
                                int32_t max_iter, void *stream, int32_t *iters_out, double *relres_out);
 
 /* The autotuner's choices for this handle (0 where not tuned yet; all outputs
- * nullable): the FP64 round's lanes per row; the FP32 precision and mean
- * rounds' shapes, packed as lanes | unroll << 8; the multi-system size split;
+ * nullable): the FP64 round's lanes per row; the FP32 precision-phase round's
+ * shape (the joint precision + mean round when options.overlap_precision = 1,
+ * else the precision-only round) and the mean round's shape, packed as
+ * lanes | unroll << 8; the multi-system size split;
  * the multi-system kernel (1 grid-persistent, 2 teams) | the grid-persistent
  * kernel's shape << 8.  The FP64 and FP32 choices are remembered for the
  * process per (device, n, directed-edge count): a later handle of a matrix of

@@ -57,7 +57,8 @@ class Options(ctypes.Structure):
         ("schedule", ctypes.c_int),
         ("fix_single_loop", ctypes.c_int),
         ("accel", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("unroll", ctypes.c_int),
+        ("reserved", ctypes.c_int),
         ("fix_step", ctypes.c_double),
     ]
 

@@ -197,7 +197,7 @@ extern "C" gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int
                                          int32_t *mean32_shape, int64_t *multi_split, int32_t *multi_mode) {
   if (!h) return GABP_ERR_INVALID;
   if (fp64_lanes) *fp64_lanes = h->tuned_L64;
-  if (prec32_shape) *prec32_shape = h->tuned_Lp32;
+  if (prec32_shape) *prec32_shape = h->opt.overlap_precision ? h->tuned_Lj32 : h->tuned_Lp32;
   if (mean32_shape) *mean32_shape = h->tuned_Lm32;
   if (multi_split) *multi_split = h->multi_big;
   if (multi_mode) *multi_mode = h->multi_mode | (h->multi_grid_shape << 8);

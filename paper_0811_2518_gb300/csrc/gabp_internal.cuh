@@ -355,6 +355,7 @@ inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, long long *
 // directed edges): a handle created for a matrix of the same size (typically the
 // same pattern with new values, e.g. one handle per training step) starts tuned.
 void tune_cache_load(gabp_handle h);
+int pinned_shape32(int lanes, int unroll);  // solve32.cu: shape code of a pinned (lanes, unroll), 0 if none
 void tune_cache_store(gabp_handle h);
 gabp_status ensure_w64(gabp_handle h);
 void free_w64(gabp_handle h);

@@ -303,6 +303,8 @@ static gabp_status check_options(const gabp_options *o) {
   if (!(o->inner_tol > 0.0) || o->inner_max_iter < 1 || o->max_refine < 1) return GABP_ERR_INVALID;
   if (o->gamma_mode < 0 || o->gamma_mode > 2 || !(o->gamma >= 0.0)) return GABP_ERR_INVALID;
   if (o->lanes != 0 && (o->lanes < 1 || o->lanes > 32 || (o->lanes & (o->lanes - 1)))) return GABP_ERR_INVALID;
+  if (o->unroll != 0 && o->unroll != 1 && o->unroll != 2 && o->unroll != 4 && o->unroll != 8) return GABP_ERR_INVALID;
+  if (o->lanes && !pinned_shape32(o->lanes, o->unroll)) return GABP_ERR_INVALID;
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
@@ -442,7 +444,8 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
 
 extern "C" gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt) {
   if (!h || !opt || check_options(opt) != GABP_OK) return GABP_ERR_INVALID;
-  bool rebuild = opt->variant != h->opt.variant || opt->lanes != h->opt.lanes || opt->check_every != h->opt.check_every ||
+  bool rebuild = opt->variant != h->opt.variant || opt->lanes != h->opt.lanes || opt->unroll != h->opt.unroll ||
+                 opt->check_every != h->opt.check_every ||
                  opt->accel != h->opt.accel;
   h->opt = *opt;
   if (rebuild) {

@@ -40,8 +40,20 @@ constexpr int kUnroll32 = 4;         // default slots per lane whose loads are i
 constexpr int shape_code(int L, int U) { return L | (U << 8); }
 constexpr int kShapes[] = {shape_code(1, 4), shape_code(2, 4), shape_code(4, 4), shape_code(8, 4),
                            shape_code(1, 8), shape_code(2, 8), shape_code(4, 8),
-                           shape_code(2, 2), shape_code(4, 2), shape_code(8, 2)};
+                           shape_code(2, 2), shape_code(4, 2), shape_code(8, 2),
+                           shape_code(16, 1), shape_code(16, 2)};
 template <int V> using IC = std::integral_constant<int, V>;
+
+// The shape a pinned (options.lanes, options.unroll) pair selects, or 0 if the
+// library has no such kernel.
+int pinned_shape32(int lanes, int unroll) {
+  const int L = lanes > 16 ? 16 : lanes;
+  const int U = unroll ? unroll : (L >= 16 ? 1 : kUnroll32);
+  for (int sc : kShapes)
+    if (sc == shape_code(L, U)) return sc;
+  return 0;
+}
+
 // f(IC<L>, IC<U>) for a shape code (unknown codes map to (4, 4)).
 template <typename F>
 void with_shape(int code, F &&f) {
@@ -55,6 +67,8 @@ void with_shape(int code, F &&f) {
     case shape_code(2, 2): f(IC<2>{}, IC<2>{}); break;
     case shape_code(4, 2): f(IC<4>{}, IC<2>{}); break;
     case shape_code(8, 2): f(IC<8>{}, IC<2>{}); break;
+    case shape_code(16, 1): f(IC<16>{}, IC<1>{}); break;
+    case shape_code(16, 2): f(IC<16>{}, IC<2>{}); break;
     default: f(IC<4>{}, IC<4>{}); break;
   }
 }
@@ -220,9 +234,11 @@ __global__ void __launch_bounds__(kBlock, 4) k32_joint(Args32 a) {
   int bad = 0, moving = 0, nonfinite = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
-    float accP = 0.f, accH = 0.f;
+    float accP = 0.f, accH = 0.f, ad_i = 0.f, rhs_i = 0.f;
     if (i < a.n) {
       const float2 q2 = t >= 2 ? Qm2[i] : make_float2(0.f, 0.f);
+      ad_i = a.ad[i];  // requested before the slots (latency overlap)
+      rhs_i = a.rhs[i];
       const int e1 = a.rp[i + 1];
       for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
         int k[U];
@@ -238,7 +254,7 @@ __global__ void __launch_bounds__(kBlock, 4) k32_joint(Args32 a) {
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (eb + u * L < e1) qk[u] = Qm1[k[u]];
+          if (eb + u * L < e1) qk[u] = __ldcg(Qm1 + k[u]);  // random gather, L2 only
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = eb + u * L;
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(kBlock, 4) k32_joint(Args32 a) {
     accP = sub_sum<L>(accP);
     accH = sub_sum<L>(accH);
     if (i < a.n && sl == 0) {
-      const float P = a.ad[i] + accP, hh = a.rhs[i] + accH;
+      const float P = ad_i + accP, hh = rhs_i + accH;
       bad |= (P == 0.f);
       Qt[i] = make_float2(P, hh);
       Pt[i] = P;
@@ -356,9 +372,13 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   float dxx = 0.f, xx = 0.f;  // per-thread partial sums stay in FP32 (the FP64 pipe is narrow)
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
-    float acc = 0.f;
+    float acc = 0.f, rhs_i = 0.f, ip = 0.f, hprev = 0.f;
     if (i < a.n) {
+      // the row's own values are requested before its slots, so that their latency overlaps the slot loads
       const float hi2 = t >= 2 ? Hm2[i] : 0.f;
+      rhs_i = a.rhs[i];
+      ip = a.invP[i];
+      hprev = Hm1[i];
       const int e1 = a.rp[i + 1];
       for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
         int k[U];
@@ -369,9 +389,10 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
           const int e = eb + u * L;
           if (e < e1) { k[u] = __ldcs(a.ci + e); cf[u] = __ldcs(a.CF + e); hs[u] = __ldcs(Hc + e); }
         }
+        // random gathers bypass L1 (no reuse there), which keeps L1 for the slot streams' sectors
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (eb + u * L < e1) hk[u] = Hm1[k[u]];
+          if (eb + u * L < e1) hk[u] = __ldcg(Hm1 + k[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = eb + u * L;
@@ -386,10 +407,9 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
     }
     acc = sub_sum<L>(acc);
     if (i < a.n && sl == 0) {
-      const float hnew = a.rhs[i] + acc;
+      const float hnew = rhs_i + acc;
       Ht[i] = hnew;
-      const float ip = a.invP[i];
-      const float x = hnew * ip, dx = (hnew - Hm1[i]) * ip;
+      const float x = hnew * ip, dx = (hnew - hprev) * ip;
       dxx = fmaf(dx, dx, dxx);
       xx = fmaf(x, x, xx);
     }
@@ -444,9 +464,11 @@ __global__ void __launch_bounds__(kBlock) k32_freeze(Args32 a) {
     const int i = base + sw;
     float acc = 0.f;
     float2 qi = make_float2(1.f, 0.f);
+    float rhs_i = 0.f;
     if (i < a.n) {
       qi = QT[i];
       const float hi2 = t >= 2 ? Hm2[i] : 0.f;
+      rhs_i = a.rhs[i];  // requested before the slots (latency overlap)
       const int e1 = a.rp[i + 1];
       for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
         int k[U];
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(kBlock) k32_freeze(Args32 a) {
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (eb + u * L < e1) qk[u] = QT[k[u]];
+          if (eb + u * L < e1) qk[u] = __ldcg(QT + k[u]);  // random gather, L2 only
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = eb + u * L;
@@ -483,7 +505,7 @@ __global__ void __launch_bounds__(kBlock) k32_freeze(Args32 a) {
       const float ip = 1.f / qi.x;
       a.invP[i] = ip;
       if (!coef_only) {
-        const float hnew = a.rhs[i] + acc;
+        const float hnew = rhs_i + acc;
         Ht[i] = hnew;
         const float x = hnew * ip, dx = (hnew - qi.y) * ip;
         dxx = fmaf(dx, dx, dxx);
@@ -716,7 +738,7 @@ static int &tuned32(gabp_handle h, int kind) {
   return kind == K32_MEAN ? h->tuned_Lm32 : kind == K32_JOINT ? h->tuned_Lj32 : h->tuned_Lp32;
 }
 static int shape32(gabp_handle h, int kind) {
-  if (h->opt.lanes) return shape_code(h->opt.lanes, kUnroll32);
+  if (h->opt.lanes) return pinned_shape32(h->opt.lanes, h->opt.unroll);  // validated by the option check
   const int tuned = tuned32(h, kind);
   if (tuned) return tuned;
   double d = h->g.avg_deg;
