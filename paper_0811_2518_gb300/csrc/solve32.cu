@@ -549,15 +549,33 @@ __global__ void __launch_bounds__(kBlock) k64_residual(int n, const int *__restr
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
+  constexpr int U = 4;  // entries per lane whose loads are issued together
   double rr = 0.0;
   for (int base = warp * RPW; base < n; base += nwarps * RPW) {
     const int i = base + sw;
-    double ax = 0.0;
-    if (i < n && !x_zero)  // x = 0 (the first residual): r = b exactly, no product needed
-      for (int p = rowptr[i] + sl; p < rowptr[i + 1]; p += L) ax = fma(val[p], x[col[p]], ax);
+    double ax = 0.0, bi = 0.0;
+    if (i < n) {
+      bi = b[i];  // requested before the row's entries (latency overlap)
+      if (!x_zero) {  // x = 0 (the first residual): r = b exactly, no product needed
+        const int p1 = rowptr[i + 1];
+        for (int pb = rowptr[i] + sl; pb < p1; pb += L * U) {
+          int c[U];
+          double v[U], xc[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (pb + u * L < p1) { c[u] = __ldcs(col + pb + u * L); v[u] = __ldcs(val + pb + u * L); }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (pb + u * L < p1) xc[u] = __ldcg(x + c[u]);  // random gather, L2 only
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (pb + u * L < p1) ax = fma(v[u], xc[u], ax);
+        }
+      }
+    }
     ax = sub_sum<L>(ax);
     if (i < n && sl == 0) {
-      const double r = b[i] - ax;
+      const double r = bi - ax;
       rr = fma(r, r, rr);
       const float rf = (float)r;
       rhs32[i] = rf;
