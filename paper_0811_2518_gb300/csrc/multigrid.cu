@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
       }
       // ---------------------------------------------------------- edge part, L lanes per row
       float facc = 0.f, frel = 0.f;
+      float rhs_i = 0.f, ip_i = 0.f, hprev_i = 0.f;  // row values of an inner round
       double dacc = 0.0;
       int bad = 0;
       if (ph == PH_PREC) {
@@ -322,15 +323,20 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
         float *Hc = (t & 1) ? a.H1 : a.H0;
         const float *Hm1 = ring(a.NH0, a.NH1, a.NH2, t + 2);
         const float hi2 = t >= 2 ? ring(a.NH0, a.NH1, a.NH2, t + 1)[i] : 0.f;
+        // the row's own values are requested before its slots (used by the node part below)
+        rhs_i = a.rhs[i];
+        ip_i = a.invP[i];
+        hprev_i = Hm1[i];
         const int e1 = a.rp[i + 1];
         for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
           int k[U];
           float2 cf[U];
           float hs[U], hk[U];
+          // slot arrays belong to the row (written only by its own lanes): streamed, evict-first
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int e = eb + u * L;
-            if (e < e1) { k[u] = a.ci[e]; cf[u] = a.CF[e]; hs[u] = Hc[e]; }
+            if (e < e1) { k[u] = __ldcs(a.ci + e); cf[u] = __ldcs(a.CF + e); hs[u] = __ldcs(Hc + e); }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u)
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
             if (e < e1) {
               const float hout = t >= 2 ? cf[u].y * (hi2 - hs[u]) : 0.f;
               const float hn = cf[u].x * (hk[u] - hout);
-              Hc[e] = hn;
+              __stcs(Hc + e, hn);
               facc += hn;
             }
           }
@@ -374,10 +380,9 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
           c0 = r * r;
           has = true;
         } else if (ph == PH_INNER) {
-          const float hnew = a.rhs[i] + facc;
+          const float hnew = rhs_i + facc;
           ring(a.NH0, a.NH1, a.NH2, t)[i] = hnew;
-          const float ip = a.invP[i];
-          const float xi = hnew * ip, dx = (hnew - ring(a.NH0, a.NH1, a.NH2, t + 2)[i]) * ip;
+          const float xi = hnew * ip_i, dx = (hnew - hprev_i) * ip_i;
           c0 = (double)(dx * dx);
           c1 = (double)(xi * xi);
           has = true;
