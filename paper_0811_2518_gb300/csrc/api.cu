@@ -27,9 +27,7 @@ bool values_usable(gabp_handle h) {
 gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                            int32_t *iters_out, double *relres_out) {
   if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || !values_usable(h)) return GABP_ERR_INVALID;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (cur != h->device) cudaSetDevice(h->device);
+  DeviceGuard dg(h->device);
   int it = 0;
   double rel = 0.0;
   gabp_status s;
@@ -57,7 +55,6 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
     s = solve64(h, b, x, tol, max_iter, &it, &rel);
     h->last_path = 0;
   }
-  if (cur != h->device) cudaSetDevice(cur);
   if (s >= 0) {
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = rel;
@@ -80,10 +77,14 @@ extern "C" gabp_status gabp_solve(gabp_handle h, const double *b, double *x, dou
 extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                                        int32_t *iters_out, double *relres_out) {
   if (!h || !b || !x) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   const size_t bytes = sizeof(double) * h->g.n;
   if (!h->hb) {
     cudaError_t e = cudaMalloc(&h->hb, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->hx, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "gabp_solve_host staging");
+  }
+  if (!h->hx) {
+    cudaError_t e = cudaMalloc(&h->hx, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "gabp_solve_host staging");
   }
   GABP_CUDA(cudaMemcpyAsync(h->hb, b, bytes, cudaMemcpyHostToDevice, h->stream));
@@ -102,18 +103,16 @@ extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const dou
     set_last_error("gabp_solve_batched: B and X must be device arrays");
     return GABP_ERR_INVALID;
   }
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (cur != h->device) cudaSetDevice(h->device);
+  DeviceGuard dg(h->device);
   int it = 0;
   gabp_status s = solve_batched32(h, nrhs, B, X, ld, tol, max_iter, &it, relres_out);
-  if (cur != h->device) cudaSetDevice(cur);
   if (s >= 0 && iters_out) *iters_out = it;
   return s;
 }
 
 extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
   if (!h || !Pi) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   if (h->last_path == 0) return marginals(h, Pi);
   if (h->last_path == 1) return marginals32(h, Pi);
   if (h->last_path == 2) return serial_marginals64(h, Pi);
@@ -122,6 +121,7 @@ extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
 
 extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
   if (!h || !P || !hm) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   if (h->last_path == 0) return messages64(h, P, hm);
   if (h->last_path != 2) return GABP_ERR_INVALID;
   double2 *M = nullptr;  // serial messages back in the input layout
@@ -138,11 +138,13 @@ extern "C" gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32
     set_last_error("gabp_serial_colours: colour must be a device array");
     return GABP_ERR_INVALID;
   }
+  DeviceGuard dg(h->device);
   return serial_colours(h, colour, ncolours);
 }
 
 extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val) {
   if (!h || !lambda || !x || !grad_val || !values_usable(h)) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   return grad_values(h, lambda, x, grad_val);
 }
 
@@ -166,12 +168,8 @@ extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int
     set_last_error("gabp_solve_systems: b and x must be device arrays");
     return GABP_ERR_INVALID;
   }
-  int cur = 0;
-  cudaGetDevice(&cur);
-  if (cur != h->device) cudaSetDevice(h->device);
-  gabp_status s = solve_systems(h, nsys, offsets, b, x, tol, max_iter, status_out, iters_out, relres_out);
-  if (cur != h->device) cudaSetDevice(cur);
-  return s;
+  DeviceGuard dg(h->device);
+  return solve_systems(h, nsys, offsets, b, x, tol, max_iter, status_out, iters_out, relres_out);
 }
 
 extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset) {

@@ -354,6 +354,21 @@ inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, long long *
 // Process-wide memory of the autotuner's kernel shapes, keyed by (device, n,
 // directed edges): a handle created for a matrix of the same size (typically the
 // same pattern with new values, e.g. one handle per training step) starts tuned.
+// Makes a device current for the scope of an entry point and restores the
+// caller's device on exit (the handle's stream and memory live on its device).
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 void tune_cache_load(gabp_handle h);
 int pinned_shape32(int lanes, int unroll);  // solve32.cu: shape code of a pinned (lanes, unroll), 0 if none
 void tune_cache_store(gabp_handle h);

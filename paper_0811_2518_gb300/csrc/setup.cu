@@ -394,6 +394,7 @@ extern "C" gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, con
 
 extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem_space) {
   if (!h || !val || (mem_space != 0 && mem_space != 1)) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   Graph &g = h->g;
   h->values_ok = false;  // until the new values pass every check
   h->last_path = -1;     // marginals / messages of the old values are gone
@@ -470,6 +471,7 @@ extern "C" gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt) 
 
 extern "C" gabp_status gabp_set_stream(gabp_handle h, void *stream) {
   if (!h) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
   if (h->stream) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gabp_set_stream");
