@@ -257,6 +257,23 @@ def gabp_last_error() -> str:
 
 
 # ----------------------------------------------------------------------------- torch convenience
+def _check_out(t, shape, device, name):
+    """An output tensor the library writes through its raw pointer: float64, contiguous, on the
+    solver's device, of the expected shape (anything else would be written out of bounds)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous() \
+            or t.device != device or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape {tuple(shape)} on {device}")
+
+
+def _check_host(a, n, name):
+    import numpy as np
+
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != n:
+        raise ValueError(f"{name} must be a C-contiguous float64 numpy array of {n} entries")
+
+
 class Solver:
     """A GaBP solver bound to one symmetric matrix A (full CSR, diagonal included).
 
@@ -319,9 +336,13 @@ class Solver:
 
         if isinstance(val, torch.Tensor):
             v = val.detach().to(self.device, torch.float64).contiguous()
+            if v.numel() != self.nnz:
+                raise ValueError(f"{v.numel()} values for {self.nnz} stored entries")
             st = gabp_set_values(self.handle, v.data_ptr(), 1)
         else:
             v = np.ascontiguousarray(val, dtype=np.float64)
+            if v.size != self.nnz:
+                raise ValueError(f"{v.size} values for {self.nnz} stored entries")
             st = gabp_set_values(self.handle, v.ctypes.data, 0)
         if st != GABP_OK:
             raise GaBPError(st, "gabp_set_values")
@@ -339,8 +360,11 @@ class Solver:
         import torch
 
         b = b.to(self.device, torch.float64).contiguous()
+        if b.numel() != self.n:
+            raise ValueError(f"b has {b.numel()} entries, the matrix {self.n} rows")
         if x is None:
             x = torch.empty_like(b)
+        _check_out(x, b.shape, self.device, "x")
         st, it, rel = gabp_solve(self.handle, b.data_ptr(), x.data_ptr(), tol, max_iter)
         if check and st < 0:
             raise GaBPError(st, "gabp_solve")
@@ -348,6 +372,8 @@ class Solver:
 
     def solve_host(self, b, x, tol=1e-12, max_iter=1000):
         """b, x: host numpy float64 arrays (pinned or pageable)."""
+        _check_host(b, self.n, "b")
+        _check_host(x, self.n, "x")
         st, it, rel = gabp_solve_host(self.handle, b.ctypes.data, x.ctypes.data, tol, max_iter)
         if st < 0:
             raise GaBPError(st, "gabp_solve_host")
@@ -364,6 +390,7 @@ class Solver:
             raise ValueError("B must be [R, n]")
         if X is None:
             X = torch.empty_like(B)
+        _check_out(X, B.shape, self.device, "X")
         rel = np.zeros(B.shape[0])
         st, it = gabp_solve_batched(self.handle, B.shape[0], B.data_ptr(), X.data_ptr(), self.n, tol, max_iter,
                                     rel.ctypes.data)
@@ -394,6 +421,8 @@ class Solver:
     def grad_values(self, lam, x):
         import torch
 
+        _check_out(lam, (self.n,), self.device, "lam")
+        _check_out(x, (self.n,), self.device, "x")
         g = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
         st = gabp_grad_values(self.handle, lam.data_ptr(), x.data_ptr(), g.data_ptr())
         if st != GABP_OK:
@@ -411,8 +440,11 @@ class Solver:
         import torch
 
         b = b.to(self.device, torch.float64).contiguous()
+        if b.numel() != self.n:
+            raise ValueError(f"b has {b.numel()} entries, the matrix {self.n} rows")
         if x is None:
             x = torch.empty_like(b)
+        _check_out(x, b.shape, self.device, "x")
         off = np.ascontiguousarray(offsets, dtype=np.int32)
         ns = off.size - 1
         sts = np.zeros(ns, dtype=np.int32)

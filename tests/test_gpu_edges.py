@@ -123,3 +123,35 @@ def test_systems_with_edgeless_and_single_node_systems(gb, mode):
     s.close()
     assert st == gb.GABP_OK and np.all(sts == 0)
     assert _relerr(x.cpu().numpy(), np.linalg.solve(oracle.to_dense(big), b)) <= 1e-10
+
+
+def test_binding_rejects_mismatched_buffers(gb):
+    """The binding hands raw pointers to the library, so every buffer the library reads or writes
+    is checked first: wrong length, dtype, layout or device raise ValueError before any launch,
+    and the solver stays usable."""
+    m = synth.grid2d(8, -1.0, 4.5)
+    s = gb.Solver.from_csr(m)
+    b = torch.from_numpy(synth.rhs(m.n, 1)).cuda()
+    with pytest.raises(ValueError):
+        s.solve(b[:-1])
+    with pytest.raises(ValueError):
+        s.solve(b, x=torch.empty(m.n, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        s.solve(b, x=torch.empty(2 * m.n, dtype=torch.float64, device="cuda")[::2])
+    with pytest.raises(ValueError):
+        s.solve(b, x=torch.empty(m.n - 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        s.solve_host(np.zeros(m.n - 1), np.zeros(m.n))
+    with pytest.raises(ValueError):
+        s.solve_host(np.zeros(m.n), np.zeros(m.n, dtype=np.float32))
+    with pytest.raises(ValueError):
+        s.solve_batched(torch.zeros(2, m.n, dtype=torch.float64, device="cuda"),
+                        X=torch.empty(3, m.n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        s.set_values(m.val[:-1])
+    with pytest.raises(ValueError):
+        s.grad_values(b[:-1], b)
+    x, st, it, rel = s.solve(b, tol=1e-12)
+    s.close()
+    assert st == gb.GABP_OK
+    assert _relerr(x.cpu().numpy(), np.linalg.solve(oracle.to_dense(m), synth.rhs(m.n, 1))) <= 1e-12
