@@ -78,11 +78,14 @@ __global__ void ks_colour(int n, const int *__restrict__ rp, const int *__restri
 }
 
 // Slots of new row j (old row oid[j]) in new-sender order: sperm[srp[j] + rank] = e
-// (e an off-diagonal slot of the input layout).
+// (e an off-diagonal slot of the input layout).  A thread ranks its row's slots
+// by counting (quadratic in the degree), so rows longer than maxdeg are left to
+// the host, which sorts them.
 __global__ void ks_sort(int n, const int *__restrict__ srp, const int *__restrict__ oid, const int *__restrict__ rp,
-                        const int *__restrict__ ci, const int *__restrict__ nid, int *__restrict__ sperm) {
+                        const int *__restrict__ ci, const int *__restrict__ nid, int *__restrict__ sperm, int maxdeg) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const int i = oid[j], e0 = rp[i], e1 = rp[i + 1], p0 = srp[j];
+    if (e1 - e0 > maxdeg) continue;
     for (int e = e0; e < e1; ++e) {
       const int ke = nid[ci[e]];
       int rank = 0;
@@ -509,27 +512,52 @@ gabp_status serial_prepare(gabp_handle h) {
   GABP_CUDA(cudaMemsetAsync(s.colour, 0xff, sizeof(int) * n, h->stream));
   GABP_CUDA(cudaMemsetAsync(misc, 0, sizeof(int) * 2, h->stream));
   const int nb = blocks_for(n, kBlock, h->max_blocks);
-  // every pass colours at least the lowest uncoloured node, so n passes always suffice
+  // Every pass colours at least the lowest uncoloured node; the number of passes
+  // is the longest chain of index-increasing neighbours (about 3 m on an m^3
+  // grid, but n on a path numbered along itself).  After kColourPasses device
+  // passes the host finishes the greedy colouring in index order, which gives
+  // the same colouring: the device passes coloured exactly what the sequential
+  // first-fit would have.
+  constexpr int kColourPasses = 64;
   int hm[2] = {1, 0};
-  for (long long done_passes = 0; hm[0] > 0;) {
-    if (done_passes > n) {
-      set_last_error("serial colouring did not finish");
-      return GABP_ERR_CUDA;
-    }
+  for (int done_passes = 0; hm[0] > 0 && done_passes < kColourPasses; done_passes += 8) {
     for (int k = 0; k < 8; ++k) {
       GABP_CUDA(cudaMemsetAsync(misc, 0, sizeof(int), h->stream));
       ks_colour<<<nb, kBlock, 0, h->stream>>>(n, g.rp, g.ci, s.colour, misc, misc + 1);
     }
-    done_passes += 8;
     GABP_CUDA(cudaMemcpyAsync(hm, misc, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream));
     GABP_CUDA(cudaStreamSynchronize(h->stream));
   }
-  s.C = hm[1] + 1;
   // relabelling: colour classes contiguous, index order inside (a stable counting sort)
   std::vector<int> col(n), rp(n + 1), oid(n), nid(n), srp(n + 1), scol(n);
   GABP_CUDA(cudaMemcpyAsync(col.data(), s.colour, sizeof(int) * n, cudaMemcpyDeviceToHost, h->stream));
   GABP_CUDA(cudaMemcpyAsync(rp.data(), g.rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
   GABP_CUDA(cudaStreamSynchronize(h->stream));
+  int maxdeg = 0;
+  for (int i = 0; i < n; ++i) maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
+  constexpr int kSortDeviceMaxDeg = 256;  // longer rows are sorted on the host
+  std::vector<int> ci_h;
+  if (hm[0] > 0 || maxdeg > kSortDeviceMaxDeg) {
+    ci_h.resize(Ea);
+    if (E > 0) {
+      GABP_CUDA(cudaMemcpyAsync(ci_h.data(), g.ci, sizeof(int) * (size_t)E, cudaMemcpyDeviceToHost, h->stream));
+      GABP_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+  if (hm[0] > 0) {  // sequential first-fit over the nodes still uncoloured, in index order
+    std::vector<int> seen(maxdeg + 2, -1);  // colours are at most the degree
+    for (int i = 0; i < n; ++i) {
+      if (col[i] >= 0) continue;
+      for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci_h[e] < i) seen[col[ci_h[e]]] = i;  // lower neighbours are coloured by now
+      int c = 0;
+      while (seen[c] == i) ++c;
+      col[i] = c;
+      hm[1] = std::max(hm[1], c);
+    }
+    GABP_CUDA(cudaMemcpyAsync(s.colour, col.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+  }
+  s.C = hm[1] + 1;
   s.cstart.assign(s.C + 1, 0);
   for (int i = 0; i < n; ++i) ++s.cstart[col[i] + 1];
   for (int c = 0; c < s.C; ++c) s.cstart[c + 1] += s.cstart[c];
@@ -564,7 +592,23 @@ gabp_status serial_prepare(gabp_handle h) {
     int *p;
     ~F2() { cudaFree(p); }
   } fr2{inv};
-  ks_sort<<<nb, kBlock, 0, h->stream>>>(n, s.srp, s.oid, g.rp, g.ci, s.nid, s.sperm);
+  ks_sort<<<nb, kBlock, 0, h->stream>>>(n, s.srp, s.oid, g.rp, g.ci, s.nid, s.sperm, kSortDeviceMaxDeg);
+  if (maxdeg > kSortDeviceMaxDeg) {  // long rows: (new sender label, slot) pairs sorted on the host
+    std::vector<std::pair<int, int>> key;
+    std::vector<int> perm;
+    for (int j = 0; j < n; ++j) {
+      const int i = oid[j], e0 = rp[i], e1 = rp[i + 1];
+      if (e1 - e0 <= kSortDeviceMaxDeg) continue;
+      key.clear();
+      for (int e = e0; e < e1; ++e) key.emplace_back(nid[ci_h[e]], e);
+      std::sort(key.begin(), key.end());
+      perm.resize(key.size());
+      for (size_t r = 0; r < key.size(); ++r) perm[r] = key[r].second;
+      GABP_CUDA(cudaMemcpyAsync(s.sperm + srp[j], perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+      GABP_CUDA(cudaStreamSynchronize(h->stream));  // perm is refilled for the next long row
+    }
+  }
   if (E > 0) {
     const int eb = (E + kBlock - 1) / kBlock;
     ks_gather<<<eb, kBlock, 0, h->stream>>>(E, s.sperm, g.ci, s.nid, g.av, s.sci, s.sav, inv);

@@ -154,4 +154,5 @@ def test_binding_rejects_mismatched_buffers(gb):
     x, st, it, rel = s.solve(b, tol=1e-12)
     s.close()
     assert st == gb.GABP_OK
-    assert _relerr(x.cpu().numpy(), np.linalg.solve(oracle.to_dense(m), synth.rhs(m.n, 1))) <= 1e-12
+    # residual 1e-12, condition number ~17: the error is within 1e-10
+    assert _relerr(x.cpu().numpy(), np.linalg.solve(oracle.to_dense(m), synth.rhs(m.n, 1))) <= 1e-10

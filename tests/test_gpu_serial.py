@@ -32,7 +32,34 @@ def _relerr(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def _path(n):
+    """Tridiagonal chain numbered along itself: the colouring's dependency chain is n long (the
+    device passes stop early and the host finishes the greedy colouring)."""
+    rng = np.random.default_rng(7)
+    w = -rng.uniform(0.5, 1.0, n - 1)
+    rows = np.concatenate([np.arange(n - 1), np.arange(1, n), np.arange(n)])
+    cols = np.concatenate([np.arange(1, n), np.arange(n - 1), np.arange(n)])
+    d = np.zeros(n)
+    d[:-1] += np.abs(w)
+    d[1:] += np.abs(w)
+    return synth.from_coo(n, rows, cols, np.concatenate([w, w, 1.1 * d]))
+
+
+def _star(n):
+    """Node 0 joined to every other node: one row far longer than the device's per-row slot sort
+    handles (sorted on the host)."""
+    rng = np.random.default_rng(8)
+    w = -rng.uniform(0.5, 1.0, n - 1)
+    leaves = np.arange(1, n)
+    rows = np.concatenate([np.zeros(n - 1, dtype=np.int64), leaves, np.arange(n)])
+    cols = np.concatenate([leaves, np.zeros(n - 1, dtype=np.int64), np.arange(n)])
+    d = np.concatenate([[1.1 * np.abs(w).sum()], 2.0 * np.abs(w)])
+    return synth.from_coo(n, rows, cols, np.concatenate([w, w, d]))
+
+
 MATS = {
+    "path": lambda: _path(3000),
+    "star": lambda: _star(2000),
     "grid2d": lambda: synth.grid2d(32, -1.0, 4.5),
     "grid3d": lambda: synth.grid3d(12, 1.05, 3),
     "random": lambda: synth.random_sym(3001, 8, 1.1, 2),
@@ -71,7 +98,7 @@ def _fp64(gb, m, b, sweeps, tol=0.0):
     return st, it, x.cpu().numpy(), P.cpu().numpy(), hm.cpu().numpy(), Pi.cpu().numpy()
 
 
-@pytest.mark.parametrize("name", ["grid2d", "grid3d", "random", "rgg", "tree"])
+@pytest.mark.parametrize("name", ["grid2d", "grid3d", "random", "rgg", "tree", "path", "star"])
 @pytest.mark.parametrize("sweeps", [1, 2, 7])
 def test_fp64_sweeps_match_oracle(gb, name, sweeps):
     m = MATS[name]()
