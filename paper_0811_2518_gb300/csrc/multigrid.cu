@@ -290,19 +290,22 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
           for (int u = 0; u < U; ++u) {
             const int e = eb + u * L;
             if (e < e1) {
+              // fast FP32 division (about 2 ulp), as in the single-system precision rounds: the
+              // precision state only has to be FP32-accurate, the FP64 refinement absorbs the rest
               const float A2 = A[u] * A[u];
               float Pout = 0.f;
               if (t >= 2) {
                 const float d1 = Pi2 - Ps[u];
                 bad |= (d1 == 0.f);
-                Pout = -A2 / d1;
+                Pout = -__fdividef(A2, d1);
               }
               const float d2 = Pk[u] - Pout;
               bad |= (d2 == 0.f);
-              const float Pn = -A2 / d2;
+              const float Pn = -__fdividef(A2, d2);
               Mc[e] = Pn;
               facc += Pn;
-              frel = nan_max(frel, rel_change(Pn, Pp[u]));
+              const float dP = fabsf(Pn - Pp[u]);
+              frel = nan_max(frel, dP == 0.f ? 0.f : __fdividef(dP, fabsf(Pn)));
             }
           }
         }
