@@ -128,7 +128,9 @@ typedef struct {
                            (lanes, unroll) pair must be one the library is built with: (1|2|4|8, 4),
                            (1|2|4, 8), (2|4|8, 2), (16, 1), (16, 2); others give GABP_ERR_INVALID.
                            Ignored when lanes = 0 (autotuned).  Default 0 */
-  int reserved;
+  int history;          /* FP64 parallel rounds: record the relative residual of the first `history`
+                           iterates of each solve (read with gabp_residual_history), the curve the
+                           paper plots against the iteration count; 0 = off.  Default 0 */
   double fix_step;      /* the single loop's step s in (0, 1], default 0.5 */
 } gabp_options;
 
@@ -299,6 +301,15 @@ gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
 gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *b, double *x, double tol,
                                int32_t max_iter, void *stream, int32_t *iters_out, double *relres_out);
+
+/* Residual history of the last solve (options.history > 0, plain FP64 parallel
+ * rounds, node or edge variant): relres[t] = ||b - A x^(t)|| / ||b|| for the
+ * iterates t = 0, 1, ... the rounds checked (x^(0) = b_i / A_ii; with Aitken's
+ * method the accelerated iterate), at most cap entries copied into the HOST
+ * array relres; *count (nullable) = entries recorded (at most options.history).
+ * Other paths record none (*count = 0).  GABP_ERR_INVALID for cap < 0 or a
+ * null relres with cap > 0. */
+gabp_status gabp_residual_history(gabp_handle h, double *relres, int32_t cap, int32_t *count);
 
 /* The autotuner's choices for this handle (0 where not tuned yet; all outputs
  * nullable): the FP64 round's lanes per row; the FP32 precision-phase round's

@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -58,7 +58,7 @@ class Options(ctypes.Structure):
         ("fix_single_loop", ctypes.c_int),
         ("accel", ctypes.c_int),
         ("unroll", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("history", ctypes.c_int),
         ("fix_step", ctypes.c_double),
     ]
 
@@ -96,6 +96,7 @@ _SIGNATURES = {
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_serial_colours": ([_P, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_residual_history": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -152,6 +153,14 @@ def gabp_serial_colours(h, colour_ptr):
     nc = ctypes.c_int32(0)
     st = lib.gabp_serial_colours(h, colour_ptr, ctypes.byref(nc))
     return st, nc.value
+
+
+def gabp_residual_history(h, relres_ptr, cap):
+    """Copies up to cap relative residuals of the last FP64 solve into a host float64 array;
+    returns (status, entries recorded)."""
+    c = ctypes.c_int32(0)
+    st = lib.gabp_residual_history(h, relres_ptr, int(cap), ctypes.byref(c))
+    return st, c.value
 
 
 def gabp_set_values(h, val_ptr, mem_space):
@@ -458,6 +467,21 @@ class Solver:
 
     def tuned(self):
         return gabp_tuned_shapes(self.handle)
+
+    def residual_history(self):
+        """Relative residual of every recorded iterate of the last FP64 solve (numpy array; empty
+        unless the solver was created with history > 0)."""
+        import numpy as np
+
+        st, cnt = gabp_residual_history(self.handle, None, 0)
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_residual_history")
+        out = np.zeros(cnt)
+        if cnt:
+            st, cnt = gabp_residual_history(self.handle, out.ctypes.data, cnt)
+            if st != GABP_OK:
+                raise GaBPError(st, "gabp_residual_history")
+        return out
 
     def profile(self, reset=False):
         st, p = gabp_profile_read(self.handle, reset)

@@ -2,6 +2,7 @@
 // options / status strings live in setup.cu).
 #include "gabp_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 using namespace gabp;
@@ -31,6 +32,7 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
   int it = 0;
   double rel = 0.0;
   gabp_status s;
+  h->hist_len = 0;  // only the FP64 parallel rounds record a history
   if (h->opt.gamma_mode != 0) {
     // convergence fix: FP32 GaBP inner solves on A + Gamma inside the FP64 outer loop
     if (!h->gamma) {
@@ -188,6 +190,19 @@ extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int r
     }
     h->prof.launches = 0;
   }
+  return GABP_OK;
+}
+
+extern "C" gabp_status gabp_residual_history(gabp_handle h, double *relres, int32_t cap, int32_t *count) {
+  if (!h || cap < 0 || (cap > 0 && !relres)) return GABP_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  const int m = std::min(cap, h->hist_len);
+  if (m > 0) {
+    GABP_CUDA(cudaMemcpyAsync(relres, h->hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));
+    GABP_CUDA(cudaStreamSynchronize(h->stream));
+    for (int j = 0; j < m; ++j) relres[j] = h->hist_bb > 0.0 ? std::sqrt(relres[j] / h->hist_bb) : 0.0;
+  }
+  if (count) *count = h->hist_len;
   return GABP_OK;
 }
 

@@ -709,6 +709,7 @@ static gabp_status batched_chunk(gabp_handle h, int R, const double *B, double *
 
 gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
                             int max_iter, int *iters, double *relres_host) {
+  NvtxRange nvtx_("gabp batched right-hand sides");
   if (nrhs < 1 || ld < h->g.n) return GABP_ERR_INVALID;
   gabp_status s = ensure_w32(h, 1);
   if (s != GABP_OK) return s;

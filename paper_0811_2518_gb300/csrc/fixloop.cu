@@ -178,6 +178,7 @@ void free_wf(gabp_handle h) {
 // Single-loop convergence fix for one right-hand side; gamma_diag = Gamma (device).
 gabp_status solve_fix_single(gabp_handle h, const double *b, double *x, double tol, int max_iter,
                              const double *gamma_diag, int *iters, double *relres) {
+  NvtxRange nvtx_("gabp single-loop convergence fix");
   Graph &g = h->g;
   WorkF &f = h->wf;
   const size_t Ea = (size_t)(g.E > 0 ? g.E : 1);

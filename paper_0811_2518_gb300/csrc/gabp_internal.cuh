@@ -10,6 +10,7 @@
 //   mean chains H[2][E][R] float, node rings.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -50,7 +51,10 @@ struct DevCtl {
   int edge_bad;      // breakdown flag raised by an edge kernel, consumed by the round's last block
   const double *b;   // right-hand side of the current FP64 run (device); read by the round kernels
   int no_stop;       // autotuning runs: advance rounds but never take a terminal decision
-  int pad1;
+  int hist_cap;      // FP64 rounds: entries of hist (0 = no history)
+  double *hist;      // FP64 rounds: squared residual of iterate t at hist[t] (device, hist_cap entries)
+  int hist_len;      // entries written
+  int pad2;
 };
 
 struct Graph {
@@ -192,6 +196,10 @@ struct gabp_handle_s {
   gabp::DevCtl *ctl_tune = nullptr;
   long long gP32_L = -1, gH32_L = -1;
   double *gamma = nullptr;          // diagonal loading of the convergence fix (device, n)
+  double *hist = nullptr;           // residual history of the last FP64 run (device, opt.history entries)
+  int hist_alloc = 0;
+  int hist_len = 0;                 // entries recorded by the last solve (0 when it kept none)
+  double hist_bb = 0.0;             // ||b||^2 of that solve
   gabp::Prof prof;
   gabp::WorkB *wb = nullptr;
   long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
@@ -354,6 +362,15 @@ inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, long long *
 // Process-wide memory of the autotuner's kernel shapes, keyed by (device, n,
 // directed edges): a handle created for a matrix of the same size (typically the
 // same pattern with new values, e.g. one handle per training step) starts tuned.
+// An NVTX range over a solver phase (visible to ncu's --nvtx filters and timeline
+// tools; a no-op unless a tool attaches).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Makes a device current for the scope of an entry point and restores the
 // caller's device on exit (the handle's stream and memory live on its device).
 struct DeviceGuard {

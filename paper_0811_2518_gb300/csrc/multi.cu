@@ -382,6 +382,7 @@ static gabp_status collect_systems(gabp_handle h, int nsys, const std::vector<in
 
 gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, const double *b, double *x, double tol,
                           int max_iter, int *status_host, int *iters_host, double *relres_host) {
+  NvtxRange nvtx_("gabp independent systems");
   Graph &g = h->g;
   if (nsys < 1 || !offsets_host || offsets_host[0] != 0 || offsets_host[nsys] != g.n) return GABP_ERR_INVALID;
   for (int s = 0; s < nsys; ++s)

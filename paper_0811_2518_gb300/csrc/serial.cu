@@ -660,6 +660,7 @@ static ArgsS64 args_s64(gabp_handle h, const double *b, double *x) {
 // sweep (Algorithm 1 step 4 over every current message).
 gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
                            double *relres) {
+  NvtxRange nvtx_("gabp fp64 serial schedule");
   gabp_status st = serial_prepare(h);
   if (st != GABP_OK) return st;
   Graph &g = h->g;

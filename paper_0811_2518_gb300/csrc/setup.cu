@@ -195,6 +195,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   cudaFree(h->hb);
   cudaFree(h->hx);
   cudaFree(h->gamma);
+  cudaFree(h->hist);
   cudaFree(h->ctl_tune);
   if (h->prof.e0) cudaEventDestroy(h->prof.e0);
   if (h->prof.e1) cudaEventDestroy(h->prof.e1);
@@ -293,6 +294,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->fix_single_loop = 0;
   o->fix_step = 0.5;
   o->accel = 0;
+  o->history = 0;
   return GABP_OK;
 }
 
@@ -309,7 +311,7 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 ||
       (o->accel && o->variant != GABP_VARIANT_NODE))
     return GABP_ERR_INVALID;
   return GABP_OK;

@@ -807,6 +807,7 @@ static gabp_status autotune32(gabp_handle h, int kind) {
 }
 
 gabp_status precision_phase32(gabp_handle h, const double *gamma_diag) {
+  NvtxRange nvtx_("gabp fp32 precision rounds");
   Work32 &w = h->w32;
   Graph &g = h->g;
   size_t E = (size_t)(g.E > 0 ? g.E : 1);
@@ -1281,6 +1282,7 @@ static gabp_status solve32_device_loop(gabp_handle h, const double *B, double *X
 
 gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int64_t ld, double tol,
                            int max_iter, const double *gamma_diag, int *iters, double *relres) {
+  NvtxRange nvtx_("gabp fp32 messages + fp64 refinement");
   if (R != 1) return GABP_ERR_INVALID;  // batched path: gabp_solve_batched
   (void)ld;
   gabp_status s = ensure_w32(h, 1);

@@ -38,6 +38,10 @@ struct Args64 {
 __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
   const int tchk = t - 1;
   ctl->round = t;
+  if (ctl->hist && tchk < ctl->hist_cap) {  // residual of iterate tchk, before any decision
+    ctl->hist[tchk] = rr;
+    ctl->hist_len = tchk + 1;
+  }
   if (ctl->no_stop) {
     ctl->rr = rr;
   } else if (tchk >= ctl->check_from && isfinite(rr) && rr <= ctl->tol2bb) {
@@ -428,6 +432,7 @@ static gabp_status get_graph64(gabp_handle h, int L, cudaGraphExec_t *out) {
 
 gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
                     double *relres) {
+  NvtxRange nvtx_("gabp fp64 rounds");
   gabp_status s = ensure_w64(h);
   if (s != GABP_OK) return s;
   Graph &g = h->g;
@@ -438,6 +443,19 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     GABP_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(DevCtl), h->stream));
     const double *bptr = b;
     GABP_CUDA(cudaMemcpyAsync(&h->ctl->b, &bptr, sizeof(bptr), cudaMemcpyHostToDevice, h->stream));
+    if (h->opt.history > 0) {  // per-round residual history (options.history entries)
+      if (h->hist_alloc < h->opt.history) {
+        cudaFree(h->hist);
+        h->hist = nullptr;
+        h->hist_alloc = 0;
+        GABP_CUDA(cudaMalloc(&h->hist, sizeof(double) * (size_t)h->opt.history));
+        h->hist_alloc = h->opt.history;
+      }
+      double *hp = h->hist;
+      const int cap = h->opt.history;
+      GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist, &hp, sizeof(hp), cudaMemcpyHostToDevice, h->stream));
+      GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, h->stream));
+    }
     GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
     k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter);
     GABP_CUDA(cudaGetLastError());
@@ -488,6 +506,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   const DevCtl c = *h->ctl_host;
   h->w64.result_round = c.result_round;
   h->w64.valid = true;
+  h->hist_len = h->opt.history > 0 ? c.hist_len : 0;
+  h->hist_bb = c.bb;
   h->stats.rounds = c.round;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;

@@ -257,3 +257,34 @@ def test_full_size_random_sym_c2(gb):
     assert g["iters"] == ref["iters"]
     idx = np.random.default_rng(0).choice(m.n, 4096, replace=False)
     assert np.allclose(g["x"][idx], ref["x"][idx], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_residual_history(gb, variant):
+    """options.history: the relative residual of every iterate x^(t) of an FP64 run, against the
+    oracle's iterates after t rounds (x^(0) = b_i / A_ii); the last entry is the returned residual;
+    an FP32 + refinement solve records none."""
+    m = synth.grid2d(20, -1.0, 4.5)
+    b = synth.rhs(m.n, 3)
+    A = oracle.to_dense(m)
+    s = gb.Solver.from_csr(m, variant=variant, history=256)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_iter=500)
+    h = s.residual_history()
+    assert st == gb.GABP_OK and h.size == it + 1
+    assert abs(h[-1] - rel) <= 1e-12 * max(rel, 1e-300) + 1e-300
+    assert h[-1] <= 1e-10 < h[-2]
+    nb = np.linalg.norm(b)
+    x0 = b / np.diag(A)
+    assert abs(h[0] - np.linalg.norm(b - A @ x0) / nb) <= 1e-12 * h[0]
+    for t in (1, 2, 7, it):
+        xt = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0)["x"]
+        ref = np.linalg.norm(b - A @ xt) / nb
+        assert abs(h[t] - ref) <= 1e-9 * ref + 1e-15, (t, h[t], ref)
+    s.set_options(history=4)
+    s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_iter=500)
+    assert s.residual_history().size == 4
+    s.close()
+    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, history=64)
+    s32.solve(torch.from_numpy(b).cuda(), tol=1e-10)
+    assert s32.residual_history().size == 0
+    s32.close()
