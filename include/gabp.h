@@ -132,6 +132,12 @@ typedef struct {
                            iterates of each solve (read with gabp_residual_history), the curve the
                            paper plots against the iteration count; 0 = off.  Default 0 */
   double fix_step;      /* the single loop's step s in (0, 1], default 0.5 */
+  int warm_start;       /* plain FP64 parallel rounds: 1 = round 0 takes the messages of the handle's
+                           last FP64 solve (or those loaded by gabp_set_messages) instead of zero
+                           messages, with the new b; the iteration has the same fixed point from any
+                           start, so a nearby b converges in fewer rounds.  Ignored until the handle
+                           has such messages, and by the other paths.  Default 0 */
+  int reserved;
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */
@@ -301,6 +307,15 @@ gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
 gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *b, double *x, double tol,
                                int32_t max_iter, void *stream, int32_t *iters_out, double *relres_out);
+
+/* Loads messages as the handle's FP64 state (the checkpoint counterpart of
+ * gabp_get_messages, same layout: device arrays of nnz doubles, P[p] = P_ki and
+ * hm[p] = P_ki mu_ki for slot p of row i with col[p] = k != i, diagonal slots
+ * ignored).  The next gabp_solve with options.warm_start = 1 (FP64 parallel
+ * rounds) starts from them; any finite messages are a valid start, a poor one
+ * costs rounds (or, outside the convergent cases, convergence).  The handle
+ * keeps its own copy.  GABP_ERR_INVALID for null pointers or host arrays. */
+gabp_status gabp_set_messages(gabp_handle h, const double *P, const double *hm);
 
 /* Residual history of the last solve (options.history > 0, plain FP64 parallel
  * rounds, node or edge variant): relres[t] = ||b - A x^(t)|| / ||b|| for the

@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_set_messages", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "Solver", "GaBPError",
 ]
 
@@ -60,6 +60,8 @@ class Options(ctypes.Structure):
         ("unroll", ctypes.c_int),
         ("history", ctypes.c_int),
         ("fix_step", ctypes.c_double),
+        ("warm_start", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -97,6 +99,7 @@ _SIGNATURES = {
                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_serial_colours": ([_P, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_residual_history": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_set_messages": ([_P, _P, _P], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -153,6 +156,11 @@ def gabp_serial_colours(h, colour_ptr):
     nc = ctypes.c_int32(0)
     st = lib.gabp_serial_colours(h, colour_ptr, ctypes.byref(nc))
     return st, nc.value
+
+
+def gabp_set_messages(h, P_ptr, hm_ptr):
+    """Loads FP64 messages (input CSR layout, device arrays of nnz doubles) as the warm-start state."""
+    return lib.gabp_set_messages(h, _P(P_ptr), _P(hm_ptr))
 
 
 def gabp_residual_history(h, relres_ptr, cap):
@@ -426,6 +434,15 @@ class Solver:
         if st != GABP_OK:
             raise GaBPError(st, "gabp_get_messages")
         return P, hm
+
+    def set_messages(self, P, hm):
+        """Loads messages in the layout ``messages()`` returns (CUDA float64 tensors of nnz entries)
+        as the state a solve with ``warm_start=1`` starts from: a checkpoint restored."""
+        _check_out(P, (self.nnz,), self.device, "P")
+        _check_out(hm, (self.nnz,), self.device, "hm")
+        st = gabp_set_messages(self.handle, P.data_ptr(), hm.data_ptr())
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_set_messages")
 
     def grad_values(self, lam, x):
         import torch

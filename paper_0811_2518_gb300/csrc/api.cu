@@ -134,6 +134,18 @@ extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
   return s;
 }
 
+extern "C" gabp_status gabp_set_messages(gabp_handle h, const double *P, const double *hm) {
+  if (!h || !P || !hm || !values_usable(h)) return GABP_ERR_INVALID;
+  if (!is_device_ptr(P) || !is_device_ptr(hm)) {
+    set_last_error("gabp_set_messages: P and hm must be device arrays");
+    return GABP_ERR_INVALID;
+  }
+  DeviceGuard dg(h->device);
+  gabp_status s = load_messages64(h, P, hm);
+  h->last_path = -1;  // marginals and messages are reported again after the next solve
+  return s;
+}
+
 extern "C" gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolours) {
   if (!h || !values_usable(h)) return GABP_ERR_INVALID;
   if (colour && !is_device_ptr(colour)) {

@@ -422,6 +422,7 @@ gabp_status serial_marginals64(gabp_handle h, double *Pi);
 gabp_status serial_freeze32(gabp_handle h, const float2 *CF, const float *invP);
 gabp_status serial_inner32(gabp_handle h, const float *rhs, int cap, double itol, int *sweeps, int *status);
 gabp_status serial_update32(gabp_handle h, double *X);
+gabp_status load_messages64(gabp_handle h, const double *P, const double *hm);
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.

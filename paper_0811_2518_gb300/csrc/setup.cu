@@ -295,6 +295,8 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->fix_step = 0.5;
   o->accel = 0;
   o->history = 0;
+  o->warm_start = 0;
+  o->reserved = 0;
   return GABP_OK;
 }
 
@@ -311,7 +313,7 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 ||
       (o->accel && o->variant != GABP_VARIANT_NODE))
     return GABP_ERR_INVALID;
   return GABP_OK;
@@ -400,6 +402,7 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
   Graph &g = h->g;
   h->values_ok = false;  // until the new values pass every check
   h->last_path = -1;     // marginals / messages of the old values are gone
+  h->w64.valid = false;  // and no warm start from them
   h->w32.coef_ready = false;
   h->w32.prec_round = -1;
   int *dflag = nullptr;

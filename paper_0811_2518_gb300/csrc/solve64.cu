@@ -76,12 +76,22 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
 }
 
 // Round 0 (Algorithm 1/2 step 1): all messages zero, so P~_i = A_ii, h~_i = b_i.
-__global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max_iter) {
+// Warm start (warm = 1): round 0 takes the messages already in M0 (a previous
+// solve's, or imported ones) and forms the aggregates from them with this b:
+// any starting messages lead to the same fixed point when the iteration converges.
+__global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max_iter, int warm) {
   const double *b = a.ctl->b;
   double bb = 0.0;
   for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) {
-    double bi = b[i], d = a.ad[i];
-    a.N0[i] = NodeRec64{d, bi, bi / d, bi / d};  // y^(0) = x^(0)
+    double bi = b[i], d = a.ad[i], P = d, h = bi;
+    if (warm)
+      for (int e = a.rp[i]; e < a.rp[i + 1]; ++e) {
+        const double2 m = a.M0[e];
+        P += m.x;
+        h += m.y;
+      }
+    const double x0 = h / P;
+    a.N0[i] = NodeRec64{P, h, x0, x0};  // y^(0) = x^(0)
     bb = fma(bi, bi, bb);
   }
   double v[1] = {bb}, tot[1];
@@ -436,6 +446,12 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   gabp_status s = ensure_w64(h);
   if (s != GABP_OK) return s;
   Graph &g = h->g;
+  // warm start: the messages of the previous FP64 solve (or imported ones) as round 0, once the
+  // round shape is tuned (the tuner's trial rounds would overwrite them)
+  const bool warm = h->opt.warm_start && h->w64.valid && (h->opt.lanes || h->tuned_L64);
+  if (warm && (h->w64.result_round & 1))
+    GABP_CUDA(cudaMemcpyAsync(h->w64.M[0], h->w64.M[1], sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1),
+                              cudaMemcpyDeviceToDevice, h->stream));
   h->w64.valid = false;
   Args64 a = args64(h);
   // round-0 state (Algorithm 1 step 1): control block pointed at b, zero messages
@@ -456,8 +472,9 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
       GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist, &hp, sizeof(hp), cudaMemcpyHostToDevice, h->stream));
       GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, h->stream));
     }
-    GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
-    k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter);
+    if (!warm)
+      GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
+    k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter, warm ? 1 : 0);
     GABP_CUDA(cudaGetLastError());
     GABP_CUDA(cudaStreamSynchronize(h->stream));  // also retires the pageable copy of bptr
     return GABP_OK;
@@ -511,9 +528,13 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   h->stats.rounds = c.round;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
-  k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x,
-                                                                     h->opt.accel);
-  h->prof.launches += 1;
+  if (warm && c.bb == 0.0) {  // b = 0: x = 0 (the warm round-0 records hold the old messages' mean)
+    GABP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.n, h->stream));
+  } else {
+    k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x,
+                                                                       h->opt.accel);
+    h->prof.launches += 1;
+  }
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   if (iters) *iters = c.iters;
@@ -528,6 +549,32 @@ gabp_status messages64(gabp_handle h, double *P, double *hm) {
       g.n, g.rowptr, g.dpos, g.rp, h->w64.M[h->w64.result_round & 1], P, hm);
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
+  return GABP_OK;
+}
+
+// Inverse of k64_messages: input-layout messages into the internal slot order.
+__global__ void k64_load_messages(int n, const int *__restrict__ rowptr, const int *__restrict__ dpos,
+                                  const int *__restrict__ rp, const double *__restrict__ P,
+                                  const double *__restrict__ hm, double2 *__restrict__ M) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = rowptr[i], d = dpos[i], e0 = rp[i], deg = rp[i + 1] - rp[i];
+  for (int q = 0; q < deg; ++q) {
+    int p = a + q + (q >= d ? 1 : 0);
+    M[e0 + q] = make_double2(P[p], hm[p]);
+  }
+}
+
+gabp_status load_messages64(gabp_handle h, const double *P, const double *hm) {
+  gabp_status s = ensure_w64(h);
+  if (s != GABP_OK) return s;
+  Graph &g = h->g;
+  k64_load_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp, P, hm,
+                                                                           h->w64.M[0]);
+  GABP_CUDA(cudaGetLastError());
+  GABP_CUDA(cudaStreamSynchronize(h->stream));
+  h->w64.result_round = 0;
+  h->w64.valid = true;
   return GABP_OK;
 }
 

@@ -288,3 +288,42 @@ def test_residual_history(gb, variant):
     s32.solve(torch.from_numpy(b).cuda(), tol=1e-10)
     assert s32.residual_history().size == 0
     s32.close()
+
+
+def test_warm_start_and_checkpoint(gb):
+    """options.warm_start: round 0 takes the last FP64 solve's messages with the new b.  The same b
+    is accepted after one round; a nearby b needs fewer rounds than a cold start and reaches the
+    oracle's solution; messages exported (gabp_get_messages) and loaded into another handle
+    (gabp_set_messages) resume the solve; b = 0 gives x = 0; new values disable the warm start."""
+    m = synth.random_sym(3001, 8, 1.1, 2)
+    b = synth.rhs(m.n, 3)
+    b2 = b + 1e-3 * synth.rhs(m.n, 4)
+    tb, tb2 = torch.from_numpy(b).cuda(), torch.from_numpy(b2).cuda()
+    cold = gb.Solver.from_csr(m)
+    x0, st, it0, _ = cold.solve(tb, tol=1e-12)
+    assert st == gb.GABP_OK
+    s = gb.Solver.from_csr(m, warm_start=1)
+    xa, st, ita, _ = s.solve(tb, tol=1e-12)  # no state yet: a cold start
+    assert st == gb.GABP_OK and ita == it0
+    x1, st, it1, _ = s.solve(tb, tol=1e-12)
+    assert st == gb.GABP_OK and it1 == 1
+    assert _relerr(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-12
+    x2w, st, it2w, _ = s.solve(tb2, tol=1e-12)
+    x2c, st2, it2c, _ = cold.solve(tb2, tol=1e-12)
+    assert st == st2 == gb.GABP_OK and it2w < it2c
+    ref = oracle.gabp_broadcast(m, b2, max_iter=1000, tol=1e-13)
+    assert _relerr(x2w.cpu().numpy(), ref["x"]) <= 1e-10
+    P, hm = s.messages()
+    r = gb.Solver.from_csr(m, warm_start=1)
+    r.set_messages(P, hm)
+    x3, st, it3, _ = r.solve(tb2, tol=1e-12)
+    assert st == gb.GABP_OK and it3 == 1
+    assert _relerr(x3.cpu().numpy(), x2w.cpu().numpy()) <= 1e-12
+    xz, st, itz, _ = r.solve(torch.zeros_like(tb), tol=1e-12)
+    assert st == gb.GABP_OK and not torch.any(xz)
+    r.close()
+    s.set_values(m.val)
+    x4, st, it4, _ = s.solve(tb, tol=1e-12)
+    assert st == gb.GABP_OK and it4 == it0
+    s.close()
+    cold.close()
