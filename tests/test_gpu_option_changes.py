@@ -99,3 +99,21 @@ def test_fix_step_change(gb):
     assert st1 == st2 == stf == gb.GABP_OK
     assert it2 == itf and it2 != it1
     assert _relerr(x2.cpu().numpy(), xf.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("path", ["fp64_parallel", "fp64_serial", "fp32_parallel", "fp32_serial"])
+def test_runs_are_bitwise_reproducible(gb, path):
+    """The synchronous rounds read round t-1 and write round t, and every reduction is a
+    fixed-order last-block reduction (no floating-point atomics): two handles give bit-identical
+    iterates and round counts."""
+    m = synth.random_sym(20011, 8, 1.1, 2)
+    b = torch.from_numpy(synth.rhs(m.n, 5)).cuda()
+    out = []
+    for _ in range(2):
+        s = gb.Solver.from_csr(m, lanes=4, **PATHS[path])
+        x, st, it, rel = s.solve(b, tol=1e-10, max_iter=2000)
+        s.close()
+        out.append((x.cpu().numpy(), st, it, rel))
+    assert out[0][1] == out[1][1] == gb.GABP_OK
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+    assert np.array_equal(out[0][0], out[1][0])
