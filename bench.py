@@ -384,153 +384,173 @@ def main():
     # serial schedule (red-black on this grid) and, for comparison, the parallel schedule
     batched = None
     if "batched" in legs:
-        s32.close()
-        s64.close()
-        mg = synth.grid3d(args.batched_grid, 1.05, 3)
-        Rb = 64
-        Bb = torch.from_numpy(synth.rhs_batch(mg.n, Rb, 3 + rank)).to(dev)
-        Eg, ng = mg.num_edges, mg.n
-        res = {}
-        for sched in (1, 0):
-            sb = gb.Solver.from_csr(mg, profile=1, reuse_precisions=0, schedule=sched)
-            Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL)
-            sb.profile(reset=True)
-            barrier()
-            eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            eb0.record()
-            Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL, X=Xb)
-            eb1.record()
-            barrier()
-            res[sched] = (eb0.elapsed_time(eb1), sb.profile(reset=True), sb.stats(), stb, itb, float(np.max(relb)),
-                          sb.serial_colours()[1] if sched else 1)
-            sb.close()
-        msb, pb, stats_b, stb, itb, maxrel, ncol = res[1]
-        mean_ms = pb["ms"]["mean32"] / max(pb["rounds"]["mean32"], 1)  # one sweep (all colour passes)
-        # per sweep: every slot once (R messages read + written, coefficient pair, sender) and every row once
-        # (R firing aggregates read + written, R right-hand sides, segment bounds / colour / row pointer)
-        bytes_b = Eg * (8 * Rb + 12) + ng * (12 * Rb + 20)
-        batched = {"workload": f"{args.batched_grid}^3 7-point grid, face coefficients LogNormal(0,1), diagonal 1.05 x "
-                               "row abs-sum, 64 right-hand sides N(0,1)", "n": ng, "edges": Eg, "rhs": Rb,
-                   "schedule": f"serial (one message store, {ncol} colours: red-black on this grid)",
-                   "status": stb, "ms_per_solve": msb, "inner_sweeps": itb, "refine_steps": stats_b["refine_steps"],
-                   "max_relres": maxrel, "rhs_edge_updates_per_s": stats_b["edge_updates"] / (msb / 1e3),
-                   "ms_per_rhs": msb / Rb,
-                   "parallel_schedule": {"ms_per_solve": res[0][0], "inner_rounds": res[0][4],
-                                         "max_relres": res[0][5]},
-                   "roofline": {"bound": "hbm", "kernel": "kbs_pass (one sweep = all colour passes)",
-                                "achieved": bytes_b / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                                "frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak,
-                                "traffic": _profiled_traffic("kbs_pass_grid3d_64_64rhs.md",
-                                                             "paper_0811_2518_gb300/csrc/batched.cu", "kbs_pass",
-                                                             scale_to=bytes_b),
-                                "traffic_note": "DRAM bytes per sweep, scaled from one captured pass of the 64^3 "
-                                                "case (the two red-black passes move equal bytes)",
-                                "bytes_per_sweep": bytes_b, "sweep_ms": mean_ms}}
+        try:
+            s32.close()
+            s64.close()
+            mg = synth.grid3d(args.batched_grid, 1.05, 3)
+            Rb = 64
+            Bb = torch.from_numpy(synth.rhs_batch(mg.n, Rb, 3 + rank)).to(dev)
+            Eg, ng = mg.num_edges, mg.n
+            res = {}
+            for sched in (1, 0):
+                sb = gb.Solver.from_csr(mg, profile=1, reuse_precisions=0, schedule=sched)
+                Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL)
+                sb.profile(reset=True)
+                barrier()
+                eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                eb0.record()
+                Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL, X=Xb)
+                eb1.record()
+                barrier()
+                res[sched] = (eb0.elapsed_time(eb1), sb.profile(reset=True), sb.stats(), stb, itb, float(np.max(relb)),
+                              sb.serial_colours()[1] if sched else 1)
+                sb.close()
+            msb, pb, stats_b, stb, itb, maxrel, ncol = res[1]
+            mean_ms = pb["ms"]["mean32"] / max(pb["rounds"]["mean32"], 1)  # one sweep (all colour passes)
+            # per sweep: every slot once (R messages read + written, coefficient pair, sender) and every row once
+            # (R firing aggregates read + written, R right-hand sides, segment bounds / colour / row pointer)
+            bytes_b = Eg * (8 * Rb + 12) + ng * (12 * Rb + 20)
+            batched = {"workload": f"{args.batched_grid}^3 7-point grid, face coefficients LogNormal(0,1), diagonal 1.05 x "
+                                   "row abs-sum, 64 right-hand sides N(0,1)", "n": ng, "edges": Eg, "rhs": Rb,
+                       "schedule": f"serial (one message store, {ncol} colours: red-black on this grid)",
+                       "status": stb, "ms_per_solve": msb, "inner_sweeps": itb, "refine_steps": stats_b["refine_steps"],
+                       "max_relres": maxrel, "rhs_edge_updates_per_s": stats_b["edge_updates"] / (msb / 1e3),
+                       "ms_per_rhs": msb / Rb,
+                       "parallel_schedule": {"ms_per_solve": res[0][0], "inner_rounds": res[0][4],
+                                             "max_relres": res[0][5]},
+                       "roofline": {"bound": "hbm", "kernel": "kbs_pass (one sweep = all colour passes)",
+                                    "achieved": bytes_b / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                    "frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak,
+                                    "traffic": _profiled_traffic("kbs_pass_grid3d_64_64rhs.md",
+                                                                 "paper_0811_2518_gb300/csrc/batched.cu", "kbs_pass",
+                                                                 scale_to=bytes_b),
+                                    "traffic_note": "DRAM bytes per sweep, scaled from one captured pass of the 64^3 "
+                                                    "case (the two red-black passes move equal bytes)",
+                                    "bytes_per_sweep": bytes_b, "sweep_ms": mean_ms}}
+        except Exception as exc:  # one GPU: keep the headline line, record the failed leg
+            if world > 1:
+                raise
+            batched = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- 512 independent random-geometric-graph systems in one persistent launch
     multi = None
     if "multi" in legs:
-        mats = synth.rgg_batch(args.multi_systems, 1024, 65536, 2.0, 4)
-        bigm = synth.block_diag(mats)
-        offm = bigm.meta["offsets"]
-        bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
-        sm = gb.Solver.from_csr(bigm)
-        xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL)  # first call autotunes the split
-        sm.profile(reset=True)
-        reps_m = 5  # timed batches (each one launch); the median is reported
-        times_m = []
-        for _ in range(reps_m):
-            barrier()
-            em0, em1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            em0.record()
-            xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL, x=xm)
-            em1.record()
-            barrier()
-            times_m.append(em0.elapsed_time(em1))
-        msm = float(np.median(times_m))
-        pm = sm.profile(reset=True)
-        stm_ = sm.stats()
-        tuned_m = sm.tuned()
-        multi = {"workload": f"{args.multi_systems} random geometric graphs, sizes ~ n^-2 on [1024, 65536], "
-                             "radius for degree 6, "
-                             "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
-                 "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
-                 "ms_per_batch": msm, "ms_per_batch_all": times_m, "kernel_ms": pm["ms"]["multi"] / reps_m,
-                 "kernel": "grid-persistent" if tuned_m["multi_mode"] == 1 else "teams",
-                 "grid_shape": {"lanes_per_row": tuned_m["multi_grid"][0], "slots_per_lane": tuned_m["multi_grid"][1]},
-                 "edge_updates": stm_["edge_updates"],
-                 "edge_updates_per_s": stm_["edge_updates"] / (msm / 1e3),
-                 "rounds_per_system": {"min": int(itsm.min()), "median": int(np.median(itsm)), "max": int(itsm.max())},
-                 "max_relres": float(relm.max()), "launches_per_batch": 1}
-        sm.close()
+        try:
+            mats = synth.rgg_batch(args.multi_systems, 1024, 65536, 2.0, 4)
+            bigm = synth.block_diag(mats)
+            offm = bigm.meta["offsets"]
+            bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
+            sm = gb.Solver.from_csr(bigm)
+            xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL)  # first call autotunes the split
+            sm.profile(reset=True)
+            reps_m = 5  # timed batches (each one launch); the median is reported
+            times_m = []
+            for _ in range(reps_m):
+                barrier()
+                em0, em1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                em0.record()
+                xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL, x=xm)
+                em1.record()
+                barrier()
+                times_m.append(em0.elapsed_time(em1))
+            msm = float(np.median(times_m))
+            pm = sm.profile(reset=True)
+            stm_ = sm.stats()
+            tuned_m = sm.tuned()
+            multi = {"workload": f"{args.multi_systems} random geometric graphs, sizes ~ n^-2 on [1024, 65536], "
+                                 "radius for degree 6, "
+                                 "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
+                     "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
+                     "ms_per_batch": msm, "ms_per_batch_all": times_m, "kernel_ms": pm["ms"]["multi"] / reps_m,
+                     "kernel": "grid-persistent" if tuned_m["multi_mode"] == 1 else "teams",
+                     "grid_shape": {"lanes_per_row": tuned_m["multi_grid"][0], "slots_per_lane": tuned_m["multi_grid"][1]},
+                     "edge_updates": stm_["edge_updates"],
+                     "edge_updates_per_s": stm_["edge_updates"] / (msm / 1e3),
+                     "rounds_per_system": {"min": int(itsm.min()), "median": int(np.median(itsm)), "max": int(itsm.max())},
+                     "max_relres": float(relm.max()), "launches_per_batch": 1}
+            sm.close()
+        except Exception as exc:  # one GPU: keep the headline line, record the failed leg
+            if world > 1:
+                raise
+            multi = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- differentiable solve: n = 2^22, degree ~6, forward + hand-written backward
     grad = None
     if "grad" in legs:
-        from paper_0811_2518_gb300 import autograd as ga
+        try:
+            from paper_0811_2518_gb300 import autograd as ga
 
-        mc = synth.random_sym(1 << 22, 3, 1.2, 5)
-        rp_t = torch.from_numpy(mc.rowptr).to(dev)
-        cl_t = torch.from_numpy(mc.col).to(dev)
-        xs_t = torch.from_numpy(synth.rhs(mc.n, 105)).to(dev)
-        b_c = synth.rhs(mc.n, 5 + rank)
+            mc = synth.random_sym(1 << 22, 3, 1.2, 5)
+            rp_t = torch.from_numpy(mc.rowptr).to(dev)
+            cl_t = torch.from_numpy(mc.col).to(dev)
+            xs_t = torch.from_numpy(synth.rhs(mc.n, 105)).to(dev)
+            b_c = synth.rhs(mc.n, 5 + rank)
 
-        vals0 = torch.from_numpy(mc.val).to(dev)
-        b0 = torch.from_numpy(b_c).to(dev)
+            vals0 = torch.from_numpy(mc.val).to(dev)
+            b0 = torch.from_numpy(b_c).to(dev)
 
-        def fwd_bwd(solver=None):
-            vals = vals0.detach().clone().requires_grad_(True)
-            bt = b0.detach().clone().requires_grad_(True)
-            xg = ga.gabp_solve_autograd(rp_t, cl_t, vals, bt, tol=TOL, solver=solver)
-            loss = 0.5 * torch.sum((xg - xs_t) ** 2)
-            loss.backward()
-            return vals.grad, bt.grad
+            def fwd_bwd(solver=None):
+                vals = vals0.detach().clone().requires_grad_(True)
+                bt = b0.detach().clone().requires_grad_(True)
+                xg = ga.gabp_solve_autograd(rp_t, cl_t, vals, bt, tol=TOL, solver=solver)
+                loss = 0.5 * torch.sum((xg - xs_t) ** 2)
+                loss.backward()
+                return vals.grad, bt.grad
 
-        def timed(f, reps=3):
-            f()
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
+            def timed(f, reps=3):
                 f()
-            e1.record()
-            barrier()
-            return e0.elapsed_time(e1) / reps
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    f()
+                e1.record()
+                barrier()
+                return e0.elapsed_time(e1) / reps
 
-        ms_fresh = timed(fwd_bwd)
-        shared = gb.Solver(mc.n, rp_t, cl_t, vals0, precision=gb.GABP_PREC_FP32_REFINE)
-        ms_shared = timed(lambda: fwd_bwd(shared))
-        shared.close()
-        grad = {"workload": "random sparse symmetric A, n=2^22, 3 picks per row (degree ~6), U(-1,1), diagonal "
-                            "1.2 x row abs-sum; loss 0.5||x - x*||^2; FP32 messages + FP64 refinement",
-                "n": mc.n, "edges": mc.num_edges, "ms_forward_backward": ms_fresh,
-                "includes": "handle creation (validation, reverse index), forward solve (precision state "
-                            "recomputed), adjoint solve on the same precision state, dL/dA and dL/db; inputs "
-                            "already on the device",
-                "ms_forward_backward_shared_solver": ms_shared,
-                "shared_solver": "one handle for the pattern, new values set each step (gabp_set_values) "
-                                 "instead of a new handle"}
+            ms_fresh = timed(fwd_bwd)
+            shared = gb.Solver(mc.n, rp_t, cl_t, vals0, precision=gb.GABP_PREC_FP32_REFINE)
+            ms_shared = timed(lambda: fwd_bwd(shared))
+            shared.close()
+            grad = {"workload": "random sparse symmetric A, n=2^22, 3 picks per row (degree ~6), U(-1,1), diagonal "
+                                "1.2 x row abs-sum; loss 0.5||x - x*||^2; FP32 messages + FP64 refinement",
+                    "n": mc.n, "edges": mc.num_edges, "ms_forward_backward": ms_fresh,
+                    "includes": "handle creation (validation, reverse index), forward solve (precision state "
+                                "recomputed), adjoint solve on the same precision state, dL/dA and dL/db; inputs "
+                                "already on the device",
+                    "ms_forward_backward_shared_solver": ms_shared,
+                    "shared_solver": "one handle for the pattern, new values set each step (gabp_set_values) "
+                                     "instead of a new handle"}
+        except Exception as exc:  # one GPU: keep the headline line, record the failed leg
+            if world > 1:
+                raise
+            grad = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- convergence fix on a non-walk-summable SPD matrix (n = 4096, diagonal 0.9 x row abs-sum):
     # the double loop (FP32 inner GaBP solves on A + Gamma) and the single loop (one FP64 round per step)
     fix = None
     if "fix" in legs:
-        mf = synth.random_sym(4096, 3, 0.9, 5)
-        bf = torch.from_numpy(synth.rhs(mf.n, 5)).to(dev)
-        fix = {"workload": "random sparse symmetric A, n=4096, 3 picks per row, diagonal 0.9 x row abs-sum "
-                           "(SPD, rho(|R|) = 1/0.9 > 1), uniform loading Gamma = 0.25 diag(A), to 1e-10"}
-        for name, kw in (("double_loop", {}), ("single_loop", {"fix_single_loop": 1, "fix_step": 0.5})):
-            sf = gb.Solver.from_csr(mf, gamma_mode=1, gamma=0.25, max_refine=2000, **kw)
-            sf.solve(bf, tol=TOL, max_iter=200000)
-            barrier()
-            ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ef0.record()
-            xf, stf, itf, relf = sf.solve(bf, tol=TOL, max_iter=200000)
-            ef1.record()
-            barrier()
-            fix[name] = {"ms": ef0.elapsed_time(ef1), "status": int(stf), "gabp_rounds": int(itf),
-                         "outer_steps": sf.stats()["refine_steps"] if not kw else int(itf), "relres": relf}
-            sf.close()
+        try:
+            mf = synth.random_sym(4096, 3, 0.9, 5)
+            bf = torch.from_numpy(synth.rhs(mf.n, 5)).to(dev)
+            fix = {"workload": "random sparse symmetric A, n=4096, 3 picks per row, diagonal 0.9 x row abs-sum "
+                               "(SPD, rho(|R|) = 1/0.9 > 1), uniform loading Gamma = 0.25 diag(A), to 1e-10"}
+            for name, kw in (("double_loop", {}), ("single_loop", {"fix_single_loop": 1, "fix_step": 0.5})):
+                sf = gb.Solver.from_csr(mf, gamma_mode=1, gamma=0.25, max_refine=2000, **kw)
+                sf.solve(bf, tol=TOL, max_iter=200000)
+                barrier()
+                ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ef0.record()
+                xf, stf, itf, relf = sf.solve(bf, tol=TOL, max_iter=200000)
+                ef1.record()
+                barrier()
+                fix[name] = {"ms": ef0.elapsed_time(ef1), "status": int(stf), "gabp_rounds": int(itf),
+                             "outer_steps": sf.stats()["refine_steps"] if not kw else int(itf), "relres": relf}
+                sf.close()
+        except Exception as exc:  # one GPU: keep the headline line, record the failed leg
+            if world > 1:
+                raise
+            fix = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
