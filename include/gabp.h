@@ -137,7 +137,12 @@ typedef struct {
                            messages, with the new b; the iteration has the same fixed point from any
                            start, so a nearby b converges in fewer rounds.  Ignored until the handle
                            has such messages, and by the other paths.  Default 0 */
-  int reserved;
+  int initial_guess;    /* gabp_solve / gabp_solve_host (every single right-hand-side path): 1 = x holds
+                           an initial iterate x0 on entry; the path solves the correction system
+                           A d = b - A x0 (FP64 residual) to the tolerance that makes
+                           ||b - A (x0 + d)|| <= tol ||b||, and returns x = x0 + d (x0 itself when it
+                           already meets tol; x = 0 for b = 0).  Rounds, stats and messages are those of
+                           the correction solve.  Default 0 */
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

@@ -61,7 +61,7 @@ class Options(ctypes.Structure):
         ("history", ctypes.c_int),
         ("fix_step", ctypes.c_double),
         ("warm_start", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("initial_guess", ctypes.c_int),
     ]
 
 
@@ -373,13 +373,16 @@ class Solver:
             raise GaBPError(st, "gabp_set_options")
 
     def solve(self, b, tol=1e-12, max_iter=1000, x=None, check=True):
-        """x = A^{-1} b.  Returns (x, status, iters, relres)."""
+        """x = A^{-1} b.  Returns (x, status, iters, relres).  With the option initial_guess=1, x
+        (required then) holds the initial iterate on entry."""
         import torch
 
         b = b.to(self.device, torch.float64).contiguous()
         if b.numel() != self.n:
             raise ValueError(f"b has {b.numel()} entries, the matrix {self.n} rows")
         if x is None:
+            if self.options.initial_guess:
+                raise ValueError("initial_guess=1: pass the initial iterate as x")
             x = torch.empty_like(b)
         _check_out(x, b.shape, self.device, "x")
         st, it, rel = gabp_solve(self.handle, b.data_ptr(), x.data_ptr(), tol, max_iter)

@@ -29,33 +29,43 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
                            int32_t *iters_out, double *relres_out) {
   if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || !values_usable(h)) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  h->hist_len = 0;  // only the FP64 parallel rounds record a history
+  // one solve of A x = b on the path the options select (x = 0 at the start)
+  auto run = [&](const double *rb, double *rx, double rtol, int *it, double *rel) -> gabp_status {
+    gabp_status s;
+    if (h->opt.gamma_mode != 0) {
+      // convergence fix: FP32 GaBP inner solves on A + Gamma inside the FP64 outer loop
+      if (!h->gamma) {
+        cudaError_t e = cudaMalloc(&h->gamma, sizeof(double) * h->g.n);
+        if (e != cudaSuccess) return cuda_fail(e, "gamma");
+      }
+      s = make_gamma(h, h->gamma);
+      if (h->opt.fix_single_loop) {
+        if (s == GABP_OK) s = solve_fix_single(h, rb, rx, rtol, max_iter, h->gamma, it, rel);
+        h->last_path = -1;  // the messages are those of A + Gamma: no marginals of A to report
+      } else {
+        if (s == GABP_OK) s = solve32_refine(h, 1, rb, rx, h->g.n, rtol, max_iter, h->gamma, it, rel);
+        h->last_path = 1;
+      }
+    } else if (h->opt.precision == GABP_PREC_FP32_REFINE) {
+      s = solve32_refine(h, 1, rb, rx, h->g.n, rtol, max_iter, nullptr, it, rel);
+      h->last_path = 1;
+    } else if (h->opt.schedule == 1) {
+      s = solve64_serial(h, rb, rx, rtol, max_iter, it, rel);
+      h->last_path = 2;
+    } else {
+      s = solve64(h, rb, rx, rtol, max_iter, it, rel);
+      h->last_path = 0;
+    }
+    return s;
+  };
   int it = 0;
   double rel = 0.0;
   gabp_status s;
-  h->hist_len = 0;  // only the FP64 parallel rounds record a history
-  if (h->opt.gamma_mode != 0) {
-    // convergence fix: FP32 GaBP inner solves on A + Gamma inside the FP64 outer loop
-    if (!h->gamma) {
-      cudaError_t e = cudaMalloc(&h->gamma, sizeof(double) * h->g.n);
-      if (e != cudaSuccess) return cuda_fail(e, "gamma");
-    }
-    s = make_gamma(h, h->gamma);
-    if (h->opt.fix_single_loop) {
-      if (s == GABP_OK) s = solve_fix_single(h, b, x, tol, max_iter, h->gamma, &it, &rel);
-      h->last_path = -1;  // the messages are those of A + Gamma: no marginals of A to report
-    } else {
-      if (s == GABP_OK) s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, h->gamma, &it, &rel);
-      h->last_path = 1;
-    }
-  } else if (h->opt.precision == GABP_PREC_FP32_REFINE) {
-    s = solve32_refine(h, 1, b, x, h->g.n, tol, max_iter, nullptr, &it, &rel);
-    h->last_path = 1;
-  } else if (h->opt.schedule == 1) {
-    s = solve64_serial(h, b, x, tol, max_iter, &it, &rel);
-    h->last_path = 2;
+  if (h->opt.initial_guess) {
+    s = solve_from_initial(h, b, x, tol, &it, &rel, run);
   } else {
-    s = solve64(h, b, x, tol, max_iter, &it, &rel);
-    h->last_path = 0;
+    s = run(b, x, tol, &it, &rel);
   }
   if (s >= 0) {
     if (iters_out) *iters_out = it;
@@ -90,6 +100,8 @@ extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x
     if (e != cudaSuccess) return cuda_fail(e, "gabp_solve_host staging");
   }
   GABP_CUDA(cudaMemcpyAsync(h->hb, b, bytes, cudaMemcpyHostToDevice, h->stream));
+  if (h->opt.initial_guess)  // x holds the initial iterate
+    GABP_CUDA(cudaMemcpyAsync(h->hx, x, bytes, cudaMemcpyHostToDevice, h->stream));
   gabp_status s = solve_dispatch(h, h->hb, h->hx, tol, max_iter, iters_out, relres_out);
   if (s < 0) return s;
   GABP_CUDA(cudaMemcpyAsync(x, h->hx, bytes, cudaMemcpyDeviceToHost, h->stream));

@@ -13,6 +13,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cstddef>
+#include <functional>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -200,6 +201,7 @@ struct gabp_handle_s {
   int hist_alloc = 0;
   int hist_len = 0;                 // entries recorded by the last solve (0 when it kept none)
   double hist_bb = 0.0;             // ||b||^2 of that solve
+  double *ig_buf = nullptr;         // initial-guess solves: r0 = b - A x0, the correction d, sums
   gabp::Prof prof;
   gabp::WorkB *wb = nullptr;
   long long multi_big = 0;          // autotuned cluster / single-CTA size split of the multi-system kernel
@@ -423,6 +425,10 @@ gabp_status serial_freeze32(gabp_handle h, const float2 *CF, const float *invP);
 gabp_status serial_inner32(gabp_handle h, const float *rhs, int cap, double itol, int *sweeps, int *status);
 gabp_status serial_update32(gabp_handle h, double *X);
 gabp_status load_messages64(gabp_handle h, const double *P, const double *hm);
+// initial.cu: x holds x0 on entry; solve(r0, d, tol', iters, relres) runs a path on A d = b - A x0
+gabp_status solve_from_initial(gabp_handle h, const double *b, double *x, double tol, int *iters, double *relres,
+                               const std::function<gabp_status(const double *, double *, double, int *, double *)>
+                                   &solve);
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.

@@ -196,6 +196,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   cudaFree(h->hx);
   cudaFree(h->gamma);
   cudaFree(h->hist);
+  cudaFree(h->ig_buf);
   cudaFree(h->ctl_tune);
   if (h->prof.e0) cudaEventDestroy(h->prof.e0);
   if (h->prof.e1) cudaEventDestroy(h->prof.e1);
@@ -296,7 +297,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->accel = 0;
   o->history = 0;
   o->warm_start = 0;
-  o->reserved = 0;
+  o->initial_guess = 0;
   return GABP_OK;
 }
 
@@ -313,7 +314,7 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 ||
       (o->accel && o->variant != GABP_VARIANT_NODE))
     return GABP_ERR_INVALID;
   return GABP_OK;

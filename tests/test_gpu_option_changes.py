@@ -117,3 +117,47 @@ def test_runs_are_bitwise_reproducible(gb, path):
     assert out[0][1] == out[1][1] == gb.GABP_OK
     assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+@pytest.mark.parametrize("opts", [dict(precision=1), dict(precision=1, device_loop=0), dict(precision=0),
+                                  dict(precision=0, schedule=1), dict(precision=1, gamma_mode=1)])
+def test_initial_guess(gb, opts):
+    """options.initial_guess: x holds x0 on entry, the path solves A d = b - A x0 and returns x0 + d.
+    From the solution of a nearby right-hand side it needs fewer rounds than from zero and meets
+    the same stop rule (checked on the host and against the oracle); an x0 that already meets the
+    tolerance comes back unchanged after no round; b = 0 gives x = 0; host buffers work too."""
+    import oracle
+
+    m = synth.random_sym(20011, 8, 1.1, 2)
+    b = synth.rhs(m.n, 5)
+    b2 = b + 1e-4 * synth.rhs(m.n, 6)
+    tb, tb2 = torch.from_numpy(b).cuda(), torch.from_numpy(b2).cuda()
+    cold = gb.Solver.from_csr(m, **opts)
+    x1, st, it1, _ = cold.solve(tb, tol=1e-10, max_iter=5000)
+    xc, stc, itc, _ = cold.solve(tb2, tol=1e-10, max_iter=5000)
+    cold.close()
+    assert st == stc == gb.GABP_OK
+    s = gb.Solver.from_csr(m, initial_guess=1, **opts)
+    xg = x1.clone()
+    xg, stg, itg, relg = s.solve(tb2, x=xg, tol=1e-10, max_iter=5000)
+    assert stg == gb.GABP_OK and itg < itc and relg <= 1e-10
+    xh = xg.cpu().numpy()
+    rows = np.repeat(np.arange(m.n), np.diff(m.rowptr))
+    r = b2 - np.bincount(rows, m.val * xh[m.col], minlength=m.n)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b2) * (1 + 1e-6)
+    assert abs(np.linalg.norm(r) / np.linalg.norm(b2) - relg) <= 1e-3 * relg + 1e-16
+    ref = oracle.gabp_broadcast(m, b2, max_iter=2000, tol=1e-13)
+    assert np.linalg.norm(xh - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    keep = xg.clone()
+    x3, st3, it3, rel3 = s.solve(tb2, x=keep.clone(), tol=1e-8, max_iter=5000)
+    assert st3 == gb.GABP_OK and it3 == 0 and torch.equal(x3, keep)
+    xz, stz, itz, _ = s.solve(torch.zeros_like(tb), x=keep.clone(), tol=1e-10)
+    assert stz == gb.GABP_OK and not torch.any(xz)
+    xhost = x1.cpu().numpy().copy()
+    sth, ith, relh = s.solve_host(b2.copy(), xhost, tol=1e-10, max_iter=5000)
+    # (a second FP32 solve on the handle reuses the frozen precision state: not bit-identical)
+    assert sth == gb.GABP_OK and relh <= 1e-10
+    assert np.linalg.norm(xhost - xh) <= 1e-8 * np.linalg.norm(xh)
+    with pytest.raises(ValueError):
+        s.solve(tb2)  # initial_guess needs x
+    s.close()
