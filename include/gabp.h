@@ -20,7 +20,10 @@
  *     double loop or a damped single loop (Chapter "Fixing convergence of
  *     GaBP");
  *   - the answer is the marginal mean vector and, optionally, the marginal
- *     precisions (Algorithm 1, steps 4-5).
+ *     precisions (Algorithm 1, steps 4-5);
+ *   - the messages are the solver's state: they can be exported and loaded
+ *     (checkpoint / resume, warm starts), a solve can start from a caller's
+ *     iterate, and FP64 runs can record their residual per round.
  *
  * Conventions for every function below
  *   - Return value: a gabp_status.  Negative values are errors; on an error
