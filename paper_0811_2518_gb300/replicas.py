@@ -40,7 +40,10 @@ class Replicas:
 
     def barrier(self):
         if self.dist is not None:
-            self.dist.barrier()
+            if self.dist.get_backend() == "nccl":  # the rank's own GPU (set by the caller)
+                self.dist.barrier(device_ids=[self.local_rank])
+            else:
+                self.dist.barrier()
 
     def max(self, value: float, device=None) -> float:
         """The slowest rank's time (the whole job ends when it does)."""
