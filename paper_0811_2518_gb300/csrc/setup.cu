@@ -155,10 +155,16 @@ __global__ void k_ctl_arm_tune(DevCtl *c, const double *b) {
   c->edge_bad = 0;
   c->b = b;
   c->no_stop = 1;
+  c->hist = nullptr;  // tuning rounds record no residual history
+  c->hist_cap = 0;
+  c->hist_len = 0;
 }
 
 gabp_status tune_ctl(gabp_handle h, const double *b) {
-  if (!h->ctl_tune) GABP_CUDA(cudaMalloc(&h->ctl_tune, sizeof(DevCtl)));
+  if (!h->ctl_tune) {
+    GABP_CUDA(cudaMalloc(&h->ctl_tune, sizeof(DevCtl)));
+    GABP_CUDA(cudaMemsetAsync(h->ctl_tune, 0, sizeof(DevCtl), h->stream));
+  }
   if (!h->ctl_tune) return GABP_ERR_NOMEM;
   k_ctl_arm_tune<<<1, 1, 0, h->stream>>>(h->ctl_tune, b ? b : h->g.ad);
   GABP_CUDA(cudaGetLastError());

@@ -327,3 +327,20 @@ def test_warm_start_and_checkpoint(gb):
     assert st == gb.GABP_OK and it4 == it0
     s.close()
     cold.close()
+
+
+def test_fp64_tuning_after_other_handles_freed(gb):
+    """The FP64 autotuner's scratch control block is initialised in full (no field read from
+    recycled device memory): an FP32 handle solves and is destroyed, then a new FP64 handle tunes
+    and solves in the same process, as the benchmark does."""
+    m = synth.random_sym(1 << 16, 8, 1.1, 2)
+    b = torch.from_numpy(synth.rhs(m.n, 2)).cuda()
+    for _ in range(2):
+        s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0)
+        for _ in range(3):
+            s32.solve(b, tol=1e-10)
+        s32.close()
+        s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64)
+        x, st, it, rel = s64.solve(b, tol=1e-10, max_iter=2000)
+        s64.close()
+        assert st == gb.GABP_OK and rel <= 1e-10
