@@ -29,6 +29,7 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
                            int32_t *iters_out, double *relres_out) {
   if (!h || !b || !x || !(tol >= 0.0) || max_iter < 0 || !values_usable(h)) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   h->hist_len = 0;  // only the FP64 parallel rounds record a history
   // one solve of A x = b on the path the options select (x = 0 at the start)
   auto run = [&](const double *rb, double *rx, double rtol, int *it, double *rel) -> gabp_status {
@@ -90,6 +91,7 @@ extern "C" gabp_status gabp_solve_host(gabp_handle h, const double *b, double *x
                                        int32_t *iters_out, double *relres_out) {
   if (!h || !b || !x) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   const size_t bytes = sizeof(double) * h->g.n;
   if (!h->hb) {
     cudaError_t e = cudaMalloc(&h->hb, bytes);
@@ -118,6 +120,7 @@ extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const dou
     return GABP_ERR_INVALID;
   }
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   int it = 0;
   gabp_status s = solve_batched32(h, nrhs, B, X, ld, tol, max_iter, &it, relres_out);
   if (s >= 0 && iters_out) *iters_out = it;
@@ -127,6 +130,7 @@ extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const dou
 extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
   if (!h || !Pi) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   if (h->last_path == 0) return marginals(h, Pi);
   if (h->last_path == 1) return marginals32(h, Pi);
   if (h->last_path == 2) return serial_marginals64(h, Pi);
@@ -136,6 +140,7 @@ extern "C" gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi) {
 extern "C" gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm) {
   if (!h || !P || !hm) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   if (h->last_path == 0) return messages64(h, P, hm);
   if (h->last_path != 2) return GABP_ERR_INVALID;
   double2 *M = nullptr;  // serial messages back in the input layout
@@ -153,6 +158,7 @@ extern "C" gabp_status gabp_set_messages(gabp_handle h, const double *P, const d
     return GABP_ERR_INVALID;
   }
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   gabp_status s = load_messages64(h, P, hm);
   h->last_path = -1;  // marginals and messages are reported again after the next solve
   return s;
@@ -165,12 +171,14 @@ extern "C" gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32
     return GABP_ERR_INVALID;
   }
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   return serial_colours(h, colour, ncolours);
 }
 
 extern "C" gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *x, double *grad_val) {
   if (!h || !lambda || !x || !grad_val || !values_usable(h)) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   return grad_values(h, lambda, x, grad_val);
 }
 
@@ -195,6 +203,7 @@ extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int
     return GABP_ERR_INVALID;
   }
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   return solve_systems(h, nsys, offsets, b, x, tol, max_iter, status_out, iters_out, relres_out);
 }
 
@@ -220,6 +229,7 @@ extern "C" gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int r
 extern "C" gabp_status gabp_residual_history(gabp_handle h, double *relres, int32_t cap, int32_t *count) {
   if (!h || cap < 0 || (cap > 0 && !relres)) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   const int m = std::min(cap, h->hist_len);
   if (m > 0) {
     GABP_CUDA(cudaMemcpyAsync(relres, h->hist, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream));

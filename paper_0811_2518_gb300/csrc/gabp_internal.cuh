@@ -162,6 +162,12 @@ struct Prof {
 struct gabp_handle_s {
   int device = 0;
   cudaStream_t stream = nullptr;
+  // When the caller gives no stream (the legacy default stream), the handle runs on a stream of
+  // its own -- round graphs cannot be captured on the legacy stream -- ordered after the caller's
+  // default-stream work at every entry point (order_after_caller).
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t caller_ev = nullptr;
+  bool order_legacy = false;
   gabp_options opt{};
   gabp::Graph g;
   gabp::Work64 w64;
@@ -210,6 +216,17 @@ struct gabp_handle_s {
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
 };
+namespace gabp {
+// Orders the handle's own stream after the work the caller queued on the legacy
+// default stream (its inputs, or earlier use of its output buffers); a no-op when
+// the caller supplied a stream.
+inline void order_after_caller(gabp_handle_s *h) {
+  if (!h->order_legacy) return;
+  cudaEventRecord(h->caller_ev, cudaStreamLegacy);
+  cudaStreamWaitEvent(h->stream, h->caller_ev, 0);
+}
+}  // namespace gabp
+
 
 namespace gabp {
 

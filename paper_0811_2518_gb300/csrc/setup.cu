@@ -202,6 +202,11 @@ static gabp_status destroy_impl(gabp_handle h) {
   cudaFree(h->hx);
   cudaFree(h->gamma);
   cudaFree(h->hist);
+  if (h->own_stream) {
+    cudaStreamSynchronize(h->own_stream);
+    cudaStreamDestroy(h->own_stream);
+  }
+  if (h->caller_ev) cudaEventDestroy(h->caller_ev);
   cudaFree(h->ig_buf);
   cudaFree(h->ctl_tune);
   if (h->prof.e0) cudaEventDestroy(h->prof.e0);
@@ -216,6 +221,7 @@ static gabp_status create_impl(gabp_handle h, int n, int64_t nnz, const int32_t 
   Graph &g = h->g;
   g.n = n;
   g.nnz = nnz;
+  order_after_caller(h);  // a device CSR may still be in flight on the caller's default stream
   GABP_CUDA(cudaMalloc(&g.rowptr, sizeof(int) * (n + 1)));
   GABP_CUDA(cudaMalloc(&g.col, sizeof(int) * nnz));
   GABP_CUDA(cudaMalloc(&g.val, sizeof(double) * nnz));
@@ -374,6 +380,14 @@ extern "C" gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, con
   h->opt = o;
   h->stream = (cudaStream_t)stream;
   cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess && !h->stream) {  // no stream given: a stream of the handle's own (see order_after_caller)
+    e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->caller_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      h->stream = h->own_stream;
+      h->order_legacy = true;
+    }
+  }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) {
     gabp_status s = cuda_fail(e, "gabp_create device query");
@@ -406,6 +420,7 @@ extern "C" gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, con
 extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem_space) {
   if (!h || !val || (mem_space != 0 && mem_space != 1)) return GABP_ERR_INVALID;
   DeviceGuard dg(h->device);
+  order_after_caller(h);
   Graph &g = h->g;
   h->values_ok = false;  // until the new values pass every check
   h->last_path = -1;     // marginals / messages of the old values are gone
@@ -488,7 +503,18 @@ extern "C" gabp_status gabp_set_stream(gabp_handle h, void *stream) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "gabp_set_stream");
   }
-  h->stream = (cudaStream_t)stream;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+    h->order_legacy = false;
+  } else {  // back to the handle's own stream, ordered after the legacy default stream
+    if (!h->own_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !h->caller_ev) e = cudaEventCreateWithFlags(&h->caller_ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "gabp_set_stream");
+    }
+    h->stream = h->own_stream;
+    h->order_legacy = true;
+  }
   return GABP_OK;
 }
 
