@@ -227,6 +227,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=0,
                     help="sub-warp width of the R = 1 kernels (0 = the library's autotuner)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel on its own instead of replaying captured CUDA graphs (for "
+                         "per-kernel profilers; results are the same)")
     ap.add_argument("--unroll", type=int, default=0,
                     help="with --lanes: slots per lane of the FP32 round kernels (0 = the library default)")
     ap.add_argument("--batched-grid", type=int, default=128,
@@ -236,6 +239,7 @@ def main():
     ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad,fix",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
+    gkw = {"graphs": 0} if args.no_graphs else {}  # solver options of every handle below
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -262,9 +266,9 @@ def main():
     b_dev = torch.from_numpy(b).to(dev)
     x_dev = torch.empty_like(b_dev)
 
-    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1, lanes=args.lanes,
+    s32 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, profile=1, lanes=args.lanes, **gkw,
                              unroll=args.unroll if args.lanes else 0)
-    s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1, lanes=args.lanes)
+    s64 = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, profile=1, lanes=args.lanes, **gkw)
 
     def step(s):
         _, st, it, rel = s.solve(b_dev, tol=TOL, max_iter=2000, x=x_dev)
@@ -274,7 +278,7 @@ def main():
 
     # ---- FP32 + refinement (headline): the library's default path -- the whole refinement loop
     # as one CUDA graph with device-side decisions, no per-phase timers -- over `steps` solves
-    sd = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes,
+    sd = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes, **gkw,
                             unroll=args.unroll if args.lanes else 0)
     for _ in range(args.warmup):
         step(sd)
@@ -375,7 +379,7 @@ def main():
     # (default options: the refinement loop runs as one CUDA graph, no per-phase timing events)
     e2e_rounds, e2e_s = 0, None
     if "e2e" in legs:
-        se = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes,
+        se = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0, lanes=args.lanes, **gkw,
                                 unroll=args.unroll if args.lanes else 0)
         bh = torch.from_numpy(b).pin_memory().numpy()
         xh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
@@ -405,7 +409,7 @@ def main():
             Eg, ng = mg.num_edges, mg.n
             res = {}
             for sched in (1, 0):
-                sb = gb.Solver.from_csr(mg, profile=1, reuse_precisions=0, schedule=sched)
+                sb = gb.Solver.from_csr(mg, profile=1, reuse_precisions=0, schedule=sched, **gkw)
                 Xb, stb, itb, relb = sb.solve_batched(Bb, tol=TOL)
                 sb.profile(reset=True)
                 barrier()
@@ -458,7 +462,7 @@ def main():
             bigm = synth.block_diag(mats)
             offm = bigm.meta["offsets"]
             bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
-            sm = gb.Solver.from_csr(bigm)
+            sm = gb.Solver.from_csr(bigm, **gkw)
             xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL)  # first call autotunes the split
             sm.profile(reset=True)
             reps_m = 5  # timed batches (each one launch); the median is reported
@@ -527,7 +531,7 @@ def main():
                 return e0.elapsed_time(e1) / reps
 
             ms_fresh = timed(fwd_bwd)
-            shared = gb.Solver(mc.n, rp_t, cl_t, vals0, precision=gb.GABP_PREC_FP32_REFINE)
+            shared = gb.Solver(mc.n, rp_t, cl_t, vals0, precision=gb.GABP_PREC_FP32_REFINE, **gkw)
             ms_shared = timed(lambda: fwd_bwd(shared))
             shared.close()
             grad = {"workload": "random sparse symmetric A, n=2^22, 3 picks per row (degree ~6), U(-1,1), diagonal "
@@ -554,7 +558,7 @@ def main():
             fix = {"workload": "random sparse symmetric A, n=4096, 3 picks per row, diagonal 0.9 x row abs-sum "
                                "(SPD, rho(|R|) = 1/0.9 > 1), uniform loading Gamma = 0.25 diag(A), to 1e-10"}
             for name, kw in (("double_loop", {}), ("single_loop", {"fix_single_loop": 1, "fix_step": 0.5})):
-                sf = gb.Solver.from_csr(mf, gamma_mode=1, gamma=0.25, max_refine=2000, **kw)
+                sf = gb.Solver.from_csr(mf, gamma_mode=1, gamma=0.25, max_refine=2000, **kw, **gkw)
                 sf.solve(bf, tol=TOL, max_iter=200000)
                 barrier()
                 ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

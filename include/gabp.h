@@ -146,6 +146,11 @@ typedef struct {
                            ||b - A (x0 + d)|| <= tol ||b||, and returns x = x0 + d (x0 itself when it
                            already meets tol; x = 0 for b = 0).  Rounds, stats and messages are those of
                            the correction solve.  Default 0 */
+  int graphs;           /* 1 = rounds replayed from captured CUDA graphs (and the FP32 refinement loop run
+                           as one graph, device_loop); 0 = every kernel launched on its own, for
+                           per-kernel profilers (kernels in graphs that can set conditional handles
+                           cannot be profiled one by one).  Same kernels and results.  Default 1 */
+  int reserved;
 } gabp_options;
 
 /* Fill *o with the defaults listed above. */

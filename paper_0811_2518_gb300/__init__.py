@@ -62,6 +62,8 @@ class Options(ctypes.Structure):
         ("fix_step", ctypes.c_double),
         ("warm_start", ctypes.c_int),
         ("initial_guess", ctypes.c_int),
+        ("graphs", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 

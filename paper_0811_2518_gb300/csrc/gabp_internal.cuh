@@ -336,7 +336,7 @@ template <typename LaunchFn>
 inline gabp_status run_rounds(gabp_handle h, cudaGraphExec_t *cache, long long *cache_key, int key, LaunchFn launch,
                               int max_rounds, int phase, int round0 = 0) {
   const int K = h->opt.check_every;
-  const bool use_graph = h->stream != nullptr;
+  const bool use_graph = h->stream != nullptr && h->opt.graphs;
   // a cached graph holds K rounds of one launch shape: both are part of its key
   const long long full_key = ((long long)K << 32) | (unsigned)key;
   if (use_graph && *cache && *cache_key != full_key) {

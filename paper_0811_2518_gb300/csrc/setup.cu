@@ -310,6 +310,8 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->history = 0;
   o->warm_start = 0;
   o->initial_guess = 0;
+  o->graphs = 1;
+  o->reserved = 0;
   return GABP_OK;
 }
 
@@ -326,7 +328,7 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 || o->graphs < 0 || o->graphs > 1 ||
       (o->accel && o->variant != GABP_VARIANT_NODE))
     return GABP_ERR_INVALID;
   return GABP_OK;

@@ -1293,7 +1293,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
   const bool serial = h->opt.schedule == 1 && !gamma_diag;
-  if (h->opt.device_loop && !gamma_diag && !h->opt.profile && h->stream && !serial)
+  if (h->opt.device_loop && h->opt.graphs && !gamma_diag && !h->opt.profile && h->stream && !serial)
     return solve32_device_loop(h, B, X, tol, max_iter, iters, relres);
   // the precision state is cached per handle when no loading is applied; when it
   // has to be computed, it is either computed first (precision-only rounds) or

@@ -487,7 +487,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   }
 
   const int L = pick_lanes(h);
-  const bool use_graph = h->stream != nullptr;
+  const bool use_graph = h->stream != nullptr && h->opt.graphs;
   cudaGraphExec_t ge = nullptr;
   if (use_graph) {
     s = get_graph64(h, L, &ge);

@@ -161,3 +161,20 @@ def test_initial_guess(gb, opts):
     with pytest.raises(ValueError):
         s.solve(tb2)  # initial_guess needs x
     s.close()
+
+
+@pytest.mark.parametrize("path", ["fp64_parallel", "fp64_serial", "fp32_parallel", "fp32_serial", "fix_single_loop"])
+def test_graphs_off_same_results(gb, path):
+    """options.graphs = 0 launches every kernel on its own (for per-kernel profilers) instead of
+    replaying captured graphs: the same kernels in the same order, so bit-identical results."""
+    m = synth.grid3d(16, 1.15, 3)
+    b = torch.from_numpy(synth.rhs(m.n, 4)).cuda()
+    out = []
+    for graphs in (1, 0):
+        s = gb.Solver.from_csr(m, lanes=4, graphs=graphs, **PATHS[path])
+        x, st, it, rel = s.solve(b, tol=1e-10, max_iter=1000)
+        s.close()
+        out.append((x.cpu().numpy(), st, it, rel))
+    assert out[0][1] == out[1][1] == gb.GABP_OK
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+    assert np.array_equal(out[0][0], out[1][0])
