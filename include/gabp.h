@@ -170,8 +170,11 @@ gabp_status gabp_options_default(gabp_options *o);
  * a row without a diagonal entry or with A_ii = 0, a stored zero off the
  * diagonal, an asymmetric pattern or value (A_ij != A_ji bit for bit), or a
  * non-finite value.  The handle owns all device memory it allocates; free it
- * with gabp_destroy.  stream is a cudaStream_t (NULL = legacy default stream).
- * opt may be NULL (defaults).
+ * with gabp_destroy.  stream is a cudaStream_t; NULL (the legacy default
+ * stream) makes the handle create and own a non-blocking stream, which every
+ * call first orders after the work already queued on the legacy default stream
+ * (round graphs cannot be captured on the legacy stream).  opt may be NULL
+ * (defaults).
  */
 gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t *rowptr,
                         const int32_t *col, const double *val, int mem_space, void *stream,
@@ -187,7 +190,9 @@ gabp_status gabp_create(gabp_handle *out, int32_t n, int64_t nnz, const int32_t 
  * holds no valid matrix and every solve fails until a valid call. */
 gabp_status gabp_set_values(gabp_handle h, const double *val, int mem_space);
 
-/* Replace the handle's options (validated) / stream. */
+/* Replace the handle's options (validated) / stream.  gabp_set_stream waits
+ * for the work on the old stream; NULL switches to the handle's own stream
+ * (as gabp_create with NULL). */
 gabp_status gabp_set_options(gabp_handle h, const gabp_options *opt);
 gabp_status gabp_set_stream(gabp_handle h, void *stream);
 
