@@ -298,7 +298,10 @@ class Solver:
 
     ``rowptr``/``col``/``val`` may be numpy arrays (host) or CUDA tensors
     (int32/int32/float64).  Solves take and return CUDA float64 tensors and run
-    on ``stream`` (default: torch's current stream at construction).
+    on ``stream`` (default: torch's current stream at construction; when that is
+    the default stream, the library runs on a stream of its own, ordered after
+    the default stream's pending work, so that its rounds can replay CUDA graphs).
+    Every call returns with its results complete.
     """
 
     def __init__(self, n, rowptr, col, val, options: Options | None = None, stream=None, **opts):
