@@ -178,3 +178,33 @@ def test_graphs_off_same_results(gb, path):
     assert out[0][1] == out[1][1] == gb.GABP_OK
     assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_streams(gb):
+    """A handle on a caller's stream and one on its own stream (created with the default stream)
+    give bit-identical results; gabp_set_stream moves a handle to another stream and back to its
+    own (NULL), and inputs written on the default stream just before a call are seen by it."""
+    m = synth.random_sym(20011, 8, 1.1, 2)
+    b = torch.from_numpy(synth.rhs(m.n, 5)).cuda()
+    kw = dict(lanes=4, precision=gb.GABP_PREC_FP32_REFINE, reuse_precisions=0)  # every solve alike
+    own = gb.Solver.from_csr(m, **kw)
+    x0, st0, it0, rel0 = own.solve(b, tol=1e-10)
+    user = torch.cuda.Stream()
+    with torch.cuda.stream(user):
+        s = gb.Solver.from_csr(m, stream=user, **kw)
+        x1, st1, it1, rel1 = s.solve(b, tol=1e-10)
+    user.synchronize()
+    assert st0 == st1 == gb.GABP_OK and it0 == it1 and torch.equal(x0, x1)
+    assert gb.gabp_set_stream(s.handle, 0) == gb.GABP_OK  # back to a stream of its own
+    bb = torch.empty_like(b)
+    bb.copy_(b)  # queued on the default stream right before the solve
+    x2, st2, it2, rel2 = s.solve(bb, tol=1e-10)
+    assert st2 == gb.GABP_OK and it2 == it0 and torch.equal(x2, x0)
+    other = torch.cuda.Stream()
+    assert gb.gabp_set_stream(s.handle, other.cuda_stream) == gb.GABP_OK
+    with torch.cuda.stream(other):
+        x3, st3, it3, rel3 = s.solve(b, tol=1e-10)
+    other.synchronize()
+    assert st3 == gb.GABP_OK and torch.equal(x3, x0)
+    s.close()
+    own.close()
