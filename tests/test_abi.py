@@ -47,3 +47,56 @@ def test_library_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "orc_gabp" not in txt and "gabp_oracle" not in txt, f
+
+
+def test_options_mirror_matches_the_c_layout(tmp_path):
+    """The ctypes mirror of gabp_options has the C struct's size and every field's offset, so a
+    field added on one side only cannot shift the others (checked with the host C compiler)."""
+    import shutil
+    import subprocess
+
+    import paper_0811_2518_gb300 as gb
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+
+        pytest.skip("no host C compiler")
+    fields = [f for f, _ in gb.Options._fields_]
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "gabp.h"', "int main(void) {",
+            '  printf("size %zu\\n", sizeof(gabp_options));']
+    prog += [f'  printf("{f} %zu\\n", offsetof(gabp_options, {f}));' for f in fields]
+    prog += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.split("\n") if line)
+    assert int(out["size"]) == ctypes.sizeof(gb.Options)
+    for f in fields:
+        assert int(out[f]) == getattr(gb.Options, f).offset, f
+
+
+def test_profile_mirror_matches_the_c_layout(tmp_path):
+    import shutil
+    import subprocess
+
+    import paper_0811_2518_gb300 as gb
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+
+        pytest.skip("no host C compiler")
+    prog = ("#include <stdio.h>\n#include <stddef.h>\n#include \"gabp.h\"\nint main(void) {\n"
+            '  printf("%zu %zu %zu %zu\\n", sizeof(gabp_profile), offsetof(gabp_profile, ms),\n'
+            "         offsetof(gabp_profile, rounds), offsetof(gabp_profile, launches));\n  return 0;\n}\n")
+    c = tmp_path / "prof.c"
+    c.write_text(prog)
+    exe = tmp_path / "prof"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    size, ms, rounds, launches = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split())
+    assert size == ctypes.sizeof(gb.Profile)
+    assert (ms, rounds, launches) == (gb.Profile.ms.offset, gb.Profile.rounds.offset, gb.Profile.launches.offset)
