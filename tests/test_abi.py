@@ -100,3 +100,16 @@ def test_profile_mirror_matches_the_c_layout(tmp_path):
                                                          check=True).stdout.split())
     assert size == ctypes.sizeof(gb.Profile)
     assert (ms, rounds, launches) == (gb.Profile.ms.offset, gb.Profile.rounds.offset, gb.Profile.launches.offset)
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every ctypes signature takes as many arguments as the header's declaration."""
+    import paper_0811_2518_gb300 as gb
+
+    src = open(os.path.join(ROOT, "include", "gabp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = dict(re.findall(r"\b(gabp_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S))
+    for name, (args, _) in gb._SIGNATURES.items():
+        params = decls[name].strip()
+        n = 0 if params in ("", "void") else len(params.split(","))
+        assert n == len(args), (name, n, len(args))
