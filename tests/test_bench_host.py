@@ -59,3 +59,25 @@ def test_committed_summaries_parse():
             continue
         assert len(m.group(1)) == 64
         bench.kernel_source_sha(m.group(3), m.group(2))  # the kernel still exists there
+
+
+def test_reference_arm_line_and_budget(monkeypatch, capsys):
+    """`bench.py --impl reference` prints one JSON line with the contract's keys, and shrinks its
+    per-step sample (same generator, smaller n) when warm-up + steps rounds would overrun its budget."""
+    import json
+    import types
+
+    monkeypatch.setattr(bench, "N_NODES", 1 << 16)
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 1e-3)  # forces the smallest sample
+    args = types.SimpleNamespace(steps=3, warmup=1)
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "cpu_baseline", "e2e", "config"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["sample_n"] == 1 << 14
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert bench.run_reference(args, rank=1, world=2) == 0  # other ranks exit without work
+    assert capsys.readouterr().out == ""
