@@ -74,3 +74,24 @@ def test_non_walk_summable_4096_and_dd_mode(gb):
         x, st, it, rel = _gpu(gb, m, b, 1e-11, 50000, gamma_mode=mode, gamma=gamma)
         assert st == gb.GABP_OK
         assert _relerr(x, x0) <= 1e-9
+
+
+@pytest.mark.parametrize("mode,gamma,G", [(1, 0.25, [0.125, 0.375]), (2, 0.2, [0.5, 0.3])])
+@pytest.mark.parametrize("s", [0.25, 0.8])
+def test_two_node_tree_closed_form(gb, mode, gamma, G, s):
+    """On a 2-node tree one GaBP round solves (A + Gamma) x = h exactly, so the single loop is the
+    recurrence h^(1) = b, x^(t) = (A + Gamma)^{-1} h^(t), h^(t+1) = (1 - s) h^(t) + s (b + Gamma x^(t)).
+    Gamma is worked out by hand for A = [[0.5, -0.9], [-0.9, 1.5]]: uniform gamma 0.25 -> (0.125,
+    0.375); diagonally dominant loading max(0, sum_j |A_ij| - A_ii) + 0.2 A_ii -> (0.4 + 0.1, 0 + 0.3).
+    The GPU's iterate after t rounds must follow the recurrence."""
+    A = np.array([[0.5, -0.9], [-0.9, 1.5]])
+    b = np.array([1.0, -0.5])
+    J = A + np.diag(G)
+    m = synth.from_dense(A)
+    h = b.copy()
+    for t in range(1, 9):
+        xt = np.linalg.solve(J, h)
+        x, st, it, rel = _gpu(gb, m, b, 0.0, t, gamma_mode=mode, gamma=gamma, s=s)
+        assert it == t
+        assert np.allclose(x, xt, rtol=1e-13, atol=1e-15)
+        h = (1.0 - s) * h + s * (b + np.asarray(G) * xt)

@@ -503,3 +503,57 @@ def test_aitken_converges_to_solution():
     r = oracle.gabp_aitken(m, b, max_iter=500, tol=1e-12)
     assert r["status"] == oracle.OK
     assert np.allclose(r["x"], np.linalg.solve(oracle.to_dense(m), b), rtol=1e-9, atol=1e-11)
+
+
+# ----------------------------------------------------------------------------- single loop: closed forms
+@pytest.mark.parametrize("s", [0.25, 0.5, 0.8])
+def test_single_loop_error_ratio_without_edges(s):
+    """Chapter "Fixing convergence of GaBP", single loop, on a diagonal A (no edges: one GaBP round
+    is the exact solve x = h / (A_ii + Gamma_ii)).  With x* = b / A_ii the damped update
+    h <- (1 - s) h + s (b + Gamma x) gives, per node, e^(t+1) = (1 - s A_ii / (A_ii + Gamma_ii)) e^(t)
+    (derived by hand from the update; e^(1) = -b Gamma / (A (A + Gamma)) since h^(1) = b).  Swapping
+    s and 1 - s, or using x one round late, changes these ratios."""
+    n = 5
+    a = np.array([1.0, 2.5, 0.75, 4.0, 1.6])
+    G = np.array([0.5, 1.0, 0.25, 3.0, 0.1])
+    b = np.array([1.0, -2.0, 0.5, 3.0, -1.25])
+    m = synth.from_dense(np.diag(a))
+    r = oracle.convergence_fix_single_loop(m, b, G, s=s, tol=0.0, max_iter=8, history=True)
+    xs = b / a
+    e = [x - xs for x in r["xs"]]
+    assert np.allclose(e[0], -b * G / (a * (a + G)), rtol=1e-14, atol=0)
+    q = 1.0 - s * a / (a + G)
+    for t in range(1, 8):
+        assert np.allclose(e[t] / e[t - 1], q, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("s", [0.25, 0.8])
+def test_single_loop_two_node_tree_closed_form(s):
+    """Single loop on a 2-node tree: GaBP is exact after one round on it (diameter 1; each cavity is
+    the node's own potential, so round t's messages depend only on the potentials h^(t)), hence
+    x^(t) = (A + Gamma)^{-1} h^(t), and the chapter's update gives the linear recurrence
+    h^(1) = b, h^(t+1) = (1 - s) h^(t) + s (b + Gamma x^(t)).  The oracle's iterates must follow it
+    (dense 2x2 solves), round by round."""
+    A = np.array([[2.0, -0.9], [-0.9, 1.5]])
+    G = np.array([0.6, 0.3])
+    b = np.array([1.0, -0.5])
+    r = oracle.convergence_fix_single_loop(synth.from_dense(A), b, G, s=s, tol=0.0, max_iter=10, history=True)
+    J = A + np.diag(G)
+    h = b.copy()
+    for t in range(10):
+        x = np.linalg.solve(J, h)
+        assert np.allclose(r["xs"][t], x, rtol=1e-13, atol=1e-15)
+        h = (1.0 - s) * h + s * (b + G * x)
+
+
+def test_diagonal_loading_dd_hand_values():
+    """Diagonal loading that makes A + Gamma diagonally dominant (the chapter's DD-making loading):
+    Gamma_ii = max(0, sum_{j != i} |A_ij| - A_ii) + delta A_ii.  Values worked out by hand on a 3x3:
+    off-diagonal abs-sums (4, 1.5, 3.5), diagonal (2, 4, 1), delta 0.1 -> (2.2, 0.4, 2.6); every row
+    of A + Gamma then exceeds its off-diagonal abs-sum by at least delta A_ii."""
+    A = np.array([[2.0, -1.0, 3.0], [-1.0, 4.0, 0.5], [3.0, 0.5, 1.0]])
+    G = oracle.diagonal_loading(A, "dd", delta=0.1)
+    assert np.allclose(G, [2.2, 0.4, 2.6], rtol=1e-15, atol=1e-15)
+    off = np.abs(A).sum(axis=1) - np.abs(np.diag(A))
+    assert np.all(np.diag(A) + G - off >= 0.1 * np.diag(A) - 1e-15)
+    assert np.allclose(oracle.diagonal_loading(A, "uniform", 0.25), [0.5, 1.0, 0.25], rtol=1e-15)
