@@ -30,6 +30,10 @@ Contents and the passage each follows:
   GaBP round per outer step with the damped potential update (numpy, FP64).
 * :func:`aitken` / :func:`gabp_aitken` -- Sec. "Convergence Acceleration": Aitken's
   extrapolation of the marginal means of Algorithm 2 (numpy, FP64).
+* :func:`steffensen_step` / :func:`gabp_steffensen` -- the same section's Steffensen
+  iterations: two GaBP rounds (or serial sweeps), Aitken's extrapolation of the
+  marginal-mean vector, the extrapolated vector replacing the iterate, GaBP continuing
+  from it; parallel and serial schedules (numpy, FP64).
 * :func:`dense_gradient`  -- gradients of 0.5 ||x - x*||^2 for x = A^{-1} b,
   written from the adjoint identity (no counterpart in the paper; it pins the
   differentiable solve).
@@ -301,6 +305,116 @@ def gabp_aitken(m, b, max_iter=1000, tol=1e-12, history=False):
             status = OK
             break
     return {"x": y, "iters": t, "status": status, "xs": xs, "ys": ys}
+
+
+def steffensen_step(x0, x1, x2):
+    """Aitken's extrapolation of three consecutive marginal-mean VECTORS, as Steffensen's
+    iterations use it (Sec. "Convergence Acceleration"): one scalar step along the newest
+    difference, y = x2 - lam (x2 - x1) with lam = <x2 - x1, D> / <D, D>, D = x2 - 2 x1 + x0.
+    For x_n = x* + c q^n (any vector c, scalar q != 1) it returns x* exactly, like the
+    scalar formula; with D = 0 (nothing moves) lam = 0 and y = x2.  Returns (y, lam)."""
+    x0, x1, x2 = (np.asarray(v, dtype=np.float64) for v in (x0, x1, x2))
+    d = x2 - x1
+    D = x2 - 2.0 * x1 + x0
+    den = float(D @ D)
+    lam = float(d @ D) / den if den > 0.0 else 0.0
+    if not np.isfinite(lam):
+        lam = 0.0
+    return x2 - lam * d, lam
+
+
+def gabp_steffensen(m, b, schedule="parallel", max_iter=1000, tol=1e-12, history=False):
+    """Steffensen's iterations on GaBP (Sec. "Convergence Acceleration"), information form.
+
+    A cycle starts from a message state whose marginal means are x_n, runs two GaBP rounds
+    (Algorithm 2, parallel schedule) or two serial sweeps (nodes firing colour by colour, one
+    store updated in place, as :func:`gabp_serial`), giving x_{n+1} and x_{n+2}, and forms
+    y_n = :func:`steffensen_step` (x_n, x_{n+1}, x_{n+2}).  "y_n replaces x_n and GaBP runs
+    again": the mean messages are moved by the same scalar step, h <- h_{n+2} - lam (h_{n+2} -
+    h_{n+1}) (precision messages unchanged), which makes the marginal means of the new state
+    exactly y_n when the precisions are stationary (x is affine in h), and the next cycle starts
+    from that state.  Round t's iterate is x^(t) after the first round of a cycle and the
+    extrapolated state's marginal means after the second; the run stops at the first t with
+    ||b - A x|| <= tol ||b|| or at max_iter rounds (sweeps).  Returns dict(x, iters, status[,
+    xs: the iterate of every round, pre: x_{n+2} of every cycle before the extrapolation,
+    lams: the step of every cycle]).
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = m.n
+    rows = np.repeat(np.arange(n), np.diff(m.rowptr))
+    off = rows != m.col
+    r, c, a = rows[off], m.col[off], m.val[off]  # slot e of row r holds the message c -> r
+    diag = np.zeros(n)
+    diag[rows[~off]] = m.val[~off]
+    key = r.astype(np.int64) * n + c
+    order = np.argsort(key)
+    rev = order[np.searchsorted(key[order], c.astype(np.int64) * n + r)]
+    if schedule == "serial":
+        colour, ncol = colour_greedy(m)
+    elif schedule != "parallel":
+        raise ValueError("schedule must be 'parallel' or 'serial'")
+
+    def beliefs(P, H):
+        return (b + np.bincount(r, H, minlength=n)) / (diag + np.bincount(r, P, minlength=n))
+
+    def one_round(P, H):
+        """Round (or sweep) from state (P, H); None on a zero cavity precision."""
+        if schedule == "parallel":
+            Pt = diag + np.bincount(r, P, minlength=n)
+            Ht = b + np.bincount(r, H, minlength=n)
+            d = Pt[c] - P[rev]
+            if np.any(d == 0.0):
+                return None
+            return -a * a / d, -a * (Ht[c] - H[rev]) / d
+        P, H = P.copy(), H.copy()
+        for col in range(ncol):  # the nodes of one colour share no edge: they fire at once
+            Pt = diag + np.bincount(r, P, minlength=n)
+            Ht = b + np.bincount(r, H, minlength=n)
+            f = colour[c] == col  # messages sent by the firing nodes
+            d = Pt[c[f]] - P[rev[f]]
+            if np.any(d == 0.0):
+                return None
+            P[f] = -a[f] ** 2 / d
+            H[f] = -a[f] * (Ht[c[f]] - H[rev[f]]) / d
+        return P, H
+
+    xs, pre, lams = [], [], []
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return {"x": np.zeros(n), "iters": 0, "status": OK, "xs": xs, "pre": pre, "lams": lams}
+    P = np.zeros(len(a))
+    H = np.zeros(len(a))
+    x = beliefs(P, H)
+    xc, Hc = x, None  # the cycle's starting iterate; the state after its first round
+    status, t = NOT_CONVERGED, 0
+    for t in range(1, max_iter + 1):
+        nxt = one_round(P, H)
+        if nxt is None:
+            status = BREAKDOWN
+            break
+        Pn, Hn = nxt
+        x = beliefs(Pn, Hn)
+        if t % 2 == 1:  # first round of a cycle
+            x1, H1 = x, Hn
+            P, H = Pn, Hn
+        else:  # second round: extrapolate and move the mean messages by the same step
+            _, lam = steffensen_step(xc, x1, x)
+            lams.append(lam)
+            if history:
+                pre.append(x.copy())
+            P, H = Pn, Hn - lam * (Hn - H1)
+            x = beliefs(P, H)
+            xc = x
+        if history:
+            xs.append(x.copy())
+        if not np.all(np.isfinite(x)):
+            status = DIVERGED
+            break
+        ax = np.bincount(rows, m.val * x[m.col], minlength=n)
+        if np.linalg.norm(b - ax) <= tol * bn:
+            status = OK
+            break
+    return {"x": x, "iters": t, "status": status, "xs": xs, "pre": pre, "lams": lams}
 
 
 def convergence_fix_single_loop(m, b, Gamma, s=0.5, tol=1e-10, max_iter=100000, history=False):
