@@ -55,7 +55,8 @@ struct DevCtl {
   int hist_cap;      // FP64 rounds: entries of hist (0 = no history)
   double *hist;      // FP64 rounds: squared residual of iterate t at hist[t] (device, hist_cap entries)
   int hist_len;      // entries written
-  int pad2;
+  int lam_round;     // Steffensen: the round whose extrapolation was applied last
+  double lam;        // Steffensen: scalar step of the latest cycle (its second round's last block)
 };
 
 struct Graph {
@@ -122,6 +123,8 @@ struct WorkS {
   double2 *SM = nullptr;       // [E] FP64 messages {P, h}
   double2 *fire = nullptr;     // [n] FP64 firing aggregates
   double *sPm = nullptr;       // [n] marginal precisions of the last FP64 sweep (new order)
+  double *sh1 = nullptr;       // [E] Steffensen: mean messages after a cycle's first sweep
+  double *sx0 = nullptr, *sx1 = nullptr;  // [n] Steffensen: iterates x_n, x_{n+1} (input order)
   bool valid = false;
   int result_round = 0;
   float2 *sCF = nullptr;       // [E] frozen coefficients in serial order

@@ -171,13 +171,19 @@ struct ArgsS64 {
   double2 *fire;  // {P~, h~} firing aggregate per node (new order)
   double *x;      // iterate in the input order
   double *sPm;    // marginal precisions in the new order
+  double *sh1;    // Steffensen (nullptr otherwise): mean messages after a cycle's first sweep
+  double *sx0;    // Steffensen: the cycle's starting iterate x_n (input order)
+  double *sx1;    // Steffensen: x_{n+1} (input order)
   DevCtl *ctl;
   double *partials;
 };
 
 __global__ void ks64_init(ArgsS64 a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < a.n) a.fire[j] = make_double2(a.sad[j], a.sb[j]);  // no message yet: P~ = A_jj, h~ = b_j
+  if (j < a.n) {
+    a.fire[j] = make_double2(a.sad[j], a.sb[j]);  // no message yet: P~ = A_jj, h~ = b_j
+    if (a.sx0) a.sx0[a.oid[j]] = a.sb[j] / a.sad[j];  // x^(0)
+  }
 }
 
 // Pass c: the nodes of colour c fire (every other row updates its colour-c
@@ -300,6 +306,77 @@ __global__ void __launch_bounds__(kBlock) ks64_decide(ArgsS64 a) {
     }
     ctl->arrive = 0;
     __threadfence();
+  }
+}
+
+// Steffensen's iterations on the serial schedule (Sec. "Convergence Acceleration"):
+// sweeps pair into cycles.  After the first sweep of a cycle (t odd) its mean
+// messages and iterate are kept; after the second (t even) the last block forms
+// the scalar step lam = <d, D> / <D, D> (d = x_{n+2} - x_{n+1},
+// D = x_{n+2} - 2 x_{n+1} + x_n; 0 where nothing moves or the quotient is not finite).
+__global__ void __launch_bounds__(kBlock) ks64_steff_a(ArgsS64 a, int E) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;  // the sweep just completed
+  const int stride = gridDim.x * kBlock, g0 = blockIdx.x * kBlock + threadIdx.x;
+  if (t & 1) {
+    for (int e = g0; e < E; e += stride) a.sh1[e] = a.SM[e].y;
+    for (int i = g0; i < a.n; i += stride) a.sx1[i] = a.x[i];
+    return;
+  }
+  double sdD = 0.0, sDD = 0.0;
+  for (int i = g0; i < a.n; i += stride) {
+    const double x0 = a.sx0[i], x1 = a.sx1[i], x2 = a.x[i];
+    const double d = x2 - x1, D = d - (x1 - x0);
+    sdD = fma(d, D, sdD);
+    sDD = fma(D, D, sDD);
+  }
+  double v[2] = {sdD, sDD}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    const double lam = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+    ctl->lam = isfinite(lam) ? lam : 0.0;
+    ctl->arrive = 0;
+    __threadfence();
+  }
+}
+
+// After a cycle's second sweep: "y replaces x_n and GaBP runs again".  The mean
+// messages move by the cycle's step, h <- h - lam (h - h_{n+1}) (precisions
+// stay), and the iterate, the next cycle's x_n and the firing aggregates of the
+// colour that fires first are rebuilt from them (x = y exactly when the
+// precisions are stationary).
+template <int L>
+__global__ void __launch_bounds__(kBlock) ks64_steff_b(ArgsS64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done || ((ctl->round + 1) & 1)) return;
+  const double lam = ctl->lam;
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int j = base + sw;
+    double P = 0.0, h = 0.0;
+    if (j < a.n)
+      for (int e = a.srp[j] + sl; e < a.srp[j + 1]; e += L) {
+        const double2 m = a.SM[e];
+        const double hn = m.y - lam * (m.y - a.sh1[e]);
+        a.SM[e].y = hn;
+        P += m.x;
+        h += hn;
+      }
+    P = sub_sum<L>(P);
+    h = sub_sum<L>(h);
+    if (j < a.n && sl == 0) {
+      P += a.sad[j];
+      h += a.sb[j];
+      const double x = h / P;
+      a.x[a.oid[j]] = x;
+      a.sx0[a.oid[j]] = x;
+      if (a.scol[j] == 0) a.fire[j] = make_double2(P, h);
+    }
   }
 }
 
@@ -487,7 +564,8 @@ void free_ws(gabp_handle h) {
   cudaFree(s.colour); cudaFree(s.co); cudaFree(s.sperm); cudaFree(s.sci); cudaFree(s.srev); cudaFree(s.sav);
   cudaFree(s.oid); cudaFree(s.nid); cudaFree(s.srp); cudaFree(s.scol); cudaFree(s.sad); cudaFree(s.sb);
   cudaFree(s.SM); cudaFree(s.fire); cudaFree(s.sPm); cudaFree(s.sCF); cudaFree(s.sH); cudaFree(s.hfire);
-  cudaFree(s.srhs); cudaFree(s.sinvP); cudaFree(s.bin); cudaFree(s.xin);
+  cudaFree(s.srhs); cudaFree(s.sinvP); cudaFree(s.bin); cudaFree(s.xin); cudaFree(s.sh1); cudaFree(s.sx0);
+  cudaFree(s.sx1);
   if (h->gS64) cudaGraphExecDestroy(h->gS64);
   if (h->gS32) cudaGraphExecDestroy(h->gS32);
   h->gS64 = h->gS32 = nullptr;
@@ -652,6 +730,10 @@ static ArgsS64 args_s64(gabp_handle h, const double *b, double *x) {
   a.n = g.n; a.C = s.C; a.co = s.co; a.sci = s.sci; a.srev = s.srev; a.scol = s.scol; a.srp = s.srp; a.oid = s.oid;
   a.sav = s.sav; a.sad = s.sad; a.sb = s.sb; a.b = b; a.rowptr = g.rowptr; a.col = g.col; a.val = g.val;
   a.SM = s.SM; a.fire = s.fire; a.x = x; a.sPm = s.sPm;
+  const bool stf = h->opt.accel == 2;
+  a.sh1 = stf ? s.sh1 : nullptr;
+  a.sx0 = stf ? s.sx0 : nullptr;
+  a.sx1 = stf ? s.sx1 : nullptr;
   a.ctl = h->ctl; a.partials = h->partials;
   return a;
 }
@@ -673,6 +755,11 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
     GABP_CUDA(cudaMalloc(&s.sb, sizeof(double) * g.n));
     GABP_CUDA(cudaMalloc(&s.bin, sizeof(double) * g.n));
     GABP_CUDA(cudaMalloc(&s.xin, sizeof(double) * g.n));
+  }
+  if (h->opt.accel == 2 && !s.sh1) {  // Steffensen's iterations
+    GABP_CUDA(cudaMalloc(&s.sh1, sizeof(double) * Ea));
+    GABP_CUDA(cudaMalloc(&s.sx0, sizeof(double) * g.n));
+    GABP_CUDA(cudaMalloc(&s.sx1, sizeof(double) * g.n));
   }
   // the captured sweeps read and write only the handle's arrays: b and x are staged
   GABP_CUDA(cudaMemcpyAsync(s.bin, b, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, h->stream));
@@ -705,14 +792,20 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   }
   ks64_ctl<<<1, 1, 0, h->stream>>>(h->ctl, std::max(1, max_iter), bb, tol * tol);
   GABP_CUDA(cudaGetLastError());
-  const int key = L | (s.C << 8);
+  const bool stf = h->opt.accel == 2;
+  const int key = L | (s.C << 8) | (stf ? 1 << 30 : 0);
   gabp_status rs = GABP_OK;
   GABP_DISPATCH_L(L, {
     const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_pass<LL>));
+    const int ab = blocks_for(std::max(g.n, g.E), kBlock, resident_grid(h->num_sms, ks64_steff_a));
     rs = run_rounds(h, &h->gS64, &h->gS64_key, key, [&] {
       for (int c = 0; c < s.C; ++c)
         ks64_pass<LL><<<nb, kBlock, 0, h->stream>>>(a, c, s.cstart[c], s.cstart[c + 1] - s.cstart[c]);
       ks64_final<LL><<<nb, kBlock, 0, h->stream>>>(a);
+      if (stf) {
+        ks64_steff_a<<<ab, kBlock, 0, h->stream>>>(a, g.E);
+        ks64_steff_b<LL><<<nb, kBlock, 0, h->stream>>>(a);
+      }
       ks64_decide<LL><<<nb, kBlock, 0, h->stream>>>(a);
     }, std::max(1, max_iter), PH_FP64);
   });

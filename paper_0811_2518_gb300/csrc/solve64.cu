@@ -135,12 +135,22 @@ __device__ __forceinline__ double aitken64(double x0, double x1, double x2) {
   return x0 - d * d / D;
 }
 
+// Acceleration modes of the FP64 node round (options.accel).
+enum { ACC_NONE = 0, ACC_AITKEN = 1, ACC_STEFFENSEN = 2 };
+
 // Fused node-centric round (GABP_VARIANT_NODE): a sub-warp of L lanes per row.
-// With AIT, every node also forms y^(t) = aitken(x^(t-2), x^(t-1), x^(t)) into
-// its record's spare slot (x^(t-2) is the record being overwritten), and the
+// ACC = ACC_AITKEN: every node also forms y^(t) = aitken(x^(t-2), x^(t-1), x^(t))
+// into its record's spare slot (x^(t-2) is the record being overwritten), and the
 // fused stop rule takes the residual of y^(t-1) instead of x^(t-1).
-template <int L, bool AIT>
+// ACC = ACC_STEFFENSEN (Steffensen's iterations, Sec. "Convergence Acceleration"):
+// rounds pair into cycles (t odd: first round, t even: second).  The first round
+// keeps the cycle's starting iterate x_n in the spare slot; the second also sums
+// <d, D> and <D, D> (d = x_{n+2} - x_{n+1}, D = x_{n+2} - 2 x_{n+1} + x_n), whose
+// quotient, the scalar step lam, its last block stores for k64_steff.
+template <int L, int ACC>
 __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
+  constexpr bool AIT = ACC == ACC_AITKEN;
+  constexpr bool STF = ACC == ACC_STEFFENSEN;
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int t = ctl->round + 1;
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
   const int sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  double rr = 0.0;
+  double rr = 0.0, sdD = 0.0, sDD = 0.0;
   int bad = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int i = base + sw;
@@ -188,16 +198,96 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
       const double xt = h * rcp64(P);
       double yt = xt;
       if (AIT && t >= 2) yt = aitken64(Nout[i].x, own.x, xt);
+      if (STF) {
+        if (!(t & 1)) {  // own.x = x_{n+1}, own.pad = x_n
+          const double dd = xt - own.x, D = dd - (own.x - own.pad);
+          sdD = fma(dd, D, sdD);
+          sDD = fma(D, D, sDD);
+        }
+        yt = own.x;  // after a first round: x_n, the cycle's starting iterate
+      }
       Nout[i] = NodeRec64{P, h, xt, yt};
       const double r = bi - fma(d, AIT ? own.pad : own.x, accr);
       rr = fma(r, r, rr);
     }
+  }
+  if (STF) {
+    double v[4] = {rr, (double)bad, sdD, sDD}, tot[4];
+    const int modes[4] = {0, 0, 0, 0};
+    block_sum<4>(v);
+    if (last_block_reduce<4>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+      if (!(t & 1)) {  // the cycle's scalar step; 0 where nothing moves or the quotient is not finite
+        const double lam = tot[3] > 0.0 ? tot[2] / tot[3] : 0.0;
+        ctl->lam = isfinite(lam) ? lam : 0.0;
+      }
+      decide64(ctl, t, tot[0], tot[1]);
+    }
+    return;
   }
   double v[2] = {rr, (double)bad}, tot[2];
   const int modes[2] = {0, 0};
   block_sum<2>(v);
   if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0)
     decide64(ctl, t, tot[0], tot[1]);
+}
+
+// Steffensen's iterations, the step after a cycle's second round t: "y replaces
+// x_n and GaBP runs again".  The mean messages of round t move by the cycle's
+// scalar step, h <- h^(t) - lam (h^(t) - h^(t-1)) (the precision messages stay),
+// and every node record is rebuilt from them: h~ = b + sum h, x = h~ / P~.  With
+// stationary precisions these means are exactly y = x^(t) - lam (x^(t) - x^(t-1)).
+// Launched after every round; it acts once per even round that has not stopped
+// the run (the next round's fused residual then checks the extrapolated iterate).
+template <int L>
+__global__ void __launch_bounds__(kBlock) k64_steff(Args64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round;
+  if ((t & 1) || t < 2 || ctl->lam_round == t) return;
+  const double lam = ctl->lam;
+  const double *__restrict__ b = ctl->b;
+  double2 *__restrict__ Mt = (t & 1) ? a.M1 : a.M0;          // round t
+  const double2 *__restrict__ Mp = (t & 1) ? a.M0 : a.M1;    // round t-1
+  NodeRec64 *__restrict__ Nt = (t & 1) ? a.N1 : a.N0;
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane & (L - 1), sw = lane / L;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    double acch = 0.0;
+    if (i < a.n) {
+      const int e1 = a.rp[i + 1];
+      for (int e = a.rp[i] + sl; e < e1; e += L) {
+        const double ht = Mt[e].y;
+        const double hn = ht - lam * (ht - Mp[e].y);
+        Mt[e].y = hn;
+        acch += hn;
+      }
+    }
+    acch = sub_sum<L>(acch);
+    if (i < a.n && sl == 0) {
+      const NodeRec64 own = Nt[i];
+      const double h = b[i] + acch;
+      const double x = h * rcp64(own.P);
+      Nt[i] = NodeRec64{own.P, h, x, x};
+    }
+  }
+  // the last block to finish marks round t as extrapolated (every block has passed
+  // the guard above by then)
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    ctl->lam_round = t;
+    ctl->arrive = 0;
+    __threadfence();
+  }
 }
 
 // Edge-centric round, part 1 (GABP_VARIANT_EDGE): one thread per directed edge
@@ -370,14 +460,17 @@ static void launch_round_L(gabp_handle h, const Args64 &a) {
     const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_edge_agg<L>));
     k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a, h->g.E);
     k64_edge_agg<L><<<nb, kBlock, 0, h->stream>>>(a);
+  } else if (h->opt.accel == ACC_AITKEN) {
+    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_AITKEN>));
+    k64_node<L, ACC_AITKEN><<<nb, kBlock, 0, h->stream>>>(a);
+  } else if (h->opt.accel == ACC_STEFFENSEN) {
+    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_STEFFENSEN>));
+    k64_node<L, ACC_STEFFENSEN><<<nb, kBlock, 0, h->stream>>>(a);
+    const int sb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_steff<L>));
+    k64_steff<L><<<sb, kBlock, 0, h->stream>>>(a);
   } else {
-    if (h->opt.accel) {
-      const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, true>));
-      k64_node<L, true><<<nb, kBlock, 0, h->stream>>>(a);
-    } else {
-      const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, false>));
-      k64_node<L, false><<<nb, kBlock, 0, h->stream>>>(a);
-    }
+    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_NONE>));
+    k64_node<L, ACC_NONE><<<nb, kBlock, 0, h->stream>>>(a);
   }
 }
 
@@ -498,7 +591,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   bool done = false;
   if ((s = read_ctl(h)) != GABP_OK) return s;
   done = h->ctl_host->done;
-  const int per_round = h->opt.variant == GABP_VARIANT_EDGE ? 2 : 1;
+  const int per_round = h->opt.variant == GABP_VARIANT_EDGE || h->opt.accel == ACC_STEFFENSEN ? 2 : 1;
   h->prof.launches += 1;  // k64_init
   int prev_round = 0;
   for (int64_t batch = 0; !done && batch < max_batches; ++batch) {
@@ -532,7 +625,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     GABP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.n, h->stream));
   } else {
     k64_finalize<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, h->w64.N[c.result_round & 1], x,
-                                                                       h->opt.accel);
+                                                                       h->opt.accel == ACC_AITKEN);
     h->prof.launches += 1;
   }
   GABP_CUDA(cudaGetLastError());
