@@ -34,6 +34,11 @@ Contents and the passage each follows:
   iterations: two GaBP rounds (or serial sweeps), Aitken's extrapolation of the
   marginal-mean vector, the extrapolated vector replacing the iterate, GaBP continuing
   from it; parallel and serial schedules (numpy, FP64).
+* :func:`lsq_augmented` / :func:`gabp_lsq` / :func:`ridge_solve` -- Sec. "Extension to
+  General Linear Systems" and Chapter "Extending GaBP to support non-square matrices":
+  the regularised least-squares (MMSE) solution x = (J^T J + gamma I)^{-1} J^T y of a
+  rectangular J, read off the first k entries of the symmetric augmented system
+  [[I_k, J^T], [J, -gamma I_m]] [x; z] = [0; y], which Algorithm 2 solves.
 * :func:`dense_gradient`  -- gradients of 0.5 ||x - x*||^2 for x = A^{-1} b,
   written from the adjoint identity (no counterpart in the paper; it pins the
   differentiable solve).
@@ -469,6 +474,49 @@ def convergence_fix_single_loop(m, b, Gamma, s=0.5, tol=1e-10, max_iter=100000, 
             status = OK
             break
     return {"x": x, "iters": t, "status": status, "xs": xs}
+
+
+def lsq_augmented(J, gamma: float):
+    """The symmetric augmented matrix of a rectangular J (m x k, ``synth.RectCSR``):
+    [[I_k, J^T], [J, -gamma I_m]] (the general-linear-systems construction with the -gamma I
+    block that makes it invertible; the non-square chapter's matrix with Psi = gamma I), as a
+    full symmetric CSR with n = k + m rows: variables x first, auxiliary z after them."""
+    if not gamma > 0.0:
+        raise ValueError("gamma must be positive")
+    m, k = J.m, J.k
+    jr = np.repeat(np.arange(m), np.diff(J.rowptr))
+    rows = np.concatenate([np.arange(k), jr + k, J.col, np.arange(m) + k])
+    cols = np.concatenate([np.arange(k), J.col, jr + k, np.arange(m) + k])
+    vals = np.concatenate([np.ones(k), J.val, J.val, np.full(m, -float(gamma))])
+    n = k + m
+    key = rows.astype(np.int64) * n + cols
+    order = np.argsort(key, kind="stable")
+    counts = np.bincount(rows, minlength=n)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return SimpleNamespace(n=n, rowptr=rowptr.astype(np.int32), col=cols[order].astype(np.int32),
+                           val=vals[order], nnz=int(rowptr[-1]))
+
+
+def ridge_solve(Jd, y, gamma: float) -> np.ndarray:
+    """x = (J^T J + gamma I)^{-1} J^T y from the dense normal equations (Cholesky)."""
+    Jd = np.asarray(Jd, dtype=np.float64)
+    G = Jd.T @ Jd + gamma * np.eye(Jd.shape[1])
+    L = np.linalg.cholesky(G)
+    return np.linalg.solve(L.T, np.linalg.solve(L, Jd.T @ np.asarray(y, dtype=np.float64)))
+
+
+def gabp_lsq(J, y, gamma: float, max_iter=1000, tol=1e-12, variant="broadcast"):
+    """Regularised least squares by GaBP: Algorithm 2 (or 1) on :func:`lsq_augmented` with the
+    right-hand side [0_k; y]; x is the first k marginal means, z the remaining m.  The stop rule
+    is the augmented system's relative residual.  Returns the solver's dict plus x, z."""
+    Ja = lsq_augmented(J, gamma)
+    b = np.concatenate([np.zeros(J.k), np.asarray(y, dtype=np.float64)])
+    r = (gabp_broadcast if variant == "broadcast" else gabp_naive)(Ja, b, max_iter=max_iter, tol=tol)
+    r = dict(r)
+    r["z"] = r["x"][J.k:]
+    r["x"] = r["x"][:J.k]
+    return r
 
 
 def dense_gradient(A, b, xstar):

@@ -19,6 +19,10 @@ Workload shapes follow the paper's experiments and the benchmark configurations:
 * ``random_tree`` -- trees, on which GaBP is exact (Sec. "Convergence and Exactness").
 * ``toy3x3`` / ``nonpsd3x3`` / ``cdma_r3`` / ``cdma_r4`` / ``run_gabp_3x3`` --
   the small matrices printed in the paper's numerical examples.
+* ``random_rect`` -- a sparse rectangular matrix (``RectCSR``), the data matrix of the
+  least-squares / MMSE-detection workloads (Sec. "Extension to General Linear Systems",
+  Chapter "Extending GaBP to support non-square matrices"); stands in for a sparse
+  spreading or measurement matrix.
 """
 from __future__ import annotations
 
@@ -30,7 +34,7 @@ __all__ = [
     "CSR", "from_coo", "from_dense", "to_dense",
     "grid2d", "poisson2d", "random_sym", "grid3d", "rgg_batch", "random_tree",
     "toy3x3", "nonpsd3x3", "cdma_r3", "cdma_r4", "run_gabp_3x3",
-    "rhs", "rhs_batch", "spd_seed", "block_diag",
+    "rhs", "rhs_batch", "spd_seed", "block_diag", "RectCSR", "random_rect",
 ]
 
 
@@ -51,6 +55,53 @@ class CSR:
     def num_edges(self) -> int:
         """Directed edges = off-diagonal stored entries."""
         return self.nnz - self.n
+
+
+@dataclass
+class RectCSR:
+    """Rectangular sparse matrix (m rows, k columns) in CSR form, strictly increasing columns."""
+    m: int
+    k: int
+    rowptr: np.ndarray  # int32 [m+1]
+    col: np.ndarray     # int32 [nnz]
+    val: np.ndarray     # float64 [nnz]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.m, self.k))
+        A[np.repeat(np.arange(self.m), np.diff(self.rowptr)), self.col] = self.val
+        return A
+
+
+def random_rect(m: int, k: int, per_row: int, seed: int) -> RectCSR:
+    """m x k matrix whose every row holds ``per_row`` distinct uniformly drawn columns with
+    values N(0, 1) / sqrt(per_row) (unit expected row norm, as a normalised spreading code)."""
+    if per_row > k:
+        raise ValueError("per_row exceeds the column count")
+    rng = np.random.default_rng(seed)
+    cols = np.empty((m, per_row), dtype=np.int64)
+    # distinct columns per row: draw with replacement, redraw the rows that repeat one
+    cols[:] = rng.integers(0, k, size=(m, per_row))
+    for _ in range(1000):
+        s = np.sort(cols, axis=1)
+        bad = np.nonzero(np.any(s[:, 1:] == s[:, :-1], axis=1))[0] if per_row > 1 else np.zeros(0, np.int64)
+        if bad.size == 0:
+            break
+        cols[bad] = rng.integers(0, k, size=(bad.size, per_row))
+    else:
+        raise RuntimeError("could not draw distinct columns")
+    cols.sort(axis=1)
+    vals = rng.standard_normal((m, per_row)) / np.sqrt(per_row)
+    vals[vals == 0.0] = 1e-3  # a stored zero is not an entry
+    rowptr = np.arange(0, m * per_row + 1, per_row, dtype=np.int64)
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32")
+    return RectCSR(m, k, rowptr.astype(np.int32), cols.ravel().astype(np.int32), vals.ravel(),
+                   {"kind": "random_rect", "per_row": per_row, "seed": seed})
 
 
 def from_coo(n: int, rows, cols, vals, meta=None) -> CSR:

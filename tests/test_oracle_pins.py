@@ -644,3 +644,51 @@ def test_steffensen_serial_saves_sweeps():
         st = oracle.gabp_steffensen(m, b, "serial", max_iter=2000, tol=1e-12)
         assert plain["status"] == st["status"] == oracle.OK
         assert st["iters"] <= 0.7 * plain["iters"]
+
+
+# ----------------------------------------------------------------------------- least squares (augmented system)
+@pytest.mark.parametrize("m,k,per_row,gamma", [(300, 120, 4, 0.5), (600, 600, 6, 1.0), (200, 400, 5, 2.0)])
+def test_lsq_matches_normal_equations(m, k, per_row, gamma):
+    """Sec. "Extension to General Linear Systems" / the non-square chapter: the first k marginal
+    means of the augmented system [[I, J^T], [J, -gamma I]] [x; z] = [0; y] are the regularised
+    least-squares (MMSE) solution (J^T J + gamma I)^{-1} J^T y (dense Cholesky of the normal
+    equations), for over-, square and under-determined J; the auxiliary block is
+    z = (J x - y) / gamma (the second block row)."""
+    J = synth.random_rect(m, k, per_row, 11)
+    y = synth.rhs(m, 12)
+    r = oracle.gabp_lsq(J, y, gamma, max_iter=5000, tol=1e-13)
+    assert r["status"] == oracle.OK
+    Jd = J.dense()
+    xr = oracle.ridge_solve(Jd, y, gamma)
+    assert np.linalg.norm(r["x"] - xr) <= 1e-10 * np.linalg.norm(xr)
+    assert np.allclose(r["z"], (Jd @ r["x"] - y) / gamma, rtol=1e-9, atol=1e-11)
+
+
+def test_lsq_cdma_mmse_detector():
+    """The non-square chapter's MMSE detector x = (S^T S + Psi)^{-1} S^T y with Psi = sigma^-2 I,
+    on a dense +-1/sqrt(N) spreading matrix (N = 16 chips, 8 users), as the dense textbook
+    formula; naive and broadcast GaBP give it."""
+    rng = np.random.default_rng(3)
+    S = rng.choice([-1.0, 1.0], size=(16, 8)) / 4.0
+    y = rng.standard_normal(16)
+    psi = 0.5
+    from scipy.sparse import csr_matrix
+    c = csr_matrix(S)
+    J = synth.RectCSR(16, 8, c.indptr.astype(np.int32), c.indices.astype(np.int32), c.data.copy())
+    xr = np.linalg.solve(S.T @ S + psi * np.eye(8), S.T @ y)
+    for variant in ("naive", "broadcast"):
+        r = oracle.gabp_lsq(J, y, psi, max_iter=5000, tol=1e-13, variant=variant)
+        assert r["status"] == oracle.OK
+        assert np.allclose(r["x"], xr, rtol=1e-9, atol=1e-12)
+
+
+def test_lsq_augmented_structure():
+    """The augmented matrix is symmetric, has unit diagonal on the x block and -gamma on the z
+    block, and J (resp. J^T) as its off-diagonal blocks -- checked against the dense J."""
+    J = synth.random_rect(40, 25, 3, 4)
+    Ja = oracle.to_dense(oracle.lsq_augmented(J, 0.7))
+    Jd = J.dense()
+    assert np.array_equal(Ja, Ja.T)
+    assert np.array_equal(Ja[25:, :25], Jd) and np.array_equal(Ja[:25, 25:], Jd.T)
+    assert np.array_equal(np.diag(Ja), np.concatenate([np.ones(25), np.full(40, -0.7)]))
+    assert not np.any(Ja[:25, :25] - np.eye(25)) and not np.any(Ja[25:, 25:] + 0.7 * np.eye(40))

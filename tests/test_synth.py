@@ -70,3 +70,14 @@ def test_tree_is_tree():
     m = synth.random_tree(50, 1)
     _check_csr(m)
     assert m.num_edges == 2 * 49
+
+
+def test_random_rect_shape_and_rows():
+    J = synth.random_rect(500, 70, 6, 9)
+    assert (J.m, J.k, J.nnz) == (500, 70, 3000)
+    for r in range(J.m):
+        c = J.col[J.rowptr[r]:J.rowptr[r + 1]]
+        assert np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < J.k
+    assert np.all(J.val != 0.0) and np.all(np.isfinite(J.val))
+    J2 = synth.random_rect(500, 70, 6, 9)
+    assert np.array_equal(J.col, J2.col) and np.array_equal(J.val, J2.val)
