@@ -15,10 +15,12 @@
  *     round's messages (parallel / synchronous schedule); the serial schedule
  *     (one store updated in place, nodes firing colour by colour) is an
  *     option (Sec. "The Gaussian BP Algorithm", scheduling paragraph);
- *   - options add Aitken's method on the marginal means (Sec. "Convergence
- *     Acceleration") and the convergence fix for non-walk-summable A, as a
- *     double loop or a damped single loop (Chapter "Fixing convergence of
- *     GaBP");
+ *   - options add Aitken's method or Steffensen's iterations on the marginal
+ *     means (Sec. "Convergence Acceleration") and the convergence fix for
+ *     non-walk-summable A, as a double loop or a damped single loop (Chapter
+ *     "Fixing convergence of GaBP");
+ *   - rectangular systems: regularised least squares through the symmetric
+ *     augmented system (Sec. "Extension to General Linear Systems");
  *   - the answer is the marginal mean vector and, optionally, the marginal
  *     precisions (Algorithm 1, steps 4-5);
  *   - the messages are the solver's state: they can be exported and loaded
@@ -265,6 +267,35 @@ gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offse
  * of n int32 (nullable); *ncolours (nullable) the number of colours.  Computed
  * once per handle (on the device) and kept. */
 gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolours);
+
+/*
+ * gabp_create_lsq -- a handle for regularised least squares / MMSE estimation with a
+ * rectangular J (m x k): x = (J^T J + gamma I)^{-1} J^T y (Sec. "Extension to General
+ * Linear Systems", the -gamma I block that makes the augmented matrix invertible; Chapter
+ * "Extending GaBP to support non-square matrices", its MMSE detector with Psi = gamma I).
+ * The handle's matrix is the sparse symmetric augmented system
+ *     [[I_k, J^T], [J, -gamma I_m]]  (n = k + m rows: x first, the auxiliary z after),
+ * so no J^T J is formed and every solver path and option applies to it; GaBP on it gives
+ * x in its first k marginal means.
+ * J: CSR rowptr[m+1], col[nnz], val[nnz] (columns strictly increasing within a row, in
+ * [0, k); finite nonzero values), host (mem_space 0) or device (1) memory; device arrays
+ * are read after synchronising `stream` (when not NULL).  gamma > 0 and finite.  The
+ * augmented CSR is assembled once in host memory (an O(nnz) transpose of J) and handed to
+ * gabp_create.  Returns GABP_ERR_INVALID for bad arguments or a bad J, or when
+ * k + m + 2 nnz does not fit int32; otherwise as gabp_create.  gabp_destroy frees it.
+ */
+gabp_status gabp_create_lsq(gabp_handle *out, int32_t m, int32_t k, int64_t nnz, const int32_t *rowptr,
+                            const int32_t *col, const double *val, double gamma, int mem_space, void *stream,
+                            const gabp_options *opt);
+
+/* Solve on a gabp_create_lsq handle: y (device, m) -> x (device, k) and, when z is not
+ * NULL, the auxiliary z = (J x - y) / gamma (device, m).  The augmented right-hand side is
+ * [0_k; y]; the run is the handle's gabp_solve path (options as set), its stop rule the
+ * augmented system's relative residual ||[0; y] - A_aug [x; z]|| <= tol ||y||.
+ * iters_out / relres_out as gabp_solve.  GABP_ERR_INVALID on a handle not created by
+ * gabp_create_lsq, on host arrays, or with options.initial_guess = 1. */
+gabp_status gabp_solve_lsq(gabp_handle h, const double *y, double *x, double *z, double tol, int32_t max_iter,
+                           int32_t *iters_out, double *relres_out);
 
 /* Marginal precisions P_i = A_ii + sum_k P_ki of the last solve (Algorithm 1,
  * step 4), device array of n doubles.  Exact (= 1/(A^{-1})_ii) on trees; an

@@ -22,7 +22,8 @@ __all__ = [
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
     "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_set_messages", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
-    "Solver", "GaBPError",
+    "gabp_create_lsq", "gabp_solve_lsq",
+    "Solver", "LSQSolver", "GaBPError",
 ]
 
 GABP_OK, GABP_NOT_CONVERGED, GABP_DIVERGED, GABP_BREAKDOWN, GABP_TIMEOUT = 0, 1, 2, 3, 4
@@ -102,6 +103,10 @@ _SIGNATURES = {
     "gabp_serial_colours": ([_P, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_residual_history": ([_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_set_messages": ([_P, _P, _P], ctypes.c_int),
+    "gabp_create_lsq": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
+                         ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(Options)], ctypes.c_int),
+    "gabp_solve_lsq": ([_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -150,6 +155,26 @@ def gabp_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, mem_space, stream_ptr, opt
     st = lib.gabp_create(ctypes.byref(h), int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
                          int(mem_space), _P(stream_ptr), ctypes.byref(options) if options is not None else None)
     return st, h
+
+
+def gabp_create_lsq(m, k, nnz, rowptr_ptr, col_ptr, val_ptr, gamma, mem_space, stream_ptr, options=None):
+    """Least-squares handle for the m x k CSR J (augmented system [[I, J^T], [J, -gamma I]]);
+    returns (status, handle)."""
+    h = _P()
+    st = lib.gabp_create_lsq(ctypes.byref(h), int(m), int(k), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
+                             float(gamma), int(mem_space), _P(stream_ptr),
+                             ctypes.byref(options) if options is not None else None)
+    return st, h
+
+
+def gabp_solve_lsq(h, y_ptr, x_ptr, z_ptr, tol, max_iter):
+    """x = (J^T J + gamma I)^{-1} J^T y on a least-squares handle (device arrays; z_ptr may be None);
+    returns (status, iters, relres)."""
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.gabp_solve_lsq(h, _P(y_ptr), _P(x_ptr), _P(z_ptr) if z_ptr else None, float(tol), int(max_iter),
+                            ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
 
 
 def gabp_serial_colours(h, colour_ptr):
@@ -522,3 +547,57 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class LSQSolver(Solver):
+    """Regularised least squares x = (J^T J + gamma I)^{-1} J^T y for a rectangular sparse J
+    (m x k CSR: numpy arrays or CUDA tensors), through the symmetric augmented system
+    [[I, J^T], [J, -gamma I]] (``gabp_create_lsq``).  ``solve`` / ``solve_batched`` of the base
+    class act on the augmented system of n = k + m unknowns; ``solve_lsq`` takes y and returns x."""
+
+    def __init__(self, m, k, rowptr, col, val, gamma, options: Options | None = None, stream=None, **opts):
+        import numpy as np
+        import torch
+
+        self.m, self.k, self.gamma = int(m), int(k), float(gamma)
+        self.n = self.k + self.m
+        self.options = options if options is not None else gabp_options_default()
+        for key, v in opts.items():
+            setattr(self.options, key, v)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if isinstance(rowptr, torch.Tensor):
+            keep = [rowptr.to(self.device, torch.int32).contiguous(), col.to(self.device, torch.int32).contiguous(),
+                    val.to(self.device, torch.float64).contiguous()]
+            ptrs, mem = tuple(t.data_ptr() for t in keep), 1
+        else:
+            keep = [np.ascontiguousarray(rowptr, dtype=np.int32), np.ascontiguousarray(col, dtype=np.int32),
+                    np.ascontiguousarray(val, dtype=np.float64)]
+            ptrs, mem = tuple(a.ctypes.data for a in keep), 0
+        if keep[0].shape[0] != self.m + 1 or keep[1].shape[0] != keep[2].shape[0]:
+            raise ValueError("J must be a CSR of m rows: rowptr[m+1], col[nnz], val[nnz]")
+        self.nnz_j = int(keep[1].shape[0])
+        st, h = gabp_create_lsq(self.m, self.k, self.nnz_j, *ptrs, self.gamma, mem, self.stream.cuda_stream,
+                                self.options)
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_create_lsq")
+        self.handle = h
+
+    @classmethod
+    def from_rect(cls, J, gamma, **kw):
+        return cls(J.m, J.k, J.rowptr, J.col, J.val, gamma, **kw)
+
+    def solve_lsq(self, y, tol=1e-12, max_iter=1000, want_z=False, check=True):
+        """x = (J^T J + gamma I)^{-1} J^T y.  Returns (x, z or None, status, iters, relres)."""
+        import torch
+
+        y = y.to(self.device, torch.float64).contiguous()
+        if y.numel() != self.m:
+            raise ValueError(f"y has {y.numel()} entries, J {self.m} rows")
+        x = torch.empty(self.k, dtype=torch.float64, device=self.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=self.device) if want_z else None
+        st, it, rel = gabp_solve_lsq(self.handle, y.data_ptr(), x.data_ptr(), z.data_ptr() if want_z else None,
+                                     tol, max_iter)
+        if check and st < 0:
+            raise GaBPError(st, "gabp_solve_lsq")
+        return x, z, st, it, rel

@@ -7,7 +7,7 @@
 
 using namespace gabp;
 
-namespace {
+namespace gabp {
 
 bool is_device_ptr(const void *p) {
   cudaPointerAttributes at;
@@ -75,7 +75,7 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
   return s;
 }
 
-}  // namespace
+}  // namespace gabp
 
 extern "C" gabp_status gabp_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                                   int32_t *iters_out, double *relres_out) {

@@ -218,6 +218,9 @@ struct gabp_handle_s {
   bool values_ok = true;            // false after a rejected gabp_set_values
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
+  // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
+  int lsq_m = 0, lsq_k = 0;         // 0: not a least-squares handle
+  double *lsq_b = nullptr, *lsq_x = nullptr;  // [k + m] augmented right-hand side and solution
 };
 namespace gabp {
 // Orders the handle's own stream after the work the caller queued on the legacy
@@ -235,6 +238,11 @@ namespace gabp {
 
 // error plumbing ---------------------------------------------------------------
 void set_last_error(const std::string &s);
+// api.cu: pointer kind test (allocates nothing) and the single-RHS dispatcher of gabp_solve
+bool is_device_ptr(const void *p);
+bool values_usable(gabp_handle_s *h);
+gabp_status solve_dispatch(gabp_handle_s *h, const double *b, double *x, double tol, int32_t max_iter,
+                           int32_t *iters_out, double *relres_out);
 gabp_status cuda_fail(cudaError_t e, const char *what);
 
 #define GABP_CUDA(call)                                     \

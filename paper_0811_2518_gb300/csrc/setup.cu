@@ -209,6 +209,8 @@ static gabp_status destroy_impl(gabp_handle h) {
   if (h->caller_ev) cudaEventDestroy(h->caller_ev);
   cudaFree(h->ig_buf);
   cudaFree(h->ctl_tune);
+  cudaFree(h->lsq_b);
+  cudaFree(h->lsq_x);
   if (h->prof.e0) cudaEventDestroy(h->prof.e0);
   if (h->prof.e1) cudaEventDestroy(h->prof.e1);
   cudaSetDevice(cur);
