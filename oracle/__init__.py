@@ -58,19 +58,33 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gabp_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libgabp_oracle.so")
+_OMP_PATH = os.path.join(_HERE, "_build", "libgabp_oracle_omp.so")
 _lib = None
+_omp = None
 _lock = threading.Lock()
 
 OK, NOT_CONVERGED, DIVERGED, BREAKDOWN, INVALID = 0, 1, 2, 3, -1
 
 
+def _compile(path, extra, force):
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        # ISO C mode: no contraction of a * b + c into FMA, so x86-64 and aarch64 hosts give the
+        # same results
+        subprocess.run(["gcc", "-O3", "-std=c99", *extra, "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, path)
+    return path
+
+
 def build(force: bool = False) -> str:
-    """Compile the C oracle with the host gcc (plain -O2, portable flags)."""
+    """Compile the C oracle with the host gcc (-O3, portable flags, one thread) and, where gcc
+    has OpenMP, the same file built for all host cores (used only to time the host baseline)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _LIB_PATH)
+    _compile(_LIB_PATH, [], force)
+    try:
+        _compile(_OMP_PATH, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        pass
     return _LIB_PATH
 
 
@@ -79,18 +93,65 @@ def _load():
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB_PATH)
-            lib.orc_colour_greedy.restype = ctypes.c_int
-            lib.orc_colour_greedy.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            for name in ("orc_gabp_naive", "orc_gabp_broadcast", "orc_gabp_serial"):
-                f = getattr(lib, name)
-                f.restype = ctypes.c_int
-                f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                              ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                              ctypes.c_void_p, ctypes.c_void_p]
-            _lib = lib
+            _lib = _bind(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def _bind(lib):
+    lib.orc_colour_greedy.restype = ctypes.c_int
+    lib.orc_colour_greedy.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    for name in ("orc_gabp_naive", "orc_gabp_broadcast", "orc_gabp_serial", "orc_gabp_broadcast_unchecked"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                      ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_threads.restype = ctypes.c_int
+    lib.orc_threads.argtypes = []
+    return lib
+
+
+def _load_omp():
+    """The OpenMP build of the oracle, or None where gcc had no OpenMP."""
+    global _omp
+    _load()
+    with _lock:
+        if _omp is None and os.path.exists(_OMP_PATH):
+            _omp = _bind(ctypes.CDLL(_OMP_PATH))
+    return _omp
+
+
+def host_threads():
+    """Threads the all-cores build runs with (None when it was not built)."""
+    lib = _load_omp()
+    return lib.orc_threads() if lib is not None else None
+
+
+def broadcast_timed(m, b, rounds, threads=False, checked=False, tol=0.0):
+    """Timing entry of the host baseline: ``rounds`` synchronous rounds of Algorithm 2 (stops
+    early only when tol > 0 is met), on one thread or, with ``threads``, on all host cores (the
+    OpenMP build of the same file).  Without ``checked`` the input checks are skipped (run a
+    checked call first).  Returns (result dict, seconds spent in the call)."""
+    import time
+
+    lib = _load_omp() if threads else _load()
+    if lib is None:
+        raise RuntimeError("the OpenMP build of the oracle is not available")
+    rowptr = np.ascontiguousarray(m.rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(m.col, dtype=np.int32)
+    val = np.ascontiguousarray(m.val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(m.n)
+    P = np.zeros(m.n)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    fn = lib.orc_gabp_broadcast if checked else lib.orc_gabp_broadcast_unchecked
+    t0 = time.perf_counter()
+    rc = fn(m.n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), int(rounds), float(tol), 0, _ptr(x), _ptr(P),
+            ctypes.byref(it), ctypes.byref(rel), None, None)
+    dt = time.perf_counter() - t0
+    return {"status": rc, "x": x, "P": P, "iters": it.value, "relres": rel.value}, dt
 
 
 def _ptr(a):

@@ -51,10 +51,20 @@
  * (a non-finite value appeared), 3 breakdown (a cavity precision P_{i\j} or a
  * marginal precision P_i is exactly zero; the paper's Matlab listing asserts
  * the same), -1 invalid input.
+ *
+ * Threads: the same file is also built with OpenMP (for the host-cores timing
+ * baseline).  The row loops of the parallel schedule then run on all cores:
+ * every row writes only its own outputs and the slots that receive its
+ * messages, so the arithmetic per message is unchanged; only the order of the
+ * residual and norm sums differs.  The serial schedule stays sequential.
+ * Without OpenMP the pragmas are ignored.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_NOT_CONVERGED 1
@@ -79,24 +89,28 @@ static double diag_entry(const int *rowptr, const int *col, const double *val, i
  * no stored zero off the diagonal. */
 static int check_input(int n, const int *rowptr, const int *col, const double *val) {
   if (n < 0) return ORC_INVALID;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(| : bad)
   for (int i = 0; i < n; ++i) {
-    if (diag_entry(rowptr, col, val, i) == 0.0) return ORC_INVALID;
-    for (long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+    if (diag_entry(rowptr, col, val, i) == 0.0) bad = 1;
+    for (long p = rowptr[i]; p < rowptr[i + 1] && !bad; ++p) {
       int k = col[p];
-      if (k < 0 || k >= n) return ORC_INVALID;
+      if (k < 0 || k >= n) { bad = 1; break; }
       if (k == i) continue;
-      if (val[p] == 0.0) return ORC_INVALID;
+      if (val[p] == 0.0) { bad = 1; break; }
       long q = slot_of(rowptr, col, k, i);
-      if (q < 0 || val[q] != val[p]) return ORC_INVALID;
+      if (q < 0 || val[q] != val[p]) bad = 1;
     }
   }
-  return ORC_OK;
+  return bad ? ORC_INVALID : ORC_OK;
 }
 
 /* Alg. 1 step 4: marginal precision P_i = P_ii + sum_k P_ki and marginal mean
  * mu_i = (P_ii mu_ii + sum_k P_ki mu_ki) / P_i over all k in N(i). */
 static int infer(int n, const int *rowptr, const int *col, const double *val, const double *b,
                  const double *Pm, const double *Mm, double *x, double *Pi) {
+  int broken = 0;
+#pragma omp parallel for schedule(static) reduction(| : broken)
   for (int i = 0; i < n; ++i) {
     double Pii = diag_entry(rowptr, col, val, i);
     double muii = b[i] / Pii;
@@ -106,17 +120,21 @@ static int infer(int n, const int *rowptr, const int *col, const double *val, co
       P += Pm[p];
       num += Pm[p] * Mm[p];
     }
-    if (P == 0.0) return ORC_BREAKDOWN;
+    if (P == 0.0) {
+      broken = 1;
+      continue;
+    }
     Pi[i] = P;
     x[i] = num / P;
   }
-  return ORC_OK;
+  return broken ? ORC_BREAKDOWN : ORC_OK;
 }
 
 /* ||b - A x||_2 and ||b||_2 over the full matrix */
 static void residual(int n, const int *rowptr, const int *col, const double *val, const double *b,
                      const double *x, double *rnorm, double *bnorm) {
   double rr = 0.0, bb = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : rr, bb)
   for (int i = 0; i < n; ++i) {
     double ax = 0.0;
     for (long p = rowptr[i]; p < rowptr[i + 1]; ++p) ax += val[p] * x[col[p]];
@@ -129,15 +147,19 @@ static void residual(int n, const int *rowptr, const int *col, const double *val
 }
 
 static int all_finite(long m, const double *a) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (long p = 0; p < m; ++p)
-    if (!isfinite(a[p])) return 0;
-  return 1;
+    if (!isfinite(a[p])) bad = 1;
+  return !bad;
 }
 
 /* One synchronous round of Algorithm 1: from the round t-1 store (Po, Mo)
  * compute every message i -> j into the round t store (Pn, Mn). */
 static int round_naive(int n, const int *rowptr, const int *col, const double *val, const double *b,
                        const double *Po, const double *Mo, double *Pn, double *Mn) {
+  int broken = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : broken)
   for (int i = 0; i < n; ++i) {
     double Pii = diag_entry(rowptr, col, val, i); /* P_ii = A_ii */
     double muii = b[i] / Pii;                       /* mu_ii = b_i / A_ii */
@@ -153,14 +175,17 @@ static int round_naive(int n, const int *rowptr, const int *col, const double *v
         Pcav += Po[p];
         hcav += Po[p] * Mo[p];
       }
-      if (Pcav == 0.0) return ORC_BREAKDOWN;
+      if (Pcav == 0.0) {
+        broken = 1;
+        continue;
+      }
       double Aij = val[q];
       long dst = slot_of(rowptr, col, j, i); /* row j's slot that receives i -> j */
       Pn[dst] = -Aij * Aij / Pcav;           /* Alg. 1: P_ij = -A_ij^2 / P_{i\j} */
       Mn[dst] = hcav / Aij;                  /* Alg. 1: mu_ij = P_{i\j} mu_{i\j} / A_ij */
     }
   }
-  return ORC_OK;
+  return broken ? ORC_BREAKDOWN : ORC_OK;
 }
 
 /* One synchronous round of Algorithm 2: aggregates first, then each message
@@ -168,6 +193,8 @@ static int round_naive(int n, const int *rowptr, const int *col, const double *v
 static int round_broadcast(int n, const int *rowptr, const int *col, const double *val, const double *b,
                            const double *Po, const double *Mo, double *Pn, double *Mn,
                            double *Ptil, double *Mtil) {
+  int broken = 0;
+#pragma omp parallel for schedule(static) reduction(| : broken)
   for (int i = 0; i < n; ++i) {
     double Pii = diag_entry(rowptr, col, val, i);
     double muii = b[i] / Pii;
@@ -177,24 +204,29 @@ static int round_broadcast(int n, const int *rowptr, const int *col, const doubl
       P += Po[p];
       num += Po[p] * Mo[p];
     }
-    if (P == 0.0) return ORC_BREAKDOWN; /* mu~_i = P~_i^{-1}(...) needs P~_i != 0 */
+    if (P == 0.0) broken = 1; /* mu~_i = P~_i^{-1}(...) needs P~_i != 0 */
     Ptil[i] = P;
     Mtil[i] = num / P;
   }
+  if (broken) return ORC_BREAKDOWN;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : broken)
   for (int i = 0; i < n; ++i) {
     for (long q = rowptr[i]; q < rowptr[i + 1]; ++q) {
       int j = col[q];
       if (j == i) continue;
       double Pji = Po[q], muji = Mo[q]; /* message j -> i lives in row i, slot q */
       double Pcav = Ptil[i] - Pji;      /* P_{i\j} = P~_i - P_ji */
-      if (Pcav == 0.0) return ORC_BREAKDOWN;
+      if (Pcav == 0.0) {
+        broken = 1;
+        continue;
+      }
       double Aij = val[q];
       long dst = slot_of(rowptr, col, j, i);
       Pn[dst] = -Aij * Aij / Pcav;                        /* Alg. 2 */
       Mn[dst] = (Ptil[i] * Mtil[i] - Pji * muji) / Aij;   /* Alg. 2 */
     }
   }
-  return ORC_OK;
+  return broken ? ORC_BREAKDOWN : ORC_OK;
 }
 
 /* Greedy colouring in index order; returns the number of colours. */
@@ -249,8 +281,8 @@ static int sweep_serial(int n, const int *rowptr, const int *col, const double *
 
 static int run(int variant, int n, const int *rowptr, const int *col, const double *val, const double *b,
                int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
-               double *relres, double *Pmsg, double *Mmsg) {
-  int rc = check_input(n, rowptr, col, val);
+               double *relres, double *Pmsg, double *Mmsg, int checked) {
+  int rc = checked ? check_input(n, rowptr, col, val) : ORC_OK;
   if (rc != ORC_OK) return rc;
   long nnz = rowptr[n];
   int *colour = NULL, ncol = 0;
@@ -291,6 +323,7 @@ static int run(int variant, int n, const int *rowptr, const int *col, const doub
     }
     if (r != ORC_OK) { rc = r; *iters = t; break; }
     double maxchange = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : maxchange)
     for (long p = 0; p < nnz; ++p) {
       double dP = fabs(Pn[p] - Po[p]), dM = fabs(Mn[p] - Mo[p]);
       if (dP > maxchange) maxchange = dP;
@@ -321,19 +354,41 @@ int orc_gabp_naive(int n, const int *rowptr, const int *col, const double *val, 
                    int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
                    double *relres, double *Pmsg, double *Mmsg) {
   *relres = NAN;
-  return run(0, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg);
+  return run(0, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg, 1);
 }
 
 int orc_gabp_broadcast(int n, const int *rowptr, const int *col, const double *val, const double *b,
                        int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
                        double *relres, double *Pmsg, double *Mmsg) {
   *relres = NAN;
-  return run(1, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg);
+  return run(1, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg, 1);
+}
+
+/* As orc_gabp_broadcast without the input checks (the caller has checked the matrix with a
+ * checked call before): the timing baseline times the rounds alone. */
+int orc_gabp_broadcast_unchecked(int n, const int *rowptr, const int *col, const double *val, const double *b,
+                                 int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
+                                 double *relres, double *Pmsg, double *Mmsg) {
+  *relres = NAN;
+  return run(1, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg, 0);
+}
+
+/* Threads the OpenMP build uses (1 without OpenMP). */
+int orc_threads(void) {
+#ifdef _OPENMP
+  int t = 1;
+#pragma omp parallel
+#pragma omp single
+  t = omp_get_num_threads();
+  return t;
+#else
+  return 1;
+#endif
 }
 
 int orc_gabp_serial(int n, const int *rowptr, const int *col, const double *val, const double *b,
                     int max_iter, double tol, int stop_rule, double *x, double *Pi, int *iters,
                     double *relres, double *Pmsg, double *Mmsg) {
   *relres = NAN;
-  return run(2, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg);
+  return run(2, n, rowptr, col, val, b, max_iter, tol, stop_rule, x, Pi, iters, relres, Pmsg, Mmsg, 1);
 }
