@@ -158,60 +158,101 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_baseline_sample(m, b, rounds=5, what="the full n=2^20 matrix"):
-    """The FP64 oracle (Algorithm 2, plain C, one thread) on a bounded sample:
-    `rounds` synchronous rounds over the matrix `m`."""
+def oracle_threads():
+    """Threads of the all-cores oracle build (None when gcc had no OpenMP)."""
     import oracle
 
-    t0 = time.perf_counter()
-    oracle.gabp_broadcast(m, b, max_iter=rounds, tol=0.0)
-    dt = time.perf_counter() - t0
-    return {"value": m.num_edges * rounds / dt, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rounds} rounds of the FP64 broadcast oracle over {what} "
-                      f"({m.num_edges} directed edges), input checks included, {dt:.1f} s"}
+    return oracle.host_threads()
+
+
+def host_cpu():
+    """CPU model and core count of the host the oracle runs on."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and ":" in line:
+                model = (model + " / " if model else "") + line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
+
+
+def cpu_baseline_sample(m, b, rounds=5, what="the full n=2^20 matrix", single_rounds=2):
+    """The FP64 oracle (Algorithm 2, plain C) on a bounded sample: `rounds` synchronous rounds over
+    the matrix `m` on all host cores (the OpenMP build of the same file), and `single_rounds` on one
+    core; the input checks run once before, outside the timed rounds."""
+    import oracle
+
+    oracle.gabp_broadcast(m, b, max_iter=0, tol=0.0)  # input checks (and the build)
+    threads = oracle.host_threads()
+    out = {"unit": "edge-updates/s", "kind": "oracle", "host": host_cpu()}
+    _, dt1 = oracle.broadcast_timed(m, b, single_rounds, threads=False)
+    single = {"value": m.num_edges * single_rounds / dt1, "cores": 1,
+              "sample": f"{single_rounds} rounds over {what} ({m.num_edges} directed edges), {dt1:.1f} s"}
+    if threads:
+        _, dt = oracle.broadcast_timed(m, b, rounds, threads=True)
+        out.update({"value": m.num_edges * rounds / dt, "cores": threads,
+                    "sample": f"{rounds} rounds of the FP64 broadcast oracle over {what} ({m.num_edges} directed "
+                              f"edges) on {threads} threads, input checks outside the timed rounds, {dt:.1f} s",
+                    "single_core": single})
+    else:
+        out.update(single)
+        out["sample"] = "one core (no OpenMP build): " + single["sample"]
+    return out
 
 
 REFERENCE_BUDGET_S = 150.0  # the whole --impl reference run (warm-up + timed steps)
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm: every step is one synchronous round of the FP64 oracle over
-    a sample of the benchmark workload -- the full n = 2^20 matrix when (warmup + steps) such rounds
-    fit the time budget, else a smaller matrix of the same family (same picks, values and diagonal
-    rule, n a power of two) sized so that the whole run does."""
+    """The oracle as the reference arm: every step is one synchronous round of the FP64 oracle
+    (Algorithm 2, plain C, the OpenMP build on all host cores) over a sample of the benchmark
+    workload -- the full n = 2^20 matrix when (warmup + steps) such rounds fit the time budget, else
+    a smaller matrix of the same family (same picks, values and diagonal rule, n a power of two)
+    sized so that the whole run does.  The input checks run once, outside the steps."""
     if rank != 0:
         return 0
+    import oracle
+
     t_all = time.perf_counter()
     m = synth.random_sym(N_NODES, PICKS, DIAG, SEED)
     b = synth.rhs(m.n, SEED)
     total = args.warmup + args.steps
-    first = cpu_baseline_sample(m, b, 1)  # the first warm-up step, also the size probe
-    t_round = m.num_edges / first["value"]
+    oracle.gabp_broadcast(m, b, max_iter=0, tol=0.0)  # input checks once (and the build)
+    threads = oracle.host_threads()
+    par = threads is not None
+    _, t_round = oracle.broadcast_timed(m, b, 1, threads=par)  # the first warm-up step, also the size probe
     n_s, what = m.n, "the full n=2^20 matrix"
     if total * t_round > REFERENCE_BUDGET_S:
-        n_s = m.n
         while n_s > (1 << 14) and total * t_round * n_s / m.n > REFERENCE_BUDGET_S:
             n_s //= 2
         m = synth.random_sym(n_s, PICKS, DIAG, SEED)
         b = synth.rhs(m.n, SEED)
+        oracle.gabp_broadcast(m, b, max_iter=0, tol=0.0)
         what = f"random_sym(n={n_s}) of the same family"
-    vals, last = [], first
-    for s in range(1, total):
-        last = cpu_baseline_sample(m, b, 1, what)
-        if s >= args.warmup:
-            vals.append(last["value"])
+    vals = []
+    for st in range(1, total):
+        _, dt = oracle.broadcast_timed(m, b, 1, threads=par)
+        if st >= args.warmup:
+            vals.append(m.num_edges / dt)
     if not vals:  # steps = 0 or only the probe ran
-        vals = [last["value"]]
+        vals = [m.num_edges / t_round]
     v = float(np.mean(vals))
     ms = m.num_edges / v * 1e3
+    cores = threads if par else 1
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "edge-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N_NODES, "sample_n": m.n, "sample_edges": m.num_edges,
                        "sample_per_step": f"1 oracle round over {what}"},
-            "cpu_baseline": {"value": v, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"1 round of the FP64 broadcast oracle per step over {what}, "
-                                       f"input checks included"},
+            "cpu_baseline": {"value": v, "unit": "edge-updates/s", "cores": cores, "kind": "oracle",
+                             "host": host_cpu(),
+                             "sample": f"1 round of the FP64 broadcast oracle per step over {what} on {cores} "
+                                       f"thread(s), input checks once before the steps"},
             "e2e": {"value": v, "unit": "edge-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
@@ -236,7 +277,7 @@ def main():
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
     ap.add_argument("--multi-systems", type=int, default=512,
                     help="number of random geometric graphs of the independent-systems leg (512 = the workload)")
-    ap.add_argument("--legs", default="fp32,fp64,e2e,batched,multi,grad,fix",
+    ap.add_argument("--legs", default="fp32,fp64,e2e,oracle,edge,c1,lsq,batched,multi,grad,fix",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
     gkw = {"graphs": 0} if args.no_graphs else {}  # solver options of every handle below
@@ -298,6 +339,7 @@ def main():
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    x_fp32 = x_dev.cpu().numpy()  # the headline's answer, compared with the oracle below
     ms_local = ev0.elapsed_time(ev1)
     launches_timed = sd.profile(reset=True)["launches"]
     sd.close()
@@ -318,10 +360,14 @@ def main():
     peak, peak_kind = _peaks()
     ph = max(("mean32", "prec32"), key=lambda k: prof["ms"][k])
     n = m.n
-    # algorithmic bytes per launch: mean round 20 B/slot (c_in,c_out 8, col 4, h read 4, h write 4)
-    # + 24 B/node; joint round (the "prec32" phase of a solve with overlap_precision) 28 B/slot (A 4,
-    # col 4, P read 4, previous-round P 4, h read 4, P and h writes 8) + 36 B/node
-    bytes_launch = (20 * E + 24 * n) if ph == "mean32" else (28 * E + 36 * n)
+    # algorithmic bytes per launch (what the method itself must move per round, node arrays taken as
+    # L2-resident): FP32 mean round at one right-hand side 16 B per directed edge (coefficient 4, sender
+    # index 4, h read 4, h write 4) + 8 B per node; FP32 full round (precision and mean messages, the
+    # "prec32" phase of a solve with joint rounds) 24 B per edge (A 4, sender 4, (P, h) read 8, (P, h)
+    # write 8) + 12 B per node.  The implementation's own bytes (recompute form: both coefficients,
+    # previous-round chains, node rings) are reported beside them.
+    bytes_launch = (16 * E + 8 * n) if ph == "mean32" else (24 * E + 12 * n)
+    impl_bytes = (20 * E + 24 * n) if ph == "mean32" else (28 * E + 36 * n)
     dur_ms = prof["ms"][ph] / max(prof["rounds"][ph], 1)
     achieved = bytes_launch / (dur_ms / 1e3) / 1e9
     kname = "k32_mean" if ph == "mean32" else "k32_joint"
@@ -357,7 +403,7 @@ def main():
                   "mean_round_vs_gather_only": (dur_ms / gms) if ph == "mean32" else None}
         del src, idx, out
 
-    ms64, r64, k64, p64 = None, 0, 1, {"ms": {"fp64": 0.0}}
+    ms64, r64, k64, p64, x_fp64 = None, 0, 1, {"ms": {"fp64": 0.0}}, None
     # ---- plain FP64 GaBP on the same system (time to 1e-10)
     for _ in range(max(1, args.warmup) if "fp64" in legs else 0):
         step(s64)
@@ -374,6 +420,7 @@ def main():
         barrier()
         ms64 = e0.elapsed_time(e1) / k64
         p64 = s64.profile(reset=True)
+        x_fp64 = x_dev.cpu().numpy()
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     # (default options: the refinement loop runs as one CUDA graph, no per-phase timing events)
@@ -421,11 +468,32 @@ def main():
                 res[sched] = (eb0.elapsed_time(eb1), sb.profile(reset=True), sb.stats(), stb, itb, float(np.max(relb)),
                               sb.serial_colours()[1] if sched else 1)
                 sb.close()
+            # plain FP64 GaBP on one right-hand side of the same grid (time to 1e-10), both schedules: the
+            # batched solve is compared with 64 x that
+            fp64_one = {}
+            for sched in (0, 1):
+                s1 = gb.Solver.from_csr(mg, precision=gb.GABP_PREC_FP64, schedule=sched, **gkw)
+                b1 = Bb[0].contiguous()
+                x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000)
+                barrier()
+                e10, e11 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e10.record()
+                x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000, x=x1)
+                e11.record()
+                barrier()
+                fp64_one["serial" if sched else "parallel"] = {"ms_one_rhs": e10.elapsed_time(e11), "rounds": int(it1),
+                                                               "status": int(st1), "relres": rel1,
+                                                               "ms_x64": 64 * e10.elapsed_time(e11)}
+                s1.close()
+                del x1
             msb, pb, stats_b, stb, itb, maxrel, ncol = res[1]
             mean_ms = pb["ms"]["mean32"] / max(pb["rounds"]["mean32"], 1)  # one sweep (all colour passes)
             # per sweep: every slot once (R messages read + written, coefficient pair, sender) and every row once
             # (R firing aggregates read + written, R right-hand sides, segment bounds / colour / row pointer)
             bytes_b = Eg * (8 * Rb + 12) + ng * (12 * Rb + 20)
+            # the method's own bytes per sweep: per edge R mean messages read and written (8 R) and the frozen
+            # coefficient with the reverse index (8), per node the R aggregates (8 R)
+            alg_b = Eg * (8 * Rb + 8) + 8 * Rb * ng
             if args.batched_grid == 128:  # measured at the full size
                 traffic_b = _profiled_traffic("kbs_pass_grid3d_128_64rhs_dram.md",
                                               "paper_0811_2518_gb300/csrc/batched.cu", "kbs_pass")
@@ -443,12 +511,18 @@ def main():
                        "ms_per_rhs": msb / Rb,
                        "parallel_schedule": {"ms_per_solve": res[0][0], "inner_rounds": res[0][4],
                                              "max_relres": res[0][5]},
+                       "fp64_plain_one_rhs": fp64_one,
+                       "batched_vs_64_fp64": {k: v["ms_x64"] / msb for k, v in fp64_one.items()},
                        "roofline": {"bound": "hbm", "kernel": "kbs_pass (one sweep = all colour passes)",
-                                    "achieved": bytes_b / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                                    "frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak,
+                                    "achieved": alg_b / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                    "frac": alg_b / (mean_ms / 1e3) / 1e9 / peak,
+                                    "algorithmic_bytes_per_sweep": alg_b,
+                                    "algorithmic_bytes_rule": "E (8 R + 8) + 8 R n per sweep, R = 64",
                                     "traffic": traffic_b,
+                                    "traffic_over_algorithmic": None if traffic_b is None else traffic_b / alg_b,
                                     "traffic_note": traffic_note_b,
-                                    "bytes_per_sweep": bytes_b, "sweep_ms": mean_ms}}
+                                    "impl_bytes_per_sweep": bytes_b,
+                                    "impl_frac": bytes_b / (mean_ms / 1e3) / 1e9 / peak, "sweep_ms": mean_ms}}
         except Exception as exc:  # one GPU: keep the headline line, record the failed leg
             if world > 1:
                 raise
@@ -479,6 +553,26 @@ def main():
             pm = sm.profile(reset=True)
             stm_ = sm.stats()
             tuned_m = sm.tuned()
+            # plain FP64 GaBP on every system by itself (a handle per system, created before the timing):
+            # the sum of the 512 solve times, each to its own 1e-10
+            hs = [gb.Solver.from_csr(ms_, precision=gb.GABP_PREC_FP64, **gkw) for ms_ in mats]
+            bms = [bm[int(offm[i]):int(offm[i + 1])].contiguous() for i in range(len(mats))]
+            xms = [torch.empty_like(v) for v in bms]
+            for h_, bv, xv in zip(hs, bms, xms):
+                h_.solve(bv, tol=TOL, max_iter=20000, x=xv)
+            barrier()
+            ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ep0.record()
+            rounds_p = 0
+            for h_, bv, xv in zip(hs, bms, xms):
+                _, stp, itp, _ = h_.solve(bv, tol=TOL, max_iter=20000, x=xv)
+                rounds_p += int(itp)
+            ep1.record()
+            barrier()
+            ms_per_sys = ep0.elapsed_time(ep1)
+            for h_ in hs:
+                h_.close()
+            del hs, bms, xms
             multi = {"workload": f"{args.multi_systems} random geometric graphs, sizes ~ n^-2 on [1024, 65536], "
                                  "radius for degree 6, "
                                  "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
@@ -489,7 +583,10 @@ def main():
                      "edge_updates": stm_["edge_updates"],
                      "edge_updates_per_s": stm_["edge_updates"] / (msm / 1e3),
                      "rounds_per_system": {"min": int(itsm.min()), "median": int(np.median(itsm)), "max": int(itsm.max())},
-                     "max_relres": float(relm.max()), "launches_per_batch": 1}
+                     "max_relres": float(relm.max()), "launches_per_batch": 1,
+                     "fp64_plain_per_system": {"ms_all_systems": ms_per_sys, "rounds_total": rounds_p,
+                                               "how": "one FP64 handle per system, solved one after another"},
+                     "batch_vs_fp64_per_system": ms_per_sys / msm}
             sm.close()
         except Exception as exc:  # one GPU: keep the headline line, record the failed leg
             if world > 1:
@@ -574,10 +671,132 @@ def main():
                 raise
             fix = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- the oracle's FP64 solution of the benchmark system (all host cores, to 1e-13): the error of
+    # every result of this system against it
+    errors = None
+    if "oracle" in legs and rank == 0 and world == 1:
+        import oracle
+
+        ro, dto = oracle.broadcast_timed(m, b, 200, threads=oracle.host_threads() is not None, tol=1e-13)
+        xo = ro["x"]
+
+        def err(x):
+            return None if x is None else {"max_abs_over_max": float(np.max(np.abs(x - xo)) / np.max(np.abs(xo))),
+                                           "rel_2norm": float(np.linalg.norm(x - xo) / np.linalg.norm(xo))}
+
+        errors = {"oracle": {"rounds": ro["iters"], "relres": ro["relres"], "status": ro["status"], "s": dto},
+                  "fp32_refine": err(x_fp32), "fp64_node": err(x_fp64)}
+
+    # ---- the same system with the edge-centric FP64 variant (GABP_VARIANT_EDGE)
+    edge = None
+    if "edge" in legs:
+        try:
+            s64e = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, variant=gb.GABP_VARIANT_EDGE, profile=1,
+                                      lanes=args.lanes, **gkw)
+            step(s64e)
+            barrier()
+            ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ke, re_ = max(1, min(args.steps, 3)), 0
+            ee0.record()
+            for _ in range(ke):
+                rr, rel_e = step(s64e)
+                re_ += rr
+            ee1.record()
+            barrier()
+            mse = ee0.elapsed_time(ee1) / ke
+            edge = {"ms_per_solve": mse, "rounds": re_ / ke, "edge_updates_per_s": E * (re_ / ke) / (mse / 1e3),
+                    "relres": rel_e}
+            if errors is not None:
+                edge["error_vs_oracle"] = err(x_dev.cpu().numpy())
+            s64e.close()
+        except Exception as exc:
+            if world > 1:
+                raise
+            edge = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- the 32 x 32 grid (n = 1024), plain FP64 GaBP to 1e-12: parallel and serial schedules, and
+    # Steffensen's iterations on the serial schedule; errors against the oracle's FP64 solution
+    c1 = None
+    if "c1" in legs:
+        try:
+            import oracle
+
+            g1 = synth.grid2d(32, -1.0, 4.5)
+            b1 = synth.rhs(g1.n, 1)
+            ref1 = oracle.gabp_broadcast(g1, b1, max_iter=2000, tol=1e-12)
+            bt1 = torch.from_numpy(b1).to(dev)
+            c1 = {"workload": "32x32 5-point grid, off-diagonal -1, diagonal 4.5, b ~ N(0,1), to 1e-12",
+                  "oracle_rounds": ref1["iters"]}
+            for name, kw in (("parallel", {}), ("serial", {"schedule": 1}),
+                             ("serial_steffensen", {"schedule": 1, "accel": 2}),
+                             ("parallel_steffensen", {"accel": 2})):
+                sc = gb.Solver.from_csr(g1, precision=gb.GABP_PREC_FP64, **kw, **gkw)
+                xc, stc, itc, relc = sc.solve(bt1, tol=1e-12, max_iter=2000)
+                times = []
+                for _ in range(20):
+                    ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ec0.record()
+                    xc, stc, itc, relc = sc.solve(bt1, tol=1e-12, max_iter=2000, x=xc)
+                    ec1.record()
+                    torch.cuda.synchronize()
+                    times.append(ec0.elapsed_time(ec1))
+                xn = xc.cpu().numpy()
+                c1[name] = {"ms_per_solve": float(np.median(times)), "status": int(stc), "rounds": int(itc),
+                            "relres": relc,
+                            "error_vs_oracle": float(np.max(np.abs(xn - ref1["x"])) / np.max(np.abs(ref1["x"])))}
+                sc.close()
+        except Exception as exc:
+            if world > 1:
+                raise
+            c1 = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- regularised least squares through the augmented symmetric system: J 2^20 x 2^19, 8 entries
+    # per row N(0,1)/sqrt(8), gamma = 1, y ~ N(0,1), to 1e-10 (FP32 + refinement and plain FP64)
+    lsq = None
+    if "lsq" in legs:
+        try:
+            from scipy.sparse import csr_matrix
+
+            J = synth.random_rect(1 << 20, 1 << 19, 8, 21)
+            yl = synth.rhs(J.m, 22 + rank)
+            S = csr_matrix((J.val, J.col, J.rowptr), shape=(J.m, J.k))
+            jty = S.T @ yl
+            yt = torch.from_numpy(yl).to(dev)
+            Ea = 2 * J.nnz
+            lsq = {"workload": "J 2^20 x 2^19 sparse, 8 entries per row N(0,1)/sqrt(8), gamma = 1, y ~ N(0,1): "
+                               "x = (J^T J + gamma I)^{-1} J^T y via [[I, J^T], [J, -gamma I]] (n = 1572864, "
+                               f"{Ea} directed edges), to relative residual 1e-10", "edges": Ea}
+            for name, prec in (("fp32_refine", gb.GABP_PREC_FP32_REFINE), ("fp64", gb.GABP_PREC_FP64)):
+                sl = gb.LSQSolver.from_rect(J, 1.0, precision=prec, reuse_precisions=0, **gkw)
+                xl, _, stl, itl, rell = sl.solve_lsq(yt, tol=TOL, max_iter=5000)
+                barrier()
+                el0, el1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                kl, rounds_l = 3, 0
+                el0.record()
+                for _ in range(kl):
+                    xl, _, stl, itl, rell = sl.solve_lsq(yt, tol=TOL, max_iter=5000)
+                    rounds_l += sl.stats()["rounds"]
+                el1.record()
+                barrier()
+                msl = el0.elapsed_time(el1) / kl
+                xn = xl.cpu().numpy()
+                lsq[name] = {"ms_per_solve": msl, "status": int(stl), "rounds": rounds_l / kl, "relres": rell,
+                             "edge_updates_per_s": Ea * (rounds_l / kl) / (msl / 1e3),
+                             "normal_equation_residual": float(np.linalg.norm(S.T @ (yl - S @ xn) - xn) /
+                                                               np.linalg.norm(jty))}
+                sl.close()
+            del S, J
+        except Exception as exc:
+            if world > 1:
+                raise
+            lsq = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(m, b, rounds=5)
 
+    traffic_main = _profiled_traffic(f"{kname}_random_sym_n1048576.md", "paper_0811_2518_gb300/csrc/solve32.cu",
+                                     kname)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "edge-updates/s", "n_gpus": world, "steps": args.steps,
@@ -593,9 +812,14 @@ def main():
                                "second run of the same solves with per-phase CUDA-event timers"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": _profiled_traffic(f"{kname}_random_sym_n1048576.md",
-                                                      "paper_0811_2518_gb300/csrc/solve32.cu", kname),
-                         "bytes_per_launch": bytes_launch, "launch_ms": dur_ms,
+                         "traffic": traffic_main,
+                         "algorithmic_bytes_per_launch": bytes_launch,
+                         "algorithmic_bytes_rule": ("16 B per directed edge + 8 B per node (FP32 mean round, one "
+                                                    "right-hand side)" if ph == "mean32" else
+                                                    "24 B per directed edge + 12 B per node (FP32 full round)"),
+                         "impl_bytes_per_launch": impl_bytes, "impl_frac": impl_bytes / (dur_ms / 1e3) / 1e9 / peak,
+                         "traffic_over_algorithmic": None if traffic_main is None else traffic_main / bytes_launch,
+                         "launch_ms": dur_ms,
                          "shape": {"lanes_per_row": tuned[kname][0], "slots_per_lane": tuned[kname][1]},
                          "random_gather_reference": gather},
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
@@ -604,7 +828,18 @@ def main():
             "time_to_1e-10_ms": {"fp32_refine": ms_step, "fp64_plain": ms64},
             "fp64_plain": None if ms64 is None else {
                 "ms_per_solve": ms64, "rounds": r64 / k64, "edge_updates_per_s": E * (r64 / k64) / (ms64 / 1e3),
-                "phase_ms": p64["ms"]["fp64"] / k64},
+                "phase_ms": p64["ms"]["fp64"] / k64,
+                "roofline": {"bound": "fp64 alu", "kernel": "k64_node",
+                             "algorithmic_bytes_per_round": 48 * E + 24 * n,
+                             "algorithmic_bytes_rule": "48 B per directed edge (A 8, sender 4, reverse index 4, "
+                                                       "reverse message 16, new message 16) + 24 B per node",
+                             "round_ms": p64["ms"]["fp64"] / max(p64["rounds"]["fp64"], 1),
+                             "hbm_frac": (48 * E + 24 * n) / (p64["ms"]["fp64"] / max(p64["rounds"]["fp64"], 1)
+                                                             / 1e3) / 1e9 / peak}},
+            "fp64_edge_variant": edge,
+            "errors_vs_oracle": errors,
+            "grid32_fp64": c1,
+            "lsq_rect_1048576x524288": lsq,
             "e2e": None if e2e_s is None else {
                 "value": E * e2e_rounds / e2e_s, "unit": "edge-updates/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s / args.steps * 1e3},

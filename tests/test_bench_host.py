@@ -78,6 +78,8 @@ def test_reference_arm_line_and_budget(monkeypatch, capsys):
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["config"]["sample_n"] == 1 << 14
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == (bench.oracle_threads() or 1)
+    assert line["cpu_baseline"]["host"]["nproc"] == os.cpu_count()
     assert bench.run_reference(args, rank=1, world=2) == 0  # other ranks exit without work
     assert capsys.readouterr().out == ""
