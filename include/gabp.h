@@ -350,18 +350,26 @@ gabp_status gabp_profile_read(gabp_handle h, gabp_profile *out, int reset);
  * no-allocation-after-start-up rules).
  *
  * A is FULL symmetric CSR as for gabp_create; rowptr, col, val, b, x are DEVICE
- * arrays owned by the caller; stream is a cudaStream_t.  Same iteration, stop
- * rule and statuses as gabp_solve with GABP_PREC_FP64; iters_out / relres_out
- * are nullable host pointers.  Returns after synchronising the stream.
+ * arrays owned by the caller (host pointers return GABP_ERR_INVALID before
+ * anything is launched); stream is a cudaStream_t.  Same iteration, stop rule
+ * and statuses as gabp_solve with GABP_PREC_FP64; iters_out / relres_out are
+ * nullable host pointers.  A matrix the kernel rejects (CSR structure,
+ * diagonal, symmetry) returns GABP_ERR_INVALID with "matrix rejected" in
+ * gabp_last_error().
+ *
+ * Every call synchronises `stream` before it returns (the status is read back
+ * to the host), so it cannot be called while that stream is being captured
+ * into a CUDA graph.
  *
  * Working memory is one fixed array (about 5.6 MB) inside the library's device
  * memory, held by every GPU that loads the library until the process exits.
  * Limits: 1 <= n <= 16384 and n <= nnz <= 131072; larger sizes return
  * GABP_ERR_INVALID without launching anything.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and caches it:
- * make that first call before any stream capture on the device.  All calls
- * share the array: calls that overlap on the GPU race and must be serialised
- * by the caller.  No cudaMalloc, cudaFree or other allocating call is made.
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it for
+ * the process; calls after a cudaDeviceReset of that device are not supported.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or other allocating call
+ * is made.
  */
 gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *b, double *x, double tol,

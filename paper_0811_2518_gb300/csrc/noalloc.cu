@@ -17,8 +17,14 @@
 // Host code may not use the array's name as a device address (in host code it
 // names a host-side stand-in).  The first call on each device therefore looks
 // the address up with cudaGetSymbolAddress, with that device current, checks
-// the result and caches it; later calls reuse the cached address.  Make that
-// first call on a device before starting any stream capture on it.
+// the result and caches it for the life of the process; later calls reuse the
+// cached address.  A cudaDeviceReset invalidates that address: calls after a
+// reset of the device are not supported.
+//
+// Every call ends by copying the run's status to the host and synchronising the
+// caller's stream, so the function cannot be called while that stream is being
+// captured into a CUDA graph.  The five arrays must be device (or managed)
+// memory: host pointers are rejected before anything is launched.
 //
 // All calls share the one array and it keeps whatever the last call left in
 // it: the kernel clears what must start at zero (the round-0 messages) and
@@ -253,6 +259,12 @@ extern "C" gabp_status gabp_solve_noalloc(int32_t n, int64_t nnz, const int32_t 
   }
   if (!rowptr || !col || !val || !b || !x || !(tol >= 0.0) || max_iter < 0) {
     gabp::set_last_error("gabp_solve_noalloc: invalid argument");
+    return GABP_ERR_INVALID;
+  }
+  // the kernel dereferences all five: a host address would fault on the device
+  if (!gabp::is_device_ptr(rowptr) || !gabp::is_device_ptr(col) || !gabp::is_device_ptr(val) ||
+      !gabp::is_device_ptr(b) || !gabp::is_device_ptr(x)) {
+    gabp::set_last_error("gabp_solve_noalloc: rowptr, col, val, b and x must be device arrays");
     return GABP_ERR_INVALID;
   }
   void *scratch = nullptr;
