@@ -172,19 +172,42 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
     double accP = 0.0, acch = 0.0, accr = 0.0;
     if (i < a.n) {
       const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + sl; e < e1; e += L) {
-        const int k = a.ci[e];
-        const double A = a.av[e];
-        const double2 rv = Min[a.rev[e]];  // message i -> k of round t-1
-        const NodeRec64 nk = Nin[k];       // node k at round t-1
-        const double den = nk.P - rv.x;    // cavity precision P_{k\i}
-        bad |= is_zero64(den);
-        const double cin = -A * rcp64(den);
-        const double2 m = make_double2(cin * A, cin * (nk.h - rv.y));
-        Mout[e] = m;
-        accP += m.x;
-        acch += m.y;
-        accr = fma(A, AIT ? nk.pad : nk.x, accr);
+      // two slots per lane per step, their loads issued before use; the slot streams and the
+      // reverse messages are read once per round (streaming: evict first), the sender records
+      // are the reused working set
+      for (int eb = a.rp[i] + sl; eb < e1; eb += 2 * L) {
+        int k[2];
+        double A[2];
+        double2 rv[2];
+        NodeRec64 nk[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            k[u] = __ldcs(a.ci + e);
+            A[u] = __ldcs(a.av + e);
+            rv[u] = __ldcs(Min + __ldcs(a.rev + e));  // message i -> k of round t-1
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (eb + u * L < e1) nk[u] = Nin[k[u]];  // node k at round t-1
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int e = eb + u * L;
+          if (e < e1) {
+            const double den = nk[u].P - rv[u].x;  // cavity precision P_{k\i}
+            bad |= is_zero64(den);
+            const double cin = -A[u] * rcp64(den);
+            // the aggregates add the stored (rounded) messages, as Algorithm 2 sums them: no
+            // contraction of a product into the sum
+            const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
+            __stcs(Mout + e, m);
+            accP = __dadd_rn(accP, m.x);
+            acch = __dadd_rn(acch, m.y);
+            accr = fma(A[u], AIT ? nk[u].pad : nk[u].x, accr);
+          }
+        }
       }
     }
     accP = sub_sum<L>(accP);
