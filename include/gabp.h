@@ -93,8 +93,10 @@ typedef struct {
   int gamma_mode;       /* convergence fix: 0 off, 1 Gamma = gamma * diag(A),
                            2 Gamma_ii = max(0, sum_j |A_ij| - A_ii) + gamma * A_ii; default 0 */
   double gamma;         /* loading parameter for gamma_mode, default 0.25 */
-  int lanes;            /* lanes per row for R = 1 kernels (1..32, power of two; the FP32 round
-                           kernels use at most 16); 0 = autotune */
+  int lanes;            /* lanes per row of the FP32 R = 1 round kernels (1..32, power of two; they
+                           use at most 16); 0 = autotune.  The FP64 parallel rounds always run one
+                           row per lane on a sliced layout (rows sorted by degree in windows of 4096,
+                           slices of 32 rows) and ignore it */
   int profile;          /* 1: time every phase with CUDA events (read with gabp_profile_read), default 0 */
   int reuse_precisions; /* FP32 path: 1 keeps the converged precision messages of A for later
                            solves (they do not depend on b); 0 re-runs the precision phase in every
@@ -394,7 +396,8 @@ gabp_status gabp_set_messages(gabp_handle h, const double *P, const double *hm);
 gabp_status gabp_residual_history(gabp_handle h, double *relres, int32_t cap, int32_t *count);
 
 /* The autotuner's choices for this handle (0 where not tuned yet; all outputs
- * nullable): the FP64 round's lanes per row; the FP32 precision-phase round's
+ * nullable): the FP64 round's lanes per row (1 once its sliced layout is built:
+ * one row per lane); the FP32 precision-phase round's
  * shape (the joint precision + mean round when options.overlap_precision = 1,
  * else the precision-only round) and the mean round's shape, packed as
  * lanes | unroll << 8; the multi-system size split;

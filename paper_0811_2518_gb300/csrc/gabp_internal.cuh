@@ -71,11 +71,30 @@ struct Graph {
   double avg_deg = 0;
 };
 
+// Sliced layout of the FP64 parallel rounds (solve64.cu).  Rows are ordered by
+// degree (descending) inside windows of kSellWindow rows and cut into slices of 32;
+// slot j of the 32 rows of slice s sits at sp[s] + 32 j + lane, so a warp reads
+// and writes whole contiguous lines and its lanes (one row each) do equal work.
+// Positions past a row's degree hold sender -1 (padding).
+struct Sell64 {
+  bool ready = false;
+  bool vals_ok = false;  // sav matches the graph's values (cleared by gabp_set_values)
+  int ns = 0;            // slices
+  int Es = 0;            // positions (slots + padding)
+  int *srow = nullptr;   // [ns * 32] row of each slice lane, -1 past n
+  int *sp = nullptr;     // [ns + 1] first position of each slice
+  int *sci = nullptr;    // [Es] sender, -1 for padding
+  int *srev = nullptr;   // [Es] position of the reverse edge
+  double *sav = nullptr; // [Es] A value
+  int *c2s = nullptr;    // [E] position of compact CSR slot e
+};
+
 struct Work64 {
-  double2 *M[2] = {nullptr, nullptr};
+  double2 *M[2] = {nullptr, nullptr};  // messages at the sliced positions
   NodeRec64 *N[2] = {nullptr, nullptr};
   bool valid = false;   // a solve has completed; messages/records are readable
   int result_round = 0;
+  Sell64 sl;
 };
 
 struct Work32 {

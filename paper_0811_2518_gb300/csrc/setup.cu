@@ -429,6 +429,7 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
   h->values_ok = false;  // until the new values pass every check
   h->last_path = -1;     // marginals / messages of the old values are gone
   h->w64.valid = false;  // and no warm start from them
+  h->w64.sl.vals_ok = false;  // the sliced copy of the values is refreshed by the next FP64 solve
   h->w32.coef_ready = false;
   h->w32.prec_round = -1;
   int *dflag = nullptr;

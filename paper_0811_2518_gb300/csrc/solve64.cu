@@ -9,28 +9,52 @@
 // Round t of the parallel schedule reads round t-1 only (two message stores that
 // swap roles, paper Sec. "The Gaussian BP Algorithm", scheduling paragraph):
 //   in-message k -> i at t  =  f(A_ik, node record of k at t-1, reverse message i -> k at t-1).
-// It is written into row i's slot e (coalesced), the reverse message is fetched
-// from row k's slot rev[e], and the new node record of i is the sum over its
-// row.  The same pass forms r_i = b_i - sum_j A_ij x_j^{(t-1)} from the node
-// records it has gathered anyway, so the residual of round t-1's iterate costs
-// one FMA per slot; the stop rule therefore decides about x^{(t-1)} during round t.
+// The in-messages of row i live in its slots; the reverse message is fetched from
+// row k's slot, and the new node record of i is the sum over its row.  The same
+// pass forms r_i = b_i - sum_j A_ij x_j^{(t-1)} from the node records it has
+// gathered anyway, so the residual of round t-1's iterate costs one FMA per slot;
+// the stop rule therefore decides about x^{(t-1)} during round t.
+//
+// Layout (Sell64): rows are ordered by degree inside windows of kSellWindow rows
+// and cut into slices of 32; one warp runs a slice, one lane a row, and slot j of
+// the slice's rows is one contiguous 32-wide line.  The round is bound by the FP64
+// pipe (a Newton reciprocal and ~12 FP64 operations per slot on GB300's narrow FP64
+// units), so what matters is that every lane of every FP64 instruction does work:
+// rows of equal degree share a warp, and the row epilogue runs on all 32 lanes.
 #include "gabp_internal.cuh"
 #include "devutil.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace gabp {
+
+constexpr int kSellWindow = 4096;  // rows sorted by degree within windows of this many (a multiple of 32)
 
 struct Args64 {
   int n;
-  const int *__restrict__ rp;
-  const int *__restrict__ ci;
-  const int *__restrict__ rev;
-  const double *__restrict__ av;
-  const double *__restrict__ ad;
+  int ns;                          // slices of 32 rows
+  int Es;                          // sliced positions
+  const int *__restrict__ srow;    // [ns * 32] row of each slice lane (-1 past n)
+  const int *__restrict__ sp;      // [ns + 1] first position of each slice
+  const int *__restrict__ sci;     // [Es] sender of each position (-1: padding)
+  const int *__restrict__ srev;    // [Es] position of the reverse edge
+  const double *__restrict__ sav;  // [Es] A_ik
+  const double *__restrict__ ad;   // [n] A_ii
   double2 *M0, *M1;
   NodeRec64 *N0, *N1;
   DevCtl *ctl;
   double *partials;
 };
+
+// Warp / lane of the calling thread and the number of warps in the grid.
+struct WarpPos {
+  int lane, warp, nwarps;
+};
+__device__ __forceinline__ WarpPos warp_pos() {
+  return WarpPos{(int)(threadIdx.x & 31), (int)((blockIdx.x * kBlock + threadIdx.x) >> 5),
+                 (int)((gridDim.x * kBlock) >> 5)};
+}
 
 // Round bookkeeping shared by the FP64 round kernels: this round checked
 // x^{(t-1)} with squared residual rr; 'bad' counts zero cavities / precisions
@@ -81,15 +105,22 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
 // any starting messages lead to the same fixed point when the iteration converges.
 __global__ void __launch_bounds__(kBlock) k64_init(Args64 a, double tol, int max_iter, int warm) {
   const double *b = a.ctl->b;
+  const WarpPos w = warp_pos();
   double bb = 0.0;
-  for (int i = blockIdx.x * kBlock + threadIdx.x; i < a.n; i += gridDim.x * kBlock) {
+  for (int sl = w.warp; sl < a.ns; sl += w.nwarps) {
+    const int i = a.srow[sl * 32 + w.lane];
+    if (i < 0) continue;
     double bi = b[i], d = a.ad[i], P = d, h = bi;
-    if (warm)
-      for (int e = a.rp[i]; e < a.rp[i + 1]; ++e) {
-        const double2 m = a.M0[e];
+    if (warm) {
+      const int p0 = a.sp[sl], wd = (a.sp[sl + 1] - p0) >> 5;
+      for (int j = 0; j < wd; ++j) {
+        const int pos = p0 + 32 * j + w.lane;
+        if (a.sci[pos] < 0) break;
+        const double2 m = a.M0[pos];
         P += m.x;
         h += m.y;
       }
+    }
     const double x0 = h / P;
     a.N0[i] = NodeRec64{P, h, x0, x0};  // y^(0) = x^(0)
     bb = fma(bi, bi, bb);
@@ -138,7 +169,7 @@ __device__ __forceinline__ double aitken64(double x0, double x1, double x2) {
 // Acceleration modes of the FP64 node round (options.accel).
 enum { ACC_NONE = 0, ACC_AITKEN = 1, ACC_STEFFENSEN = 2 };
 
-// Fused node-centric round (GABP_VARIANT_NODE): a sub-warp of L lanes per row.
+// Fused node-centric round (GABP_VARIANT_NODE): a warp per slice, a lane per row.
 // ACC = ACC_AITKEN: every node also forms y^(t) = aitken(x^(t-2), x^(t-1), x^(t))
 // into its record's spare slot (x^(t-2) is the record being overwritten), and the
 // fused stop rule takes the residual of y^(t-1) instead of x^(t-1).
@@ -147,7 +178,7 @@ enum { ACC_NONE = 0, ACC_AITKEN = 1, ACC_STEFFENSEN = 2 };
 // keeps the cycle's starting iterate x_n in the spare slot; the second also sums
 // <d, D> and <D, D> (d = x_{n+2} - x_{n+1}, D = x_{n+2} - 2 x_{n+1} + x_n), whose
 // quotient, the scalar step lam, its last block stores for k64_steff.
-template <int L, int ACC>
+template <int ACC>
 __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
   constexpr bool AIT = ACC == ACC_AITKEN;
   constexpr bool STF = ACC == ACC_STEFFENSEN;
@@ -159,61 +190,50 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
   double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;       // round t
   const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
   NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
-
-  constexpr int RPW = 32 / L;
-  const int lane = threadIdx.x & 31;
-  const int sl = lane & (L - 1), sw = lane / L;
-  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * kBlock) >> 5;
+  const WarpPos w = warp_pos();
   double rr = 0.0, sdD = 0.0, sDD = 0.0;
   int bad = 0;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
+  for (int sl = w.warp; sl < a.ns; sl += w.nwarps) {
+    const int i = a.srow[sl * 32 + w.lane];
+    const int p0 = a.sp[sl] + w.lane, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
     double accP = 0.0, acch = 0.0, accr = 0.0;
-    if (i < a.n) {
-      const int e1 = a.rp[i + 1];
-      // two slots per lane per step, their loads issued before use; the slot streams and the
-      // reverse messages are read once per round (streaming: evict first), the sender records
-      // are the reused working set
-      for (int eb = a.rp[i] + sl; eb < e1; eb += 2 * L) {
-        int k[2];
-        double A[2];
-        double2 rv[2];
-        NodeRec64 nk[2];
+    // two slots per lane per step, their loads issued before use; the slot lines and the
+    // reverse messages are read once per round (streaming), the sender records are the
+    // reused working set
+    for (int j = 0; j < wd; j += 2) {
+      int k[2];
+      double A[2];
+      double2 rv[2];
+      NodeRec64 nk[2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = eb + u * L;
-          if (e < e1) {
-            k[u] = __ldcs(a.ci + e);
-            A[u] = __ldcs(a.av + e);
-            rv[u] = __ldcs(Min + __ldcs(a.rev + e));  // message i -> k of round t-1
-          }
+      for (int u = 0; u < 2; ++u) {
+        const int pos = p0 + 32 * (j + u);
+        k[u] = j + u < wd ? __ldcs(a.sci + pos) : -1;
+        if (k[u] >= 0) {
+          A[u] = __ldcs(a.sav + pos);
+          rv[u] = __ldcs(Min + __ldcs(a.srev + pos));  // message i -> k of round t-1
         }
+      }
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (eb + u * L < e1) nk[u] = Nin[k[u]];  // node k at round t-1
+      for (int u = 0; u < 2; ++u)
+        if (k[u] >= 0) nk[u] = Nin[k[u]];  // node k at round t-1
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = eb + u * L;
-          if (e < e1) {
-            const double den = nk[u].P - rv[u].x;  // cavity precision P_{k\i}
-            bad |= is_zero64(den);
-            const double cin = -A[u] * rcp64(den);
-            // the aggregates add the stored (rounded) messages, as Algorithm 2 sums them: no
-            // contraction of a product into the sum
-            const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
-            __stcs(Mout + e, m);
-            accP = __dadd_rn(accP, m.x);
-            acch = __dadd_rn(acch, m.y);
-            accr = fma(A[u], AIT ? nk[u].pad : nk[u].x, accr);
-          }
+      for (int u = 0; u < 2; ++u) {
+        if (k[u] >= 0) {
+          const double den = nk[u].P - rv[u].x;  // cavity precision P_{k\i}
+          bad |= is_zero64(den);
+          const double cin = -A[u] * rcp64(den);
+          // the aggregates add the stored (rounded) messages, as Algorithm 2 sums them: no
+          // contraction of a product into the sum
+          const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
+          __stcs(Mout + p0 + 32 * (j + u), m);
+          accP = __dadd_rn(accP, m.x);
+          acch = __dadd_rn(acch, m.y);
+          accr = fma(A[u], AIT ? nk[u].pad : nk[u].x, accr);
         }
       }
     }
-    accP = sub_sum<L>(accP);
-    acch = sub_sum<L>(acch);
-    accr = sub_sum<L>(accr);
-    if (i < a.n && sl == 0) {
+    if (i >= 0) {
       const double bi = b[i], d = a.ad[i];
       const double P = d + accP, h = bi + acch;
       bad |= is_zero64(P);
@@ -261,7 +281,6 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
 // stationary precisions these means are exactly y = x^(t) - lam (x^(t) - x^(t-1)).
 // Launched after every round; it acts once per even round that has not stopped
 // the run (the next round's fused residual then checks the extrapolated iterate).
-template <int L>
 __global__ void __launch_bounds__(kBlock) k64_steff(Args64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -269,28 +288,23 @@ __global__ void __launch_bounds__(kBlock) k64_steff(Args64 a) {
   if ((t & 1) || t < 2 || ctl->lam_round == t) return;
   const double lam = ctl->lam;
   const double *__restrict__ b = ctl->b;
-  double2 *__restrict__ Mt = (t & 1) ? a.M1 : a.M0;          // round t
-  const double2 *__restrict__ Mp = (t & 1) ? a.M0 : a.M1;    // round t-1
-  NodeRec64 *__restrict__ Nt = (t & 1) ? a.N1 : a.N0;
-  constexpr int RPW = 32 / L;
-  const int lane = threadIdx.x & 31;
-  const int sl = lane & (L - 1), sw = lane / L;
-  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * kBlock) >> 5;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
+  double2 *__restrict__ Mt = a.M0;              // round t (even)
+  const double2 *__restrict__ Mp = a.M1;        // round t-1
+  NodeRec64 *__restrict__ Nt = a.N0;
+  const WarpPos w = warp_pos();
+  for (int sl = w.warp; sl < a.ns; sl += w.nwarps) {
+    const int i = a.srow[sl * 32 + w.lane];
+    const int p0 = a.sp[sl] + w.lane, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
     double acch = 0.0;
-    if (i < a.n) {
-      const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + sl; e < e1; e += L) {
-        const double ht = Mt[e].y;
-        const double hn = ht - lam * (ht - Mp[e].y);
-        Mt[e].y = hn;
-        acch += hn;
-      }
+    for (int j = 0; j < wd; ++j) {
+      const int pos = p0 + 32 * j;
+      if (a.sci[pos] < 0) break;
+      const double ht = Mt[pos].y;
+      const double hn = ht - lam * (ht - Mp[pos].y);
+      Mt[pos].y = hn;
+      acch = __dadd_rn(acch, hn);
     }
-    acch = sub_sum<L>(acch);
-    if (i < a.n && sl == 0) {
+    if (i >= 0) {
       const NodeRec64 own = Nt[i];
       const double h = b[i] + acch;
       const double x = h * rcp64(own.P);
@@ -313,10 +327,10 @@ __global__ void __launch_bounds__(kBlock) k64_steff(Args64 a) {
   }
 }
 
-// Edge-centric round, part 1 (GABP_VARIANT_EDGE): one thread per directed edge
-// computes the in-message of its slot from the sender's aggregate minus the
-// reverse message (Algorithm 2).
-__global__ void __launch_bounds__(kBlock) k64_edge_msg(Args64 a, int E) {
+// Edge-centric round, part 1 (GABP_VARIANT_EDGE): one thread per position computes
+// the in-message of its slot from the sender's aggregate minus the reverse message
+// (Algorithm 2); padding positions do nothing.
+__global__ void __launch_bounds__(kBlock) k64_edge_msg(Args64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int t = ctl->round + 1;
@@ -324,22 +338,22 @@ __global__ void __launch_bounds__(kBlock) k64_edge_msg(Args64 a, int E) {
   double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
   const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
   int bad = 0;
-  for (int e = blockIdx.x * kBlock + threadIdx.x; e < E; e += gridDim.x * kBlock) {
-    const int k = a.ci[e];
-    const double A = a.av[e];
-    const double2 rv = Min[a.rev[e]];
+  for (int pos = blockIdx.x * kBlock + threadIdx.x; pos < a.Es; pos += gridDim.x * kBlock) {
+    const int k = __ldcs(a.sci + pos);
+    if (k < 0) continue;
+    const double A = __ldcs(a.sav + pos);
+    const double2 rv = __ldcs(Min + __ldcs(a.srev + pos));
     const NodeRec64 nk = Nin[k];
     const double den = nk.P - rv.x;
     bad |= is_zero64(den);
     const double cin = -A * rcp64(den);
-    Mout[e] = make_double2(cin * A, cin * (nk.h - rv.y));
+    __stcs(Mout + pos, make_double2(__dmul_rn(cin, A), __dmul_rn(cin, nk.h - rv.y)));
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->edge_bad, 1);
 }
 
 // Edge-centric round, part 2: row aggregates (the "broadcast" sums of
 // Algorithm 2), x^{(t)}, and the residual of x^{(t-1)}.
-template <int L>
 __global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -348,29 +362,23 @@ __global__ void __launch_bounds__(kBlock) k64_edge_agg(Args64 a) {
   const double2 *__restrict__ Mnew = (t & 1) ? a.M1 : a.M0;
   const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
   NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
-  constexpr int RPW = 32 / L;
-  const int lane = threadIdx.x & 31;
-  const int sl = lane & (L - 1), sw = lane / L;
-  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * kBlock) >> 5;
+  const WarpPos w = warp_pos();
   double rr = 0.0;
   int bad = 0;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
+  for (int sl = w.warp; sl < a.ns; sl += w.nwarps) {
+    const int i = a.srow[sl * 32 + w.lane];
+    const int p0 = a.sp[sl] + w.lane, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
     double accP = 0.0, acch = 0.0, accr = 0.0;
-    if (i < a.n) {
-      const int e1 = a.rp[i + 1];
-      for (int e = a.rp[i] + sl; e < e1; e += L) {
-        const double2 m = Mnew[e];
-        accP += m.x;
-        acch += m.y;
-        accr = fma(a.av[e], Nin[a.ci[e]].x, accr);
-      }
+    for (int j = 0; j < wd; ++j) {
+      const int pos = p0 + 32 * j;
+      const int k = __ldcs(a.sci + pos);
+      if (k < 0) break;
+      const double2 m = __ldcs(Mnew + pos);
+      accP += m.x;
+      acch += m.y;
+      accr = fma(__ldcs(a.sav + pos), Nin[k].x, accr);
     }
-    accP = sub_sum<L>(accP);
-    acch = sub_sum<L>(acch);
-    accr = sub_sum<L>(accr);
-    if (i < a.n && sl == 0) {
+    if (i >= 0) {
       const double bi = b[i], d = a.ad[i];
       const double P = d + accP, h = bi + acch;
       bad |= is_zero64(P);
@@ -394,10 +402,12 @@ __global__ void k64_finalize(int n, const NodeRec64 *__restrict__ N, double *__r
   if (i < n) x[i] = aitken ? N[i].pad : N[i].x;
 }
 
-// Messages of the returned round in the layout of the input CSR.
+// Messages of the returned round in the layout of the input CSR.  M is indexed by
+// position c2s[e] of compact slot e (the sliced layout), or by e itself when c2s
+// is null.
 __global__ void k64_messages(int n, const int *__restrict__ rowptr, const int *__restrict__ dpos,
-                             const int *__restrict__ rp, const double2 *__restrict__ M, double *__restrict__ P,
-                             double *__restrict__ hm) {
+                             const int *__restrict__ rp, const int *__restrict__ c2s,
+                             const double2 *__restrict__ M, double *__restrict__ P, double *__restrict__ hm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int a = rowptr[i], d = dpos[i], e0 = rp[i], deg = rp[i + 1] - rp[i];
@@ -405,10 +415,37 @@ __global__ void k64_messages(int n, const int *__restrict__ rowptr, const int *_
   hm[a + d] = 0.0;
   for (int q = 0; q < deg; ++q) {
     int p = a + q + (q >= d ? 1 : 0);
-    double2 m = M[e0 + q];
+    double2 m = M[c2s ? c2s[e0 + q] : e0 + q];
     P[p] = m.x;
     hm[p] = m.y;
   }
+}
+
+// ------------------------------------------------------------------------- sliced layout set-up
+// Slot j of row i = srow[q] (q = 32 s + lane) goes to position sp[s] + 32 j + lane.
+__global__ void k_sell_fill(int nq, const int *__restrict__ srow, const int *__restrict__ sp,
+                            const int *__restrict__ rp, const int *__restrict__ ci, int *__restrict__ c2s,
+                            int *__restrict__ sci) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int i = srow[q];
+  if (i < 0) return;
+  const int p0 = sp[q >> 5] + (q & 31), e0 = rp[i], deg = rp[i + 1] - e0;
+  for (int j = 0; j < deg; ++j) {
+    c2s[e0 + j] = p0 + 32 * j;
+    sci[p0 + 32 * j] = ci[e0 + j];
+  }
+}
+
+// Reverse positions and values (values again after gabp_set_values).
+__global__ void k_sell_rev_vals(int E, const int *__restrict__ c2s, const int *__restrict__ rev,
+                                const double *__restrict__ av, int *__restrict__ srev, double *__restrict__ sav,
+                                int with_rev) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int pos = c2s[e];
+  if (with_rev) srev[pos] = c2s[rev[e]];
+  sav[pos] = av[e];
 }
 
 __global__ void k64_marginals(int n, const NodeRec64 *__restrict__ N, double *__restrict__ Pi) {
@@ -430,12 +467,82 @@ __global__ void k_grad_values(int n, const int *__restrict__ rowptr, const int *
 }
 
 // ------------------------------------------------------------------------- host side
+// The sliced layout of the handle's graph (once per handle; the values again after
+// gabp_set_values).  The row order (degree-sorted windows) and the slice offsets are
+// computed on the host from the row lengths; the arrays are filled on the device.
+static gabp_status ensure_sell64(gabp_handle h) {
+  Sell64 &S = h->w64.sl;
+  Graph &g = h->g;
+  const int n = g.n, E = g.E;
+  if (!S.ready) {
+    std::vector<int> rp((size_t)n + 1);
+    GABP_CUDA(cudaMemcpy(rp.data(), g.rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+    const int ns = (n + 31) / 32;
+    std::vector<int> srow((size_t)ns * 32, -1), sp((size_t)ns + 1, 0);
+    std::vector<int> idx;
+    for (int w0 = 0; w0 < n; w0 += kSellWindow) {  // a window is a whole number of slices
+      const int w1 = std::min(n, w0 + kSellWindow);
+      idx.resize(w1 - w0);
+      for (int i = w0; i < w1; ++i) idx[i - w0] = i;
+      std::stable_sort(idx.begin(), idx.end(),
+                       [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+      std::copy(idx.begin(), idx.end(), srow.begin() + w0);
+    }
+    int64_t pos = 0;
+    for (int sl = 0; sl < ns; ++sl) {
+      sp[sl] = (int)pos;
+      int wd = 0;
+      for (int l = 0; l < 32; ++l) {
+        const int i = srow[(size_t)sl * 32 + l];
+        if (i >= 0) wd = std::max(wd, rp[i + 1] - rp[i]);
+      }
+      pos += 32 * (int64_t)wd;
+      if (pos >= INT32_MAX) {
+        set_last_error("FP64 rounds: the sliced layout does not fit int32 positions");
+        return GABP_ERR_INVALID;
+      }
+    }
+    sp[ns] = (int)pos;
+    S.ns = ns;
+    S.Es = (int)pos;
+    const size_t Ea = (size_t)std::max(S.Es, 1), Ec = (size_t)std::max(E, 1);
+    GABP_CUDA(cudaMalloc(&S.srow, sizeof(int) * srow.size()));
+    GABP_CUDA(cudaMalloc(&S.sp, sizeof(int) * sp.size()));
+    GABP_CUDA(cudaMalloc(&S.sci, sizeof(int) * Ea));
+    GABP_CUDA(cudaMalloc(&S.srev, sizeof(int) * Ea));
+    GABP_CUDA(cudaMalloc(&S.sav, sizeof(double) * Ea));
+    GABP_CUDA(cudaMalloc(&S.c2s, sizeof(int) * Ec));
+    GABP_CUDA(cudaMemcpyAsync(S.srow, srow.data(), sizeof(int) * srow.size(), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaMemcpyAsync(S.sp, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaMemsetAsync(S.sci, 0xff, sizeof(int) * Ea, h->stream));  // -1: padding
+    GABP_CUDA(cudaMemsetAsync(S.srev, 0, sizeof(int) * Ea, h->stream));
+    GABP_CUDA(cudaMemsetAsync(S.sav, 0, sizeof(double) * Ea, h->stream));
+    const int nq = ns * 32;
+    k_sell_fill<<<(nq + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(nq, S.srow, S.sp, g.rp, g.ci, S.c2s, S.sci);
+    if (E > 0)
+      k_sell_rev_vals<<<(E + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(E, S.c2s, g.rev, g.av, S.srev, S.sav, 1);
+    GABP_CUDA(cudaGetLastError());
+    GABP_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors are released on return
+    S.ready = true;
+    S.vals_ok = true;
+    h->tuned_L64 = 1;  // one row per lane
+  } else if (!S.vals_ok) {
+    if (E > 0)
+      k_sell_rev_vals<<<(E + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(E, S.c2s, g.rev, g.av, S.srev, S.sav, 0);
+    GABP_CUDA(cudaGetLastError());
+    S.vals_ok = true;
+  }
+  return GABP_OK;
+}
+
 gabp_status ensure_w64(gabp_handle h) {
+  gabp_status s = ensure_sell64(h);
+  if (s != GABP_OK) return s;
   Work64 &w = h->w64;
   if (w.M[0]) return GABP_OK;
-  size_t E = (size_t)(h->g.E > 0 ? h->g.E : 1), n = (size_t)h->g.n;
-  GABP_CUDA(cudaMalloc(&w.M[0], sizeof(double2) * E));
-  GABP_CUDA(cudaMalloc(&w.M[1], sizeof(double2) * E));
+  size_t Es = (size_t)std::max(w.sl.Es, 1), n = (size_t)h->g.n;
+  GABP_CUDA(cudaMalloc(&w.M[0], sizeof(double2) * Es));
+  GABP_CUDA(cudaMalloc(&w.M[1], sizeof(double2) * Es));
   GABP_CUDA(cudaMalloc(&w.N[0], sizeof(NodeRec64) * n));
   GABP_CUDA(cudaMalloc(&w.N[1], sizeof(NodeRec64) * n));
   return GABP_OK;
@@ -444,27 +551,22 @@ gabp_status ensure_w64(gabp_handle h) {
 void free_w64(gabp_handle h) {
   Work64 &w = h->w64;
   cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]);
+  Sell64 &S = w.sl;
+  cudaFree(S.srow); cudaFree(S.sp); cudaFree(S.sci); cudaFree(S.srev); cudaFree(S.sav); cudaFree(S.c2s);
   w = Work64{};
-}
-
-static int pick_lanes(gabp_handle h) {
-  if (h->opt.lanes) return h->opt.lanes;
-  if (h->tuned_L64) return h->tuned_L64;
-  // The FP64 round is bound by the FP64 pipe.  A row's epilogue (aggregate,
-  // x_i, residual) runs on one lane of its sub-warp while the others wait, and
-  // the sub-warp reduction adds FP64 adds, so narrow sub-warps win: 2 lanes for
-  // rows of average degree >= 12, else 1 (measured on the n = 2^20 random graph
-  // of degree 16 and on the 128^3 grid).
-  return h->g.avg_deg >= 12.0 ? 2 : 1;
 }
 
 static Args64 args64(gabp_handle h) {
   Args64 a;
+  const Sell64 &S = h->w64.sl;
   a.n = h->g.n;
-  a.rp = h->g.rp;
-  a.ci = h->g.ci;
-  a.rev = h->g.rev;
-  a.av = h->g.av;
+  a.ns = S.ns;
+  a.Es = S.Es;
+  a.srow = S.srow;
+  a.sp = S.sp;
+  a.sci = S.sci;
+  a.srev = S.srev;
+  a.sav = S.sav;
   a.ad = h->g.ad;
   a.M0 = h->w64.M[0];
   a.M1 = h->w64.M[1];
@@ -475,67 +577,31 @@ static Args64 args64(gabp_handle h) {
   return a;
 }
 
-template <int L>
-static void launch_round_L(gabp_handle h, const Args64 &a) {
-  const int rows_per_block = kBlock / L;
+template <typename K>
+static int slice_grid(gabp_handle h, K kernel) {
+  return blocks_for(h->w64.sl.ns, kBlock / 32, resident_grid(h->num_sms, kernel));
+}
+
+static void launch_round(gabp_handle h, const Args64 &a) {
   if (h->opt.variant == GABP_VARIANT_EDGE) {
-    const int eb = blocks_for(h->g.E, kBlock, resident_grid(h->num_sms, k64_edge_msg));
-    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_edge_agg<L>));
-    k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a, h->g.E);
-    k64_edge_agg<L><<<nb, kBlock, 0, h->stream>>>(a);
+    const int eb = blocks_for(a.Es, kBlock, resident_grid(h->num_sms, k64_edge_msg));
+    k64_edge_msg<<<eb, kBlock, 0, h->stream>>>(a);
+    k64_edge_agg<<<slice_grid(h, k64_edge_agg), kBlock, 0, h->stream>>>(a);
   } else if (h->opt.accel == ACC_AITKEN) {
-    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_AITKEN>));
-    k64_node<L, ACC_AITKEN><<<nb, kBlock, 0, h->stream>>>(a);
+    k64_node<ACC_AITKEN><<<slice_grid(h, k64_node<ACC_AITKEN>), kBlock, 0, h->stream>>>(a);
   } else if (h->opt.accel == ACC_STEFFENSEN) {
-    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_STEFFENSEN>));
-    k64_node<L, ACC_STEFFENSEN><<<nb, kBlock, 0, h->stream>>>(a);
-    const int sb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_steff<L>));
-    k64_steff<L><<<sb, kBlock, 0, h->stream>>>(a);
+    k64_node<ACC_STEFFENSEN><<<slice_grid(h, k64_node<ACC_STEFFENSEN>), kBlock, 0, h->stream>>>(a);
+    k64_steff<<<slice_grid(h, k64_steff), kBlock, 0, h->stream>>>(a);
   } else {
-    const int nb = blocks_for(h->g.n, rows_per_block, resident_grid(h->num_sms, k64_node<L, ACC_NONE>));
-    k64_node<L, ACC_NONE><<<nb, kBlock, 0, h->stream>>>(a);
+    k64_node<ACC_NONE><<<slice_grid(h, k64_node<ACC_NONE>), kBlock, 0, h->stream>>>(a);
   }
-}
-
-static void launch_round(gabp_handle h, const Args64 &a, int L) {
-  switch (L) {
-    case 1: launch_round_L<1>(h, a); break;
-    case 2: launch_round_L<2>(h, a); break;
-    case 4: launch_round_L<4>(h, a); break;
-    case 8: launch_round_L<8>(h, a); break;
-    case 16: launch_round_L<16>(h, a); break;
-    default: launch_round_L<32>(h, a); break;
-  }
-}
-
-// Autotuner of the sub-warp width: a few rounds of each candidate, run from the
-// solve's round-0 state under a scratch control block that never stops; the
-// fastest width is kept for the life of the handle.
-static gabp_status autotune64(gabp_handle h, const double *b) {
-  if (h->opt.lanes || h->tuned_L64) return GABP_OK;
-  gabp_status s = tune_ctl(h, b);  // allocates the scratch control block on first use
-  if (s != GABP_OK) return s;
-  Args64 a = args64(h);
-  a.ctl = h->ctl_tune;
-  const int cands[3] = {1, 2, 4};
-  float best = 1e30f;
-  int bestL = 1;
-  for (int L : cands) {
-    if ((s = tune_ctl(h, b)) != GABP_OK) return s;
-    float ms = time_launches(h, [&] { launch_round(h, a, L); }, 3);
-    if (ms < best) { best = ms; bestL = L; }
-  }
-  GABP_CUDA(cudaGetLastError());
-  h->tuned_L64 = bestL;
-  tune_cache_store(h);
-  return GABP_OK;
 }
 
 // K rounds as one CUDA graph (the round index lives in device memory, so the
 // same graph serves every replay and every solve on this handle).
-static gabp_status get_graph64(gabp_handle h, int L, cudaGraphExec_t *out) {
+static gabp_status get_graph64(gabp_handle h, cudaGraphExec_t *out) {
   const int K = h->opt.check_every;
-  const int key = (L << 16) ^ (h->opt.variant << 12) ^ (h->opt.accel << 24) ^ K;
+  const int key = (h->opt.variant << 12) ^ (h->opt.accel << 24) ^ K;
   if (h->g64 && h->g64_key == key) {
     *out = h->g64;
     return GABP_OK;
@@ -545,7 +611,7 @@ static gabp_status get_graph64(gabp_handle h, int L, cudaGraphExec_t *out) {
   Args64 a = args64(h);
   cudaGraph_t graph;
   GABP_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < K; ++k) launch_round(h, a, L);
+  for (int k = 0; k < K; ++k) launch_round(h, a);
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (e != cudaSuccess) return cuda_fail(e, "capture FP64 rounds");
   e = cudaGraphInstantiate(&h->g64, graph, 0);
@@ -562,12 +628,12 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   gabp_status s = ensure_w64(h);
   if (s != GABP_OK) return s;
   Graph &g = h->g;
-  // warm start: the messages of the previous FP64 solve (or imported ones) as round 0, once the
-  // round shape is tuned (the tuner's trial rounds would overwrite them)
-  const bool warm = h->opt.warm_start && h->w64.valid && (h->opt.lanes || h->tuned_L64);
+  const size_t Es = (size_t)std::max(h->w64.sl.Es, 1);
+  // warm start: the messages of the previous FP64 solve (or imported ones) as round 0
+  const bool warm = h->opt.warm_start && h->w64.valid;
   if (warm && (h->w64.result_round & 1))
-    GABP_CUDA(cudaMemcpyAsync(h->w64.M[0], h->w64.M[1], sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1),
-                              cudaMemcpyDeviceToDevice, h->stream));
+    GABP_CUDA(cudaMemcpyAsync(h->w64.M[0], h->w64.M[1], sizeof(double2) * Es, cudaMemcpyDeviceToDevice,
+                              h->stream));
   h->w64.valid = false;
   Args64 a = args64(h);
   // round-0 state (Algorithm 1 step 1): control block pointed at b, zero messages
@@ -588,25 +654,18 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
       GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist, &hp, sizeof(hp), cudaMemcpyHostToDevice, h->stream));
       GABP_CUDA(cudaMemcpyAsync(&h->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, h->stream));
     }
-    if (!warm)
-      GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * (size_t)(g.E > 0 ? g.E : 1), h->stream));
-    k64_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter, warm ? 1 : 0);
+    if (!warm) GABP_CUDA(cudaMemsetAsync(h->w64.M[0], 0, sizeof(double2) * Es, h->stream));
+    k64_init<<<blocks_for(a.ns, kBlock / 32, h->max_blocks), kBlock, 0, h->stream>>>(a, tol, max_iter, warm ? 1 : 0);
     GABP_CUDA(cudaGetLastError());
     GABP_CUDA(cudaStreamSynchronize(h->stream));  // also retires the pageable copy of bptr
     return GABP_OK;
   };
   if ((s = init()) != GABP_OK) return s;
-  if (!h->opt.lanes && !h->tuned_L64) {
-    // tune on this solve's own round-0 state, then start it again from round 0
-    if ((s = autotune64(h, b)) != GABP_OK) return s;
-    if ((s = init()) != GABP_OK) return s;
-  }
 
-  const int L = pick_lanes(h);
   const bool use_graph = h->stream != nullptr && h->opt.graphs;
   cudaGraphExec_t ge = nullptr;
   if (use_graph) {
-    s = get_graph64(h, L, &ge);
+    s = get_graph64(h, &ge);
     if (s != GABP_OK) return s;
   }
   const int K = h->opt.check_every;
@@ -622,7 +681,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     if (use_graph) {
       GABP_CUDA(cudaGraphLaunch(ge, h->stream));
     } else {
-      for (int k = 0; k < K; ++k) launch_round(h, a, L);
+      for (int k = 0; k < K; ++k) launch_round(h, a);
       GABP_CUDA(cudaGetLastError());
     }
     prof_end(h);
@@ -662,22 +721,23 @@ gabp_status messages64(gabp_handle h, double *P, double *hm) {
   if (!h->w64.valid) return GABP_ERR_INVALID;
   Graph &g = h->g;
   k64_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(
-      g.n, g.rowptr, g.dpos, g.rp, h->w64.M[h->w64.result_round & 1], P, hm);
+      g.n, g.rowptr, g.dpos, g.rp, h->w64.sl.c2s, h->w64.M[h->w64.result_round & 1], P, hm);
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   return GABP_OK;
 }
 
-// Inverse of k64_messages: input-layout messages into the internal slot order.
+// Inverse of k64_messages: input-layout messages into the sliced positions.
 __global__ void k64_load_messages(int n, const int *__restrict__ rowptr, const int *__restrict__ dpos,
-                                  const int *__restrict__ rp, const double *__restrict__ P,
-                                  const double *__restrict__ hm, double2 *__restrict__ M) {
+                                  const int *__restrict__ rp, const int *__restrict__ c2s,
+                                  const double *__restrict__ P, const double *__restrict__ hm,
+                                  double2 *__restrict__ M) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int a = rowptr[i], d = dpos[i], e0 = rp[i], deg = rp[i + 1] - rp[i];
   for (int q = 0; q < deg; ++q) {
     int p = a + q + (q >= d ? 1 : 0);
-    M[e0 + q] = make_double2(P[p], hm[p]);
+    M[c2s[e0 + q]] = make_double2(P[p], hm[p]);
   }
 }
 
@@ -685,8 +745,8 @@ gabp_status load_messages64(gabp_handle h, const double *P, const double *hm) {
   gabp_status s = ensure_w64(h);
   if (s != GABP_OK) return s;
   Graph &g = h->g;
-  k64_load_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp, P, hm,
-                                                                           h->w64.M[0]);
+  k64_load_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp,
+                                                                           h->w64.sl.c2s, P, hm, h->w64.M[0]);
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   h->w64.result_round = 0;
@@ -696,7 +756,8 @@ gabp_status load_messages64(gabp_handle h, const double *P, const double *hm) {
 
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm) {
   Graph &g = h->g;
-  k64_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp, M, P, hm);
+  k64_messages<<<(g.n + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(g.n, g.rowptr, g.dpos, g.rp, nullptr, M, P,
+                                                                       hm);
   GABP_CUDA(cudaGetLastError());
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   return GABP_OK;

@@ -49,18 +49,22 @@ def test_iterates_match_oracle(gb, rounds):
     assert _relerr(x, r["x"]) <= 1e-11
 
 
-@pytest.mark.parametrize("make", [lambda: _poisson(), lambda: (synth.grid2d(32, -1.0, 4.5), synth.rhs(1024, 2)),
-                                  lambda: (synth.random_sym(5000, 4, 1.1, 6), synth.rhs(5000, 6))])
-def test_converged_equal_rounds(gb, make):
+# The Poisson example is compared at 1e-10: there the residual of Aitken's iterate levels off near 1e-12
+# from round ~68 on (the second differences are rounding noise), so the first round below 1e-12 is
+# decided by the last bits of x (the oracle's is 73, it moves by tens of rounds with summation order).
+@pytest.mark.parametrize("make,tol", [(lambda: _poisson(), 1e-10),
+                                      (lambda: (synth.grid2d(32, -1.0, 4.5), synth.rhs(1024, 2)), 1e-12),
+                                      (lambda: (synth.random_sym(5000, 4, 1.1, 6), synth.rhs(5000, 6)), 1e-12)])
+def test_converged_equal_rounds(gb, make, tol):
     m, b = make()
-    r = oracle.gabp_aitken(m, b, max_iter=3000, tol=1e-12)
-    x, st, it = _solve(gb, m, b, 1e-12, 3000)
+    r = oracle.gabp_aitken(m, b, max_iter=3000, tol=tol)
+    x, st, it = _solve(gb, m, b, tol, 3000)
     assert st == gb.GABP_OK and r["status"] == oracle.OK
     # near convergence the second differences are rounding-sized and the extrapolation amplifies
     # the last bits in which the GPU's x^(t) and the oracle's differ (x = h / P by a Newton
     # reciprocal vs IEEE division): the residual of y then reaches 1e-12 a few rounds apart
     assert abs(it - r["iters"]) <= max(2, 0.1 * r["iters"])
-    assert _relerr(x, np.linalg.solve(oracle.to_dense(m), b)) <= 1e-10
+    assert _relerr(x, np.linalg.solve(oracle.to_dense(m), b)) <= 100 * tol
 
 
 def test_poisson_fewer_rounds(gb):
