@@ -692,3 +692,23 @@ def test_lsq_augmented_structure():
     assert np.array_equal(Ja[25:, :25], Jd) and np.array_equal(Ja[:25, 25:], Jd.T)
     assert np.array_equal(np.diag(Ja), np.concatenate([np.ones(25), np.full(40, -0.7)]))
     assert not np.any(Ja[:25, :25] - np.eye(25)) and not np.any(Ja[25:, 25:] + 0.7 * np.eye(40))
+
+
+def test_timing_entries_equal_the_checked_oracle():
+    """The host-baseline entries (Algorithm 2 without the input checks, on one thread and, where gcc
+    has OpenMP, on all cores) run the same arithmetic per message as the checked call: identical
+    marginal means and precisions after a fixed number of rounds (the residual sums may differ in
+    order only), and the same stop round at a tolerance."""
+    m = synth.random_sym(3000, 6, 1.1, 9)
+    b = synth.rhs(m.n, 9)
+    ref = oracle.gabp_broadcast(m, b, max_iter=7, tol=0.0)
+    for threads in (False, True):
+        if threads and oracle.host_threads() is None:
+            continue
+        r, dt = oracle.broadcast_timed(m, b, 7, threads=threads)
+        assert r["status"] == ref["status"] and r["iters"] == 7 and dt > 0.0
+        assert np.array_equal(r["x"], ref["x"]) and np.array_equal(r["P"], ref["P"])
+    conv = oracle.gabp_broadcast(m, b, max_iter=500, tol=1e-12)
+    r, _ = oracle.broadcast_timed(m, b, 500, threads=oracle.host_threads() is not None, tol=1e-12)
+    assert r["status"] == conv["status"] == oracle.OK and r["iters"] == conv["iters"]
+    assert np.allclose(r["x"], conv["x"], rtol=0, atol=1e-15 * np.max(np.abs(conv["x"])))
