@@ -158,6 +158,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def oracle_rounds_sample(m, b, rounds=3):
+    """The oracle (Algorithm 2, plain C) on `rounds` rounds of matrix m, input checks outside the timed
+    rounds: edge-updates/s on all host cores (OpenMP build) and on one core (one round)."""
+    import oracle
+
+    oracle.gabp_broadcast(m, b, max_iter=0, tol=0.0)
+    par = oracle.host_threads()
+    out = {"rounds": rounds, "edges": m.num_edges}
+    if par:
+        _, dt = oracle.broadcast_timed(m, b, rounds, threads=True)
+        out.update({"all_cores": m.num_edges * rounds / dt, "cores": par})
+    _, dt1 = oracle.broadcast_timed(m, b, 1, threads=False)
+    out["one_core"] = m.num_edges / dt1
+    return out
+
+
 def oracle_threads():
     """Threads of the all-cores oracle build (None when gcc had no OpenMP)."""
     import oracle
@@ -486,6 +502,9 @@ def main():
                                                                "ms_x64": 64 * e10.elapsed_time(e11)}
                 s1.close()
                 del x1
+            cpu_b = None
+            if not args.no_cpu_baseline and rank == 0:
+                cpu_b = oracle_rounds_sample(mg, synth.rhs_batch(mg.n, 1, 3)[0])
             msb, pb, stats_b, stb, itb, maxrel, ncol = res[1]
             mean_ms = pb["ms"]["mean32"] / max(pb["rounds"]["mean32"], 1)  # one sweep (all colour passes)
             # per sweep: every slot once (R messages read + written, coefficient pair, sender) and every row once
@@ -511,7 +530,7 @@ def main():
                        "ms_per_rhs": msb / Rb,
                        "parallel_schedule": {"ms_per_solve": res[0][0], "inner_rounds": res[0][4],
                                              "max_relres": res[0][5]},
-                       "fp64_plain_one_rhs": fp64_one,
+                       "fp64_plain_one_rhs": fp64_one, "cpu_oracle_one_rhs": cpu_b,
                        "batched_vs_64_fp64": {k: v["ms_x64"] / msb for k, v in fp64_one.items()},
                        "roofline": {"bound": "hbm", "kernel": "kbs_pass (one sweep = all colour passes)",
                                     "achieved": alg_b / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
@@ -586,7 +605,9 @@ def main():
                      "max_relres": float(relm.max()), "launches_per_batch": 1,
                      "fp64_plain_per_system": {"ms_all_systems": ms_per_sys, "rounds_total": rounds_p,
                                                "how": "one FP64 handle per system, solved one after another"},
-                     "batch_vs_fp64_per_system": ms_per_sys / msm}
+                     "batch_vs_fp64_per_system": ms_per_sys / msm,
+                     "cpu_oracle": (oracle_rounds_sample(bigm, synth.rhs(bigm.n, 4))
+                                    if not args.no_cpu_baseline and rank == 0 else None)}
             sm.close()
         except Exception as exc:  # one GPU: keep the headline line, record the failed leg
             if world > 1:
@@ -638,6 +659,8 @@ def main():
                                 "recomputed), adjoint solve on the same precision state, dL/dA and dL/db; inputs "
                                 "already on the device",
                     "ms_forward_backward_shared_solver": ms_shared,
+                    "cpu_oracle": (oracle_rounds_sample(mc, b_c) if not args.no_cpu_baseline and rank == 0
+                                   else None),
                     "shared_solver": "one handle for the pattern, new values set each step (gabp_set_values) "
                                      "instead of a new handle"}
         except Exception as exc:  # one GPU: keep the headline line, record the failed leg
@@ -727,6 +750,12 @@ def main():
             bt1 = torch.from_numpy(b1).to(dev)
             c1 = {"workload": "32x32 5-point grid, off-diagonal -1, diagonal 4.5, b ~ N(0,1), to 1e-12",
                   "oracle_rounds": ref1["iters"]}
+            if not args.no_cpu_baseline and rank == 0:  # the oracle's own time to 1e-12 (checks excluded)
+                _, t1c = oracle.broadcast_timed(g1, b1, 2000, threads=False, tol=1e-12)
+                c1["oracle_ms_one_core"] = t1c * 1e3
+                if oracle.host_threads():
+                    _, tac = oracle.broadcast_timed(g1, b1, 2000, threads=True, tol=1e-12)
+                    c1["oracle_ms_all_cores"] = tac * 1e3
             for name, kw in (("parallel", {}), ("serial", {"schedule": 1}),
                              ("serial_steffensen", {"schedule": 1, "accel": 2}),
                              ("parallel_steffensen", {"accel": 2})):
@@ -785,6 +814,11 @@ def main():
                              "normal_equation_residual": float(np.linalg.norm(S.T @ (yl - S @ xn) - xn) /
                                                                np.linalg.norm(jty))}
                 sl.close()
+            if not args.no_cpu_baseline and rank == 0:
+                import oracle
+
+                lsq["cpu_oracle"] = oracle_rounds_sample(oracle.lsq_augmented(J, 1.0),
+                                                         np.concatenate([np.zeros(J.k), yl]))
             del S, J
         except Exception as exc:
             if world > 1:

@@ -31,6 +31,18 @@ namespace gabp {
 
 constexpr int kSellWindow = 4096;  // rows sorted by degree within windows of this many (a multiple of 32)
 
+// Slots per lane whose loads the FP64 node round issues together, and the blocks per SM its
+// register budget is sized for (__launch_bounds__).  Measured on the 2^20 random graph: 2 slots and
+// 3 blocks (24 warps per SM) 0.558 ms per round; 4 blocks (64 registers) 0.589; 2 blocks 0.73;
+// 1 slot with 4 blocks 0.633; 4 slots with 2 blocks 0.678.
+#ifndef GABP_K64_UNROLL
+#define GABP_K64_UNROLL 2
+#endif
+#ifndef GABP_K64_MINB
+#define GABP_K64_MINB 3
+#endif
+constexpr int kU64 = GABP_K64_UNROLL;
+
 struct Args64 {
   int n;
   int ns;                          // slices of 32 rows
@@ -179,7 +191,7 @@ enum { ACC_NONE = 0, ACC_AITKEN = 1, ACC_STEFFENSEN = 2 };
 // <d, D> and <D, D> (d = x_{n+2} - x_{n+1}, D = x_{n+2} - 2 x_{n+1} + x_n), whose
 // quotient, the scalar step lam, its last block stores for k64_steff.
 template <int ACC>
-__global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
+__global__ void __launch_bounds__(kBlock, GABP_K64_MINB) k64_node(Args64 a) {
   constexpr bool AIT = ACC == ACC_AITKEN;
   constexpr bool STF = ACC == ACC_STEFFENSEN;
   DevCtl *ctl = a.ctl;
@@ -197,16 +209,16 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
     const int i = a.srow[sl * 32 + w.lane];
     const int p0 = a.sp[sl] + w.lane, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
     double accP = 0.0, acch = 0.0, accr = 0.0;
-    // two slots per lane per step, their loads issued before use; the slot lines and the
+    // kU64 slots per lane per step, their loads issued before use; the slot lines and the
     // reverse messages are read once per round (streaming), the sender records are the
     // reused working set
-    for (int j = 0; j < wd; j += 2) {
-      int k[2];
-      double A[2];
-      double2 rv[2];
-      NodeRec64 nk[2];
+    for (int j = 0; j < wd; j += kU64) {
+      int k[kU64];
+      double A[kU64];
+      double2 rv[kU64];
+      NodeRec64 nk[kU64];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kU64; ++u) {
         const int pos = p0 + 32 * (j + u);
         k[u] = j + u < wd ? __ldcs(a.sci + pos) : -1;
         if (k[u] >= 0) {
@@ -215,10 +227,10 @@ __global__ void __launch_bounds__(kBlock) k64_node(Args64 a) {
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
+      for (int u = 0; u < kU64; ++u)
         if (k[u] >= 0) nk[u] = Nin[k[u]];  // node k at round t-1
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kU64; ++u) {
         if (k[u] >= 0) {
           const double den = nk[u].P - rv[u].x;  // cavity precision P_{k\i}
           bad |= is_zero64(den);
