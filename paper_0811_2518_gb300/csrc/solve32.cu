@@ -765,8 +765,8 @@ static int shape32(gabp_handle h, int kind) {
   return shape_code(L, kUnroll32);
 }
 
-// Autotuner of the FP32 round kernels' shapes (see autotune64): a few rounds of
-// every candidate (lanes, unroll) under a scratch control block, fastest kept.
+// Autotuner of the FP32 round kernels' shapes: a few rounds of every candidate
+// (lanes, unroll) under a scratch control block, fastest kept.
 static gabp_status autotune32(gabp_handle h, int kind) {
   if (h->opt.lanes || tuned32(h, kind)) return GABP_OK;
   Graph &g = h->g;
