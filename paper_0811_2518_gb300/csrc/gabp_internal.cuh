@@ -95,6 +95,7 @@ struct Work64 {
   bool valid = false;   // a solve has completed; messages/records are readable
   int result_round = 0;
   Sell64 sl;
+  unsigned *bar = nullptr;  // grid barrier of the cooperative rounds: arrivals, generation, error flag
 };
 
 struct Work32 {
@@ -238,6 +239,7 @@ struct gabp_handle_s {
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
   // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
+  int coop64 = 0;                   // blocks of the FP64 cooperative rounds (0: graph too large or no support)
   int lsq_m = 0, lsq_k = 0;         // 0: not a least-squares handle
   double *lsq_b = nullptr, *lsq_x = nullptr;  // [k + m] augmented right-hand side and solution
 };

@@ -286,6 +286,141 @@ __global__ void __launch_bounds__(kBlock, GABP_K64_MINB) k64_node(Args64 a) {
     decide64(ctl, t, tot[0], tot[1]);
 }
 
+// Small and medium graphs (at most kCoopMaxSlices slices): every round of a plain
+// solve (node variant) in ONE cooperative launch of small blocks spread over many
+// SMs.  Per round: the same per-row arithmetic and decision as k64_node<ACC_NONE>;
+// then a grid barrier whose last arriving block sums the blocks' partials (in block
+// order) and takes the decision before it releases the others.  At these sizes a
+// round is a few dependent memory accesses plus little FP64 work per SM (GB300 retires
+// 2 FP64 operations per SM and clock, so the work must stay spread: one block running
+// every round measured slower than a launch per round), and the launch and the
+// separate reduction per round would cost more than the round.  Data written by other
+// blocks (messages, records, control block) is read through L2 only (__ldcg: L1 is not
+// invalidated across the barrier); the layout and A are read-only for the whole launch.
+// The barrier's wait is bounded (kCoopBarrierLimit clock cycles, ~2 s; all blocks are
+// co-resident, so it always completes): if it ever gave up, the kernel raises *err and
+// every block returns.  The loop is bounded by max_rounds.
+#ifndef GABP_COOP_THREADS
+#define GABP_COOP_THREADS 64
+#endif
+#ifndef GABP_COOP_SLEEP
+#define GABP_COOP_SLEEP 32
+#endif
+constexpr int kCoopThreads = GABP_COOP_THREADS;
+constexpr int kCoopMaxSlices = 4096;
+constexpr long long kCoopBarrierLimit = 4000000000LL;
+
+__global__ void __launch_bounds__(kCoopThreads) k64_coop(Args64 a, unsigned *bar, int *err, int max_rounds) {
+  DevCtl *ctl = a.ctl;
+  __shared__ int s_last, s_go;
+  __shared__ unsigned s_gen;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kCoopThreads + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kCoopThreads) >> 5;
+  const double *__restrict__ b = ctl->b;
+  for (int iter = 0; iter < max_rounds; ++iter) {
+    const int t = __ldcg(&ctl->round) + 1;
+    const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;
+    double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
+    const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+    NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
+    double rr = 0.0;
+    int bad = 0;
+    for (int sl = warp; sl < a.ns; sl += nwarps) {
+      const int i = __ldg(a.srow + sl * 32 + lane);
+      const int q0 = __ldg(a.sp + sl);
+      const int p0 = q0 + lane, wd = (__ldg(a.sp + sl + 1) - q0) >> 5;
+      double accP = 0.0, acch = 0.0, accr = 0.0;
+      for (int j = 0; j < wd; j += 2) {
+        int k[2];
+        double A[2];
+        double2 rv[2];
+        NodeRec64 nk[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int pos = p0 + 32 * (j + u);
+          k[u] = j + u < wd ? __ldg(a.sci + pos) : -1;
+          if (k[u] >= 0) {
+            A[u] = __ldg(a.sav + pos);
+            rv[u] = __ldcg(Min + __ldg(a.srev + pos));  // message i -> k of round t-1
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (k[u] >= 0) {  // node k at round t-1
+            const double2 *r = reinterpret_cast<const double2 *>(Nin + k[u]);
+            const double2 q = __ldcg(r), q1 = __ldcg(r + 1);
+            nk[u] = NodeRec64{q.x, q.y, q1.x, q1.y};
+          }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (k[u] >= 0) {
+            const double den = nk[u].P - rv[u].x;
+            bad |= is_zero64(den);
+            const double cin = -A[u] * rcp64(den);
+            const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
+            Mout[p0 + 32 * (j + u)] = m;
+            accP = __dadd_rn(accP, m.x);
+            acch = __dadd_rn(acch, m.y);
+            accr = fma(A[u], nk[u].x, accr);
+          }
+        }
+      }
+      if (i >= 0) {
+        const double bi = __ldg(b + i), d = __ldg(a.ad + i);
+        const double P = d + accP, h = bi + acch;
+        bad |= is_zero64(P);
+        const double ownx = __ldcg(&Nin[i].x);
+        const double xt = h * rcp64(P);
+        Nout[i] = NodeRec64{P, h, xt, xt};
+        const double r = bi - fma(d, ownx, accr);
+        rr = fma(r, r, rr);
+      }
+    }
+    // grid barrier; the last block to arrive reduces and decides
+    double v[2] = {rr, (double)bad};
+    block_sum_nt<2, kCoopThreads>(v);
+    if (threadIdx.x == 0) {
+      a.partials[blockIdx.x] = v[0];
+      a.partials[gridDim.x + blockIdx.x] = v[1];
+      const unsigned g = *(volatile unsigned *)(bar + 1);
+      __threadfence();
+      s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
+      s_gen = g;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double w[2] = {0.0, 0.0};
+      for (int q = threadIdx.x; q < (int)gridDim.x; q += kCoopThreads) {
+        w[0] += __ldcg(a.partials + q);
+        w[1] += __ldcg(a.partials + gridDim.x + q);
+      }
+      block_sum_nt<2, kCoopThreads>(w);
+      if (threadIdx.x == 0) {
+        decide64(ctl, t, w[0], w[1]);
+        s_go = !ctl->done;
+        bar[0] = 0;
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      }
+    } else if (threadIdx.x == 0) {
+      volatile unsigned *gen = bar + 1;
+      const long long t0 = clock64();
+      int ok = 1;
+      while (*gen == s_gen) {
+        if (*(volatile int *)err || clock64() - t0 > kCoopBarrierLimit) { ok = 0; break; }
+        if (GABP_COOP_SLEEP) __nanosleep(GABP_COOP_SLEEP);
+      }
+      if (!ok) atomicExch(err, 1);
+      __threadfence();
+      s_go = ok && !__ldcg(&ctl->done);
+    }
+    __syncthreads();
+    if (!s_go) break;
+  }
+}
+
 // Steffensen's iterations, the step after a cycle's second round t: "y replaces
 // x_n and GaBP runs again".  The mean messages of round t move by the cycle's
 // scalar step, h <- h^(t) - lam (h^(t) - h^(t-1)) (the precision messages stay),
@@ -538,6 +673,17 @@ static gabp_status ensure_sell64(gabp_handle h) {
     S.ready = true;
     S.vals_ok = true;
     h->tuned_L64 = 1;  // one row per lane
+    // the cooperative launch for small graphs: one block per two slices, all co-resident
+    h->coop64 = 0;
+    int coop_attr = 0;
+    cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, h->device);
+    if (coop_attr && S.ns <= kCoopMaxSlices) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k64_coop, kCoopThreads, 0) == cudaSuccess &&
+          per_sm > 0)
+        h->coop64 = std::min((S.ns * 32 + kCoopThreads - 1) / kCoopThreads, std::min(per_sm * h->num_sms, h->max_blocks));
+      cudaGetLastError();
+    }
   } else if (!S.vals_ok) {
     if (E > 0)
       k_sell_rev_vals<<<(E + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(E, S.c2s, g.rev, g.av, S.srev, S.sav, 0);
@@ -562,7 +708,7 @@ gabp_status ensure_w64(gabp_handle h) {
 
 void free_w64(gabp_handle h) {
   Work64 &w = h->w64;
-  cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]);
+  cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]); cudaFree(w.bar);
   Sell64 &S = w.sl;
   cudaFree(S.srow); cudaFree(S.sp); cudaFree(S.sci); cudaFree(S.srev); cudaFree(S.sav); cudaFree(S.c2s);
   w = Work64{};
@@ -674,7 +820,10 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   };
   if ((s = init()) != GABP_OK) return s;
 
-  const bool use_graph = h->stream != nullptr && h->opt.graphs;
+  // small and medium graphs: every round in one cooperative launch
+  const bool coop = h->w64.sl.ns <= kCoopMaxSlices && h->opt.variant == GABP_VARIANT_NODE &&
+                    h->opt.accel == ACC_NONE && h->coop64;
+  const bool use_graph = !coop && h->stream != nullptr && h->opt.graphs;
   cudaGraphExec_t ge = nullptr;
   if (use_graph) {
     s = get_graph64(h, &ge);
@@ -688,7 +837,31 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   const int per_round = h->opt.variant == GABP_VARIANT_EDGE || h->opt.accel == ACC_STEFFENSEN ? 2 : 1;
   h->prof.launches += 1;  // k64_init
   int prev_round = 0;
-  for (int64_t batch = 0; !done && batch < max_batches; ++batch) {
+  if (!done && coop) {
+    Work64 &w = h->w64;
+    if (!w.bar) GABP_CUDA(cudaMalloc(&w.bar, 16));  // [0] arrivals, [1] generation, [2] error flag
+    GABP_CUDA(cudaMemsetAsync(w.bar, 0, 16, h->stream));
+    unsigned *bar = w.bar;
+    int *err = reinterpret_cast<int *>(w.bar + 2);
+    int max_rounds = max_iter + 2;
+    void *args[] = {(void *)&a, (void *)&bar, (void *)&err, (void *)&max_rounds};
+    prof_begin(h);
+    cudaError_t le = cudaLaunchCooperativeKernel((void *)k64_coop, dim3(h->coop64), dim3(kCoopThreads), args, 0,
+                                                 h->stream);
+    if (le != cudaSuccess) return cuda_fail(le, "FP64 cooperative rounds");
+    prof_end(h);
+    h->prof.launches += 1;
+    int herr = 0;
+    GABP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if ((s = read_ctl(h)) != GABP_OK) return s;
+    prof_collect(h, PH_FP64, h->ctl_host->round);
+    if (herr) {
+      set_last_error("FP64 cooperative rounds: a grid barrier gave up");
+      return GABP_TIMEOUT;
+    }
+    done = h->ctl_host->done;
+  }
+  for (int64_t batch = 0; !done && !coop && batch < max_batches; ++batch) {
     prof_begin(h);
     if (use_graph) {
       GABP_CUDA(cudaGraphLaunch(ge, h->stream));

@@ -344,3 +344,30 @@ def test_fp64_tuning_after_other_handles_freed(gb):
         x, st, it, rel = s64.solve(b, tol=1e-10, max_iter=2000)
         s64.close()
         assert st == gb.GABP_OK and rel <= 1e-10
+
+
+@pytest.mark.parametrize("p", [362, 363])
+def test_cooperative_threshold(gb, p):
+    """Graphs of up to 4096 slices of 32 rows run every round of a plain FP64 solve in one cooperative
+    launch, larger ones launch a round kernel per round: a 362 x 362 grid (131,044 rows, 4096 slices)
+    and a 363 x 363 grid (131,769 rows, 4118 slices) on either side of the threshold give the oracle's
+    iterates at fixed rounds (1e-13), its round count at convergence, and the expected launches."""
+    m = synth.grid2d(p, -1.0, 4.5)
+    b = synth.rhs(m.n, 7)
+    for t in (1, 9):
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0)
+        g = _gpu_solve(gb, m, b, 0.0, t)
+        assert g["iters"] == t and _relerr(g["x"], r["x"]) <= 1e-13
+    ref = oracle.gabp_broadcast(m, b, max_iter=3000, tol=1e-10)
+    s = _solver(gb, m, profile=1)
+    s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_iter=3000)
+    s.profile(reset=True)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-10, max_iter=3000)
+    launches = s.profile()["launches"]
+    s.close()
+    assert st == gb.GABP_OK and it == ref["iters"]
+    assert _relerr(x.cpu().numpy(), ref["x"]) <= 1e-9
+    if (m.n + 31) // 32 <= 4096:
+        assert launches == 3  # round 0, every round, the answer
+    else:
+        assert launches > 3
