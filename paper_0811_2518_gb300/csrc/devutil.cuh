@@ -9,14 +9,16 @@ namespace gabp {
 // carry its instructions.
 static __device__ __noinline__ double rcp64_slow(double d) { return 1.0 / d; }
 
-// Reciprocal of a double by Newton-Raphson iteration, y <- y + y (1 - d y).
-// The seed is the single-precision hardware approximation (PTX rcp.approx.ftz.f32)
-// of d rounded toward zero to 20 mantissa bits.  The float operand and the
-// double seed are assembled from the IEEE-754 fields with integer operations,
-// which keeps the conversions off the (narrow) FP64 pipe.  The seed's relative
-// error is below 2^-19; each step squares it, so two steps reach FP64 rounding
-// level.  Exponents outside [-120, 120] (and 0, subnormals, inf, NaN) take the
-// IEEE division.
+// Reciprocal of a double by one step of Chebyshev's third-order iteration for 1/d:
+// with e = 1 - d y, y <- y (1 + e + e^2) = y + y (e + e^2).  If y = (1 - eps)/d, then
+// e = eps and the step gives (1 - eps^3)/d: the relative error is cubed (Newton's
+// y + y e would only square it).  The seed is the single-precision hardware
+// approximation (PTX rcp.approx.ftz.f32) of d rounded toward zero to 20 mantissa
+// bits, relative error below 2^-19, so one step leaves ~2^-57 plus the final
+// rounding: three FMAs on the (narrow) FP64 pipe instead of the four of two Newton
+// steps.  The float operand and the double seed are assembled from the IEEE-754
+// fields with integer operations, which keeps the conversions off the FP64 pipe.
+// Exponents outside [-120, 120] (and 0, subnormals, inf, NaN) take the IEEE division.
 __device__ __forceinline__ double rcp64(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
   const unsigned hi = (unsigned)(u >> 32);
@@ -28,10 +30,8 @@ __device__ __forceinline__ double rcp64(double d) {
   const int ey = (int)((yb >> 23) & 0xffu) - 127;
   const unsigned yhi = (yb & 0x80000000u) | ((unsigned)(ey + 1023) << 20) | ((yb >> 3) & 0xfffffu);
   double y = __hiloint2double((int)yhi, (int)((yb & 7u) << 29));
-  double r = fma(-d, y, 1.0);
-  y = fma(y, r, y);
-  r = fma(-d, y, 1.0);
-  y = fma(y, r, y);
+  const double r = fma(-d, y, 1.0);  // e
+  y = fma(y, fma(r, r, r), y);       // y (1 + e + e^2)
   if (e < -120 || e > 120) y = rcp64_slow(d);
   return y;
 }
