@@ -83,7 +83,10 @@ typedef enum {
 typedef struct {
   int variant;          /* gabp_variant, default GABP_VARIANT_NODE */
   int precision;        /* gabp_precision, default GABP_PREC_FP64 */
-  int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16 */
+  int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16.
+                           Plain FP64 solves (node variant, no acceleration) of graphs of at most
+                           131,072 rows run every round in one cooperative launch that decides on
+                           the device, and do not use it */
   int freeze_precisions;/* reserved for the FP64 path (precisions co-iterate there), default 1 */
   double inner_tol;     /* loosest target of an FP32 inner solve (relative change of its iterate); each
                            inner solve aims at min(inner_tol, max(1e-6, 0.1 tol ||b|| / ||r||)),
