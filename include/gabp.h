@@ -281,7 +281,9 @@ gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolour
  * The handle's matrix is the sparse symmetric augmented system
  *     [[I_k, J^T], [J, -gamma I_m]]  (n = k + m rows: x first, the auxiliary z after),
  * so no J^T J is formed and every solver path and option applies to it; GaBP on it gives
- * x in its first k marginal means.
+ * x in its first k marginal means.  The model is walk-summable for gamma > sigma_max(|J|)^2
+ * (the section's condition); below that plain FP64 GaBP often still converges, while the
+ * FP32-messages path may report GABP_DIVERGED.
  * J: CSR rowptr[m+1], col[nnz], val[nnz] (columns strictly increasing within a row, in
  * [0, k); finite nonzero values), host (mem_space 0) or device (1) memory; device arrays
  * are read after synchronising `stream` (when not NULL).  gamma > 0 and finite.  The

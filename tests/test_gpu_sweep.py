@@ -38,7 +38,8 @@ def _case(seed):
 
 
 PATHS = [dict(precision=0), dict(precision=0, variant=1), dict(precision=0, schedule=1),
-         dict(precision=0, accel=1), dict(precision=1), dict(precision=1, device_loop=0),
+         dict(precision=0, accel=1), dict(precision=0, accel=2), dict(precision=0, schedule=1, accel=2),
+         dict(precision=0, graphs=0), dict(precision=1), dict(precision=1, device_loop=0),
          dict(precision=1, schedule=1), dict(precision=1, overlap_precision=0)]
 
 
@@ -78,3 +79,30 @@ def test_small_systems_batched_and_independent(gb, seed):
     assert st == gb.GABP_OK and np.all(sts == gb.GABP_OK)
     ref = np.linalg.solve(oracle.to_dense(big), bb)
     assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_rectangular_least_squares(gb, seed):
+    """Rectangular J of random shape (1 to ~200 rows and columns, over- and under-determined, some
+    empty rows and columns) through the augmented system, against the dense ridge normal equations.
+    Plain FP64 GaBP with gamma in [0.5, 2] (models that are NOT walk-summable: rho(|R|) up to ~14, and
+    it converged on every case tried); FP32 + refinement with gamma = 1.5 sigma_max(|J|)^2, the loading
+    for which the general-linear-systems section states the model is walk-summable (its frozen
+    coefficients diverge on some of the loosely loaded cases, reported as GABP_DIVERGED)."""
+    from scipy.sparse import csr_matrix
+
+    rng = np.random.default_rng(500 + seed)
+    m_, k_ = int(rng.integers(1, 200)), int(rng.integers(1, 200))
+    Jd = rng.standard_normal((m_, k_)) * (rng.random((m_, k_)) < min(1.0, 6.0 / k_))
+    c = csr_matrix(Jd)
+    J = synth.RectCSR(m_, k_, c.indptr.astype(np.int32), c.indices.astype(np.int32), c.data.copy())
+    y = rng.standard_normal(m_)
+    g_loose = float(rng.uniform(0.5, 2.0))
+    g_ws = 1.5 * max(float(np.linalg.norm(np.abs(Jd), 2)) ** 2, 1e-3)
+    for prec, gamma in ((0, g_loose), (0, g_ws), (1, g_ws)):
+        xr = np.linalg.solve(Jd.T @ Jd + gamma * np.eye(k_), Jd.T @ y)
+        s = gb.LSQSolver.from_rect(J, gamma, precision=prec)
+        x, z, st, it, rel = s.solve_lsq(torch.from_numpy(y).cuda(), tol=1e-12, max_iter=20000)
+        s.close()
+        assert st == gb.GABP_OK, (seed, prec, gamma, st)
+        assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-9 * max(np.linalg.norm(xr), 1e-300), (seed, prec)
