@@ -87,7 +87,19 @@ typedef struct {
                            Plain FP64 solves (node variant, no acceleration) of graphs of at most
                            131,072 rows run every round in one cooperative launch that decides on
                            the device, and do not use it */
-  int freeze_precisions;/* reserved for the FP64 path (precisions co-iterate there), default 1 */
+  int freeze_precisions;/* plain FP64 solves (node variant, no acceleration): 1 = freeze the precision
+                           messages once they have stopped moving.  Screen: after two consecutive
+                           rounds in which no node's P~_i moved by more than 16 units in the last
+                           place (~2^-48 relative), one round checks every precision message against its previous
+                           round's the same way while it stores each edge's coefficient
+                           -A_ki / P_k\i and each node's 1/P~; if none moved, later rounds update
+                           the mean messages only (the precisions do not depend on b), else the
+                           screen resumes.  Every round up to the stored one is bitwise the plain
+                           solve's; after it x differs from the plain iterate by rounding only.
+                           Pays on solves that need many more rounds than the precisions do
+                           (FP64-bound rounds); the screen costs a few percent per round.  0 =
+                           every round updates both (Algorithm 2 as printed).  Other paths
+                           ignore it (the FP32 path always freezes).  Default 0 */
   double inner_tol;     /* loosest target of an FP32 inner solve (relative change of its iterate); each
                            inner solve aims at min(inner_tol, max(1e-6, 0.1 tol ||b|| / ||r||)),
                            the reduction still needed.  Default 1e-4 */
@@ -330,6 +342,14 @@ gabp_status gabp_grad_values(gabp_handle h, const double *lambda, const double *
  * round, summed over rounds, right-hand sides and systems), and refinement steps. */
 gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *num_edges, int64_t *edge_updates,
                             int32_t *refine_steps);
+
+/* The precision freeze of the last FP64 solve (options.freeze_precisions), outputs
+ * nullable: *round receives the round whose coefficients -A_ki / P_k\i and 1/P~
+ * were stored (that round and every earlier one are the plain solve's; later rounds
+ * update the mean messages only), or 0 if the freeze was off or never verified;
+ * *checks the number of verification rounds run (failed ones included).
+ * GABP_ERR_INVALID for a null handle. */
+gabp_status gabp_last_freeze(gabp_handle h, int32_t *round, int32_t *checks);
 
 /* Per-phase device time of the solves since the last reset (options.profile = 1):
  * phase 0 FP64 GaBP rounds, 1 FP32 precision rounds (joint precision + mean

@@ -21,7 +21,7 @@ __all__ = [
     "Options", "lib", "library_path", "exported_symbols",
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
-    "gabp_grad_values", "gabp_last_stats", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_set_messages", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
+    "gabp_grad_values", "gabp_last_stats", "gabp_last_freeze", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_set_messages", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
     "gabp_create_lsq", "gabp_solve_lsq",
     "Solver", "LSQSolver", "GaBPError",
 ]
@@ -92,6 +92,7 @@ _SIGNATURES = {
     "gabp_grad_values": ([_P, _P, _P, _P], ctypes.c_int),
     "gabp_last_stats": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "gabp_last_freeze": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "gabp_solve_systems": ([_P, ctypes.c_int32, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P],
                            ctypes.c_int),
     "gabp_profile_read": ([_P, ctypes.POINTER(Profile), ctypes.c_int], ctypes.c_int),
@@ -251,6 +252,13 @@ def gabp_last_stats(h):
     r, e, u, s = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
     st = lib.gabp_last_stats(h, ctypes.byref(r), ctypes.byref(e), ctypes.byref(u), ctypes.byref(s))
     return st, r.value, e.value, u.value, s.value
+
+
+def gabp_last_freeze(h):
+    """Returns (status, round whose precisions the last FP64 solve froze or 0, verification rounds)."""
+    r, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    st = lib.gabp_last_freeze(h, ctypes.byref(r), ctypes.byref(c))
+    return st, r.value, c.value
 
 
 def gabp_solve_systems(h, nsys, offsets_host_ptr, b_ptr, x_ptr, tol, max_iter, status_ptr=None, iters_ptr=None,
@@ -490,7 +498,8 @@ class Solver:
 
     def stats(self):
         st, rounds, E, eu, steps = gabp_last_stats(self.handle)
-        return {"rounds": rounds, "edges": E, "edge_updates": eu, "refine_steps": steps}
+        return {"rounds": rounds, "edges": E, "edge_updates": eu, "refine_steps": steps,
+                "freeze_round": gabp_last_freeze(self.handle)[1], "freeze_checks": gabp_last_freeze(self.handle)[2]}
 
     def solve_systems(self, b, offsets, tol=1e-10, max_iter=5000, x=None, check=True):
         """Independent systems of a block-diagonal A (row offsets ``offsets``, host ints) in one

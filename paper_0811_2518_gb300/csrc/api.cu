@@ -31,6 +31,7 @@ gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol
   DeviceGuard dg(h->device);
   order_after_caller(h);
   h->hist_len = 0;  // only the FP64 parallel rounds record a history
+  h->stats.freeze_round = h->stats.freeze_checks = 0;  // and only they freeze on the device
   // one solve of A x = b on the path the options select (x = 0 at the start)
   auto run = [&](const double *rb, double *rx, double rtol, int *it, double *rel) -> gabp_status {
     gabp_status s;
@@ -121,6 +122,7 @@ extern "C" gabp_status gabp_solve_batched(gabp_handle h, int32_t nrhs, const dou
   }
   DeviceGuard dg(h->device);
   order_after_caller(h);
+  h->stats.freeze_round = h->stats.freeze_checks = 0;
   int it = 0;
   gabp_status s = solve_batched32(h, nrhs, B, X, ld, tol, max_iter, &it, relres_out);
   if (s >= 0 && iters_out) *iters_out = it;
@@ -193,6 +195,13 @@ extern "C" gabp_status gabp_last_stats(gabp_handle h, int64_t *rounds, int64_t *
   return GABP_OK;
 }
 
+extern "C" gabp_status gabp_last_freeze(gabp_handle h, int32_t *round, int32_t *checks) {
+  if (!h) return GABP_ERR_INVALID;
+  if (round) *round = h->stats.freeze_round;
+  if (checks) *checks = h->stats.freeze_checks;
+  return GABP_OK;
+}
+
 extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offsets, const double *b,
                                           double *x, double tol, int32_t max_iter, int32_t *status_out,
                                           int32_t *iters_out, double *relres_out) {
@@ -204,6 +213,7 @@ extern "C" gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int
   }
   DeviceGuard dg(h->device);
   order_after_caller(h);
+  h->stats.freeze_round = h->stats.freeze_checks = 0;
   return solve_systems(h, nsys, offsets, b, x, tol, max_iter, status_out, iters_out, relres_out);
 }
 

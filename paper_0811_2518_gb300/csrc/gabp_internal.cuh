@@ -57,6 +57,11 @@ struct DevCtl {
   int hist_len;      // entries written
   int lam_round;     // Steffensen: the round whose extrapolation was applied last
   double lam;        // Steffensen: scalar step of the latest cycle (its second round's last block)
+  int fstate;        // FP64 precision freeze: 0 co-iterating, 1 store the coefficients this round, 2 frozen
+  int pstat;         // FP64 precision freeze: consecutive rounds with every precision message stagnant
+  int fround;        // FP64 precision freeze: the round that stored the coefficients (0: not yet)
+  int pfail;         // FP64 precision freeze: failed verifications
+  int fchecks;       // FP64 precision freeze: verification rounds run
 };
 
 struct Graph {
@@ -96,6 +101,7 @@ struct Work64 {
   int result_round = 0;
   Sell64 sl;
   unsigned *bar = nullptr;  // grid barrier of the cooperative rounds: arrivals, generation, error flag
+  double *C = nullptr;      // [Es] frozen coefficients c = -A / (P~ - P) (options.freeze_precisions)
 };
 
 struct Work32 {
@@ -169,6 +175,8 @@ struct Stats {
   int64_t edge_updates = -1;  // set by paths whose systems differ in size (else rounds x E x nrhs)
   int refine_steps = 0;
   int nrhs = 1;
+  int freeze_round = 0;   // FP64 precision freeze: the round whose coefficients were stored (0: none)
+  int freeze_checks = 0;  // FP64 precision freeze: verification rounds run
 };
 
 // Phase timing (options.profile): CUDA events around each phase's launches.
@@ -240,6 +248,7 @@ struct gabp_handle_s {
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
   // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
   int coop64 = 0;                   // blocks of the FP64 cooperative rounds (0: graph too large or no support)
+  int coop64f = 0;                  // the same for the cooperative rounds with the precision freeze
   int lsq_m = 0, lsq_k = 0;         // 0: not a least-squares handle
   double *lsq_b = nullptr, *lsq_x = nullptr;  // [k + m] augmented right-hand side and solution
 };

@@ -292,7 +292,7 @@ extern "C" gabp_status gabp_options_default(gabp_options *o) {
   o->variant = GABP_VARIANT_NODE;
   o->precision = GABP_PREC_FP64;
   o->check_every = 16;
-  o->freeze_precisions = 1;
+  o->freeze_precisions = 0;
   o->inner_tol = 1e-4;
   o->inner_max_iter = 400;
   o->max_refine = 30;
@@ -330,7 +330,7 @@ static gabp_status check_options(const gabp_options *o) {
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
       o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
-      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 2 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 || o->graphs < 0 || o->graphs > 1 ||
+      o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 2 || o->freeze_precisions < 0 || o->freeze_precisions > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 || o->graphs < 0 || o->graphs > 1 ||
       (o->accel && o->variant != GABP_VARIANT_NODE) || (o->accel == 1 && o->schedule == 1))
     return GABP_ERR_INVALID;
   return GABP_OK;

@@ -57,6 +57,8 @@ struct Args64 {
   NodeRec64 *N0, *N1;
   DevCtl *ctl;
   double *partials;
+  double *C;   // [Es] frozen coefficients (freeze != 0)
+  int freeze;  // options.freeze_precisions on a plain node solve
 };
 
 // Warp / lane of the calling thread and the number of warps in the grid.
@@ -109,6 +111,152 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
   }
   ctl->arrive = 0;
   __threadfence();
+}
+
+// Precision freeze (options.freeze_precisions).  The precision messages do not
+// depend on b and converge on their own; once they have stopped moving (to
+// rounding) the coefficients c = -A / P_k\i are constant and later rounds need
+// only the mean messages.  States (fs, the state a round ran in):
+//   0 screen: every node's P~_i is compared with its previous round's; after
+//     2 << min(failed verifications, 5) consecutive rounds in which none moved,
+//     the next round verifies;
+//   1 verify: every precision message is compared with its own previous round's
+//     while the round stores its coefficients and 1/P~; if none moved the
+//     precisions are frozen from the next round on, else back to screening (a
+//     message can still move while every aggregate it enters is stagnant, where
+//     a cavity P~_k - P_ik cancels; the longer screens bound the verify rounds);
+//   2 frozen: mean messages only, with the stored coefficients.
+// "Moved": more than 16 units in the last place apart (bit patterns as integers;
+// about 2^-48 relative).  Stagnant precision messages still jitter by a few units
+// in the last place (rounding of the sums and differences they come from, larger
+// where P~_k = A_kk + sum of negative messages cancels), so a tighter bar may never
+// pass; the mean iteration with coefficients this close to their limits stays
+// within rounding of the plain iterate.
+__device__ __forceinline__ void freeze_step(DevCtl *ctl, int fs, int t, double moving) {
+  if (fs == 0) {
+    ctl->pstat = moving == 0.0 ? ctl->pstat + 1 : 0;
+    if (ctl->pstat >= (2 << min(ctl->pfail, 5))) ctl->fstate = 1;
+  } else if (fs == 1) {
+    ctl->fchecks += 1;
+    if (moving == 0.0) {
+      ctl->fstate = 2;
+      ctl->fround = t;
+    } else {
+      ctl->fstate = 0;
+      ctl->pstat = 0;
+      ctl->pfail += 1;
+    }
+  }
+}
+
+// More than 16 units in the last place apart (any NaN, a sign change or a zero
+// against a non-zero counts as apart; two equal bit patterns do not).
+__device__ __forceinline__ bool ulp_apart(double u, double v) {
+  return (unsigned long long)(__double_as_longlong(u) - __double_as_longlong(v) + 16) > 32ull;
+}
+
+// Load flavours of the plain round body: the launch-per-round kernel streams its slot
+// lines (evict first); the cooperative kernel reads data other blocks wrote through L2
+// only and the read-only layout through the non-coherent path (L1 is not invalidated
+// across its grid barrier).
+template <bool COOP> __device__ __forceinline__ int ld_idx(const int *p) { return COOP ? __ldg(p) : __ldcs(p); }
+template <bool COOP> __device__ __forceinline__ double ld_val(const double *p) { return COOP ? __ldg(p) : __ldcs(p); }
+template <bool COOP> __device__ __forceinline__ double2 ld_msg(const double2 *p) { return COOP ? __ldcg(p) : __ldcs(p); }
+template <bool COOP> __device__ __forceinline__ double ld_msgh(const double2 *p) {
+  const double *q = reinterpret_cast<const double *>(p) + 1;
+  return COOP ? __ldcg(q) : __ldcs(q);
+}
+template <bool COOP> __device__ __forceinline__ NodeRec64 ld_rec(const NodeRec64 *p) {
+  if (!COOP) return *p;
+  const double2 *r = reinterpret_cast<const double2 *>(p);
+  const double2 q = __ldcg(r), q1 = __ldcg(r + 1);
+  return NodeRec64{q.x, q.y, q1.x, q1.y};
+}
+
+// One slice of a plain round (node variant, no acceleration), a lane per row.
+// MODE 0: Algorithm 2's round.  MODE 1 (freeze screen): the same, flagging rows whose
+// P~_i moved since the previous round.  MODE 2 (freeze verify): the same, flagging
+// precision messages that moved since the previous round (the slot's own previous
+// message) and storing each slot's coefficient c = -A / (P~_k - P_ik) and each row's
+// 1/P~ (the record's spare slot).  MODE 3 (frozen precisions): only the mean
+// messages, h_ki = c (h~_k - h_ik), with the stored coefficients; P~ and 1/P~
+// carried over.  All modes form x and the residual of the previous iterate as the
+// round kernels do.
+template <bool COOP, int MODE>
+__device__ __forceinline__ void plain_slice(const Args64 &a, int sl, int lane, const double *__restrict__ b,
+                                            const double2 *__restrict__ Min, double2 *__restrict__ Mout,
+                                            const NodeRec64 *__restrict__ Nin, NodeRec64 *__restrict__ Nout,
+                                            double &rr, int &bad, int &moving) {
+  const int i = COOP ? __ldg(a.srow + sl * 32 + lane) : a.srow[sl * 32 + lane];
+  const int q0 = COOP ? __ldg(a.sp + sl) : a.sp[sl];
+  const int p0 = q0 + lane, wd = ((COOP ? __ldg(a.sp + sl + 1) : a.sp[sl + 1]) - q0) >> 5;
+  double accP = 0.0, acch = 0.0, accr = 0.0;
+  for (int j = 0; j < wd; j += kU64) {
+    int k[kU64];
+    double A[kU64], c[kU64], rh[kU64];
+    double2 rv[kU64];
+    NodeRec64 nk[kU64];
+#pragma unroll
+    for (int u = 0; u < kU64; ++u) {
+      const int pos = p0 + 32 * (j + u);
+      k[u] = j + u < wd ? ld_idx<COOP>(a.sci + pos) : -1;
+      if (k[u] >= 0) {
+        A[u] = ld_val<COOP>(a.sav + pos);
+        const int rp = ld_idx<COOP>(a.srev + pos);
+        if (MODE == 3) {
+          c[u] = ld_val<COOP>(a.C + pos);
+          rh[u] = ld_msgh<COOP>(Min + rp);  // mean message i -> k of round t-1
+        } else {
+          rv[u] = ld_msg<COOP>(Min + rp);   // message i -> k of round t-1
+          if (MODE == 2) rh[u] = ld_msg<COOP>(Min + pos).x;  // this slot's precision message at t-1
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU64; ++u)
+      if (k[u] >= 0) nk[u] = ld_rec<COOP>(Nin + k[u]);  // node k at round t-1
+#pragma unroll
+    for (int u = 0; u < kU64; ++u) {
+      if (k[u] < 0) continue;
+      const int pos = p0 + 32 * (j + u);
+      if (MODE == 3) {
+        const double hn = __dmul_rn(c[u], nk[u].h - rh[u]);
+        double *dst = reinterpret_cast<double *>(Mout + pos) + 1;
+        if (COOP) *dst = hn; else __stcs(dst, hn);
+        acch = __dadd_rn(acch, hn);
+      } else {
+        const double den = nk[u].P - rv[u].x;  // cavity precision P_{k\i}
+        bad |= is_zero64(den);
+        const double cin = -A[u] * rcp64(den);
+        // the aggregates add the stored (rounded) messages, as Algorithm 2 sums them
+        const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
+        if (COOP) Mout[pos] = m; else __stcs(Mout + pos, m);
+        if (MODE == 2) {
+          moving |= ulp_apart(m.x, rh[u]);
+          a.C[pos] = cin;
+        }
+        accP = __dadd_rn(accP, m.x);
+        acch = __dadd_rn(acch, m.y);
+      }
+      accr = fma(A[u], nk[u].x, accr);
+    }
+  }
+  if (i >= 0) {
+    const double bi = COOP ? __ldg(b + i) : b[i], d = COOP ? __ldg(a.ad + i) : a.ad[i];
+    const NodeRec64 own = ld_rec<COOP>(Nin + i);
+    if (MODE == 3) {
+      const double h = bi + acch;
+      Nout[i] = NodeRec64{own.P, h, h * own.pad, own.pad};
+    } else {
+      const double P = d + accP, h = bi + acch;
+      bad |= is_zero64(P);
+      if (MODE == 1) moving |= ulp_apart(P, own.P);
+      const double ip = rcp64(P);
+      Nout[i] = NodeRec64{P, h, h * ip, MODE == 2 ? ip : h * ip};
+    }
+    const double r = bi - fma(d, own.x, accr);
+    rr = fma(r, r, rr);
+  }
 }
 
 // Round 0 (Algorithm 1/2 step 1): all messages zero, so P~_i = A_ii, h~_i = b_i.
@@ -181,6 +329,49 @@ __device__ __forceinline__ double aitken64(double x0, double x1, double x2) {
 // Acceleration modes of the FP64 node round (options.accel).
 enum { ACC_NONE = 0, ACC_AITKEN = 1, ACC_STEFFENSEN = 2 };
 
+// One plain round over this kernel's slices in mode MODE of plain_slice, then the
+// block sums and, in the last block, the freeze state's step and the decision.
+template <int MODE>
+__device__ __forceinline__ void plain_round(const Args64 &a, DevCtl *ctl, int t, const double *__restrict__ b,
+                                            const double2 *__restrict__ Min, double2 *__restrict__ Mout,
+                                            const NodeRec64 *__restrict__ Nin, NodeRec64 *__restrict__ Nout,
+                                            const WarpPos &w) {
+  double rr = 0.0;
+  int bad = 0, moving = 0;
+  for (int sl = w.warp; sl < a.ns; sl += w.nwarps)
+    plain_slice<false, MODE>(a, sl, w.lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
+  constexpr int NV = MODE > 0 ? 3 : 2;  // the moving count only when the freeze is on
+  double v[NV], tot[NV];
+  int modes[NV];
+  v[0] = rr;
+  v[1] = (double)bad;
+  if constexpr (NV > 2) v[2] = (double)moving;
+  for (int q = 0; q < NV; ++q) modes[q] = 0;
+  block_sum<NV>(v);
+  if (last_block_reduce<NV>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
+    if constexpr (MODE > 0) freeze_step(ctl, MODE - 1, t, tot[2]);
+    decide64(ctl, t, tot[0], tot[1]);
+  }
+}
+
+// The plain round with the precision freeze on: MODE 1 (screen), 2 (verify and store)
+// or 3 (frozen).  A round launches k64_frz<3>, <2>, <1> in that order and each
+// returns unless the freeze state is MODE - 1.  The state only grows by one step at
+// a time, except that a failed verification returns it to 0: so one of the three
+// runs, or k64_frz<2> and then k64_frz<1> (two rounds; the round count and the stop
+// rule live on the device, so a launch slot may hold two rounds).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, GABP_K64_MINB) k64_frz(Args64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done || ctl->fstate != MODE - 1) return;
+  const int t = ctl->round + 1;
+  const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;
+  double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
+  const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+  NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
+  plain_round<MODE>(a, ctl, t, ctl->b, Min, Mout, Nin, Nout, warp_pos());
+}
+
 // Fused node-centric round (GABP_VARIANT_NODE): a warp per slice, a lane per row.
 // ACC = ACC_AITKEN: every node also forms y^(t) = aitken(x^(t-2), x^(t-1), x^(t))
 // into its record's spare slot (x^(t-2) is the record being overwritten), and the
@@ -203,6 +394,10 @@ __global__ void __launch_bounds__(kBlock, GABP_K64_MINB) k64_node(Args64 a) {
   const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
   NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
   const WarpPos w = warp_pos();
+  if (ACC == ACC_NONE) {
+    plain_round<0>(a, ctl, t, b, Min, Mout, Nin, Nout, w);
+    return;
+  }
   double rr = 0.0, sdD = 0.0, sDD = 0.0;
   int bad = 0;
   for (int sl = w.warp; sl < a.ns; sl += w.nwarps) {
@@ -310,7 +505,8 @@ constexpr int kCoopThreads = GABP_COOP_THREADS;
 constexpr int kCoopMaxSlices = 4096;
 constexpr long long kCoopBarrierLimit = 4000000000LL;
 
-__global__ void __launch_bounds__(kCoopThreads) k64_coop(Args64 a, unsigned *bar, int *err, int max_rounds) {
+template <bool FRZ>
+__global__ void __launch_bounds__(kCoopThreads, FRZ ? 8 : 0) k64_coop(Args64 a, unsigned *bar, int *err, int max_rounds) {
   DevCtl *ctl = a.ctl;
   __shared__ int s_last, s_go;
   __shared__ unsigned s_gen;
@@ -320,69 +516,30 @@ __global__ void __launch_bounds__(kCoopThreads) k64_coop(Args64 a, unsigned *bar
   const double *__restrict__ b = ctl->b;
   for (int iter = 0; iter < max_rounds; ++iter) {
     const int t = __ldcg(&ctl->round) + 1;
+    const int fs = FRZ ? __ldcg(&ctl->fstate) : -1;
     const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;
     double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
     const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
     NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
     double rr = 0.0;
-    int bad = 0;
+    int bad = 0, moving = 0;
     for (int sl = warp; sl < a.ns; sl += nwarps) {
-      const int i = __ldg(a.srow + sl * 32 + lane);
-      const int q0 = __ldg(a.sp + sl);
-      const int p0 = q0 + lane, wd = (__ldg(a.sp + sl + 1) - q0) >> 5;
-      double accP = 0.0, acch = 0.0, accr = 0.0;
-      for (int j = 0; j < wd; j += 2) {
-        int k[2];
-        double A[2];
-        double2 rv[2];
-        NodeRec64 nk[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int pos = p0 + 32 * (j + u);
-          k[u] = j + u < wd ? __ldg(a.sci + pos) : -1;
-          if (k[u] >= 0) {
-            A[u] = __ldg(a.sav + pos);
-            rv[u] = __ldcg(Min + __ldg(a.srev + pos));  // message i -> k of round t-1
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-          if (k[u] >= 0) {  // node k at round t-1
-            const double2 *r = reinterpret_cast<const double2 *>(Nin + k[u]);
-            const double2 q = __ldcg(r), q1 = __ldcg(r + 1);
-            nk[u] = NodeRec64{q.x, q.y, q1.x, q1.y};
-          }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (k[u] >= 0) {
-            const double den = nk[u].P - rv[u].x;
-            bad |= is_zero64(den);
-            const double cin = -A[u] * rcp64(den);
-            const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
-            Mout[p0 + 32 * (j + u)] = m;
-            accP = __dadd_rn(accP, m.x);
-            acch = __dadd_rn(acch, m.y);
-            accr = fma(A[u], nk[u].x, accr);
-          }
-        }
-      }
-      if (i >= 0) {
-        const double bi = __ldg(b + i), d = __ldg(a.ad + i);
-        const double P = d + accP, h = bi + acch;
-        bad |= is_zero64(P);
-        const double ownx = __ldcg(&Nin[i].x);
-        const double xt = h * rcp64(P);
-        Nout[i] = NodeRec64{P, h, xt, xt};
-        const double r = bi - fma(d, ownx, accr);
-        rr = fma(r, r, rr);
-      }
+      if (!FRZ) plain_slice<true, 0>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
+      else if (fs == 0) plain_slice<true, 1>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
+      else if (fs == 1) plain_slice<true, 2>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
+      else plain_slice<true, 3>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
     }
     // grid barrier; the last block to arrive reduces and decides
-    double v[2] = {rr, (double)bad};
-    block_sum_nt<2, kCoopThreads>(v);
+    constexpr int NV = FRZ ? 3 : 2;
+    double v[NV];
+    v[0] = rr;
+    v[1] = (double)bad;
+    if constexpr (FRZ) v[2] = (double)moving;
+    block_sum_nt<NV, kCoopThreads>(v);
     if (threadIdx.x == 0) {
       a.partials[blockIdx.x] = v[0];
       a.partials[gridDim.x + blockIdx.x] = v[1];
+      if constexpr (FRZ) a.partials[2 * gridDim.x + blockIdx.x] = v[2];
       const unsigned g = *(volatile unsigned *)(bar + 1);
       __threadfence();
       s_last = atomicAdd(bar, 1u) == gridDim.x - 1;
@@ -391,13 +548,16 @@ __global__ void __launch_bounds__(kCoopThreads) k64_coop(Args64 a, unsigned *bar
     __syncthreads();
     if (s_last) {
       __threadfence();
-      double w[2] = {0.0, 0.0};
+      double w[NV];
+      for (int q = 0; q < NV; ++q) w[q] = 0.0;
       for (int q = threadIdx.x; q < (int)gridDim.x; q += kCoopThreads) {
         w[0] += __ldcg(a.partials + q);
         w[1] += __ldcg(a.partials + gridDim.x + q);
+        if constexpr (FRZ) w[2] += __ldcg(a.partials + 2 * gridDim.x + q);
       }
-      block_sum_nt<2, kCoopThreads>(w);
+      block_sum_nt<NV, kCoopThreads>(w);
       if (threadIdx.x == 0) {
+        if constexpr (FRZ) freeze_step(ctl, fs, t, w[2]);
         decide64(ctl, t, w[0], w[1]);
         s_go = !ctl->done;
         bar[0] = 0;
@@ -674,14 +834,19 @@ static gabp_status ensure_sell64(gabp_handle h) {
     S.vals_ok = true;
     h->tuned_L64 = 1;  // one row per lane
     // the cooperative launch for small graphs: one block per two slices, all co-resident
-    h->coop64 = 0;
+    h->coop64 = h->coop64f = 0;
     int coop_attr = 0;
     cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, h->device);
     if (coop_attr && S.ns <= kCoopMaxSlices) {
+      const int want = (S.ns * 32 + kCoopThreads - 1) / kCoopThreads;
       int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k64_coop, kCoopThreads, 0) == cudaSuccess &&
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k64_coop<false>, kCoopThreads, 0) == cudaSuccess &&
           per_sm > 0)
-        h->coop64 = std::min((S.ns * 32 + kCoopThreads - 1) / kCoopThreads, std::min(per_sm * h->num_sms, h->max_blocks));
+        h->coop64 = std::min(want, std::min(per_sm * h->num_sms, h->max_blocks));
+      per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k64_coop<true>, kCoopThreads, 0) == cudaSuccess &&
+          per_sm > 0)
+        h->coop64f = std::min(want, std::min(per_sm * h->num_sms, h->max_blocks));
       cudaGetLastError();
     }
   } else if (!S.vals_ok) {
@@ -708,7 +873,7 @@ gabp_status ensure_w64(gabp_handle h) {
 
 void free_w64(gabp_handle h) {
   Work64 &w = h->w64;
-  cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]); cudaFree(w.bar);
+  cudaFree(w.M[0]); cudaFree(w.M[1]); cudaFree(w.N[0]); cudaFree(w.N[1]); cudaFree(w.bar); cudaFree(w.C);
   Sell64 &S = w.sl;
   cudaFree(S.srow); cudaFree(S.sp); cudaFree(S.sci); cudaFree(S.srev); cudaFree(S.sav); cudaFree(S.c2s);
   w = Work64{};
@@ -732,6 +897,9 @@ static Args64 args64(gabp_handle h) {
   a.N1 = h->w64.N[1];
   a.ctl = h->ctl;
   a.partials = h->partials;
+  a.C = h->w64.C;
+  a.freeze = h->opt.freeze_precisions && h->opt.variant == GABP_VARIANT_NODE && h->opt.accel == ACC_NONE &&
+             h->w64.C != nullptr;
   return a;
 }
 
@@ -750,6 +918,10 @@ static void launch_round(gabp_handle h, const Args64 &a) {
   } else if (h->opt.accel == ACC_STEFFENSEN) {
     k64_node<ACC_STEFFENSEN><<<slice_grid(h, k64_node<ACC_STEFFENSEN>), kBlock, 0, h->stream>>>(a);
     k64_steff<<<slice_grid(h, k64_steff), kBlock, 0, h->stream>>>(a);
+  } else if (a.freeze) {
+    k64_frz<3><<<slice_grid(h, k64_frz<3>), kBlock, 0, h->stream>>>(a);
+    k64_frz<2><<<slice_grid(h, k64_frz<2>), kBlock, 0, h->stream>>>(a);
+    k64_frz<1><<<slice_grid(h, k64_frz<1>), kBlock, 0, h->stream>>>(a);
   } else {
     k64_node<ACC_NONE><<<slice_grid(h, k64_node<ACC_NONE>), kBlock, 0, h->stream>>>(a);
   }
@@ -759,7 +931,7 @@ static void launch_round(gabp_handle h, const Args64 &a) {
 // same graph serves every replay and every solve on this handle).
 static gabp_status get_graph64(gabp_handle h, cudaGraphExec_t *out) {
   const int K = h->opt.check_every;
-  const int key = (h->opt.variant << 12) ^ (h->opt.accel << 24) ^ K;
+  const int key = (h->opt.variant << 12) ^ (h->opt.accel << 24) ^ (h->opt.freeze_precisions << 28) ^ K;
   if (h->g64 && h->g64_key == key) {
     *out = h->g64;
     return GABP_OK;
@@ -793,6 +965,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     GABP_CUDA(cudaMemcpyAsync(h->w64.M[0], h->w64.M[1], sizeof(double2) * Es, cudaMemcpyDeviceToDevice,
                               h->stream));
   h->w64.valid = false;
+  if (h->opt.freeze_precisions && !h->w64.C)  // the frozen coefficients' store
+    GABP_CUDA(cudaMalloc(&h->w64.C, sizeof(double) * Es));
   Args64 a = args64(h);
   // round-0 state (Algorithm 1 step 1): control block pointed at b, zero messages
   auto init = [&]() -> gabp_status {
@@ -821,8 +995,9 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   if ((s = init()) != GABP_OK) return s;
 
   // small and medium graphs: every round in one cooperative launch
+  const int coop_grid = a.freeze ? h->coop64f : h->coop64;
   const bool coop = h->w64.sl.ns <= kCoopMaxSlices && h->opt.variant == GABP_VARIANT_NODE &&
-                    h->opt.accel == ACC_NONE && h->coop64;
+                    h->opt.accel == ACC_NONE && coop_grid > 0;
   const bool use_graph = !coop && h->stream != nullptr && h->opt.graphs;
   cudaGraphExec_t ge = nullptr;
   if (use_graph) {
@@ -834,7 +1009,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   bool done = false;
   if ((s = read_ctl(h)) != GABP_OK) return s;
   done = h->ctl_host->done;
-  const int per_round = h->opt.variant == GABP_VARIANT_EDGE || h->opt.accel == ACC_STEFFENSEN ? 2 : 1;
+  const int per_round =
+      a.freeze ? 3 : h->opt.variant == GABP_VARIANT_EDGE || h->opt.accel == ACC_STEFFENSEN ? 2 : 1;
   h->prof.launches += 1;  // k64_init
   int prev_round = 0;
   if (!done && coop) {
@@ -846,8 +1022,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     int max_rounds = max_iter + 2;
     void *args[] = {(void *)&a, (void *)&bar, (void *)&err, (void *)&max_rounds};
     prof_begin(h);
-    cudaError_t le = cudaLaunchCooperativeKernel((void *)k64_coop, dim3(h->coop64), dim3(kCoopThreads), args, 0,
-                                                 h->stream);
+    cudaError_t le = cudaLaunchCooperativeKernel(a.freeze ? (void *)k64_coop<true> : (void *)k64_coop<false>,
+                                                 dim3(coop_grid), dim3(kCoopThreads), args, 0, h->stream);
     if (le != cudaSuccess) return cuda_fail(le, "FP64 cooperative rounds");
     prof_end(h);
     h->prof.launches += 1;
@@ -888,6 +1064,8 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
   h->stats.rounds = c.round;
   h->stats.edge_updates = -1;
   h->stats.refine_steps = 0;
+  h->stats.freeze_round = a.freeze ? c.fround : 0;
+  h->stats.freeze_checks = a.freeze ? c.fchecks : 0;
   if (warm && c.bb == 0.0) {  // b = 0: x = 0 (the warm round-0 records hold the old messages' mean)
     GABP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * g.n, h->stream));
   } else {
