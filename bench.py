@@ -420,7 +420,7 @@ def main():
                   "mean_round_vs_gather_only": (dur_ms / gms) if ph == "mean32" else None}
         del src, idx, out
 
-    ms64, r64, k64, p64, x_fp64 = None, 0, 1, {"ms": {"fp64": 0.0}}, None
+    ms64, r64, k64, p64, x_fp64, ms64fz = None, 0, 1, {"ms": {"fp64": 0.0}}, None, None
     # ---- plain FP64 GaBP on the same system (time to 1e-10)
     for _ in range(max(1, args.warmup) if "fp64" in legs else 0):
         step(s64)
@@ -438,6 +438,24 @@ def main():
         ms64 = e0.elapsed_time(e1) / k64
         p64 = s64.profile(reset=True)
         x_fp64 = x_dev.cpu().numpy()
+        # the same with the precision freeze (options.freeze_precisions): on this graph the
+        # precisions settle about when the means do, so few rounds run frozen
+        sfz = gb.Solver.from_csr(m, precision=gb.GABP_PREC_FP64, freeze_precisions=1, **gkw)
+        for _ in range(max(1, args.warmup)):
+            step(sfz)
+        barrier()
+        e0.record()
+        rfz = 0
+        for _ in range(k64):
+            rr, relfz = step(sfz)
+            rfz += rr
+        e1.record()
+        barrier()
+        fz = sfz.stats()
+        ms64fz = {"ms_per_solve": e0.elapsed_time(e1) / k64, "rounds": rfz / k64, "relres": relfz,
+                  "freeze_round": fz["freeze_round"], "verifications": fz["freeze_checks"],
+                  "max_abs_diff_vs_fp64_plain": float(np.max(np.abs(x_dev.cpu().numpy() - x_fp64)))}
+        sfz.close()
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     # (default options: the refinement loop runs as one CUDA graph, no per-phase timing events)
@@ -488,8 +506,9 @@ def main():
             # plain FP64 GaBP on one right-hand side of the same grid (time to 1e-10), both schedules: the
             # batched solve is compared with 64 x that
             fp64_one = {}
-            for sched in (0, 1):
-                s1 = gb.Solver.from_csr(mg, precision=gb.GABP_PREC_FP64, schedule=sched, **gkw)
+            for sched in (0, 1, 2):  # 2: the parallel schedule with the precision freeze
+                s1 = gb.Solver.from_csr(mg, precision=gb.GABP_PREC_FP64, schedule=int(sched == 1),
+                                        freeze_precisions=int(sched == 2), **gkw)
                 b1 = Bb[0].contiguous()
                 x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000)
                 barrier()
@@ -498,9 +517,9 @@ def main():
                 x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000, x=x1)
                 e11.record()
                 barrier()
-                fp64_one["serial" if sched else "parallel"] = {"ms_one_rhs": e10.elapsed_time(e11), "rounds": int(it1),
-                                                               "status": int(st1), "relres": rel1,
-                                                               "ms_x64": 64 * e10.elapsed_time(e11)}
+                fp64_one[("parallel", "serial", "parallel_frozen_precisions")[sched]] = {
+                    "ms_one_rhs": e10.elapsed_time(e11), "rounds": int(it1), "status": int(st1), "relres": rel1,
+                    "ms_x64": 64 * e10.elapsed_time(e11), "freeze_round": s1.stats()["freeze_round"]}
                 s1.close()
                 del x1
             cpu_b = None
@@ -754,7 +773,8 @@ def main():
                 if oracle.host_threads():
                     _, tac = oracle.broadcast_timed(g1, b1, 2000, threads=True, tol=1e-12)
                     c1["oracle_ms_all_cores"] = tac * 1e3
-            for name, kw in (("parallel", {}), ("serial", {"schedule": 1}),
+            for name, kw in (("parallel", {}), ("parallel_frozen_precisions", {"freeze_precisions": 1}),
+                             ("serial", {"schedule": 1}),
                              ("serial_steffensen", {"schedule": 1, "accel": 2}),
                              ("parallel_steffensen", {"accel": 2})):
                 sc = gb.Solver.from_csr(g1, precision=gb.GABP_PREC_FP64, **kw, **gkw)
@@ -857,7 +877,9 @@ def main():
             "phases_ms_per_step": {k: v / args.steps for k, v in prof["ms"].items()},
             "rounds_per_step_by_phase": {k: v / args.steps for k, v in prof["rounds"].items()},
             "gpu_launches": launches_timed,
-            "time_to_1e-10_ms": {"fp32_refine": ms_step, "fp64_plain": ms64},
+            "time_to_1e-10_ms": {"fp32_refine": ms_step, "fp64_plain": ms64,
+                                 "fp64_frozen_precisions": None if ms64fz is None else ms64fz["ms_per_solve"]},
+            "fp64_frozen_precisions": ms64fz,
             "fp64_plain": None if ms64 is None else {
                 "ms_per_solve": ms64, "rounds": r64 / k64, "edge_updates_per_s": E * (r64 / k64) / (ms64 / 1e3),
                 "phase_ms": p64["ms"]["fp64"] / k64,
