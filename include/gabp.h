@@ -324,7 +324,10 @@ gabp_status gabp_marginal_precisions(gabp_handle h, double *Pi);
 /* Messages of the last FP64 solve at its returned round (or sweep), in the receiver
  * layout of the input CSR: for slot p of row i with col[p] = k != i,
  * P[p] = P_ki and hm[p] = P_ki * mu_ki (the information-form mean message);
- * diagonal slots get 0.  Device arrays of nnz doubles. */
+ * diagonal slots get 0.  After a solve with options.freeze_precisions the precision
+ * messages are those of the stored round or the round before it (later rounds do not
+ * rewrite them; the two agree to 16 units in the last place).  Device arrays of nnz
+ * doubles. */
 gabp_status gabp_get_messages(gabp_handle h, double *P, double *hm);
 
 /* Gradient of a scalar loss through x = A^{-1} b, given lambda = A^{-1} dL/dx

@@ -36,9 +36,14 @@ __device__ __forceinline__ double rcp64(double d) {
   return y;
 }
 
-// d == +0 or -0, tested on the bit pattern (integer pipe).
+// d == +0 or -0, tested on the bit pattern.  The two 32-bit halves come out of an
+// inline move so the test stays on the integer pipe: written on the 64-bit pattern
+// in C, it is recognised as d == 0.0 and becomes an FP64 compare, one more
+// instruction per message on the FP64 pipe that bounds the FP64 rounds.
 __device__ __forceinline__ bool is_zero64(double d) {
-  return (((unsigned long long)__double_as_longlong(d)) << 1) == 0ull;
+  unsigned lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(d));
+  return ((hi << 1) | lo) == 0u;
 }
 
 template <typename T>

@@ -204,7 +204,7 @@ __device__ __forceinline__ void plain_slice(const Args64 &a, int sl, int lane, c
         A[u] = ld_val<COOP>(a.sav + pos);
         const int rp = ld_idx<COOP>(a.srev + pos);
         if (MODE == 3) {
-          c[u] = ld_val<COOP>(a.C + pos);
+          c[u] = COOP ? __ldcg(a.C + pos) : __ldcs(a.C + pos);  // written by this launch when COOP
           rh[u] = ld_msgh<COOP>(Min + rp);  // mean message i -> k of round t-1
         } else {
           rv[u] = ld_msg<COOP>(Min + rp);   // message i -> k of round t-1
