@@ -342,8 +342,16 @@ struct ArgsBS {
   double *col;                     // [2][RP] pass sums, then [2][RP] sweep sums, [RP] previous step
 };
 
+#ifndef GABP_KBS_U
+#define GABP_KBS_U 3
+#endif
+#ifndef GABP_KBS_MINB
+#define GABP_KBS_MINB 6
+#endif
+constexpr int kBsU = GABP_KBS_U;  // slots of a row whose loads are issued together
+
 template <int VEC>
-__global__ void __launch_bounds__(kBlock, 6) kbs_pass(ArgsBS a, int c, int skip0, int skipn) {
+__global__ void __launch_bounds__(kBlock, GABP_KBS_MINB) kbs_pass(ArgsBS a, int c, int skip0, int skipn) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
   const int RP = a.RP;
@@ -364,25 +372,32 @@ __global__ void __launch_bounds__(kBlock, 6) kbs_pass(ArgsBS a, int c, int skip0
     for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
     const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
     int e = s0;
-    for (; e + 1 < s1; e += 2) {  // two slots with their loads issued together
-      const int k0 = a.sci[e], k1 = a.sci[e + 1];
-      const float2 cf0 = a.sCF[e], cf1 = a.sCF[e + 1];
-      float hs0[VEC], hs1[VEC], hk0[VEC], hk1[VEC], hn0[VEC], hn1[VEC];
-      ldv_cs<VEC>(a.sH + (size_t)e * RP + c0, hs0);
-      ldv_cs<VEC>(a.sH + (size_t)(e + 1) * RP + c0, hs1);
-      ldv<VEC>(a.hfire + (size_t)k0 * RP + c0, hk0);
-      ldv<VEC>(a.hfire + (size_t)k1 * RP + c0, hk1);
+    for (; e + kBsU <= s1; e += kBsU) {  // kBsU slots with their loads issued together
+      int k[kBsU];
+      float2 cf[kBsU];
+      float hs[kBsU][VEC], hk[kBsU][VEC];
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) {
-        hn0[v] = cf0.x * (hk0[v] - cf0.y * (hj[v] - hs0[v]));  // message k -> j, k firing now
-        hn1[v] = cf1.x * (hk1[v] - cf1.y * (hj[v] - hs1[v]));  // (reverse message recomputed)
-        acc[v] += hn0[v];
-        acc[v] += hn1[v];
+      for (int u = 0; u < kBsU; ++u) {
+        k[u] = a.sci[e + u];
+        cf[u] = a.sCF[e + u];
       }
-      stv_cs<VEC>(a.sH + (size_t)e * RP + c0, hn0);
-      stv_cs<VEC>(a.sH + (size_t)(e + 1) * RP + c0, hn1);
+#pragma unroll
+      for (int u = 0; u < kBsU; ++u) {
+        ldv_cs<VEC>(a.sH + (size_t)(e + u) * RP + c0, hs[u]);
+        ldv<VEC>(a.hfire + (size_t)k[u] * RP + c0, hk[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kBsU; ++u) {
+        float hn[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          hn[v] = cf[u].x * (hk[u][v] - cf[u].y * (hj[v] - hs[u][v]));  // message k -> j, k firing now
+          acc[v] += hn[v];                                              // (reverse message recomputed)
+        }
+        stv_cs<VEC>(a.sH + (size_t)(e + u) * RP + c0, hn);
+      }
     }
-    if (e < s1) {
+    for (; e < s1; ++e) {
       const int k = a.sci[e];
       const float2 cf = a.sCF[e];
       float hs[VEC], hk[VEC], hn[VEC];
