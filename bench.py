@@ -506,9 +506,9 @@ def main():
             # plain FP64 GaBP on one right-hand side of the same grid (time to 1e-10), both schedules: the
             # batched solve is compared with 64 x that
             fp64_one = {}
-            for sched in (0, 1, 2):  # 2: the parallel schedule with the precision freeze
-                s1 = gb.Solver.from_csr(mg, precision=gb.GABP_PREC_FP64, schedule=int(sched == 1),
-                                        freeze_precisions=int(sched == 2), **gkw)
+            for sched in (0, 1, 2, 3):  # 2, 3: the parallel and serial schedules with the precision freeze
+                s1 = gb.Solver.from_csr(mg, precision=gb.GABP_PREC_FP64, schedule=int(sched in (1, 3)),
+                                        freeze_precisions=int(sched >= 2), **gkw)
                 b1 = Bb[0].contiguous()
                 x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000)
                 barrier()
@@ -517,7 +517,7 @@ def main():
                 x1, st1, it1, rel1 = s1.solve(b1, tol=TOL, max_iter=5000, x=x1)
                 e11.record()
                 barrier()
-                fp64_one[("parallel", "serial", "parallel_frozen_precisions")[sched]] = {
+                fp64_one[("parallel", "serial", "parallel_frozen_precisions", "serial_frozen_precisions")[sched]] = {
                     "ms_one_rhs": e10.elapsed_time(e11), "rounds": int(it1), "status": int(st1), "relres": rel1,
                     "ms_x64": 64 * e10.elapsed_time(e11), "freeze_round": s1.stats()["freeze_round"]}
                 s1.close()

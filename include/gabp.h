@@ -87,8 +87,9 @@ typedef struct {
                            Plain FP64 solves (node variant, no acceleration) of graphs of at most
                            131,072 rows run every round in one cooperative launch that decides on
                            the device, and do not use it */
-  int freeze_precisions;/* plain FP64 solves (node variant, no acceleration): 1 = freeze the precision
-                           messages once they have stopped moving.  Screen: after two consecutive
+  int freeze_precisions;/* plain FP64 solves (node variant or serial schedule, no acceleration): 1 =
+                           freeze the precision messages once they have stopped moving (on the serial
+                           schedule "round" below reads "sweep").  Screen: after two consecutive
                            rounds in which no node's P~_i moved by more than 16 units in the last
                            place (~2^-48 relative), one round checks every precision message against its previous
                            round's the same way while it stores each edge's coefficient
@@ -98,8 +99,9 @@ typedef struct {
                            solve's; after it x differs from the plain iterate by rounding only.
                            Pays on solves that need many more rounds than the precisions do
                            (FP64-bound rounds); the screen costs a few percent per round.  0 =
-                           every round updates both (Algorithm 2 as printed).  Other paths
-                           ignore it (the FP32 path always freezes).  Default 0 */
+                           every round updates both (Algorithm 2 as printed).  The edge variant
+                           and the accelerated solves ignore it (the FP32 path always freezes).
+                           Default 0 */
   double inner_tol;     /* loosest target of an FP32 inner solve (relative change of its iterate); each
                            inner solve aims at min(inner_tol, max(1e-6, 0.1 tol ||b|| / ||r||)),
                            the reduction still needed.  Default 1e-4 */

@@ -174,6 +174,8 @@ struct ArgsS64 {
   double *sh1;    // Steffensen (nullptr otherwise): mean messages after a cycle's first sweep
   double *sx0;    // Steffensen: the cycle's starting iterate x_n (input order)
   double *sx1;    // Steffensen: x_{n+1} (input order)
+  double *coef;   // precision freeze: coefficient -A_kj / P_k\j per serial slot (freeze != 0)
+  int freeze;     // options.freeze_precisions on a plain serial solve
   DevCtl *ctl;
   double *partials;
 };
@@ -188,17 +190,22 @@ __global__ void ks64_init(ArgsS64 a) {
 
 // Pass c: the nodes of colour c fire (every other row updates its colour-c
 // segment), then the rows of colour c + 1 form their firing aggregates.
+// With the precision freeze (state fs of the sweep, see freeze_step): a verify
+// sweep (fs 1) also compares every new precision message with the one it
+// replaces and stores the coefficient -A / P_k\j; a frozen sweep (fs 2) updates
+// the mean messages only, with the stored coefficients.
 template <int L>
 __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0, int skipn) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
+  const int fs = a.freeze ? ctl->fstate : -1;
   const int cn = c + 1 == a.C ? 0 : c + 1;
   const int nv = a.n - skipn;
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  int bad = 0;
+  int bad = 0, moving = 0;
   for (int base = warp * RPW; base < nv; base += nwarps * RPW) {
     const int v = base + sw;
     const int j = pass_row(v, skip0, skipn);
@@ -206,15 +213,28 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
     bool fires_next = false;
     if (v < nv) {
       const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
-      for (int e = s0 + sl; e < s1; e += L) {
-        const int k = a.sci[e];
-        const double A = a.sav[e];
-        const double2 fk = a.fire[k];         // k's aggregate when it fires
-        const double2 rv = a.SM[a.srev[e]];   // message j -> k as k holds it
-        const double d = fk.x - rv.x;         // P_{k\j}
-        bad |= is_zero64(d);
-        const double r = rcp64(d);
-        a.SM[e] = make_double2(-A * A * r, -A * (fk.y - rv.y) * r);
+      if (fs == 2) {
+        for (int e = s0 + sl; e < s1; e += L) {
+          const double2 fk = a.fire[a.sci[e]];
+          const double rh = reinterpret_cast<const double *>(a.SM + a.srev[e])[1];
+          reinterpret_cast<double *>(a.SM + e)[1] = a.coef[e] * (fk.y - rh);  // mean message only
+        }
+      } else {
+        for (int e = s0 + sl; e < s1; e += L) {
+          const int k = a.sci[e];
+          const double A = a.sav[e];
+          const double2 fk = a.fire[k];         // k's aggregate when it fires
+          const double2 rv = a.SM[a.srev[e]];   // message j -> k as k holds it
+          const double d = fk.x - rv.x;         // P_{k\j}
+          bad |= is_zero64(d);
+          const double r = rcp64(d);
+          const double2 m = make_double2(-A * A * r, -A * (fk.y - rv.y) * r);
+          if (fs == 1) {
+            moving |= ulp_apart(m.x, a.SM[e].x);  // the message this one replaces
+            a.coef[e] = -A * r;
+          }
+          a.SM[e] = m;
+        }
       }
       fires_next = a.scol[j] == cn;
     }
@@ -231,19 +251,23 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
     if (fires_next && sl == 0) a.fire[j] = make_double2(a.sad[j] + P, a.sb[j] + h);
   }
   if (bad) atomicOr(&ctl->edge_bad, 1);
+  if (moving) atomicOr(&ctl->fmove, 1);
 }
 
 // After a sweep: x = h~ / P~ and P from every current message (Algorithm 1
 // step 4), x written in the input order.
+// A screening sweep of the precision freeze (fs 0, from the second sweep on) also
+// flags a node whose P moved since the previous sweep.
 template <int L>
 __global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
+  const bool screen = a.freeze && ctl->fstate == 0 && ctl->round >= 1;
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  int bad = 0;
+  int bad = 0, moving = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int j = base + sw;
     double P = 0.0, h = 0.0;
@@ -259,11 +283,13 @@ __global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
       P += a.sad[j];
       h += a.sb[j];
       bad |= is_zero64(P);
+      if (screen) moving |= ulp_apart(P, a.sPm[j]);
       a.sPm[j] = P;
       a.x[a.oid[j]] = h / P;
     }
   }
   if (bad) atomicOr(&ctl->edge_bad, 2);
+  if (moving) atomicOr(&ctl->fmove, 1);
 }
 
 // ||b - A x||^2 of the sweep's x (input order) and the decision (Algorithm 1
@@ -295,6 +321,11 @@ __global__ void __launch_bounds__(kBlock) ks64_decide(ArgsS64 a) {
     const int t = ctl->round + 1;
     ctl->round = t;
     ctl->rr = tot[0];
+    if (a.freeze) {  // the freeze state after this sweep (the first sweep screens nothing)
+      const int fs = ctl->fstate;
+      if (fs < 2 && (fs == 1 || t >= 2)) freeze_step(ctl, fs, t, (double)ctl->fmove);
+      ctl->fmove = 0;
+    }
     if (ctl->edge_bad) {
       ctl->status = GABP_BREAKDOWN; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
     } else if (!isfinite(tot[0])) {
@@ -395,6 +426,7 @@ __global__ void ks64_ctl(DevCtl *c, int max_iter, double bb, double tol2) {
   c->arrive = 0;
   c->edge_bad = 0;
   c->no_stop = 0;
+  c->fstate = c->pstat = c->fround = c->pfail = c->fchecks = c->fmove = 0;
 }
 
 // ||b||^2 (FP64, deterministic)
@@ -565,7 +597,7 @@ void free_ws(gabp_handle h) {
   cudaFree(s.oid); cudaFree(s.nid); cudaFree(s.srp); cudaFree(s.scol); cudaFree(s.sad); cudaFree(s.sb);
   cudaFree(s.SM); cudaFree(s.fire); cudaFree(s.sPm); cudaFree(s.sCF); cudaFree(s.sH); cudaFree(s.hfire);
   cudaFree(s.srhs); cudaFree(s.sinvP); cudaFree(s.bin); cudaFree(s.xin); cudaFree(s.sh1); cudaFree(s.sx0);
-  cudaFree(s.sx1);
+  cudaFree(s.sx1); cudaFree(s.coef);
   if (h->gS64) cudaGraphExecDestroy(h->gS64);
   if (h->gS32) cudaGraphExecDestroy(h->gS32);
   h->gS64 = h->gS32 = nullptr;
@@ -734,6 +766,8 @@ static ArgsS64 args_s64(gabp_handle h, const double *b, double *x) {
   a.sh1 = stf ? s.sh1 : nullptr;
   a.sx0 = stf ? s.sx0 : nullptr;
   a.sx1 = stf ? s.sx1 : nullptr;
+  a.freeze = h->opt.freeze_precisions && h->opt.accel == 0 && s.coef != nullptr;
+  a.coef = a.freeze ? s.coef : nullptr;
   a.ctl = h->ctl; a.partials = h->partials;
   return a;
 }
@@ -756,6 +790,8 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
     GABP_CUDA(cudaMalloc(&s.bin, sizeof(double) * g.n));
     GABP_CUDA(cudaMalloc(&s.xin, sizeof(double) * g.n));
   }
+  if (h->opt.freeze_precisions && h->opt.accel == 0 && !s.coef)  // the frozen coefficients
+    GABP_CUDA(cudaMalloc(&s.coef, sizeof(double) * Ea));
   if (h->opt.accel == 2 && !s.sh1) {  // Steffensen's iterations
     GABP_CUDA(cudaMalloc(&s.sh1, sizeof(double) * Ea));
     GABP_CUDA(cudaMalloc(&s.sx0, sizeof(double) * g.n));
@@ -793,7 +829,7 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   ks64_ctl<<<1, 1, 0, h->stream>>>(h->ctl, std::max(1, max_iter), bb, tol * tol);
   GABP_CUDA(cudaGetLastError());
   const bool stf = h->opt.accel == 2;
-  const int key = L | (s.C << 8) | (stf ? 1 << 30 : 0);
+  const int key = L | (s.C << 8) | (stf ? 1 << 30 : 0) | (a.freeze ? 1 << 29 : 0);
   gabp_status rs = GABP_OK;
   GABP_DISPATCH_L(L, {
     const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_pass<LL>));
@@ -814,6 +850,8 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   const DevCtl c = *h->ctl_host;
   h->stats.rounds = c.round;
+  h->stats.freeze_round = a.freeze ? c.fround : 0;
+  h->stats.freeze_checks = a.freeze ? c.fchecks : 0;
   s.result_round = c.round;
   if (iters) *iters = c.iters;
   if (relres) *relres = std::sqrt(c.rr / bb);

@@ -113,48 +113,6 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
   __threadfence();
 }
 
-// Precision freeze (options.freeze_precisions).  The precision messages do not
-// depend on b and converge on their own; once they have stopped moving (to
-// rounding) the coefficients c = -A / P_k\i are constant and later rounds need
-// only the mean messages.  States (fs, the state a round ran in):
-//   0 screen: every node's P~_i is compared with its previous round's; after
-//     2 << min(failed verifications, 5) consecutive rounds in which none moved,
-//     the next round verifies;
-//   1 verify: every precision message is compared with its own previous round's
-//     while the round stores its coefficients and 1/P~; if none moved the
-//     precisions are frozen from the next round on, else back to screening (a
-//     message can still move while every aggregate it enters is stagnant, where
-//     a cavity P~_k - P_ik cancels; the longer screens bound the verify rounds);
-//   2 frozen: mean messages only, with the stored coefficients.
-// "Moved": more than 16 units in the last place apart (bit patterns as integers;
-// about 2^-48 relative).  Stagnant precision messages still jitter by a few units
-// in the last place (rounding of the sums and differences they come from, larger
-// where P~_k = A_kk + sum of negative messages cancels), so a tighter bar may never
-// pass; the mean iteration with coefficients this close to their limits stays
-// within rounding of the plain iterate.
-__device__ __forceinline__ void freeze_step(DevCtl *ctl, int fs, int t, double moving) {
-  if (fs == 0) {
-    ctl->pstat = moving == 0.0 ? ctl->pstat + 1 : 0;
-    if (ctl->pstat >= (2 << min(ctl->pfail, 5))) ctl->fstate = 1;
-  } else if (fs == 1) {
-    ctl->fchecks += 1;
-    if (moving == 0.0) {
-      ctl->fstate = 2;
-      ctl->fround = t;
-    } else {
-      ctl->fstate = 0;
-      ctl->pstat = 0;
-      ctl->pfail += 1;
-    }
-  }
-}
-
-// More than 16 units in the last place apart (any NaN, a sign change or a zero
-// against a non-zero counts as apart; two equal bit patterns do not).
-__device__ __forceinline__ bool ulp_apart(double u, double v) {
-  return (unsigned long long)(__double_as_longlong(u) - __double_as_longlong(v) + 16) > 32ull;
-}
-
 // Load flavours of the plain round body: the launch-per-round kernel streams its slot
 // lines (evict first); the cooperative kernel reads data other blocks wrote through L2
 // only and the read-only layout through the non-coherent path (L1 is not invalidated

@@ -161,11 +161,11 @@ def test_failed_verification_then_freeze(gb):
 
 
 def test_paths_without_freeze_unchanged(gb):
-    """The option applies to plain FP64 node rounds only: Aitken, Steffensen, the edge variant, the
-    serial schedule and FP32 + refinement give bitwise the same result with it on."""
+    """The option applies to plain FP64 node rounds and plain serial sweeps only: Aitken, Steffensen
+    (both schedules), the edge variant and FP32 + refinement give bitwise the same result with it on."""
     m = synth.grid2d(32, -1.0, 4.5)
     b = synth.rhs(m.n, 1)
-    for opts in ({"accel": 1}, {"accel": 2}, {"variant": 1}, {"schedule": 1},
+    for opts in ({"accel": 1}, {"accel": 2}, {"variant": 1}, {"schedule": 1, "accel": 2},
                  {"precision": gb.GABP_PREC_FP32_REFINE}):
         a = _solve(gb, m, b, 1e-12, 2000, **opts)
         c = _solve(gb, m, b, 1e-12, 2000, freeze_precisions=1, **opts)
@@ -205,3 +205,39 @@ def test_warm_start_zero_rhs_and_options(gb):
     s.close()
     with pytest.raises(gb.GaBPError):
         gb.Solver.from_csr(m, freeze_precisions=2)
+
+
+SERIAL_CASES = [
+    ("grid2d_32", lambda: synth.grid2d(32, -1.0, 4.5), 1e-12),
+    ("grid3d_32", lambda: synth.grid3d(32, 1.1, 2), 1e-10),
+    ("random_20011", lambda: synth.random_sym(20011, 8, 1.1, 2), 1e-12),
+]
+
+
+@pytest.mark.parametrize("name,make,tol", SERIAL_CASES, ids=[c[0] for c in SERIAL_CASES])
+def test_serial_freeze(gb, name, make, tol):
+    """The serial schedule (sweeps of colour passes, one message store): a screen on the marginal
+    precisions after each sweep, a verifying sweep that stores the coefficients, then mean-only
+    sweeps.  x after a fixed number of sweeps is bitwise the plain sweeps' up to the stored sweep
+    and the oracle's serial iterate to 1e-12 after it; converged, the sweep count is the plain one
+    within one and x the oracle's to 100 tol."""
+    m = make()
+    b = synth.rhs(m.n, 4)
+    p = _solve(gb, m, b, tol, 5000, schedule=1)
+    f = _solve(gb, m, b, tol, 5000, schedule=1, freeze_precisions=1)
+    assert p["status"] == f["status"] == gb.GABP_OK
+    F = f["freeze_round"]
+    assert 0 < F < f["iters"] and f["freeze_checks"] >= 1, (F, f["iters"], f["freeze_checks"])
+    assert abs(f["iters"] - p["iters"]) <= 1
+    ref = oracle.gabp_serial(m, b, max_iter=5000, tol=tol)
+    assert ref["status"] == oracle.OK
+    assert _maxrel(f["x"], ref["x"]) <= 100 * tol
+    for t in (F, F + 1, F + 7):
+        g = _solve(gb, m, b, 0.0, t, schedule=1, freeze_precisions=1)
+        assert g["iters"] == t
+        if t <= F:
+            q = _solve(gb, m, b, 0.0, t, schedule=1)
+            assert np.array_equal(g["x"], q["x"]), t
+        else:
+            r = oracle.gabp_serial(m, b, max_iter=t, tol=0.0)
+            assert np.allclose(g["x"], r["x"], rtol=1e-12, atol=1e-14 * np.max(np.abs(r["x"]))), t
