@@ -615,7 +615,8 @@ def main():
                      "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
                      "ms_per_batch": msm, "ms_per_batch_all": times_m, "kernel_ms": pm["ms"]["multi"] / reps_m,
                      "kernel": "grid-persistent" if tuned_m["multi_mode"] == 1 else "teams",
-                     "grid_shape": {"lanes_per_row": tuned_m["multi_grid"][0], "slots_per_lane": tuned_m["multi_grid"][1]},
+                     "grid_shape": {"lanes_per_row": tuned_m["multi_grid"][0], "slots_per_lane": tuned_m["multi_grid"][1],
+                                    "sliced_layout": tuned_m["multi_grid_sliced"]},
                      "edge_updates": stm_["edge_updates"],
                      "edge_updates_per_s": stm_["edge_updates"] / (msm / 1e3),
                      "rounds_per_system": {"min": int(itsm.min()), "median": int(np.median(itsm)), "max": int(itsm.max())},

@@ -123,7 +123,10 @@ typedef struct {
   int prec_stop_log2;   /* FP32 precision phase stops at a max relative change <= 2^-prec_stop_log2 in
                            two consecutive rounds (10..23).  Default 16 */
   int multi_mode;       /* gabp_solve_systems kernel: 0 autotune, 1 grid-persistent (every round sweeps
-                           all running systems), 2 cluster / single-block teams.  Default 0 */
+                           all running systems; its shape autotuned over the row-CSR and the sliced
+                           layouts), 2 cluster / single-block teams, 3 grid-persistent on the sliced
+                           layout only (each system's rows sorted by degree and cut into 32-row
+                           slices, one lane per row; built once per offsets array).  Default 0 */
   int overlap_precision; /* FP32_REFINE, one right-hand side: 1 = while the precisions converge, the
                            rounds update precision AND mean messages (Algorithm 2's full round), so
                            the first inner solve starts with the precision phase; 0 = precision-only
@@ -432,7 +435,8 @@ gabp_status gabp_residual_history(gabp_handle h, double *relres, int32_t cap, in
  * else the precision-only round) and the mean round's shape, packed as
  * lanes | unroll << 8; the multi-system size split;
  * the multi-system kernel (1 grid-persistent, 2 teams) | the grid-persistent
- * kernel's shape << 8.  The FP64 and FP32 choices are remembered for the
+ * kernel's shape << 8 (shape: lanes | unroll << 8, plus 1 << 16 on the sliced
+ * layout).  The FP64 and FP32 choices are remembered for the
  * process per (device, n, directed-edge count): a later handle of a matrix of
  * that size starts with them instead of tuning again. */
 gabp_status gabp_tuned_shapes(gabp_handle h, int32_t *fp64_lanes, int32_t *prec32_shape, int32_t *mean32_shape,

@@ -287,12 +287,14 @@ def gabp_solve_noalloc(n, nnz, rowptr_ptr, col_ptr, val_ptr, b_ptr, x_ptr, tol, 
 
 def gabp_tuned_shapes(h):
     """Returns dict of the autotuner's choices: fp64 lanes, (lanes, unroll) of the FP32 kernels, multi-system
-    split and kernel (1 grid-persistent, 2 teams)."""
+    split and kernel (1 grid-persistent, 2 teams), the grid-persistent kernel's (lanes, unroll) and whether
+    it runs on the sliced layout."""
     a, b, c, d, e = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int32(0)
     lib.gabp_tuned_shapes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d), ctypes.byref(e))
     sh = lambda v: (v & 0xFF, v >> 8)
     return {"fp64_lanes": a.value, "prec32": sh(b.value), "mean32": sh(c.value), "multi_split": d.value,
-            "multi_mode": e.value & 0xFF, "multi_grid": sh(e.value >> 8)}
+            "multi_mode": e.value & 0xFF, "multi_grid": ((e.value >> 8) & 0xFF, (e.value >> 16) & 0xFF),
+            "multi_grid_sliced": bool((e.value >> 24) & 1)}
 
 
 def gabp_destroy(h):

@@ -205,6 +205,26 @@ struct WorkS {
   float *sinvP = nullptr;      // [n] 1 / P~ (new order)
 };
 
+// Sliced layout of the independent-systems grid kernel: every system's rows sorted by
+// degree (descending, stable) in windows of 4096 and cut into 32-row slices, the last
+// slice of a system padded with rows -1, so that a slice belongs to one system; slot j
+// of the slice's rows is the contiguous line sp[s] + 32 j + lane (sender -1 past a
+// row's degree).  Built for one offsets array; the values are refreshed after
+// gabp_set_values.
+struct GSell {
+  std::vector<int> off;        // the offsets the layout was built for
+  int ns = 0;                  // slices
+  int Es = 0;                  // slots, padding included
+  bool vals_ok = false;
+  int *srow = nullptr;         // [32 ns] row of each slice lane, -1 for padding
+  int *sp = nullptr;           // [ns + 1] first slot of each slice (multiples of 32)
+  int *ssys = nullptr;         // [ns] system of each slice
+  int *sci = nullptr;          // [Es] sender, -1 for padding
+  float *sav = nullptr;        // [Es] A_ij (FP32), 0 for padding
+  float *MP[2] = {nullptr, nullptr}, *H[2] = {nullptr, nullptr};  // [Es] precision / mean chains
+  float2 *CF = nullptr;        // [Es] frozen coefficients
+};
+
 // Single-loop convergence fix (fixloop.cu)
 struct WorkF {
   double2 *M[2] = {nullptr, nullptr};
@@ -291,6 +311,7 @@ struct gabp_handle_s {
   bool values_ok = true;            // false after a rejected gabp_set_values
   int multi_mode = 0;               // 0 untuned, 1 grid-persistent kernel, 2 cluster / single-block teams
   int multi_grid_shape = 0;         // autotuned shape of the grid-persistent kernel (0 untuned)
+  gabp::GSell *gsl = nullptr;       // sliced layout of the grid-persistent kernel (built on first use)
   // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
   int coop64 = 0;                   // blocks of the FP64 cooperative rounds (0: graph too large or no support)
   int coop64f = 0;                  // the same for the cooperative rounds with the precision freeze
@@ -535,11 +556,16 @@ gabp_status solve_from_initial(gabp_handle h, const double *b, double *x, double
 gabp_status messages64_from(gabp_handle h, const double2 *M, double *P, double *hm);
 // Shapes (lanes per row L | slots per lane U << 8) of the grid-persistent
 // multi-system kernel the autotuner chooses from.
-constexpr int kGridShapes[9] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8),
-                                 1 | (2 << 8), 2 | (2 << 8), 1 | (1 << 8), 2 | (1 << 8)};
-gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
-                               int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
-                               int shape, float *ms_out);
+// kSliced marks the kernel on the sliced layout (GSell: one lane per row, U slots of a
+// row issued together; L is 1).
+constexpr int kSliced = 1 << 16;
+constexpr int kGridShapes[12] = {1 | (4 << 8), 2 | (4 << 8), 4 | (2 << 8), 4 | (4 << 8), 8 | (2 << 8),
+                                  1 | (2 << 8), 2 | (2 << 8), 1 | (1 << 8), 2 | (1 << 8),
+                                  kSliced | 1 | (1 << 8), kSliced | 1 | (2 << 8), kSliced | 1 | (4 << 8)};
+gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const int *off_host, const double *b,
+                               double *x, double tol, int max_iter, int *d_status, int *d_iters, int *d_refine,
+                               double *d_relres, int shape, float *ms_out);
+void free_gsell(gabp_handle h);
 gabp_status solve_batched32(gabp_handle h, int nrhs, const double *B, double *X, int64_t ld, double tol,
                             int max_iter, int *iters, double *relres_host);
 

@@ -511,21 +511,23 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
     return collect_systems(h, nsys, slots, d_res, d_rel, t, status_host, iters_host, relres_host);
   };
   auto run_grid_shape = [&](int shape, float *t) {
-    return solve_systems_grid(h, nsys, d_off, b, x, tol, max_iter, d_res, d_res + nsys, d_res + 2 * nsys, d_rel,
-                              shape, t);
+    return solve_systems_grid(h, nsys, d_off, offsets_host, b, x, tol, max_iter, d_res, d_res + nsys, d_res + 2 * nsys,
+                              d_rel, shape, t);
   };
   // grid-kernel shape: the lanes option, else the tuned one, else tune it now
   // (each candidate one complete run; the fastest is kept)
+  const int mode = h->opt.multi_split > 0 ? 2 : h->opt.multi_mode ? h->opt.multi_mode : h->multi_mode;
   auto run_grid = [&](float *t) -> gabp_status {
     int shape = 0;
     if (h->opt.lanes >= 1 && h->opt.lanes <= 8) shape = h->opt.lanes | ((h->opt.lanes >= 4 ? 2 : 4) << 8);
-    else shape = h->multi_grid_shape;
+    else if (mode != 3 || (h->multi_grid_shape & kSliced)) shape = h->multi_grid_shape;
     if (shape) return run_grid_shape(shape, t);
     // one run of every candidate, then a second run of the two fastest: the one with the smaller
     // total of its two runs is kept (a single run can be off by a few percent)
     float t1 = 1e30f, t2 = 1e30f;
-    int s1 = kGridShapes[0], s2 = 0;
+    int s1 = 0, s2 = 0;
     for (int c : kGridShapes) {
+      if (mode == 3 && !(c & kSliced)) continue;  // the sliced layout's shapes only
       float tc = 0.f;
       gabp_status e = run_grid_shape(c, &tc);
       if (e != GABP_OK) return e;
@@ -546,8 +548,7 @@ gabp_status solve_systems(gabp_handle h, int nsys, const int *offsets_host, cons
   // kernel choice: the options may force the grid-persistent kernel (mode 1) or
   // teams (mode 2, or any fixed split); otherwise the first call on a handle
   // times both and later calls reuse the faster one
-  const int mode = h->opt.multi_split > 0 ? 2 : h->opt.multi_mode ? h->opt.multi_mode : h->multi_mode;
-  if (mode == 1) {
+  if (mode == 1 || mode == 3) {
     if ((st = run_grid(&ms)) != GABP_OK) return st;
     return finish(ms);
   }

@@ -44,7 +44,12 @@ struct SysState {
 
 struct GridArgs {
   int n, nsys;
-  int chunk;                        // warp steps per chunk (enough chunks per warp to balance the round)
+  int chunk;                        // warp steps (sliced kernel: slices) per chunk, enough chunks per warp
+                                    // to balance the round
+  int ns;                           // sliced kernel: slices, their rows, first slots and systems
+  const int *__restrict__ srow;
+  const int *__restrict__ sp;
+  const int *__restrict__ ssys;
   const int *__restrict__ sys_of;   // row -> system
   const int *__restrict__ rp;
   const int *__restrict__ ci;
@@ -128,6 +133,47 @@ struct WarpAcc {
         atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * sys + 1), (unsigned long long)__double_as_longlong(v1));
       else
         atomicAdd(acc + 4 * sys + 1, v1);
+    }
+  }
+};
+
+// Per-lane running sums of one system for the sliced kernel, whose slices each belong
+// to one system (the system is warp-uniform): the precision and inner rounds' row
+// values fold in FP32 registers (sum, and max for the precision rounds' relative
+// change; a NaN survives the max), the FP64 residual's in FP64, and a warp meets the
+// FP64 pipe only when it flushes (another system, or the end of its pass).
+struct SliceAcc {
+  int s = -1;
+  bool max1 = false;
+  float f0 = 0.f, f1 = 0.f;
+  double d0 = 0.0;
+
+  __device__ __forceinline__ void flush(double *acc) {
+    if (s < 0) return;  // warp-uniform
+    double a0 = (double)f0 + d0, a1 = (double)f1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      const double b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+      a1 = max1 ? nan_max(a1, b1) : a1 + b1;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(acc + 4 * s, a0);
+      if (max1)
+        atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * s + 1), (unsigned long long)__double_as_longlong(a1));
+      else
+        atomicAdd(acc + 4 * s + 1, a1);
+    }
+    s = -1;
+    f0 = f1 = 0.f;
+    d0 = 0.0;
+  }
+  // all lanes call it with the same sys and mx
+  __device__ __forceinline__ void to(double *acc, int sys, bool mx) {
+    if (sys != s) {
+      flush(acc);
+      s = sys;
+      max1 = mx;
     }
   }
 };
@@ -401,6 +447,177 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : (U == 2 ? 4 : 5)) kg_solv
   }
 }
 
+// The same global rounds on the sliced layout (GSell): a warp per 32-row slice, a lane
+// per row, slot j of the slice's rows one contiguous line (ci, av and the message and
+// coefficient arrays are the layout's); U slots of a row have their loads issued
+// together.  A slice belongs to one system, so its phase is warp-uniform and the
+// slices of finished systems are skipped.  Per slot the arithmetic is kg_solve's
+// with one lane per row; the FP64 residual reads the input CSR row by row.
+template <int U>
+__global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : 4) kgs_solve(GridArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  const int nchunks = (a.ns + a.chunk - 1) / a.chunk;
+  for (int round = 0; round < a.max_rounds; ++round) {
+    SliceAcc sacc;
+    int sc = -1, ph = PH_DONE, t = 0, T = 0;  // the current slice's system state (fixed within a round)
+    for (int chunk = warp; chunk < nchunks; chunk += nwarps)
+    for (int sl = chunk * a.chunk; sl < min(a.ns, (chunk + 1) * a.chunk); ++sl) {
+      const int s = a.ssys[sl];
+      if (s != sc) {
+        const SysState S = load_state(a.st + s);
+        sc = s;
+        ph = S.phase;
+        t = S.t;
+        T = S.phase == PH_COEF ? S.Tp : S.Tm;
+      }
+      if (ph == PH_DONE) continue;  // warp-uniform
+      const int i = a.srow[sl * 32 + lane];
+      const int q0 = a.sp[sl];
+      const int p0 = q0 + lane, wd = (a.sp[sl + 1] - q0) >> 5;
+      float facc = 0.f, frel = 0.f;
+      float rhs_i = 0.f, ip_i = 0.f, hprev_i = 0.f;
+      double dacc = 0.0;
+      int bad = 0;
+      if (ph == PH_PREC) {
+        float *Mc = (t & 1) ? a.MP1 : a.MP0;
+        const float *Mo = (t & 1) ? a.MP0 : a.MP1;
+        const float *Pm1 = ring(a.NP0, a.NP1, a.NP2, t + 2);
+        const float Pi2 = (t >= 2 && i >= 0) ? ring(a.NP0, a.NP1, a.NP2, t + 1)[i] : 0.f;
+        for (int j = 0; j < wd; j += U) {
+          int k[U];
+          float A[U], Ps[U], Pp[U], Pk[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int pos = p0 + 32 * (j + u);
+            k[u] = j + u < wd ? __ldcs(a.ci + pos) : -1;
+            if (k[u] >= 0) { A[u] = __ldcs(a.av + pos); Ps[u] = __ldcs(Mc + pos); Pp[u] = __ldcs(Mo + pos); }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (k[u] >= 0) Pk[u] = __ldcg(Pm1 + k[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (k[u] < 0) continue;
+            const float A2 = A[u] * A[u];
+            float Pout = 0.f;
+            if (t >= 2) {
+              const float d1 = Pi2 - Ps[u];
+              bad |= (d1 == 0.f);
+              Pout = -__fdividef(A2, d1);
+            }
+            const float d2 = Pk[u] - Pout;
+            bad |= (d2 == 0.f);
+            const float Pn = -__fdividef(A2, d2);
+            __stcs(Mc + p0 + 32 * (j + u), Pn);
+            facc += Pn;
+            const float dP = fabsf(Pn - Pp[u]);
+            frel = nan_max(frel, dP == 0.f ? 0.f : __fdividef(dP, fabsf(Pn)));
+          }
+        }
+      } else if (ph == PH_COEF) {
+        if (i >= 0) {
+          const float *Ms = (T & 1) ? a.MP1 : a.MP0;
+          const float *PT = ring(a.NP0, a.NP1, a.NP2, T);
+          const float Pi = PT[i];
+          for (int j = 0; j < wd; ++j) {
+            const int pos = p0 + 32 * j;
+            const int k = __ldcs(a.ci + pos);
+            if (k < 0) break;  // a row's padding slots follow its real ones
+            const float A = __ldcs(a.av + pos);
+            const float cout = -A / (Pi - Ms[pos]);
+            const float cin = -A / (__ldcg(PT + k) - cout * A);
+            a.CF[pos] = make_float2(cin, cout);
+          }
+        }
+      } else if (ph == PH_RESID) {
+        if (i >= 0)
+          for (int p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) dacc = fma(a.val[p], __ldcg(a.x + a.col[p]), dacc);
+        for (int j = 0; j < wd; ++j) a.H0[p0 + 32 * j] = 0.f;
+      } else if (ph == PH_INNER) {
+        float *Hc = (t & 1) ? a.H1 : a.H0;
+        const float *Hm1 = ring(a.NH0, a.NH1, a.NH2, t + 2);
+        float hi2 = 0.f;
+        if (i >= 0) {  // the row's own values are requested before its slots
+          hi2 = t >= 2 ? ring(a.NH0, a.NH1, a.NH2, t + 1)[i] : 0.f;
+          rhs_i = a.rhs[i];
+          ip_i = a.invP[i];
+          hprev_i = Hm1[i];
+        }
+        for (int j = 0; j < wd; j += U) {
+          int k[U];
+          float2 cf[U];
+          float hs[U], hk[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int pos = p0 + 32 * (j + u);
+            k[u] = j + u < wd ? __ldcs(a.ci + pos) : -1;
+            if (k[u] >= 0) { cf[u] = __ldcs(a.CF + pos); hs[u] = __ldcs(Hc + pos); }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (k[u] >= 0) hk[u] = __ldcg(Hm1 + k[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (k[u] < 0) continue;
+            const float hout = t >= 2 ? cf[u].y * (hi2 - hs[u]) : 0.f;
+            const float hn = cf[u].x * (hk[u] - hout);
+            __stcs(Hc + p0 + 32 * (j + u), hn);
+            facc += hn;
+          }
+        }
+      }
+      // ---------------------------------------------------------- node part, one lane per row
+      sacc.to(a.acc, s, ph == PH_PREC);
+      if (i >= 0) {
+        if (ph == PH_PREC) {
+          const float P = a.ad[i] + facc;
+          bad |= (P == 0.f);
+          ring(a.NP0, a.NP1, a.NP2, t)[i] = P;
+          sacc.f0 += (float)bad;
+          sacc.f1 = nan_max(sacc.f1, frel);
+        } else if (ph == PH_COEF) {
+          a.invP[i] = 1.f / ring(a.NP0, a.NP1, a.NP2, T)[i];
+          a.x[i] = 0.0;
+        } else if (ph == PH_RESID) {
+          const double r = a.b[i] - dacc;
+          a.rhs[i] = (float)r;
+          a.NH0[i] = (float)r;
+          sacc.d0 = fma(r, r, sacc.d0);
+        } else if (ph == PH_INNER) {
+          const float hnew = rhs_i + facc;
+          ring(a.NH0, a.NH1, a.NH2, t)[i] = hnew;
+          const float xi = hnew * ip_i, dx = (hnew - hprev_i) * ip_i;
+          sacc.f0 = fmaf(dx, dx, sacc.f0);
+          sacc.f1 = fmaf(xi, xi, sacc.f1);
+        } else if (ph == PH_UPDATE) {
+          a.x[i] += (double)(ring(a.NH0, a.NH1, a.NH2, T)[i] * a.invP[i]);
+        }
+      }
+    }
+    sacc.flush(a.acc);
+    const int act = round_end(a);
+    if (act <= 0) return;
+  }
+}
+
+// Slot arrays of the sliced layout from the off-diagonal CSR (one thread per slice lane).
+__global__ void kgs_fill(int nq, const int *__restrict__ srow, const int *__restrict__ sp,
+                         const int *__restrict__ rp, const int *__restrict__ ci, const float *__restrict__ av,
+                         int *sci, float *sav) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int sl = q >> 5, lane = q & 31, i = srow[q];
+  const int p0 = sp[sl] + lane, wd = (sp[sl + 1] - sp[sl]) >> 5;
+  const int e0 = i >= 0 ? rp[i] : 0, deg = i >= 0 ? rp[i + 1] - e0 : 0;
+  for (int j = 0; j < wd; ++j) {
+    const int pos = p0 + 32 * j;
+    sci[pos] = j < deg ? ci[e0 + j] : -1;
+    sav[pos] = j < deg ? av[e0 + j] : 0.f;
+  }
+}
+
 __global__ void kg_init(int nsys, SysState *st, double *acc, const int *__restrict__ offsets, int *sys_of) {
   const int s = blockIdx.x;
   if (s >= nsys) return;
@@ -423,13 +640,17 @@ __global__ void kg_rows_init(int n, const int *__restrict__ rp, const double *__
     ad32[i] = d;
     NP0[i] = d;
     x[i] = 0.0;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) { MP0[e] = 0.f; MP1[e] = 0.f; }
+    if (MP0)  // the CSR kernels' messages (the sliced layout's are cleared with a memset)
+      for (int e = rp[i]; e < rp[i + 1]; ++e) { MP0[e] = 0.f; MP1[e] = 0.f; }
   }
 }
 
-// kernel for a shape code L | U << 8 (unknown codes: (4, 2))
+// kernel for a shape code L | U << 8 (| kSliced for the sliced layout; unknown codes: (4, 2))
 void (*grid_kernel(int code))(GridArgs) {
   switch (code) {
+    case kGridShapes[9]: return kgs_solve<1>;
+    case kGridShapes[10]: return kgs_solve<2>;
+    case kGridShapes[11]: return kgs_solve<4>;
     case kGridShapes[0]: return kg_solve<1, 4>;
     case kGridShapes[1]: return kg_solve<2, 4>;
     case kGridShapes[3]: return kg_solve<4, 4>;
@@ -444,9 +665,85 @@ void (*grid_kernel(int code))(GridArgs) {
 
 }  // namespace
 
-gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const double *b, double *x, double tol,
-                               int max_iter, int *d_status, int *d_iters, int *d_refine, double *d_relres,
-                               int shape, float *ms_out) {
+void free_gsell(gabp_handle h) {
+  GSell *L = h->gsl;
+  if (!L) return;
+  cudaFree(L->srow); cudaFree(L->sp); cudaFree(L->ssys); cudaFree(L->sci); cudaFree(L->sav);
+  cudaFree(L->MP[0]); cudaFree(L->MP[1]); cudaFree(L->H[0]); cudaFree(L->H[1]); cudaFree(L->CF);
+  delete L;
+  h->gsl = nullptr;
+}
+
+// The sliced layout for these offsets (rebuilt when they differ from the cached one),
+// its slot values refreshed after gabp_set_values.
+static gabp_status ensure_gsell(gabp_handle h, int nsys, const int *off) {
+  Graph &g = h->g;
+  GSell *L = h->gsl;
+  if (!(L && (int)L->off.size() == nsys + 1 && std::equal(L->off.begin(), L->off.end(), off))) {
+    free_gsell(h);
+    L = h->gsl = new GSell();
+    std::vector<int> rp(g.n + 1);
+    GABP_CUDA(cudaMemcpyAsync(rp.data(), g.rp, sizeof(int) * (g.n + 1), cudaMemcpyDeviceToHost, h->stream));
+    GABP_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<int> srow, sp(1, 0), ssys, rows;
+    long long slots = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const int a0 = off[s], ns = off[s + 1] - off[s];
+      rows.resize(ns);
+      for (int r = 0; r < ns; ++r) rows[r] = a0 + r;
+      for (int w0 = 0; w0 < ns; w0 += 4096)
+        std::stable_sort(rows.begin() + w0, rows.begin() + std::min(ns, w0 + 4096),
+                         [&](int x, int y) { return rp[x + 1] - rp[x] > rp[y + 1] - rp[y]; });
+      for (int q = 0; q < ns; q += 32) {
+        int wd = 0;
+        for (int l = 0; l < 32; ++l) {
+          const int r = q + l < ns ? rows[q + l] : -1;
+          srow.push_back(r);
+          if (r >= 0) wd = std::max(wd, rp[r + 1] - rp[r]);
+        }
+        slots += 32LL * wd;
+        if (slots > 0x7fffffffLL) {
+          set_last_error("gabp_solve_systems: the sliced layout would exceed 2^31 slots");
+          free_gsell(h);
+          return GABP_ERR_NOMEM;
+        }
+        sp.push_back((int)slots);
+        ssys.push_back(s);
+      }
+    }
+    L->off.assign(off, off + nsys + 1);
+    L->ns = (int)ssys.size();
+    L->Es = (int)slots;
+    const size_t Ea = std::max<size_t>(1, (size_t)L->Es);
+    GABP_CUDA(cudaMalloc(&L->srow, sizeof(int) * srow.size()));
+    GABP_CUDA(cudaMalloc(&L->sp, sizeof(int) * sp.size()));
+    GABP_CUDA(cudaMalloc(&L->ssys, sizeof(int) * ssys.size()));
+    GABP_CUDA(cudaMalloc(&L->sci, sizeof(int) * Ea));
+    GABP_CUDA(cudaMalloc(&L->sav, sizeof(float) * Ea));
+    for (int c = 0; c < 2; ++c) {
+      GABP_CUDA(cudaMalloc(&L->MP[c], sizeof(float) * Ea));
+      GABP_CUDA(cudaMalloc(&L->H[c], sizeof(float) * Ea));
+    }
+    GABP_CUDA(cudaMalloc(&L->CF, sizeof(float2) * Ea));
+    GABP_CUDA(cudaMemcpyAsync(L->srow, srow.data(), sizeof(int) * srow.size(), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaMemcpyAsync(L->sp, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaMemcpyAsync(L->ssys, ssys.data(), sizeof(int) * ssys.size(), cudaMemcpyHostToDevice, h->stream));
+    GABP_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors are released on return
+    L->vals_ok = false;
+  }
+  if (!L->vals_ok) {
+    const int nq = 32 * L->ns;
+    kgs_fill<<<(nq + kBlock - 1) / kBlock, kBlock, 0, h->stream>>>(nq, L->srow, L->sp, g.rp, g.ci, g.av32, L->sci,
+                                                                   L->sav);
+    GABP_CUDA(cudaGetLastError());
+    L->vals_ok = true;
+  }
+  return GABP_OK;
+}
+
+gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const int *off_host, const double *b,
+                               double *x, double tol, int max_iter, int *d_status, int *d_iters, int *d_refine,
+                               double *d_relres, int shape, float *ms_out) {
   Graph &g = h->g;
   Work32 &w = h->w32;
   struct Free {
@@ -468,8 +765,16 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
   bar = reinterpret_cast<unsigned int *>(misc + 2);
   GABP_CUDA(cudaMemsetAsync(misc, 0, sizeof(int) * 2 + sizeof(unsigned int) * 2, h->stream));
   kg_init<<<nsys, kBlock, 0, h->stream>>>(nsys, st, acc, d_off, sys_of);
-  kg_rows_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(g.n, g.rp, g.ad, g.ad32, w.NP[0],
-                                                                                  w.MP[0], w.MP[1], x);
+  const bool sliced = (shape & kSliced) != 0;
+  if (sliced) {
+    gabp_status e = ensure_gsell(h, nsys, off_host);
+    if (e != GABP_OK) return e;
+    const size_t Ea = std::max<size_t>(1, (size_t)h->gsl->Es);
+    GABP_CUDA(cudaMemsetAsync(h->gsl->MP[0], 0, sizeof(float) * Ea, h->stream));
+    GABP_CUDA(cudaMemsetAsync(h->gsl->MP[1], 0, sizeof(float) * Ea, h->stream));
+  }
+  kg_rows_init<<<blocks_for(g.n, kBlock, h->max_blocks), kBlock, 0, h->stream>>>(
+      g.n, g.rp, g.ad, g.ad32, w.NP[0], sliced ? nullptr : w.MP[0], sliced ? nullptr : w.MP[1], x);
   GABP_CUDA(cudaGetLastError());
   GridArgs a;
   a.n = g.n; a.nsys = nsys; a.sys_of = sys_of;
@@ -479,6 +784,13 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
   a.CF = w.CF; a.invP = w.invP;
   a.H0 = w.H[0]; a.H1 = w.H[1]; a.NH0 = w.NH[0]; a.NH1 = w.NH[1]; a.NH2 = w.NH[2];
   a.rhs = w.rhs32; a.b = b; a.x = x;
+  a.ns = 0; a.srow = a.sp = a.ssys = nullptr;
+  if (sliced) {  // the slot arrays of the sliced layout
+    GSell *L = h->gsl;
+    a.ns = L->ns; a.srow = L->srow; a.sp = L->sp; a.ssys = L->ssys;
+    a.ci = L->sci; a.av = L->sav;
+    a.MP0 = L->MP[0]; a.MP1 = L->MP[1]; a.H0 = L->H[0]; a.H1 = L->H[1]; a.CF = L->CF;
+  }
   a.st = st; a.acc = acc; a.bar = bar; a.active = misc; a.err = misc + 1;
   a.tol = tol; a.inner_tol = h->opt.inner_tol; a.prec_thr = std::ldexp(1.0, -h->opt.prec_stop_log2);
   a.inner_max = h->opt.inner_max_iter; a.max_refine = h->opt.max_refine; a.max_iter = max_iter;
@@ -498,7 +810,8 @@ gabp_status solve_systems_grid(gabp_handle h, int nsys, const int *d_off, const 
     // than the average one; longer chunks (fewer accumulator flushes) when the rows allow
     const int lanes = shape & 0xff;
     const long long warps = (long long)grid * (kBlock / 32);
-    const long long steps_per_warp = ((long long)g.n * lanes + 32LL * warps - 1) / (32LL * warps);
+    const long long steps_per_warp = sliced ? ((long long)a.ns + warps - 1) / warps
+                                            : ((long long)g.n * lanes + 32LL * warps - 1) / (32LL * warps);
     a.chunk = (int)std::max(1LL, std::min<long long>(kGChunkMax, steps_per_warp / 4));
   }
   cudaEvent_t e0, e1;

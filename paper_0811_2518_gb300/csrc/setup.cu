@@ -194,6 +194,7 @@ static gabp_status destroy_impl(gabp_handle h) {
   free_wb(h);
   free_ws(h);
   free_wf(h);
+  free_gsell(h);
   free_graph(h->g);
   cudaFree(h->ctl);
   cudaFreeHost(h->ctl_host);
@@ -328,7 +329,7 @@ static gabp_status check_options(const gabp_options *o) {
   if (o->lanes && !pinned_shape32(o->lanes, o->unroll)) return GABP_ERR_INVALID;
   if ((o->profile != 0 && o->profile != 1) || (o->reuse_precisions != 0 && o->reuse_precisions != 1) ||
       o->multi_split < 0 || o->prec_stop_log2 < 10 || o->prec_stop_log2 > 23 || o->multi_mode < 0 ||
-      o->multi_mode > 2 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
+      o->multi_mode > 3 || o->overlap_precision < 0 || o->overlap_precision > 1 ||
       o->device_loop < 0 || o->device_loop > 1 || o->schedule < 0 || o->schedule > 1 || o->fix_single_loop < 0 ||
       o->fix_single_loop > 1 || !(o->fix_step > 0.0 && o->fix_step <= 1.0) || o->accel < 0 || o->accel > 2 || o->freeze_precisions < 0 || o->freeze_precisions > 1 || o->history < 0 || o->warm_start < 0 || o->warm_start > 1 || o->initial_guess < 0 || o->initial_guess > 1 || o->graphs < 0 || o->graphs > 1 ||
       (o->accel && o->variant != GABP_VARIANT_NODE) || (o->accel == 1 && o->schedule == 1))
@@ -430,6 +431,7 @@ extern "C" gabp_status gabp_set_values(gabp_handle h, const double *val, int mem
   h->last_path = -1;     // marginals / messages of the old values are gone
   h->w64.valid = false;  // and no warm start from them
   h->w64.sl.vals_ok = false;  // the sliced copy of the values is refreshed by the next FP64 solve
+  if (h->gsl) h->gsl->vals_ok = false;  // and the independent-systems one by the next such solve
   h->w32.coef_ready = false;
   h->w32.prec_round = -1;
   int *dflag = nullptr;

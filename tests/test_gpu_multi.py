@@ -63,24 +63,27 @@ def test_systems_autotuned_split(gb):
     _check(gb, mats, 0)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_systems_forced_kernel(gb, mode):
     """mode 1: the grid-persistent kernel (one global round sweeps the rows of every running
-    system); mode 2: cluster / single-block teams with an autotuned split."""
+    system); mode 2: cluster / single-block teams with an autotuned split; mode 3: the
+    grid-persistent kernel on the sliced layout (32-row slices of degree-sorted rows, each
+    system padded to whole slices)."""
     mats = synth.rgg_batch(16, 1024, 16384, 2.0, 7)
     _check(gb, mats, 0, zero_system=5, mode=mode)
 
 
-def test_systems_grid_breakdown_isolated(gb):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_systems_grid_breakdown_isolated(gb, mode):
     """One system whose precision recursion breaks down (a zero cavity precision) stops with
-    BREAKDOWN in the grid-persistent kernel while the others still converge."""
+    BREAKDOWN in the grid-persistent kernel (row CSR or sliced) while the others still converge."""
     good = synth.rgg_batch(3, 1024, 2048, 2.0, 8)
     star = synth.from_dense(np.array([[2.0, 1, 0, 0], [1, 3, 1, 1], [0, 1, 1, 0], [0, 1, 0, 0.5]]))
     mats = [good[0], star, good[1], good[2]]
     big = synth.block_diag(mats)
     off = big.meta["offsets"]
     b = synth.rhs(big.n, 3)
-    s = gb.Solver.from_csr(big, multi_mode=1)
+    s = gb.Solver.from_csr(big, multi_mode=mode)
     x, st, sts, its, rel = s.solve_systems(torch.from_numpy(b).cuda(), off, tol=1e-12)
     s.close()
     assert st == gb.GABP_BREAKDOWN
@@ -128,3 +131,33 @@ def test_512_power_law_systems(gb):
         sl = slice(off[k], off[k + 1])
         ref = oracle.gabp_broadcast(mats[k], b[sl], max_iter=5000, tol=1e-12)
         assert _relerr(x[sl], ref["x"]) <= 1e-9
+
+
+def test_sliced_layout_new_values_and_offsets(gb):
+    """The sliced layout follows the handle: new values (gabp_set_values: A scaled by 2 halves x)
+    are picked up, and another offsets array (two neighbouring systems merged into one, still a
+    block-diagonal split) rebuilds it; each result against the oracle per system."""
+    mats = synth.rgg_batch(9, 1024, 8192, 2.0, 11)
+    big = synth.block_diag(mats)
+    off = big.meta["offsets"]
+    b = synth.rhs(big.n, 12)
+    bt = torch.from_numpy(b).cuda()
+    s = gb.Solver.from_csr(big, multi_mode=3)
+    x1, st, sts, its, rel = s.solve_systems(bt, off, tol=1e-12)
+    assert st == gb.GABP_OK
+    assert s.tuned()["multi_mode"] == 0 and s.tuned()["multi_grid_sliced"]
+    s.set_values(2.0 * big.val)
+    x2, st2, _, _, _ = s.solve_systems(bt, off, tol=1e-12)
+    assert st2 == gb.GABP_OK
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    for k, m in enumerate(mats):
+        sl = slice(off[k], off[k + 1])
+        ref = oracle.gabp_broadcast(m, b[sl], max_iter=5000, tol=1e-13)
+        assert _relerr(x1[sl], ref["x"]) <= 1e-10, k
+        assert _relerr(x2[sl], 0.5 * ref["x"]) <= 1e-10, k
+    off2 = np.concatenate([off[:3], off[4:]])  # systems 2 and 3 as one
+    x3, st3, sts3, _, _ = s.solve_systems(bt, off2, tol=1e-12)
+    s.close()
+    assert st3 == gb.GABP_OK and len(sts3) == len(mats) - 1
+    x3 = x3.cpu().numpy()
+    assert _relerr(x3, x2) <= 1e-10
