@@ -292,6 +292,9 @@ def main():
                     help="with --lanes: slots per lane of the FP32 round kernels (0 = the library default)")
     ap.add_argument("--batched-grid", type=int, default=128,
                     help="edge length m of the m^3 grid of the batched leg (128 = the 64-RHS workload)")
+    ap.add_argument("--multi-mode", type=int, default=0,
+                    help="independent-systems kernel: 0 autotune, 1 grid-persistent, 2 teams, 3 grid-persistent "
+                         "on the sliced layout")
     ap.add_argument("--multi-systems", type=int, default=512,
                     help="number of random geometric graphs of the independent-systems leg (512 = the workload)")
     ap.add_argument("--legs", default="fp32,fp64,e2e,oracle,edge,c1,lsq,batched,multi,grad,fix",
@@ -572,7 +575,7 @@ def main():
             bigm = synth.block_diag(mats)
             offm = bigm.meta["offsets"]
             bm = torch.from_numpy(synth.rhs(bigm.n, 4 + rank)).to(dev)
-            sm = gb.Solver.from_csr(bigm, **gkw)
+            sm = gb.Solver.from_csr(bigm, multi_mode=args.multi_mode, **gkw)
             xm, stm, stsm, itsm, relm = sm.solve_systems(bm, offm, tol=TOL)  # first call autotunes the split
             sm.profile(reset=True)
             reps_m = 5  # timed batches (each one launch); the median is reported
@@ -614,7 +617,7 @@ def main():
                                  "weights -U(0.5,1), diagonal 1.1 x row abs-sum, one b ~ N(0,1) each",
                      "systems": len(mats), "n_total": bigm.n, "edges_total": bigm.num_edges, "status": int(stm),
                      "ms_per_batch": msm, "ms_per_batch_all": times_m, "kernel_ms": pm["ms"]["multi"] / reps_m,
-                     "kernel": "grid-persistent" if tuned_m["multi_mode"] == 1 else "teams",
+                     "kernel": "grid-persistent" if (args.multi_mode in (1, 3) or tuned_m["multi_mode"] == 1) else "teams",
                      "grid_shape": {"lanes_per_row": tuned_m["multi_grid"][0], "slots_per_lane": tuned_m["multi_grid"][1],
                                     "sliced_layout": tuned_m["multi_grid_sliced"]},
                      "edge_updates": stm_["edge_updates"],
