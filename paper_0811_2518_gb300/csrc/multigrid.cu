@@ -140,40 +140,52 @@ struct WarpAcc {
 // Per-lane running sums of one system for the sliced kernel, whose slices each belong
 // to one system (the system is warp-uniform): the precision and inner rounds' row
 // values fold in FP32 registers (sum, and max for the precision rounds' relative
-// change; a NaN survives the max), the FP64 residual's in FP64, and a warp meets the
-// FP64 pipe only when it flushes (another system, or the end of its pass).
+// change; a NaN survives the max) and are reduced across the warp in FP32, lane 0
+// converting the two totals to FP64 for the system's accumulators; only the FP64
+// residual is summed and reduced in FP64.  A warp flushes whenever it meets another
+// system, which with short chunks is about once per slice, so the flush keeps off
+// the FP64 pipe.
 struct SliceAcc {
   int s = -1;
-  bool max1 = false;
+  bool max1 = false, dbl = false;
   float f0 = 0.f, f1 = 0.f;
   double d0 = 0.0;
 
   __device__ __forceinline__ void flush(double *acc) {
     if (s < 0) return;  // warp-uniform
-    double a0 = (double)f0 + d0, a1 = (double)f1;
+    if (dbl) {
+      double a0 = d0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      const double b1 = __shfl_xor_sync(0xffffffffu, a1, o);
-      a1 = max1 ? nan_max(a1, b1) : a1 + b1;
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(acc + 4 * s, a0);
-      if (max1)
-        atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * s + 1), (unsigned long long)__double_as_longlong(a1));
-      else
-        atomicAdd(acc + 4 * s + 1, a1);
+      for (int o = 16; o > 0; o >>= 1) a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(acc + 4 * s, a0);
+    } else {
+      float a0 = f0, a1 = f1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+        a1 = max1 ? nan_max(a1, b1) : a1 + b1;
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc + 4 * s, (double)a0);
+        if (max1)  // values >= 0 or NaN: the bit patterns order as the values
+          atomicMax(reinterpret_cast<unsigned long long *>(acc + 4 * s + 1),
+                    (unsigned long long)__double_as_longlong((double)a1));
+        else
+          atomicAdd(acc + 4 * s + 1, (double)a1);
+      }
     }
     s = -1;
     f0 = f1 = 0.f;
     d0 = 0.0;
   }
-  // all lanes call it with the same sys and mx
-  __device__ __forceinline__ void to(double *acc, int sys, bool mx) {
+  // all lanes call it with the same sys and phase
+  __device__ __forceinline__ void to(double *acc, int sys, int ph) {
     if (sys != s) {
       flush(acc);
       s = sys;
-      max1 = mx;
+      max1 = ph == PH_PREC;
+      dbl = ph == PH_RESID;
     }
   }
 };
@@ -569,7 +581,7 @@ __global__ void __launch_bounds__(kBlock, U >= 4 ? 3 : 4) kgs_solve(GridArgs a) 
         }
       }
       // ---------------------------------------------------------- node part, one lane per row
-      sacc.to(a.acc, s, ph == PH_PREC);
+      sacc.to(a.acc, s, ph);
       if (i >= 0) {
         if (ph == PH_PREC) {
           const float P = a.ad[i] + facc;
