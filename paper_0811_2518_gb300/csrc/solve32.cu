@@ -940,7 +940,10 @@ struct RefineCtl {
   int max_refine, max_iter, inner_max, prec_cap;
   // loop state
   double rr, bb, it2;
-  int steps, total_inner, status, skip, joint_pending, prec_round, cap, pad;
+  int steps, total_inner, status, skip, joint_pending, prec_round, cap;
+  int joint_rounds; // rounds the joint loop ran
+  int launches;     // kernels the graph launched after its first residual and decision
+  int inner_start;  // round at which the current inner solve's while loop starts
 };
 
 struct RefineParams {
@@ -997,6 +1000,7 @@ __global__ void k_ref_decide(RefineCtl *rc, const DevCtl *ctlR, DevCtl *ctl, int
     else if (rc->steps >= rc->max_refine || rc->total_inner >= rc->max_iter) rc->status = GABP_NOT_CONVERGED;
     else {
       go = 1;
+      rc->inner_start = 0;
       rc->cap = min(rc->inner_max, max(1, rc->max_iter - rc->total_inner));
       const double it = inner_target(rc->inner_tol, rc->tol, bb, rr);
       rc->it2 = it * it;
@@ -1018,6 +1022,7 @@ __global__ void k_joint_prep(RefineCtl *rc, DevCtl *ctl, cudaGraphConditionalHan
 __global__ void k_joint_after(RefineCtl *rc, DevCtl *ctl, cudaGraphConditionalHandle h_inner) {
   const int T = ctl->result_round, st = ctl->status;
   rc->joint_pending = 0;
+  rc->joint_rounds = ctl->round;
   if (st == GABP_BREAKDOWN || st == GABP_DIVERGED) {
     rc->status = st;
     rc->skip = 1;
@@ -1029,7 +1034,23 @@ __global__ void k_joint_after(RefineCtl *rc, DevCtl *ctl, cudaGraphConditionalHa
   cudaGraphSetConditional(h_inner, T < rc->cap);
 }
 
+// kLoopK round kernels per while-body iteration (later ones exit at once when decided)
+constexpr int kLoopK = 2;
+
+// The joint rounds' while loop ran ceil(rounds / kLoopK) bodies; with the prep, the
+// joint-after, the freeze and this kernel: the launches of the joint block.  Marks
+// the round from which the first inner solve's loop continues.
+__global__ void k_joint_mark(RefineCtl *rc, const DevCtl *ctl) {
+  rc->launches += 2 + 2 + 1 + kLoopK * ((rc->joint_rounds + kLoopK - 1) / kLoopK);
+  rc->inner_start = ctl->round;
+}
+
 __global__ void k_ref_after_inner(RefineCtl *rc, const DevCtl *ctl) {
+  // this step's inner loop ran ceil(rounds / kLoopK) bodies; then this kernel, the
+  // update, the residual and the decision
+  const int worked = max(0, ctl->round - rc->inner_start);
+  rc->launches += kLoopK * ((worked + kLoopK - 1) / kLoopK) + 4;
+  rc->inner_start = ctl->round;
   if (rc->skip) return;
   rc->total_inner += ctl->result_round;
   if (ctl->status == GABP_DIVERGED) {
@@ -1047,8 +1068,6 @@ __global__ void k64_update_ctl(int n, double *__restrict__ x, const float *NH0, 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] += (double)(hT[i] * invP[i]);
 }
-
-constexpr int kLoopK = 2;  // round kernels per while-body iteration (later ones exit at once when decided)
 
 // A graph under construction: nodes are appended in sequence after `last`.
 struct SeqGraph {
@@ -1171,6 +1190,7 @@ static gabp_status build_refine_graph(gabp_handle h, int SHm, int SHj, int LR) {
         k32_freeze<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_freeze<LL, UU>)), kBlock, 0,
                              st>>>(af);
       });
+      k_joint_mark<<<1, 1, 0, st>>>(rc, h->ctl);
     });
   // the inner solve's frozen-coefficient rounds
   if (e == cudaSuccess) e = seq_conditional(outer, h_inner, cudaGraphCondTypeWhile, &inner);
@@ -1263,7 +1283,7 @@ static gabp_status solve32_device_loop(gabp_handle h, const double *B, double *X
   GABP_CUDA(cudaMemcpyAsync(w.rc_host, w.rc, sizeof(RefineCtl), cudaMemcpyDeviceToHost, h->stream));
   GABP_CUDA(cudaStreamSynchronize(h->stream));
   const RefineCtl r = *w.rc_host;
-  h->prof.launches += 4 + 2 * (int64_t)r.total_inner + 4 * (int64_t)r.steps;
+  h->prof.launches += 3 + (int64_t)r.launches;  // k_ref_setup, the first residual and decision, the loop
   if (run_joint) {
     if (r.prec_round >= 0) {
       w.prec_round = r.prec_round;
