@@ -297,7 +297,9 @@ def main():
                          "on the sliced layout")
     ap.add_argument("--multi-systems", type=int, default=512,
                     help="number of random geometric graphs of the independent-systems leg (512 = the workload)")
-    ap.add_argument("--legs", default="fp32,fp64,e2e,oracle,edge,c1,lsq,batched,multi,grad,fix",
+    ap.add_argument("--dense-n", type=int, default=8192,
+                    help="points of the dense kernel-regression leg (n x n dense matrix)")
+    ap.add_argument("--legs", default="fp32,fp64,e2e,oracle,edge,c1,lsq,dense,batched,multi,grad,fix",
                     help="comma list of timed legs (fp32 is the headline; the others add keys)")
     args = ap.parse_args()
     gkw = {"graphs": 0} if args.no_graphs else {}  # solver options of every handle below
@@ -801,6 +803,65 @@ def main():
                 raise
             c1 = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- dense kernel-regression system: Gaussian kernel on n points in [0, 1]^3 (sigma 0.1), main
+    # diagonal weighted to 1.1 x the row sum; FP32 + refinement and plain FP64 to 1e-10
+    dense = None
+    if "dense" in legs:
+        try:
+            nd = args.dense_n
+            Ad = synth.rbf_kernel_system(nd, 3, 0.1, 1.1, 9)
+            bdn = synth.rhs(nd, 9)
+            Adt = torch.from_numpy(Ad).to(dev)
+            bdt = torch.from_numpy(bdn).to(dev)
+            dense = {"workload": f"dense {nd} x {nd} kernel matrix: Gaussian kernel (sigma 0.1) on {nd} points uniform "
+                                 "in [0,1]^3, main diagonal 1.1 x the row sum; b ~ N(0,1); to 1e-10",
+                     "n": nd}
+            for name, prec in (("fp32_refine", gb.GABP_PREC_FP32_REFINE), ("fp64", gb.GABP_PREC_FP64)):
+                sdn = gb.Solver.from_dense(Adt, precision=prec, reuse_precisions=0, **gkw)
+                Edn = sdn.nnz - nd
+                xd_, std_, itd_, reld_ = sdn.solve(bdt, tol=TOL, max_iter=2000)
+                times = []
+                for _ in range(3):
+                    ed0, ed1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ed0.record()
+                    xd_, std_, itd_, reld_ = sdn.solve(bdt, tol=TOL, max_iter=2000, x=xd_)
+                    ed1.record()
+                    torch.cuda.synchronize()
+                    times.append(ed0.elapsed_time(ed1))
+                rounds_d = sdn.stats()["rounds"]
+                msd = float(np.median(times))
+                xh = xd_.cpu().numpy()
+                entry = {"ms_per_solve": msd, "status": int(std_), "rounds": int(rounds_d), "relres": reld_,
+                         "host_relres": float(np.linalg.norm(bdn - Ad @ xh) / np.linalg.norm(bdn)),
+                         "edge_updates_per_s": Edn * rounds_d / (msd / 1e3), "edges": Edn}
+                if prec == gb.GABP_PREC_FP32_REFINE:  # the mean round's live time from a profiled run
+                    sdn.set_options(profile=1, device_loop=0)
+                    sdn.solve(bdt, tol=TOL, max_iter=2000, x=xd_)
+                    sdn.profile(reset=True)
+                    sdn.solve(bdt, tol=TOL, max_iter=2000, x=xd_)
+                    pd = sdn.profile(reset=True)
+                    mean_ms = pd["ms"]["mean32"] / max(pd["rounds"]["mean32"], 1)
+                    alg = 16 * Edn + 8 * nd
+                    entry["roofline"] = {"bound": "hbm", "kernel": "k32_mean", "launch_ms": mean_ms,
+                                         "algorithmic_bytes_per_launch": alg,
+                                         "algorithmic_bytes_rule": "16 B per directed edge + 8 B per node",
+                                         "achieved": alg / (mean_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                         "frac": alg / (mean_ms / 1e3) / 1e9 / peak,
+                                         "impl_frac": (20 * Edn + 24 * nd) / (mean_ms / 1e3) / 1e9 / peak}
+                    x32 = xh
+                else:
+                    entry["max_abs_diff_fp32_refine_vs_fp64"] = float(np.max(np.abs(xh - x32)))
+                dense[name] = entry
+                sdn.close()
+            if not args.no_cpu_baseline and rank == 0:  # the oracle scans rows: a 1024-point instance
+                As = synth.rbf_kernel_system(1024, 3, 0.1, 1.1, 9)
+                dense["cpu_oracle_n1024"] = oracle_rounds_sample(synth.from_dense(As), synth.rhs(1024, 9), rounds=2)
+            del Adt, Ad
+        except Exception as exc:
+            if world > 1:
+                raise
+            dense = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- regularised least squares through the augmented symmetric system: J 2^20 x 2^19, 8 entries
     # per row N(0,1)/sqrt(8), gamma = 1, y ~ N(0,1), to 1e-10 (FP32 + refinement and plain FP64)
     lsq = None
@@ -898,6 +959,7 @@ def main():
             "errors_vs_oracle": errors,
             "grid32_fp64": c1,
             "lsq_rect_1048576x524288": lsq,
+            f"dense_rbf_n{args.dense_n}": dense,
             "e2e": None if e2e_s is None else {
                 "value": E * e2e_rounds / e2e_s, "unit": "edge-updates/s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_s / args.steps * 1e3},

@@ -291,6 +291,21 @@ gabp_status gabp_solve_systems(gabp_handle h, int32_t nsys, const int32_t *offse
 gabp_status gabp_serial_colours(gabp_handle h, int32_t *colour, int32_t *ncolours);
 
 /*
+ * gabp_create_dense -- a handle for a dense symmetric matrix A (n x n, row-major, leading
+ * dimension lda >= n, FP64), e.g. the kernel matrices of Chapter "Support Vector Regression"
+ * (Sec. "Our novel construction": the kernel matrix with its main diagonal weighted until it
+ * is diagonally dominant, solved by GaBP with the n node aggregates broadcast every round).
+ * The broadcast form (Algorithm 2) needs no sparsity: the entry keeps A's nonzero entries
+ * (and the diagonal), builds their row-CSR on the device and creates an ordinary handle on
+ * it, so every solve path and option applies.  A in host (mem_space 0) or device (1) memory;
+ * a host A is copied to the device first.  *nnz_out (nullable) receives the entries kept.
+ * GABP_ERR_INVALID for bad arguments, more than 2^31 - 1 kept entries, or an A that
+ * gabp_create rejects (not symmetric, non-finite, zero diagonal); otherwise as gabp_create.
+ */
+gabp_status gabp_create_dense(gabp_handle *out, int32_t n, const double *A, int64_t lda, int mem_space,
+                              void *stream, const gabp_options *options, int64_t *nnz_out);
+
+/*
  * gabp_create_lsq -- a handle for regularised least squares / MMSE estimation with a
  * rectangular J (m x k): x = (J^T J + gamma I)^{-1} J^T y (Sec. "Extension to General
  * Linear Systems", the -gamma I block that makes the augmented matrix invertible; Chapter

@@ -22,7 +22,7 @@ __all__ = [
     "gabp_options_default", "gabp_create", "gabp_set_values", "gabp_set_options", "gabp_set_stream", "gabp_solve",
     "gabp_solve_host", "gabp_solve_batched", "gabp_marginal_precisions", "gabp_get_messages",
     "gabp_grad_values", "gabp_last_stats", "gabp_last_freeze", "gabp_profile_read", "gabp_solve_noalloc", "gabp_solve_systems", "gabp_tuned_shapes", "gabp_serial_colours", "gabp_set_messages", "gabp_residual_history", "gabp_destroy", "gabp_status_string", "gabp_last_error",
-    "gabp_create_lsq", "gabp_solve_lsq",
+    "gabp_create_lsq", "gabp_solve_lsq", "gabp_create_dense",
     "Solver", "LSQSolver", "GaBPError",
 ]
 
@@ -108,6 +108,8 @@ _SIGNATURES = {
                          ctypes.c_double, ctypes.c_int, _P, ctypes.POINTER(Options)], ctypes.c_int),
     "gabp_solve_lsq": ([_P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "gabp_create_dense": ([ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int, _P,
+                           ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "gabp_destroy": ([_P], ctypes.c_int),
     "gabp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "gabp_last_error": ([], ctypes.c_char_p),
@@ -156,6 +158,15 @@ def gabp_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, mem_space, stream_ptr, opt
     st = lib.gabp_create(ctypes.byref(h), int(n), int(nnz), _P(rowptr_ptr), _P(col_ptr), _P(val_ptr),
                          int(mem_space), _P(stream_ptr), ctypes.byref(options) if options is not None else None)
     return st, h
+
+
+def gabp_create_dense(n, a_ptr, lda, mem_space, stream_ptr, options=None):
+    """Handle for a dense symmetric n x n matrix (row-major, leading dimension lda); returns
+    (status, handle, nnz kept)."""
+    h, nnz = _P(), ctypes.c_int64(0)
+    st = lib.gabp_create_dense(ctypes.byref(h), int(n), _P(a_ptr), int(lda), int(mem_space), _P(stream_ptr),
+                               ctypes.byref(options) if options is not None else None, ctypes.byref(nnz))
+    return st, h, nnz.value
 
 
 def gabp_create_lsq(m, k, nnz, rowptr_ptr, col_ptr, val_ptr, gamma, mem_space, stream_ptr, options=None):
@@ -370,6 +381,41 @@ class Solver:
         if st != GABP_OK:
             raise GaBPError(st, "gabp_create")
         self.handle = h
+
+    @classmethod
+    def from_dense(cls, A, options: Options | None = None, stream=None, **opts):
+        """Solver for a dense symmetric matrix (numpy array or CUDA float64 tensor, rows
+        contiguous): ``gabp_create_dense`` keeps its nonzero entries in the row-CSR the
+        broadcast rounds use."""
+        import numpy as np
+        import torch
+
+        self = cls.__new__(cls)
+        self.options = options if options is not None else gabp_options_default()
+        for k, v in opts.items():
+            setattr(self.options, k, v)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if isinstance(A, torch.Tensor):
+            a = A.to(self.device, torch.float64)
+            if a.dim() != 2 or a.shape[0] != a.shape[1] or a.stride(1) != 1:
+                a = a.contiguous()
+            ptr, lda, mem = a.data_ptr(), a.stride(0), 1
+        else:
+            a = np.asarray(A, dtype=np.float64)
+            if a.ndim != 2 or a.shape[0] != a.shape[1] or a.strides[1] != 8:
+                a = np.ascontiguousarray(a)
+            ptr, lda, mem = a.ctypes.data, a.strides[0] // 8, 0
+        if a.ndim != 2 or a.shape[0] != a.shape[1]:
+            raise ValueError("A must be a square matrix")
+        self.n = int(a.shape[0])
+        self._keep = [a]
+        st, h, nnz = gabp_create_dense(self.n, ptr, lda, mem, self.stream.cuda_stream, self.options)
+        self._keep = []
+        if st != GABP_OK:
+            raise GaBPError(st, "gabp_create_dense")
+        self.handle, self.nnz = h, nnz
+        return self
 
     @classmethod
     def from_csr(cls, m, **kw):

@@ -343,3 +343,37 @@ def spd_seed(make, seed0: int, tries: int = 50):
         except np.linalg.LinAlgError:
             continue
     raise RuntimeError("no SPD seed found")
+
+
+def dense_dd(n: int, diag_factor: float, seed: int) -> np.ndarray:
+    """Dense symmetric n x n matrix: off-diagonal U(-1, 1), diagonal diag_factor x the row's
+    off-diagonal absolute sum (diagonally dominant for diag_factor > 1; 1 for n = 1)."""
+    rng = np.random.default_rng(seed)
+    A = np.triu(rng.uniform(-1.0, 1.0, size=(n, n)), 1)
+    A = A + A.T
+    rs = np.abs(A).sum(axis=1)
+    A[np.diag_indices(n)] = np.where(rs > 0.0, diag_factor * rs, 1.0)
+    return A
+
+
+def rbf_kernel_system(n: int, d: int, sigma: float, diag_factor: float, seed: int,
+                      block: int = 2048) -> np.ndarray:
+    """Dense kernel-regression system: n points uniform in [0, 1]^d, Gaussian kernel
+    K_ij = exp(-|x_i - x_j|^2 / (2 sigma^2)) off the diagonal, and the main diagonal weighted to
+    diag_factor x the row's off-diagonal sum, so that the matrix is diagonally dominant.  Built in
+    row blocks (n = 16384 is 2 GB of FP64)."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.0, 1.0, size=(n, d))
+    A = np.empty((n, n), dtype=np.float64)
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        d2 = np.zeros((r1 - r0, n))
+        for k in range(d):  # (x_ik - x_jk)^2 is the same for (i, j) and (j, i): A is exactly symmetric
+            diff = X[r0:r1, k][:, None] - X[None, :, k]
+            d2 += diff * diff
+        blk = np.exp(d2 * (-0.5 / (sigma * sigma)))
+        idx = np.arange(r0, r1)
+        blk[idx - r0, idx] = 0.0
+        A[r0:r1] = blk
+    A[np.diag_indices(n)] = diag_factor * A.sum(axis=1)
+    return A
