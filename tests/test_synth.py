@@ -81,3 +81,23 @@ def test_random_rect_shape_and_rows():
     assert np.all(J.val != 0.0) and np.all(np.isfinite(J.val))
     J2 = synth.random_rect(500, 70, 6, 9)
     assert np.array_equal(J.col, J2.col) and np.array_equal(J.val, J2.val)
+
+
+def test_dense_generators():
+    """dense_dd: symmetric, diagonal diag_factor x the off-diagonal row sum (1 for n = 1);
+    rbf_kernel_system: exactly symmetric, the Gaussian kernel off the diagonal, the weighted
+    diagonal; both seeded."""
+    A = synth.dense_dd(50, 1.1, 3)
+    assert np.array_equal(A, A.T)
+    off = np.abs(A).sum(axis=1) - np.abs(np.diag(A))
+    assert np.allclose(np.diag(A), 1.1 * off)
+    assert np.array_equal(A, synth.dense_dd(50, 1.1, 3))
+    assert synth.dense_dd(1, 1.1, 0)[0, 0] == 1.0
+    K = synth.rbf_kernel_system(300, 3, 0.2, 1.1, 4)
+    assert np.array_equal(K, K.T)
+    X = np.random.default_rng(4).uniform(0.0, 1.0, size=(300, 3))
+    i, j = 5, 17
+    assert np.isclose(K[i, j], np.exp(-np.sum((X[i] - X[j]) ** 2) / (2 * 0.2 ** 2)), rtol=1e-14)
+    assert np.allclose(np.diag(K), 1.1 * (K.sum(axis=1) - np.diag(K)))
+    assert np.all(K > 0)
+    assert np.array_equal(K, synth.rbf_kernel_system(300, 3, 0.2, 1.1, 4, block=64))
