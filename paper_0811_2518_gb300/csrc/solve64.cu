@@ -59,6 +59,7 @@ struct Args64 {
   double *partials;
   double *C;   // [Es] frozen coefficients (freeze != 0)
   int freeze;  // options.freeze_precisions on a plain node solve
+  int wide;    // plain node rounds of a matrix of long rows: k64_wide
 };
 
 // Warp / lane of the calling thread and the number of warps in the grid.
@@ -310,6 +311,68 @@ __device__ __forceinline__ void plain_round(const Args64 &a, DevCtl *ctl, int t,
     if constexpr (MODE > 0) freeze_step(ctl, MODE - 1, t, tot[2]);
     decide64(ctl, t, tot[0], tot[1]);
   }
+}
+
+// The plain round for long rows (Algorithm 2's round, as plain_slice's mode 0): a warp
+// per row of the sliced layout, its lanes on the row's slots j, j + 32, ... (slot j
+// of slice row r is sp[s] + 32 j + r), the aggregates and the residual term reduced
+// across the warp, the row's epilogue on lane 0.  A layout with one lane per row
+// gives a matrix of few long rows (dense ones) only n / 32 warps.
+__global__ void __launch_bounds__(kBlock) k64_wide(Args64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int t = ctl->round + 1;
+  const double *__restrict__ b = ctl->b;
+  const double2 *__restrict__ Min = (t & 1) ? a.M0 : a.M1;
+  double2 *__restrict__ Mout = (t & 1) ? a.M1 : a.M0;
+  const NodeRec64 *__restrict__ Nin = (t & 1) ? a.N0 : a.N1;
+  NodeRec64 *__restrict__ Nout = (t & 1) ? a.N1 : a.N0;
+  const WarpPos w = warp_pos();
+  double rr = 0.0;
+  int bad = 0;
+  for (int q = w.warp; q < a.ns * 32; q += w.nwarps) {
+    const int i = a.srow[q];
+    if (i < 0) continue;  // warp-uniform
+    const int sl = q >> 5, r = q & 31;
+    const int p0 = a.sp[sl] + r, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
+    double accP = 0.0, acch = 0.0, accr = 0.0;
+    for (int j = w.lane; j < wd; j += 32) {
+      const int pos = p0 + 32 * j;
+      const int k = __ldcs(a.sci + pos);
+      if (k < 0) continue;
+      const double A = __ldcs(a.sav + pos);
+      const double2 rv = __ldcs(Min + __ldcs(a.srev + pos));  // message i -> k of round t-1
+      const NodeRec64 nk = Nin[k];                              // node k at round t-1
+      const double den = nk.P - rv.x;
+      bad |= is_zero64(den);
+      const double cin = -A * rcp64(den);
+      const double2 m = make_double2(__dmul_rn(cin, A), __dmul_rn(cin, nk.h - rv.y));
+      __stcs(Mout + pos, m);
+      accP = __dadd_rn(accP, m.x);
+      acch = __dadd_rn(acch, m.y);
+      accr = fma(A, nk.x, accr);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      accP += __shfl_xor_sync(0xffffffffu, accP, o);
+      acch += __shfl_xor_sync(0xffffffffu, acch, o);
+      accr += __shfl_xor_sync(0xffffffffu, accr, o);
+    }
+    if (w.lane == 0) {
+      const double bi = b[i], d = a.ad[i];
+      const NodeRec64 own = Nin[i];
+      const double P = d + accP, h = bi + acch;
+      bad |= is_zero64(P);
+      const double ip = rcp64(P);
+      Nout[i] = NodeRec64{P, h, h * ip, h * ip};
+      const double rres = bi - fma(d, own.x, accr);
+      rr = fma(rres, rres, rr);
+    }
+  }
+  double v[2] = {rr, (double)bad}, tot[2];
+  const int modes[2] = {0, 0};
+  block_sum<2>(v);
+  if (last_block_reduce<2>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) decide64(ctl, t, tot[0], tot[1]);
 }
 
 // The plain round with the precision freeze on: MODE 1 (screen), 2 (verify and store)
@@ -858,6 +921,9 @@ static Args64 args64(gabp_handle h) {
   a.C = h->w64.C;
   a.freeze = h->opt.freeze_precisions && h->opt.variant == GABP_VARIANT_NODE && h->opt.accel == ACC_NONE &&
              h->w64.C != nullptr;
+  // long rows and too few slices to give every SM eight warps: a warp per row instead
+  a.wide = !a.freeze && h->opt.variant == GABP_VARIANT_NODE && h->opt.accel == ACC_NONE && S.ns > 0 &&
+           (double)S.Es >= 64.0 * 32.0 * S.ns && S.ns < 8 * h->num_sms;
   return a;
 }
 
@@ -876,6 +942,8 @@ static void launch_round(gabp_handle h, const Args64 &a) {
   } else if (h->opt.accel == ACC_STEFFENSEN) {
     k64_node<ACC_STEFFENSEN><<<slice_grid(h, k64_node<ACC_STEFFENSEN>), kBlock, 0, h->stream>>>(a);
     k64_steff<<<slice_grid(h, k64_steff), kBlock, 0, h->stream>>>(a);
+  } else if (a.wide) {
+    k64_wide<<<resident_grid(h->num_sms, k64_wide), kBlock, 0, h->stream>>>(a);
   } else if (a.freeze) {
     k64_frz<3><<<slice_grid(h, k64_frz<3>), kBlock, 0, h->stream>>>(a);
     k64_frz<2><<<slice_grid(h, k64_frz<2>), kBlock, 0, h->stream>>>(a);
@@ -954,7 +1022,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
 
   // small and medium graphs: every round in one cooperative launch
   const int coop_grid = a.freeze ? h->coop64f : h->coop64;
-  const bool coop = h->w64.sl.ns <= kCoopMaxSlices && h->opt.variant == GABP_VARIANT_NODE &&
+  const bool coop = !a.wide && h->w64.sl.ns <= kCoopMaxSlices && h->opt.variant == GABP_VARIANT_NODE &&
                     h->opt.accel == ACC_NONE && coop_grid > 0;
   const bool use_graph = !coop && h->stream != nullptr && h->opt.graphs;
   cudaGraphExec_t ge = nullptr;
