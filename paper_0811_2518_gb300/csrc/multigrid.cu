@@ -723,7 +723,6 @@ static gabp_status ensure_gsell(gabp_handle h, int nsys, const int *off) {
         ssys.push_back(s);
       }
     }
-    L->off.assign(off, off + nsys + 1);
     L->ns = (int)ssys.size();
     L->Es = (int)slots;
     const size_t Ea = std::max<size_t>(1, (size_t)L->Es);
@@ -741,6 +740,7 @@ static gabp_status ensure_gsell(gabp_handle h, int nsys, const int *off) {
     GABP_CUDA(cudaMemcpyAsync(L->sp, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice, h->stream));
     GABP_CUDA(cudaMemcpyAsync(L->ssys, ssys.data(), sizeof(int) * ssys.size(), cudaMemcpyHostToDevice, h->stream));
     GABP_CUDA(cudaStreamSynchronize(h->stream));  // the host vectors are released on return
+    L->off.assign(off, off + nsys + 1);            // complete: reusable for these offsets
     L->vals_ok = false;
   }
   if (!L->vals_ok) {
