@@ -361,6 +361,8 @@ def main():
     barrier()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = float(clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)  # the timed region's SM clock
     x_fp32 = x_dev.cpu().numpy()  # the headline's answer, compared with the oracle below
     ms_local = ev0.elapsed_time(ev1)
     launches_timed = sd.profile(reset=True)["launches"]
@@ -949,6 +951,13 @@ def main():
                 "ms_per_solve": ms64, "rounds": r64 / k64, "edge_updates_per_s": E * (r64 / k64) / (ms64 / 1e3),
                 "phase_ms": p64["ms"]["fp64"] / k64,
                 "roofline": {"bound": "fp64 alu", "kernel": "k64_node",
+                             # FP64 instructions of a round, counted by ncu's per-opcode counters: per message
+                             # 4 DADD + 4 DFMA + 3 DMUL, per row 3 + 5 + 1; GB300 retires 2 FP64 operations per
+                             # SM and clock (1.25 TFLOP/s FMA at 2.07 GHz on 152 SMs)
+                             "fp64_ops_per_round": 11 * E + 9 * n,
+                             "fp64_peak_ops_per_s": 2.0 * n_sms * clk_mhz * 1e6,
+                             "alu_frac": (11 * E + 9 * n) / (p64["ms"]["fp64"] / max(p64["rounds"]["fp64"], 1) / 1e3)
+                                         / (2.0 * n_sms * clk_mhz * 1e6),
                              "algorithmic_bytes_per_round": 48 * E + 24 * n,
                              "algorithmic_bytes_rule": "48 B per directed edge (A 8, sender 4, reverse index 4, "
                                                        "reverse message 16, new message 16) + 24 B per node",
