@@ -113,3 +113,42 @@ def test_binding_argument_counts_match_the_header():
         params = decls[name].strip()
         n = 0 if params in ("", "void") else len(params.split(","))
         assert n == len(args), (name, n, len(args))
+
+
+def test_limits_and_bad_arguments_rejected_without_gpu():
+    """Size limits and bad arguments are refused before any CUDA call (so on a machine without a
+    GPU too): nnz >= 2^31 - 1, n < 1, nnz < n, null arrays, a memory space other than 0 or 1,
+    out-of-range options (freeze_precisions, accel, multi_mode), and the dense and least-squares
+    entries' bad shapes; queries on a null handle."""
+    import numpy as np
+
+    import paper_0811_2518_gb300 as gb
+
+    L = gb.lib
+    P = ctypes.c_void_p
+    h = P()
+    rp = np.zeros(3, dtype=np.int32)
+    ci = np.zeros(2, dtype=np.int32)
+    va = np.ones(2)
+    ptrs = (P(rp.ctypes.data), P(ci.ctypes.data), P(va.ctypes.data))
+    INV = gb.GABP_ERR_INVALID
+    for n, nnz in ((2, 2 ** 31 - 1), (2, 2 ** 31), (0, 2), (3, 2)):
+        assert L.gabp_create(ctypes.byref(h), n, nnz, *ptrs, 0, None, None) == INV, (n, nnz)
+    assert L.gabp_create(ctypes.byref(h), 2, 2, None, ptrs[1], ptrs[2], 0, None, None) == INV
+    assert L.gabp_create(ctypes.byref(h), 2, 2, *ptrs, 2, None, None) == INV
+    for field, bad in (("freeze_precisions", 2), ("accel", 3), ("multi_mode", 4), ("check_every", 0)):
+        o = gb.gabp_options_default()
+        setattr(o, field, bad)
+        assert L.gabp_create(ctypes.byref(h), 2, 2, *ptrs, 0, None, ctypes.byref(o)) == INV, field
+    A = np.eye(3)
+    nnz = ctypes.c_int64(0)
+    for n, lda, mem in ((0, 3, 0), (3, 2, 0), (3, 3, 2)):
+        assert L.gabp_create_dense(ctypes.byref(h), n, P(A.ctypes.data), lda, mem, None, None,
+                                   ctypes.byref(nnz)) == INV, (n, lda, mem)
+    assert L.gabp_create_dense(ctypes.byref(h), 3, None, 3, 0, None, None, None) == INV
+    assert L.gabp_create_lsq(ctypes.byref(h), 0, 2, 2, *ptrs, 1.0, 0, None, None) == INV
+    assert L.gabp_create_lsq(ctypes.byref(h), 2, 2, 2, *ptrs, -1.0, 0, None, None) == INV
+    r = ctypes.c_int32(0)
+    assert L.gabp_last_freeze(None, ctypes.byref(r), None) == INV
+    assert L.gabp_solve(None, None, None, ctypes.c_double(1e-10), 10, None, None) == INV
+    assert L.gabp_destroy(None) == gb.GABP_OK
