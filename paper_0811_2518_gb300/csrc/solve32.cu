@@ -75,6 +75,7 @@ void with_shape(int code, F &&f) {
 
 struct Args32 {
   int n;
+  int dense;  // complete pattern (a dense matrix): k32_mean derives the sender from the slot
   const int *__restrict__ rp;
   const int *__restrict__ ci;
   const float *__restrict__ av;
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kBlock) k32_coef(Args32 a, int T) {
 // Round t of the frozen-precision mean iteration (recompute form).  The inner
 // solve stops when ||x^(t) - x^(t-1)|| <= inner_tol ||x^(t)|| (node-local
 // quantities, no extra edge traffic) or at max_iter.
-template <int L, int U>
+template <int L, int U, bool DENSE = false>
 __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
@@ -379,20 +380,26 @@ __global__ void __launch_bounds__(kBlock) k32_mean(Args32 a) {
       rhs_i = a.rhs[i];
       ip = a.invP[i];
       hprev = Hm1[i];
-      const int e1 = a.rp[i + 1];
-      for (int eb = a.rp[i] + sl; eb < e1; eb += L * U) {
+      const int e0 = a.rp[i], e1 = a.rp[i + 1];
+      for (int eb = e0 + sl; eb < e1; eb += L * U) {
         int k[U];
         float2 cf[U];
         float hs[U], hk[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = eb + u * L;
-          if (e < e1) { k[u] = __ldcs(a.ci + e); cf[u] = __ldcs(a.CF + e); hs[u] = __ldcs(Hc + e); }
+          if (e < e1) {
+            // a complete pattern: slot p of row i holds column p + (p >= i), no column stream
+            k[u] = DENSE ? (e - e0) + (e - e0 >= i) : __ldcs(a.ci + e);
+            cf[u] = __ldcs(a.CF + e);
+            hs[u] = __ldcs(Hc + e);
+          }
         }
-        // random gathers bypass L1 (no reuse there), which keeps L1 for the slot streams' sectors
+        // random gathers bypass L1 (no reuse there), which keeps L1 for the slot streams' sectors; a
+        // complete pattern reads the aggregates in column order, the same vector in every row: L1
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (eb + u * L < e1) hk[u] = __ldcg(Hm1 + k[u]);
+          if (eb + u * L < e1) hk[u] = DENSE ? __ldg(Hm1 + k[u]) : __ldcg(Hm1 + k[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = eb + u * L;
@@ -734,6 +741,7 @@ static Args32 args32(gabp_handle h) {
   Graph &g = h->g;
   Work32 &w = h->w32;
   a.n = g.n; a.rp = g.rp; a.ci = g.ci; a.av = g.av32; a.ad = g.ad32;
+  a.dense = g.n > 1 && (int64_t)g.E == (int64_t)g.n * (g.n - 1);  // every off-diagonal entry stored
   a.MP0 = w.MP[0]; a.MP1 = w.MP[1];
   a.NP0 = w.NP[0]; a.NP1 = w.NP[1]; a.NP2 = w.NP[2];
   a.CF = w.CF; a.invP = w.invP;
@@ -746,6 +754,18 @@ static Args32 args32(gabp_handle h) {
   a.ctl = h->ctl;
   a.partials = h->partials;
   return a;
+}
+
+// A mean round of shape (LL, UU) on stream st: the complete-pattern variant when the
+// matrix is dense.
+template <int LL, int UU>
+static void launch_mean(gabp_handle h, const Args32 &a, cudaStream_t st) {
+  const int n = h->g.n;
+  if (a.dense)
+    k32_mean<LL, UU, true><<<blocks_for(n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU, true>)), kBlock, 0,
+                             st>>>(a);
+  else
+    k32_mean<LL, UU><<<blocks_for(n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>)), kBlock, 0, st>>>(a);
 }
 
 // Shape (lanes per row, unroll) of an FP32 round kernel: the option if set, else
@@ -783,10 +803,7 @@ static gabp_status autotune32(gabp_handle h, int kind) {
     with_shape(sc, [&](auto Lc, auto Uc) {
       constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
       if (kind == K32_MEAN)
-        ms = time_launches(h, [&] {
-          k32_mean<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>)), kBlock, 0,
-                             h->stream>>>(a);
-        }, 5);
+        ms = time_launches(h, [&] { launch_mean<LL, UU>(h, a, h->stream); }, 5);
       else if (kind == K32_JOINT)
         ms = time_launches(h, [&] {
           k32_joint<LL, UU><<<blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_joint<LL, UU>)), kBlock, 0,
@@ -1201,8 +1218,7 @@ static gabp_status build_refine_graph(gabp_handle h, int SHm, int SHj, int LR) {
       am.use_cond = 1;
       with_shape(SHm, [&](auto Lc, auto Uc) {
         constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
-        const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
-        for (int k = 0; k < kLoopK; ++k) k32_mean<LL, UU><<<nb, kBlock, 0, st>>>(am);
+        for (int k = 0; k < kLoopK; ++k) launch_mean<LL, UU>(h, am, st);
       });
     });
   if (e == cudaSuccess)
@@ -1408,8 +1424,7 @@ gabp_status solve32_refine(gabp_handle h, int R, const double *B, double *X, int
       with_shape(SH, [&](auto Lc, auto Uc) {
         constexpr int LL = decltype(Lc)::value, UU = decltype(Uc)::value;
         s = run_rounds(h, &h->gH32, &h->gH32_L, SH, [&] {
-          const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, k32_mean<LL, UU>));
-          k32_mean<LL, UU><<<nb, kBlock, 0, h->stream>>>(a);
+          launch_mean<LL, UU>(h, a, h->stream);
         }, cap - T, PH_MEAN32, T > 0 ? T + 1 : 0);
       });
       if (s != GABP_OK) return s;
