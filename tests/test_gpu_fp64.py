@@ -371,3 +371,29 @@ def test_cooperative_threshold(gb, p):
         assert launches == 3  # round 0, every round, the answer
     else:
         assert launches > 3
+
+
+@pytest.mark.parametrize("n", [1, 33, 200, 1024, 1280, 1281, 2048])
+def test_cluster_rounds_small_graphs(gb, n):
+    """Graphs of at most 40 slices (1280 rows) run every plain FP64 round in one thread-block
+    cluster (hardware cluster barrier, partial sums through distributed shared memory); 1281 rows
+    (41 slices) and 2048 take the cooperative grid.  Iterates at fixed rounds equal the oracle's to 1e-13,
+    the converged round count is the oracle's, and the solve is three launches."""
+    m = synth.random_sym(n, min(4, n - 1), 1.1, 3) if n > 1 else synth.from_dense(np.array([[2.0]]))
+    b = synth.rhs(m.n, 8)
+    for t in (1, 2, 7):
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0)
+        g = _gpu_solve(gb, m, b, 0.0, t)
+        # a residual of exactly 0 meets tol = 0 (the one-node system is solved at round 1)
+        assert g["iters"] == t or (g["status"] == gb.GABP_OK and g["relres"] == 0.0), t
+        assert _relerr(g["x"], r["x"]) <= 1e-13, t
+    ref = oracle.gabp_broadcast(m, b, max_iter=3000, tol=1e-12)
+    s = _solver(gb, m, profile=1)
+    s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
+    s.profile(reset=True)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
+    launches = s.profile()["launches"]
+    s.close()
+    assert st == gb.GABP_OK and it == ref["iters"]
+    assert _relerr(x.cpu().numpy(), ref["x"]) <= 1e-12
+    assert launches == 3
