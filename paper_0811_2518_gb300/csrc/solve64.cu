@@ -657,16 +657,23 @@ __global__ void __launch_bounds__(kClusterThreads) k64_cluster(Args64 a, int max
     if (threadIdx.x == 0)
       for (int q = 0; q < NV; ++q) part[t & 1][q] = v[q];
     cl.sync();
-    if (rank == 0 && threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x < 32) {
+      // lane r fetches CTA r's partials (the remote reads in parallel), lane 0 adds them in rank order
+      double mine[NV];
+      for (int q = 0; q < NV; ++q) mine[q] = 0.0;
+      if (threadIdx.x < csize) {
+        const double *pr = cl.map_shared_rank(&part[t & 1][0], threadIdx.x);
+        for (int q = 0; q < NV; ++q) mine[q] = pr[q];
+      }
       double tot[NV];
       for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-      for (unsigned r = 0; r < csize; ++r) {
-        const double *pr = cl.map_shared_rank(&part[t & 1][0], r);
-        for (int q = 0; q < NV; ++q) tot[q] += pr[q];
+      for (unsigned r = 0; r < csize; ++r)
+        for (int q = 0; q < NV; ++q) tot[q] += __shfl_sync(0xffffffffu, mine[q], r);
+      if (threadIdx.x == 0) {
+        if constexpr (FRZ) freeze_step(ctl, fs, t, tot[2]);
+        decide64(ctl, t, tot[0], tot[1]);
+        s_done = ctl->done;
       }
-      if constexpr (FRZ) freeze_step(ctl, fs, t, tot[2]);
-      decide64(ctl, t, tot[0], tot[1]);
-      s_done = ctl->done;
     }
     cl.sync();
     const int done = *cl.map_shared_rank(&s_done, 0);
