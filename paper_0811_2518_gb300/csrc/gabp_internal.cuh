@@ -314,6 +314,8 @@ struct gabp_handle_s {
   gabp::GSell *gsl = nullptr;       // sliced layout of the grid-persistent kernel (built on first use)
   // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
   int clu64 = 0;                    // CTAs of the FP64 cluster rounds (0: graph too large or no support)
+  int chip64_bytes = 0;             // shared memory per CTA of those rounds with all state on chip (0: no fit)
+  int chip64_smax = 0, chip64_rmax = 0;  // own slots and own rows of the largest CTA there
   int coop64 = 0;                   // blocks of the FP64 cooperative rounds (0: graph too large or no support)
   int coop64f = 0;                  // the same for the cooperative rounds with the precision freeze
   int lsq_m = 0, lsq_k = 0;         // 0: not a least-squares handle

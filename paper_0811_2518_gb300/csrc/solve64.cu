@@ -76,16 +76,38 @@ __device__ __forceinline__ WarpPos warp_pos() {
 // Round bookkeeping shared by the FP64 round kernels: this round checked
 // x^{(t-1)} with squared residual rr; 'bad' counts zero cavities / precisions
 // met while computing round t.
-__device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
+// The stopping parameters of a run, read once by a kernel that decides every round itself.
+struct StopRule {
+  double tol2bb;
+  double *hist;
+  int hist_cap, no_stop, check_from, max_iter;
+};
+__device__ __forceinline__ StopRule stop_rule(const DevCtl *ctl) {
+  return StopRule{ctl->tol2bb, ctl->hist, ctl->hist_cap, ctl->no_stop, ctl->check_from, ctl->max_iter};
+}
+// decide64's decision alone: 1 when round t's sums end the run
+__device__ __forceinline__ int stops64(const StopRule &q, int t, double rr, double bad) {
+  const int tchk = t - 1;
+  if (q.no_stop) return 0;
+  return (tchk >= q.check_from && isfinite(rr) && rr <= q.tol2bb) || !isfinite(rr) ||
+         (bad > 0.0 && t <= q.max_iter) || tchk >= q.max_iter;
+}
+
+// Records round t's residual and decision in the control block, with the stopping
+// parameters q (stores only).  FENCE: a kernel whose other blocks read the decision after a
+// grid barrier of its own publishes it with a device-scope fence; a cluster kernel's barrier
+// orders it already.
+template <bool FENCE = true>
+__device__ __forceinline__ void record64(DevCtl *ctl, const StopRule &q, int t, double rr, double bad) {
   const int tchk = t - 1;
   ctl->round = t;
-  if (ctl->hist && tchk < ctl->hist_cap) {  // residual of iterate tchk, before any decision
-    ctl->hist[tchk] = rr;
+  if (q.hist && tchk < q.hist_cap) {  // residual of iterate tchk, before any decision
+    q.hist[tchk] = rr;
     ctl->hist_len = tchk + 1;
   }
-  if (ctl->no_stop) {
+  if (q.no_stop) {
     ctl->rr = rr;
-  } else if (tchk >= ctl->check_from && isfinite(rr) && rr <= ctl->tol2bb) {
+  } else if (tchk >= q.check_from && isfinite(rr) && rr <= q.tol2bb) {
     ctl->status = GABP_OK;
     ctl->iters = tchk;
     ctl->result_round = tchk;
@@ -97,13 +119,13 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
     ctl->result_round = tchk;
     ctl->rr = rr;
     ctl->done = 1;
-  } else if (bad > 0.0 && t <= ctl->max_iter) {
+  } else if (bad > 0.0 && t <= q.max_iter) {
     ctl->status = GABP_BREAKDOWN;
     ctl->iters = t;
     ctl->result_round = tchk;
     ctl->rr = rr;
     ctl->done = 1;
-  } else if (tchk >= ctl->max_iter) {
+  } else if (tchk >= q.max_iter) {
     ctl->status = GABP_NOT_CONVERGED;
     ctl->iters = tchk;
     ctl->result_round = tchk;
@@ -113,7 +135,12 @@ __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double b
     ctl->rr = rr;
   }
   ctl->arrive = 0;
-  __threadfence();
+  if (FENCE) __threadfence();
+}
+
+template <bool FENCE = true>
+__device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
+  record64<FENCE>(ctl, stop_rule(ctl), t, rr, bad);
 }
 
 // Load flavours of the plain round body: the launch-per-round kernel streams its slot
@@ -620,19 +647,53 @@ constexpr int kClusterMax = 16;
 // Larger graphs take the cooperative grid: per round 9.3 against 11.0 us on a 32x32 grid
 // (32 slices), but 12.6 against 10.8 us at 64 slices, where the grid's many SMs win.
 constexpr int kClusterMaxSlices = GABP_CLUSTER_MAX_SLICES;
+
+struct __align__(16) ClusterPart {
+  double rr;  // a warp's sum of its lanes' squared residuals
+  int flags;  // bit 0: a zero cavity or node precision; bit 1: a precision moved (the freeze's screen)
+  int pad;
+};
+struct ClusterSums {
+  double rr;
+  int flags;
+};
+// The sums of a cluster round, the same bits in every thread of the cluster: each warp adds its
+// lanes' residual terms by an xor butterfly (at every step a lane and its partner add the same two
+// values, so all lanes end equal) and lane 0 posts the sum in its CTA's shared memory; after the
+// cluster barrier lane l of every warp fetches warp l's post (warp w of CTA r is warp NW r + w,
+// at most 32 of them) and a second butterfly adds them.  The flags are or-ed.
+template <int NW>
+__device__ __forceinline__ ClusterSums cluster_sums(cooperative_groups::cluster_group &cl, ClusterPart *part,
+                                                    double rr, int flags, int lane, int wib, int nwarps) {
+  const double w = warp_sum(rr);
+  const int f = (int)__reduce_or_sync(0xffffffffu, (unsigned)flags);
+  if (lane == 0) {
+    part[wib].rr = w;
+    part[wib].flags = f;
+  }
+  cl.sync();
+  double x = 0.0;
+  unsigned g = 0;
+  if (lane < nwarps) {
+    const ClusterPart *q = cl.map_shared_rank(part + lane % NW, (unsigned)(lane / NW));
+    x = q->rr;
+    g = (unsigned)q->flags;
+  }
+  return ClusterSums{warp_sum(x), (int)__reduce_or_sync(0xffffffffu, g)};
+}
+
 template <bool FRZ>
 __global__ void __launch_bounds__(kClusterThreads) k64_cluster(Args64 a, int max_rounds) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
-  constexpr int NV = FRZ ? 3 : 2;  // the moving count only with the precision freeze
-  __shared__ double part[2][NV];   // [round parity] {rr, bad, moving}
-  __shared__ int s_done;
+  __shared__ ClusterPart part[2][kClusterThreads / 32];  // [round parity][warp]
   DevCtl *ctl = a.ctl;
   const double *__restrict__ b = ctl->b;
   const int t0 = ctl->round;  // read by every CTA before the first barrier, written only after it
-  const int lane = threadIdx.x & 31;
-  const int warp = (int)(rank * (kClusterThreads / 32) + (threadIdx.x >> 5));
+  const StopRule rule = stop_rule(ctl);  // CTA 0 writes none of these fields
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = (int)(rank * (kClusterThreads / 32)) + wib;
   const int nwarps = (int)(csize * (kClusterThreads / 32));
   for (int iter = 0; iter < max_rounds; ++iter) {
     const int t = t0 + 1 + iter;
@@ -649,37 +710,201 @@ __global__ void __launch_bounds__(kClusterThreads) k64_cluster(Args64 a, int max
       else if (fs == 1) plain_slice<true, 2>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
       else plain_slice<true, 3>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
     }
-    double v[NV];
-    v[0] = rr;
-    v[1] = (double)bad;
-    if constexpr (FRZ) v[2] = (double)moving;
-    block_sum_nt<NV, kClusterThreads>(v);
-    if (threadIdx.x == 0)
-      for (int q = 0; q < NV; ++q) part[t & 1][q] = v[q];
-    cl.sync();
-    if (rank == 0 && threadIdx.x < 32) {
-      // lane r fetches CTA r's partials (the remote reads in parallel), lane 0 adds them in rank order
-      double mine[NV];
-      for (int q = 0; q < NV; ++q) mine[q] = 0.0;
-      if (threadIdx.x < csize) {
-        const double *pr = cl.map_shared_rank(&part[t & 1][0], threadIdx.x);
-        for (int q = 0; q < NV; ++q) mine[q] = pr[q];
+    const ClusterSums tot =
+        cluster_sums<kClusterThreads / 32>(cl, part[t & 1], rr, (bad ? 1 : 0) | (moving ? 2 : 0), lane, wib, nwarps);
+    const bool stop = stops64(rule, t, tot.rr, tot.flags & 1);
+    if (rank == 0 && threadIdx.x == 0) {
+      if constexpr (FRZ) freeze_step(ctl, fs, t, (tot.flags & 2) ? 1.0 : 0.0);
+      record64<false>(ctl, rule, t, tot.rr, tot.flags & 1);
+    }
+    if (stop) break;
+    if constexpr (FRZ) cl.sync();  // the freeze state CTA 0 wrote is read by every CTA next round
+  }
+  cl.sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
+// The cluster rounds with the whole state in the cluster's shared memory, for graphs
+// whose state fits: each CTA holds its own rows' records (both rounds'), b and A_ii,
+// and its own slots' reverse references, values and messages (both rounds').  A slot
+// reads the sender's record and the reverse message from the CTA that owns the sender
+// -- the reverse slot sits in the sender's row, so one CTA holds both -- through
+// distributed shared memory; everything a round writes stays in its own CTA, and the
+// round's only global-memory traffic is the control block.  The slices, warps, lanes
+// and sums are k64_cluster's, so every value is bitwise the same; the state is loaded
+// from and written back to the global arrays (both parities) around the rounds.
+struct ChipShape {
+  int smax;  // own slots of the largest CTA
+  int rmax;  // own rows (32 per own slice) of the largest CTA
+};
+__host__ __device__ inline size_t chip_bytes(const ChipShape &c, int ns) {
+  return (size_t)48 * c.smax + (size_t)84 * c.rmax + (size_t)8 * ns + (size_t)128 * ns;
+}
+// a row's place in its owner CTA: slice s belongs to warp s mod 2cs, i.e. CTA (s mod 2cs) / 2,
+// which holds its slices in increasing order, 32 rows each
+__device__ __forceinline__ int chip_row_ref(int s, int lane, int nwarps) {
+  const int o = (s % nwarps) >> 1, q = 2 * (s / nwarps) + ((s % nwarps) & 1);
+  return (o << 24) | (q * 32 + lane);
+}
+
+__global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape c, int max_rounds) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+  extern __shared__ __align__(32) unsigned char smem[];
+  NodeRec64 *R0 = reinterpret_cast<NodeRec64 *>(smem);  // own rows, by local row
+  NodeRec64 *R1 = R0 + c.rmax;
+  double2 *Ml0 = reinterpret_cast<double2 *>(R1 + c.rmax);  // own slots, by local slot
+  double2 *Ml1 = Ml0 + c.smax;
+  double *savl = reinterpret_cast<double *>(Ml1 + c.smax);
+  double *bl = savl + c.smax;
+  double *dl = bl + c.rmax;
+  int *kref = reinterpret_cast<int *>(dl + c.rmax);  // sender: owner rank << 24 | its local row (-1: padding)
+  int *rref = kref + c.smax;                         // reverse slot: owner rank << 24 | its local slot
+  int *srowl = rref + c.smax;
+  int2 *tab = reinterpret_cast<int2 *>(srowl + c.rmax);  // per slice: owner rank, local first slot
+  int *inv = reinterpret_cast<int *>(tab + a.ns);        // per row: its slice position (set-up only)
+  __shared__ ClusterPart part[2][kClusterThreads / 32];
+  DevCtl *ctl = a.ctl;
+  const double *__restrict__ b = ctl->b;
+  const int t0 = ctl->round;
+  const StopRule rule = stop_rule(ctl);  // CTA 0 writes none of these fields
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = (int)(rank * (kClusterThreads / 32)) + wib;
+  const int nwarps = (int)(csize * (kClusterThreads / 32));
+  if (threadIdx.x == 0) {
+    int base[kClusterMax];
+    for (int r = 0; r < kClusterMax; ++r) base[r] = 0;
+    for (int sl = 0; sl < a.ns; ++sl) {
+      const int o = (sl % nwarps) / 2;
+      tab[sl] = make_int2(o, base[o]);
+      base[o] += a.sp[sl + 1] - a.sp[sl];
+    }
+  }
+  for (int e = threadIdx.x; e < 32 * a.ns; e += kClusterThreads) {
+    const int i = a.srow[e];
+    if (i >= 0) inv[i] = e;
+  }
+  __syncthreads();
+  {
+    int q = 0;  // own slice index
+    for (int sl = 0; sl < a.ns; ++sl) {
+      if ((int)tab[sl].x != (int)rank) continue;
+      const int p0 = a.sp[sl], wd = (a.sp[sl + 1] - p0) >> 5, lb = tab[sl].y;
+      for (int e = threadIdx.x; e < 32; e += kClusterThreads) {
+        const int i = a.srow[sl * 32 + e], lr = q * 32 + e;
+        srowl[lr] = i;
+        bl[lr] = i >= 0 ? b[i] : 0.0;
+        dl[lr] = i >= 0 ? a.ad[i] : 0.0;
+        if (i >= 0) {  // both parities, so the write-back returns what the rounds do not change
+          R0[lr] = a.N0[i];
+          R1[lr] = a.N1[i];
+        }
       }
-      double tot[NV];
-      for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-      for (unsigned r = 0; r < csize; ++r)
-        for (int q = 0; q < NV; ++q) tot[q] += __shfl_sync(0xffffffffu, mine[q], r);
-      if (threadIdx.x == 0) {
-        if constexpr (FRZ) freeze_step(ctl, fs, t, tot[2]);
-        decide64(ctl, t, tot[0], tot[1]);
-        s_done = ctl->done;
+      for (int e = threadIdx.x; e < 32 * wd; e += kClusterThreads) {
+        const int pos = p0 + e, li = lb + e;
+        const int k = a.sci[pos];
+        savl[li] = a.sav[pos];
+        Ml0[li] = a.M0[pos];
+        Ml1[li] = a.M1[pos];
+        int kr = -1, rr = 0;
+        if (k >= 0) {
+          const int ek = inv[k];
+          kr = chip_row_ref(ek >> 5, ek & 31, nwarps);
+          const int rp = a.srev[pos];
+          int lo = 0, hi = a.ns - 1;  // the slice holding position rp
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.sp[mid] <= rp) lo = mid; else hi = mid - 1;
+          }
+          rr = (tab[lo].x << 24) | (tab[lo].y + (rp - a.sp[lo]));
+        }
+        kref[li] = kr;
+        rref[li] = rr;
+      }
+      ++q;
+    }
+  }
+  cl.sync();  // every CTA's state is in place before any peer reads it
+  int ran = 0;
+  for (int iter = 0; iter < max_rounds; ++iter) {
+    const int t = t0 + 1 + iter;
+    const NodeRec64 *Rin = (t & 1) ? R0 : R1;  // round t-1
+    NodeRec64 *Rout = (t & 1) ? R1 : R0;
+    double2 *Min = (t & 1) ? Ml0 : Ml1;
+    double2 *Mout = (t & 1) ? Ml1 : Ml0;
+    double rr = 0.0;
+    int bad = 0;
+    for (int sl = warp, qq = wib; sl < a.ns; sl += nwarps, qq += 2) {
+      const int lb = tab[sl].y, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
+      const int lr = qq * 32 + lane, i = srowl[lr];
+      double accP = 0.0, acch = 0.0, accr = 0.0;
+      for (int j = 0; j < wd; j += kU64) {
+        int kr[kU64];
+        double A[kU64];
+        double2 rv[kU64];
+        NodeRec64 nk[kU64];
+#pragma unroll
+        for (int u = 0; u < kU64; ++u) {
+          const int li = lb + 32 * (j + u) + lane;
+          kr[u] = j + u < wd ? kref[li] : -1;
+          if (kr[u] >= 0) {
+            A[u] = savl[li];
+            const int ref = rref[li];
+            rv[u] = *cl.map_shared_rank(Min + (ref & 0xffffff), (unsigned)(ref >> 24));  // message i -> k at t-1
+            nk[u] = *cl.map_shared_rank(Rin + (kr[u] & 0xffffff), (unsigned)(kr[u] >> 24));  // node k at t-1
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU64; ++u) {
+          if (kr[u] < 0) continue;
+          const double den = nk[u].P - rv[u].x;
+          bad |= is_zero64(den);
+          const double cin = -A[u] * rcp64(den);
+          const double2 m = make_double2(__dmul_rn(cin, A[u]), __dmul_rn(cin, nk[u].h - rv[u].y));
+          Mout[lb + 32 * (j + u) + lane] = m;
+          accP = __dadd_rn(accP, m.x);
+          acch = __dadd_rn(acch, m.y);
+          accr = fma(A[u], nk[u].x, accr);
+        }
+      }
+      if (i >= 0) {
+        const double bi = bl[lr], d = dl[lr];
+        const NodeRec64 own = Rin[lr];
+        const double P = d + accP, h = bi + acch;
+        bad |= is_zero64(P);
+        const double ip = rcp64(P);
+        Rout[lr] = NodeRec64{P, h, h * ip, h * ip};
+        const double res = bi - fma(d, own.x, accr);
+        rr = fma(res, res, rr);
       }
     }
-    cl.sync();
-    const int done = *cl.map_shared_rank(&s_done, 0);
-    if (done) break;
+    ++ran;
+    const ClusterSums tot = cluster_sums<kClusterThreads / 32>(cl, part[t & 1], rr, bad, lane, wib, nwarps);
+    if (rank == 0 && threadIdx.x == 0) record64<false>(ctl, rule, t, tot.rr, tot.flags & 1);
+    if (stops64(rule, t, tot.rr, tot.flags & 1)) break;
   }
-  cl.sync();  // CTA 0's shared memory stays until every CTA has read it
+  // back to the global arrays, both parities: the own slots' messages and the own rows' records
+  // (rounds run: the last wrote after its barrier's arrival of every warp, read here after it)
+  if (ran > 0) {
+    int q = 0;
+    for (int sl = 0; sl < a.ns; ++sl) {
+      if ((int)tab[sl].x != (int)rank) continue;
+      const int p0 = a.sp[sl], wd = (a.sp[sl + 1] - p0) >> 5, lb = tab[sl].y;
+      for (int e = threadIdx.x; e < 32 * wd; e += kClusterThreads) {
+        a.M0[p0 + e] = Ml0[lb + e];
+        a.M1[p0 + e] = Ml1[lb + e];
+      }
+      for (int e = threadIdx.x; e < 32; e += kClusterThreads) {
+        const int i = srowl[q * 32 + e];
+        if (i >= 0) {
+          a.N0[i] = R0[q * 32 + e];
+          a.N1[i] = R1[q * 32 + e];
+        }
+      }
+      ++q;
+    }
+  }
+  cl.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
 // Steffensen's iterations, the step after a cycle's second round t: "y replaces
@@ -959,6 +1184,46 @@ static gabp_status ensure_sell64(gabp_handle h) {
         h->clu64 = cs;
       cudaGetLastError();
     }
+    // the same cluster with every array in shared memory, where it fits: the slices' owners as the
+    // kernel assigns them (slice s to warp s mod 2cs, two warps a CTA)
+    h->chip64_bytes = h->chip64_smax = h->chip64_rmax = 0;
+    if (h->clu64 > 0) {
+      const int cs = h->clu64, nw = 2 * cs;
+      std::vector<int64_t> own_slots(cs, 0), own_rows(cs, 0);
+      for (int sl = 0; sl < ns; ++sl) {
+        const int o = (sl % nw) / 2;
+        own_slots[o] += sp[sl + 1] - sp[sl];
+        own_rows[o] += 32;
+      }
+      const int64_t smax = *std::max_element(own_slots.begin(), own_slots.end());
+      const int64_t rmax = *std::max_element(own_rows.begin(), own_rows.end());
+      int optin = 0;
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+      const ChipShape c{(int)std::min<int64_t>(smax, INT32_MAX), (int)rmax};
+      const size_t bytes = chip_bytes(c, ns);
+      if (smax < (1 << 24) && bytes + 256 <= (size_t)optin &&
+          cudaFuncSetAttribute(k64_chip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+          (cs <= 8 || cudaFuncSetAttribute(k64_chip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(kClusterThreads);
+        cfg.dynamicSmemBytes = bytes;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, (void *)k64_chip, &cfg) == cudaSuccess && nc > 0) {
+          h->chip64_bytes = (int)bytes;
+          h->chip64_smax = c.smax;
+          h->chip64_rmax = c.rmax;
+        }
+      }
+      cudaGetLastError();
+    }
     h->coop64 = h->coop64f = 0;
     int coop_attr = 0;
     cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, h->device);
@@ -1158,9 +1423,14 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const int max_rounds = max_iter + 2;
+    // plain rounds with the state on chip where it fits (the same values: same slices, lanes and sums)
+    const bool chip = !a.freeze && h->chip64_bytes > 0;
+    if (chip) cfg.dynamicSmemBytes = h->chip64_bytes;
     prof_begin(h);
-    cudaError_t le = a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true>, a, max_rounds)
-                              : cudaLaunchKernelEx(&cfg, k64_cluster<false>, a, max_rounds);
+    cudaError_t le =
+        chip ? cudaLaunchKernelEx(&cfg, k64_chip, a, ChipShape{h->chip64_smax, h->chip64_rmax}, max_rounds)
+        : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true>, a, max_rounds)
+                   : cudaLaunchKernelEx(&cfg, k64_cluster<false>, a, max_rounds);
     if (le != cudaSuccess) return cuda_fail(le, "FP64 cluster rounds");
     prof_end(h);
     h->prof.launches += 1;

@@ -373,20 +373,27 @@ def test_cooperative_threshold(gb, p):
         assert launches > 3
 
 
-@pytest.mark.parametrize("n", [1, 33, 200, 1024, 1280, 1281, 2048])
-def test_cluster_rounds_small_graphs(gb, n):
+@pytest.mark.parametrize("n,deg", [(1, 0), (33, 4), (200, 4), (1024, 4), (1280, 4), (1280, 20), (1281, 4),
+                                   (2048, 4)])
+def test_cluster_rounds_small_graphs(gb, n, deg):
     """Graphs of at most 40 slices (1280 rows) run every plain FP64 round in one thread-block
-    cluster (hardware cluster barrier, partial sums through distributed shared memory); 1281 rows
-    (41 slices) and 2048 take the cooperative grid.  Iterates at fixed rounds equal the oracle's to 1e-13,
-    the converged round count is the oracle's, and the solve is three launches."""
-    m = synth.random_sym(n, min(4, n - 1), 1.1, 3) if n > 1 else synth.from_dense(np.array([[2.0]]))
+    cluster (hardware cluster barrier, partial sums through distributed shared memory); those whose
+    state fits in the cluster's shared memory keep it there (every degree-4 case up to 1280 rows),
+    the 1280-row graph of degree 20 (about 280 KB a CTA) reads it from global memory; 1281 rows (41
+    slices) and 2048 take the cooperative grid.  Iterates at fixed rounds equal the oracle's to
+    1e-13, the converged round count is the oracle's, and the solve is three launches."""
+    m = synth.random_sym(n, deg, 1.1, 3) if n > 1 else synth.from_dense(np.array([[2.0]]))
     b = synth.rhs(m.n, 8)
     for t in (1, 2, 7):
-        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0)
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0, messages=True)
         g = _gpu_solve(gb, m, b, 0.0, t)
         # a residual of exactly 0 meets tol = 0 (the one-node system is solved at round 1)
         assert g["iters"] == t or (g["status"] == gb.GABP_OK and g["relres"] == 0.0), t
         assert _relerr(g["x"], r["x"]) <= 1e-13, t
+        if g["iters"] == t and n > 1:  # the messages of round t, written back from the cluster
+            off = ~_diag_mask(m)
+            assert np.allclose(g["Pmsg"][off], r["Pmsg"][off], rtol=1e-13, atol=1e-15), t
+            assert np.allclose(g["hmsg"][off], (r["Pmsg"] * r["mumsg"])[off], rtol=1e-12, atol=1e-14), t
     ref = oracle.gabp_broadcast(m, b, max_iter=3000, tol=1e-12)
     s = _solver(gb, m, profile=1)
     s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
