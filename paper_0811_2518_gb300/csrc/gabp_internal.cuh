@@ -314,6 +314,7 @@ struct gabp_handle_s {
   gabp::GSell *gsl = nullptr;       // sliced layout of the grid-persistent kernel (built on first use)
   // least squares (gabp_create_lsq): the handle's matrix is [[I_k, J^T], [J, -gamma I_m]]
   int clu64 = 0;                    // CTAs of the FP64 cluster rounds (0: graph too large or no support)
+  int clu64_nw = 0;                 // warps per CTA there (2 or 4)
   int chip64_bytes = 0;             // shared memory per CTA of those rounds with all state on chip (0: no fit)
   int chip64_smax = 0, chip64_rmax = 0;  // own slots and own rows of the largest CTA there
   int coop64 = 0;                   // blocks of the FP64 cooperative rounds (0: graph too large or no support)

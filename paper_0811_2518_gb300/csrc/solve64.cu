@@ -631,21 +631,19 @@ __global__ void __launch_bounds__(kCoopThreads, FRZ ? 8 : 0) k64_coop(Args64 a, 
   }
 }
 
-// Every plain round of a small graph in one thread-block cluster (up to 16 CTAs of
-// two warps, one SM each): the cluster's hardware barrier replaces the grid
-// barrier.  Per round each CTA writes its partial sums to its shared memory; after
-// a cluster barrier CTA 0 sums them in rank order (distributed shared memory),
-// decides and publishes the decision in its shared memory; after a second barrier
-// every CTA reads it, so all leave after the same round (no wait can be left
-// open).  Data written by other CTAs is read through L2 (plain_slice's cooperative
-// flavour); the barriers release and acquire at cluster scope.
-constexpr int kClusterThreads = 64;
+// Every plain round of a small graph in one thread-block cluster (up to 16 CTAs of NW
+// warps, one SM each, a slice per warp): the cluster's hardware barrier replaces the
+// grid barrier.  Per round every warp posts its residual sum in its CTA's shared
+// memory; after the cluster barrier every warp fetches all posts (distributed shared
+// memory), adds them the same way and takes the same decision, so all CTAs leave after
+// the same round (no wait can be left open) and CTA 0 records it.  Data written by
+// other CTAs is read through L2 (plain_slice's cooperative flavour); the barrier
+// releases and acquires at cluster scope.  Two warps a CTA up to 32 slices; four (all
+// four schedulers of the SM, each with its own FP64 unit) up to 64.
 constexpr int kClusterMax = 16;
 #ifndef GABP_CLUSTER_MAX_SLICES
-#define GABP_CLUSTER_MAX_SLICES 40
+#define GABP_CLUSTER_MAX_SLICES 64
 #endif
-// Larger graphs take the cooperative grid: per round 9.3 against 11.0 us on a 32x32 grid
-// (32 slices), but 12.6 against 10.8 us at 64 slices, where the grid's many SMs win.
 constexpr int kClusterMaxSlices = GABP_CLUSTER_MAX_SLICES;
 
 struct __align__(16) ClusterPart {
@@ -660,8 +658,8 @@ struct ClusterSums {
 // The sums of a cluster round, the same bits in every thread of the cluster: each warp adds its
 // lanes' residual terms by an xor butterfly (at every step a lane and its partner add the same two
 // values, so all lanes end equal) and lane 0 posts the sum in its CTA's shared memory; after the
-// cluster barrier lane l of every warp fetches warp l's post (warp w of CTA r is warp NW r + w,
-// at most 32 of them) and a second butterfly adds them.  The flags are or-ed.
+// cluster barrier lane l of every warp fetches the posts of warps l and l + 32 (warp w of CTA r
+// is warp NW r + w, at most 64 of them) and a second butterfly adds them.  The flags are or-ed.
 template <int NW>
 __device__ __forceinline__ ClusterSums cluster_sums(cooperative_groups::cluster_group &cl, ClusterPart *part,
                                                     double rr, int flags, int lane, int wib, int nwarps) {
@@ -674,27 +672,27 @@ __device__ __forceinline__ ClusterSums cluster_sums(cooperative_groups::cluster_
   cl.sync();
   double x = 0.0;
   unsigned g = 0;
-  if (lane < nwarps) {
-    const ClusterPart *q = cl.map_shared_rank(part + lane % NW, (unsigned)(lane / NW));
-    x = q->rr;
-    g = (unsigned)q->flags;
+  for (int v = lane; v < nwarps; v += 32) {  // lane l: warps l and l + 32
+    const ClusterPart *q = cl.map_shared_rank(part + v % NW, (unsigned)(v / NW));
+    x += q->rr;
+    g |= (unsigned)q->flags;
   }
   return ClusterSums{warp_sum(x), (int)__reduce_or_sync(0xffffffffu, g)};
 }
 
-template <bool FRZ>
-__global__ void __launch_bounds__(kClusterThreads) k64_cluster(Args64 a, int max_rounds) {
+template <bool FRZ, int NW>
+__global__ void __launch_bounds__(32 * NW) k64_cluster(Args64 a, int max_rounds) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
-  __shared__ ClusterPart part[2][kClusterThreads / 32];  // [round parity][warp]
+  __shared__ ClusterPart part[2][NW];  // [round parity][warp]
   DevCtl *ctl = a.ctl;
   const double *__restrict__ b = ctl->b;
   const int t0 = ctl->round;  // read by every CTA before the first barrier, written only after it
   const StopRule rule = stop_rule(ctl);  // CTA 0 writes none of these fields
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int warp = (int)(rank * (kClusterThreads / 32)) + wib;
-  const int nwarps = (int)(csize * (kClusterThreads / 32));
+  const int warp = (int)(rank * NW) + wib;
+  const int nwarps = (int)(csize * NW);
   for (int iter = 0; iter < max_rounds; ++iter) {
     const int t = t0 + 1 + iter;
     const int fs = FRZ ? __ldcg(&ctl->fstate) : -1;  // written by CTA 0 before the last barrier
@@ -711,7 +709,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_cluster(Args64 a, int max
       else plain_slice<true, 3>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
     }
     const ClusterSums tot =
-        cluster_sums<kClusterThreads / 32>(cl, part[t & 1], rr, (bad ? 1 : 0) | (moving ? 2 : 0), lane, wib, nwarps);
+        cluster_sums<NW>(cl, part[t & 1], rr, (bad ? 1 : 0) | (moving ? 2 : 0), lane, wib, nwarps);
     const bool stop = stops64(rule, t, tot.rr, tot.flags & 1);
     if (rank == 0 && threadIdx.x == 0) {
       if constexpr (FRZ) freeze_step(ctl, fs, t, (tot.flags & 2) ? 1.0 : 0.0);
@@ -739,14 +737,17 @@ struct ChipShape {
 __host__ __device__ inline size_t chip_bytes(const ChipShape &c, int ns) {
   return (size_t)48 * c.smax + (size_t)84 * c.rmax + (size_t)8 * ns + (size_t)128 * ns;
 }
-// a row's place in its owner CTA: slice s belongs to warp s mod 2cs, i.e. CTA (s mod 2cs) / 2,
-// which holds its slices in increasing order, 32 rows each
-__device__ __forceinline__ int chip_row_ref(int s, int lane, int nwarps) {
-  const int o = (s % nwarps) >> 1, q = 2 * (s / nwarps) + ((s % nwarps) & 1);
+// a row's place in its owner CTA: slice s belongs to warp s mod (NW cs), i.e. CTA
+// (s mod NW cs) / NW, which holds its slices in increasing order, 32 rows each
+template <int NW>
+__host__ __device__ __forceinline__ int chip_row_ref(int s, int lane, int nwarps) {
+  const int o = (s % nwarps) / NW, q = NW * (s / nwarps) + (s % nwarps) % NW;
   return (o << 24) | (q * 32 + lane);
 }
 
-__global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape c, int max_rounds) {
+template <int NW>
+__global__ void __launch_bounds__(32 * NW) k64_chip(Args64 a, ChipShape c, int max_rounds) {
+  constexpr int NT = 32 * NW;
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
@@ -763,24 +764,24 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
   int *srowl = rref + c.smax;
   int2 *tab = reinterpret_cast<int2 *>(srowl + c.rmax);  // per slice: owner rank, local first slot
   int *inv = reinterpret_cast<int *>(tab + a.ns);        // per row: its slice position (set-up only)
-  __shared__ ClusterPart part[2][kClusterThreads / 32];
+  __shared__ ClusterPart part[2][NW];
   DevCtl *ctl = a.ctl;
   const double *__restrict__ b = ctl->b;
   const int t0 = ctl->round;
   const StopRule rule = stop_rule(ctl);  // CTA 0 writes none of these fields
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int warp = (int)(rank * (kClusterThreads / 32)) + wib;
-  const int nwarps = (int)(csize * (kClusterThreads / 32));
+  const int warp = (int)(rank * NW) + wib;
+  const int nwarps = (int)(csize * NW);
   if (threadIdx.x == 0) {
     int base[kClusterMax];
     for (int r = 0; r < kClusterMax; ++r) base[r] = 0;
     for (int sl = 0; sl < a.ns; ++sl) {
-      const int o = (sl % nwarps) / 2;
+      const int o = (sl % nwarps) / NW;
       tab[sl] = make_int2(o, base[o]);
       base[o] += a.sp[sl + 1] - a.sp[sl];
     }
   }
-  for (int e = threadIdx.x; e < 32 * a.ns; e += kClusterThreads) {
+  for (int e = threadIdx.x; e < 32 * a.ns; e += NT) {
     const int i = a.srow[e];
     if (i >= 0) inv[i] = e;
   }
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
     for (int sl = 0; sl < a.ns; ++sl) {
       if ((int)tab[sl].x != (int)rank) continue;
       const int p0 = a.sp[sl], wd = (a.sp[sl + 1] - p0) >> 5, lb = tab[sl].y;
-      for (int e = threadIdx.x; e < 32; e += kClusterThreads) {
+      for (int e = threadIdx.x; e < 32; e += NT) {
         const int i = a.srow[sl * 32 + e], lr = q * 32 + e;
         srowl[lr] = i;
         bl[lr] = i >= 0 ? b[i] : 0.0;
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
           R1[lr] = a.N1[i];
         }
       }
-      for (int e = threadIdx.x; e < 32 * wd; e += kClusterThreads) {
+      for (int e = threadIdx.x; e < 32 * wd; e += NT) {
         const int pos = p0 + e, li = lb + e;
         const int k = a.sci[pos];
         savl[li] = a.sav[pos];
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
         int kr = -1, rr = 0;
         if (k >= 0) {
           const int ek = inv[k];
-          kr = chip_row_ref(ek >> 5, ek & 31, nwarps);
+          kr = chip_row_ref<NW>(ek >> 5, ek & 31, nwarps);
           const int rp = a.srev[pos];
           int lo = 0, hi = a.ns - 1;  // the slice holding position rp
           while (lo < hi) {
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
     double2 *Mout = (t & 1) ? Ml1 : Ml0;
     double rr = 0.0;
     int bad = 0;
-    for (int sl = warp, qq = wib; sl < a.ns; sl += nwarps, qq += 2) {
+    for (int sl = warp, qq = wib; sl < a.ns; sl += nwarps, qq += NW) {
       const int lb = tab[sl].y, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
       const int lr = qq * 32 + lane, i = srowl[lr];
       double accP = 0.0, acch = 0.0, accr = 0.0;
@@ -879,7 +880,7 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
       }
     }
     ++ran;
-    const ClusterSums tot = cluster_sums<kClusterThreads / 32>(cl, part[t & 1], rr, bad, lane, wib, nwarps);
+    const ClusterSums tot = cluster_sums<NW>(cl, part[t & 1], rr, bad, lane, wib, nwarps);
     if (rank == 0 && threadIdx.x == 0) record64<false>(ctl, rule, t, tot.rr, tot.flags & 1);
     if (stops64(rule, t, tot.rr, tot.flags & 1)) break;
   }
@@ -890,11 +891,11 @@ __global__ void __launch_bounds__(kClusterThreads) k64_chip(Args64 a, ChipShape 
     for (int sl = 0; sl < a.ns; ++sl) {
       if ((int)tab[sl].x != (int)rank) continue;
       const int p0 = a.sp[sl], wd = (a.sp[sl + 1] - p0) >> 5, lb = tab[sl].y;
-      for (int e = threadIdx.x; e < 32 * wd; e += kClusterThreads) {
+      for (int e = threadIdx.x; e < 32 * wd; e += NT) {
         a.M0[p0 + e] = Ml0[lb + e];
         a.M1[p0 + e] = Ml1[lb + e];
       }
-      for (int e = threadIdx.x; e < 32; e += kClusterThreads) {
+      for (int e = threadIdx.x; e < 32; e += NT) {
         const int i = srowl[q * 32 + e];
         if (i >= 0) {
           a.N0[i] = R0[q * 32 + e];
@@ -1103,6 +1104,63 @@ __global__ void k_grad_values(int n, const int *__restrict__ rowptr, const int *
 // The sliced layout of the handle's graph (once per handle; the values again after
 // gabp_set_values).  The row order (degree-sorted windows) and the slice offsets are
 // computed on the host from the row lengths; the arrays are filled on the device.
+// The cluster rounds' shape for a graph of sp.size() - 1 slices, NW warps a CTA: the cluster
+// size when both k64_cluster flavours fit on the device, and the shared memory of k64_chip,
+// from the slices its CTAs own (slice s to CTA (s mod NW cs) / NW), when that fits too.
+template <int NW>
+static void cluster_setup(gabp_handle h, const std::vector<int> &sp) {
+  const int ns = (int)sp.size() - 1;
+  const int cs = std::min(kClusterMax, std::max(1, (ns + NW - 1) / NW));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(32 * NW);
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cs > 8) {
+    cudaFuncSetAttribute(k64_cluster<false, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k64_cluster<true, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  int nc0 = 0, nc1 = 0;  // both flavours must fit (the same cluster serves both)
+  if (cudaOccupancyMaxActiveClusters(&nc0, (void *)k64_cluster<false, NW>, &cfg) == cudaSuccess && nc0 > 0 &&
+      cudaOccupancyMaxActiveClusters(&nc1, (void *)k64_cluster<true, NW>, &cfg) == cudaSuccess && nc1 > 0) {
+    h->clu64 = cs;
+    h->clu64_nw = NW;
+  }
+  cudaGetLastError();
+  if (h->clu64 == 0) return;
+  const int nw = NW * cs;
+  std::vector<int64_t> own_slots(cs, 0), own_rows(cs, 0);
+  for (int sl = 0; sl < ns; ++sl) {
+    const int o = (sl % nw) / NW;
+    own_slots[o] += sp[sl + 1] - sp[sl];
+    own_rows[o] += 32;
+  }
+  const int64_t smax = *std::max_element(own_slots.begin(), own_slots.end());
+  const int64_t rmax = *std::max_element(own_rows.begin(), own_rows.end());
+  if (smax >= (1 << 24)) return;
+  const ChipShape c{(int)smax, (int)rmax};
+  const size_t bytes = chip_bytes(c, ns);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (bytes + 256 > (size_t)optin) return;
+  if (cudaFuncSetAttribute(k64_chip<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+      (cs <= 8 || cudaFuncSetAttribute(k64_chip<NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+    cfg.dynamicSmemBytes = bytes;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (void *)k64_chip<NW>, &cfg) == cudaSuccess && nc > 0) {
+      h->chip64_bytes = (int)bytes;
+      h->chip64_smax = c.smax;
+      h->chip64_rmax = c.rmax;
+    }
+  }
+  cudaGetLastError();
+}
+
 static gabp_status ensure_sell64(gabp_handle h) {
   Sell64 &S = h->w64.sl;
   Graph &g = h->g;
@@ -1159,71 +1217,15 @@ static gabp_status ensure_sell64(gabp_handle h) {
     S.ready = true;
     S.vals_ok = true;
     h->tuned_L64 = 1;  // one row per lane
-    // the cooperative launch for small graphs: one block per two slices, all co-resident
-    // one cluster of up to 16 CTAs (two warps each, a slice per warp) for the smallest graphs
-    h->clu64 = 0;
-    if (S.ns <= kClusterMaxSlices) {
-      const int cs = std::min(kClusterMax, std::max(1, (S.ns + 1) / 2));
-      if (cs > 8) {
-        cudaFuncSetAttribute(k64_cluster<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(k64_cluster<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = cs;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(cs);
-      cfg.blockDim = dim3(kClusterThreads);
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int nc0 = 0, nc1 = 0;  // both flavours must fit (the same cluster size serves both)
-      if (cudaOccupancyMaxActiveClusters(&nc0, (void *)k64_cluster<false>, &cfg) == cudaSuccess && nc0 > 0 &&
-          cudaOccupancyMaxActiveClusters(&nc1, (void *)k64_cluster<true>, &cfg) == cudaSuccess && nc1 > 0)
-        h->clu64 = cs;
-      cudaGetLastError();
-    }
-    // the same cluster with every array in shared memory, where it fits: the slices' owners as the
-    // kernel assigns them (slice s to warp s mod 2cs, two warps a CTA)
+    // one cluster of up to 16 CTAs (a slice per warp) for the smallest graphs, its state on chip
+    // where it fits
+    h->clu64 = h->clu64_nw = 0;
     h->chip64_bytes = h->chip64_smax = h->chip64_rmax = 0;
-    if (h->clu64 > 0) {
-      const int cs = h->clu64, nw = 2 * cs;
-      std::vector<int64_t> own_slots(cs, 0), own_rows(cs, 0);
-      for (int sl = 0; sl < ns; ++sl) {
-        const int o = (sl % nw) / 2;
-        own_slots[o] += sp[sl + 1] - sp[sl];
-        own_rows[o] += 32;
-      }
-      const int64_t smax = *std::max_element(own_slots.begin(), own_slots.end());
-      const int64_t rmax = *std::max_element(own_rows.begin(), own_rows.end());
-      int optin = 0;
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-      const ChipShape c{(int)std::min<int64_t>(smax, INT32_MAX), (int)rmax};
-      const size_t bytes = chip_bytes(c, ns);
-      if (smax < (1 << 24) && bytes + 256 <= (size_t)optin &&
-          cudaFuncSetAttribute(k64_chip, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
-          (cs <= 8 || cudaFuncSetAttribute(k64_chip, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = cs;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(cs);
-        cfg.blockDim = dim3(kClusterThreads);
-        cfg.dynamicSmemBytes = bytes;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, (void *)k64_chip, &cfg) == cudaSuccess && nc > 0) {
-          h->chip64_bytes = (int)bytes;
-          h->chip64_smax = c.smax;
-          h->chip64_rmax = c.rmax;
-        }
-      }
-      cudaGetLastError();
+    if (S.ns <= kClusterMaxSlices) {
+      if (S.ns <= 32) cluster_setup<2>(h, sp);
+      else cluster_setup<4>(h, sp);
     }
+    // the cooperative launch for small graphs: one block per two slices, all co-resident
     h->coop64 = h->coop64f = 0;
     int coop_attr = 0;
     cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, h->device);
@@ -1418,7 +1420,7 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(h->clu64);
-    cfg.blockDim = dim3(kClusterThreads);
+    cfg.blockDim = dim3(32 * h->clu64_nw);
     cfg.stream = h->stream;
     cfg.attrs = at;
     cfg.numAttrs = 1;
@@ -1427,10 +1429,16 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
     const bool chip = !a.freeze && h->chip64_bytes > 0;
     if (chip) cfg.dynamicSmemBytes = h->chip64_bytes;
     prof_begin(h);
-    cudaError_t le =
-        chip ? cudaLaunchKernelEx(&cfg, k64_chip, a, ChipShape{h->chip64_smax, h->chip64_rmax}, max_rounds)
-        : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true>, a, max_rounds)
-                   : cudaLaunchKernelEx(&cfg, k64_cluster<false>, a, max_rounds);
+    const ChipShape cs{h->chip64_smax, h->chip64_rmax};
+    cudaError_t le;
+    if (h->clu64_nw == 2)
+      le = chip ? cudaLaunchKernelEx(&cfg, k64_chip<2>, a, cs, max_rounds)
+           : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true, 2>, a, max_rounds)
+                      : cudaLaunchKernelEx(&cfg, k64_cluster<false, 2>, a, max_rounds);
+    else
+      le = chip ? cudaLaunchKernelEx(&cfg, k64_chip<4>, a, cs, max_rounds)
+           : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true, 4>, a, max_rounds)
+                      : cudaLaunchKernelEx(&cfg, k64_cluster<false, 4>, a, max_rounds);
     if (le != cudaSuccess) return cuda_fail(le, "FP64 cluster rounds");
     prof_end(h);
     h->prof.launches += 1;

@@ -374,14 +374,15 @@ def test_cooperative_threshold(gb, p):
 
 
 @pytest.mark.parametrize("n,deg", [(1, 0), (33, 4), (200, 4), (1024, 4), (1280, 4), (1280, 20), (1281, 4),
-                                   (2048, 4)])
+                                   (2048, 4), (2048, 20), (2049, 4), (4096, 4)])
 def test_cluster_rounds_small_graphs(gb, n, deg):
-    """Graphs of at most 40 slices (1280 rows) run every plain FP64 round in one thread-block
-    cluster (hardware cluster barrier, partial sums through distributed shared memory); those whose
-    state fits in the cluster's shared memory keep it there (every degree-4 case up to 1280 rows),
-    the 1280-row graph of degree 20 (about 280 KB a CTA) reads it from global memory; 1281 rows (41
-    slices) and 2048 take the cooperative grid.  Iterates at fixed rounds equal the oracle's to
-    1e-13, the converged round count is the oracle's, and the solve is three launches."""
+    """Graphs of at most 64 slices (2048 rows) run every plain FP64 round in one thread-block
+    cluster (hardware cluster barrier, sums through distributed shared memory; two warps a CTA up
+    to 32 slices, four from 33); those whose state fits in the cluster's shared memory keep it
+    there (every degree-4 case up to 2048 rows), the graphs of degree 20 (about 270 and 330 KB a
+    CTA) read it from global memory; 2049 rows (65 slices) and 4096 take the cooperative grid.
+    Iterates and messages at fixed rounds equal the oracle's to 1e-13, the converged round count
+    is the oracle's, and the solve is three launches."""
     m = synth.random_sym(n, deg, 1.1, 3) if n > 1 else synth.from_dense(np.array([[2.0]]))
     b = synth.rhs(m.n, 8)
     for t in (1, 2, 7):
