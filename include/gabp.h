@@ -86,7 +86,7 @@ typedef struct {
   int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16.
                            Plain FP64 solves (node variant, no acceleration) of graphs of at most
                            131,072 rows run every round in one launch that decides on the device
-                           (up to 1,280 rows: one thread-block cluster; above: a cooperative grid),
+                           (up to 2,048 rows: one thread-block cluster; above: a cooperative grid),
                            and do not use it */
   int freeze_precisions;/* plain FP64 solves (node variant or serial schedule, no acceleration): 1 =
                            freeze the precision messages once they have stopped moving (on the serial

@@ -26,6 +26,7 @@ gabp_status cuda_fail(cudaError_t e, const char *what) {
   char buf[512];
   snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
   g_last_error = buf;
+  cudaGetLastError();  // a failed call's error is reported here, not again by a later check
   if (e == cudaErrorMemoryAllocation) return GABP_ERR_NOMEM;
   return GABP_ERR_CUDA;
 }

@@ -1147,8 +1147,12 @@ static void cluster_setup(gabp_handle h, const std::vector<int> &sp) {
   const size_t bytes = chip_bytes(c, ns);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  if (bytes + 256 > (size_t)optin) return;
-  if (cudaFuncSetAttribute(k64_chip<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess &&
+  constexpr int kStaticRoom = 1024;  // the kernel's static shared memory (a few hundred bytes) fits below
+  if (bytes + kStaticRoom > (size_t)optin) return;
+  // The limit is a property of the function, shared by every handle: always the same value, the
+  // device's whole opt-in room, so no handle lowers it below another handle's launch size.
+  if (cudaFuncSetAttribute(k64_chip<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - kStaticRoom) ==
+          cudaSuccess &&
       (cs <= 8 || cudaFuncSetAttribute(k64_chip<NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
     cfg.dynamicSmemBytes = bytes;
     int nc = 0;

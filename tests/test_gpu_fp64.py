@@ -373,6 +373,27 @@ def test_cooperative_threshold(gb, p):
         assert launches > 3
 
 
+def test_cluster_handles_interleaved(gb):
+    """The on-chip cluster rounds' shared memory differs per graph (about 80 KB a CTA on the
+    1280-row random graph, 44 KB on the 45x45 grid with four warps a CTA, 4 KB on the 8x8 grid) and
+    the kernel's launch limit is shared by every handle: handles set up and solved in alternation
+    all run and all reach the oracle's answer in the oracle's round count."""
+    mats = {"big": synth.random_sym(1280, 4, 1.1, 3), "mid": synth.grid2d(45, -1.0, 4.5),
+            "small": synth.grid2d(8, -1.0, 4.5)}
+    solvers = {k: _solver(gb, m) for k, m in mats.items()}
+    refs = {}
+    for k in ("big", "small", "big", "mid", "small", "mid", "big"):
+        m = mats[k]
+        b = synth.rhs(m.n, 5)
+        if k not in refs:
+            refs[k] = oracle.gabp_broadcast(m, b, max_iter=3000, tol=1e-12)
+        x, st, it, rel = solvers[k].solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
+        assert st == gb.GABP_OK and it == refs[k]["iters"], k
+        assert _relerr(x.cpu().numpy(), refs[k]["x"]) <= 1e-12, k
+    for s in solvers.values():
+        s.close()
+
+
 @pytest.mark.parametrize("n,deg", [(1, 0), (33, 4), (200, 4), (1024, 4), (1280, 4), (1280, 20), (1281, 4),
                                    (2048, 4), (2048, 20), (2049, 4), (4096, 4)])
 def test_cluster_rounds_small_graphs(gb, n, deg):
