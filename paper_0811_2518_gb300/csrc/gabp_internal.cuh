@@ -196,6 +196,9 @@ struct WorkS {
   double *sh1 = nullptr;       // [E] Steffensen: mean messages after a cycle's first sweep
   double *sx0 = nullptr, *sx1 = nullptr;  // [n] Steffensen: iterates x_n, x_{n+1} (input order)
   double *coef = nullptr;      // [E] precision freeze: coefficients -A_kj / P_k\j in the serial order
+  int *dcstart = nullptr;      // [C+1] cstart on the device (the one-cluster sweeps)
+  int clu = -1;                // CTAs of the one-cluster FP64 sweeps (0: none; -1: not yet sized)
+  int clu_nw = 0;              // warps per CTA there
   bool valid = false;
   int result_round = 0;
   float2 *sCF = nullptr;       // [E] frozen coefficients in serial order

@@ -32,6 +32,7 @@
 //   fired since) -- the same recompute identity as the parallel FP32 rounds.
 #include "gabp_internal.cuh"
 #include "devutil.cuh"
+#include "cluster.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -188,24 +189,24 @@ __global__ void ks64_init(ArgsS64 a) {
   }
 }
 
+// Loads of data a kernel's own launch writes: from L2 in the cluster kernel (its
+// CTAs' L1 caches are not coherent across its barriers), plain otherwise.
+template <bool COOP, typename T> __device__ __forceinline__ T ld_mut(const T *p) { return COOP ? __ldcg(p) : *p; }
+
 // Pass c: the nodes of colour c fire (every other row updates its colour-c
 // segment), then the rows of colour c + 1 form their firing aggregates.
 // With the precision freeze (state fs of the sweep, see freeze_step): a verify
 // sweep (fs 1) also compares every new precision message with the one it
 // replaces and stores the coefficient -A / P_k\j; a frozen sweep (fs 2) updates
-// the mean messages only, with the stored coefficients.
-template <int L>
-__global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0, int skipn) {
-  DevCtl *ctl = a.ctl;
-  if (ctl->done) return;
-  const int fs = a.freeze ? ctl->fstate : -1;
+// the mean messages only, with the stored coefficients.  warp / nwarps: this
+// warp among the warps that share the pass.
+template <int L, bool COOP>
+__device__ __forceinline__ void s64_pass_rows(const ArgsS64 &a, int c, int skip0, int skipn, int fs, int warp,
+                                              int nwarps, int &bad, int &moving) {
   const int cn = c + 1 == a.C ? 0 : c + 1;
   const int nv = a.n - skipn;
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
-  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * kBlock) >> 5;
-  int bad = 0, moving = 0;
   for (int base = warp * RPW; base < nv; base += nwarps * RPW) {
     const int v = base + sw;
     const int j = pass_row(v, skip0, skipn);
@@ -215,22 +216,22 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
       const int s0 = a.co[(size_t)c * a.n + j], s1 = a.co[(size_t)(c + 1) * a.n + j];
       if (fs == 2) {
         for (int e = s0 + sl; e < s1; e += L) {
-          const double2 fk = a.fire[a.sci[e]];
-          const double rh = reinterpret_cast<const double *>(a.SM + a.srev[e])[1];
-          reinterpret_cast<double *>(a.SM + e)[1] = a.coef[e] * (fk.y - rh);  // mean message only
+          const double2 fk = ld_mut<COOP>(a.fire + a.sci[e]);
+          const double rh = ld_mut<COOP>(reinterpret_cast<const double *>(a.SM + a.srev[e]) + 1);
+          reinterpret_cast<double *>(a.SM + e)[1] = ld_mut<COOP>(a.coef + e) * (fk.y - rh);  // mean message only
         }
       } else {
         for (int e = s0 + sl; e < s1; e += L) {
           const int k = a.sci[e];
           const double A = a.sav[e];
-          const double2 fk = a.fire[k];         // k's aggregate when it fires
-          const double2 rv = a.SM[a.srev[e]];   // message j -> k as k holds it
-          const double d = fk.x - rv.x;         // P_{k\j}
+          const double2 fk = ld_mut<COOP>(a.fire + k);        // k's aggregate when it fires
+          const double2 rv = ld_mut<COOP>(a.SM + a.srev[e]);  // message j -> k as k holds it
+          const double d = fk.x - rv.x;                       // P_{k\j}
           bad |= is_zero64(d);
           const double r = rcp64(d);
           const double2 m = make_double2(-A * A * r, -A * (fk.y - rv.y) * r);
           if (fs == 1) {
-            moving |= ulp_apart(m.x, a.SM[e].x);  // the message this one replaces
+            moving |= ulp_apart(m.x, ld_mut<COOP>(a.SM + e).x);  // the message this one replaces
             a.coef[e] = -A * r;
           }
           a.SM[e] = m;
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
     __syncwarp();
     if (fires_next) {
       for (int e = a.srp[j] + sl; e < a.srp[j + 1]; e += L) {
-        const double2 m = a.SM[e];
+        const double2 m = ld_mut<COOP>(a.SM + e);
         P += m.x;
         h += m.y;
       }
@@ -250,6 +251,17 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
     h = sub_sum<L>(h);
     if (fires_next && sl == 0) a.fire[j] = make_double2(a.sad[j] + P, a.sb[j] + h);
   }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0, int skipn) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const int fs = a.freeze ? ctl->fstate : -1;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  int bad = 0, moving = 0;
+  s64_pass_rows<L, false>(a, c, skip0, skipn, fs, warp, nwarps, bad, moving);
   if (bad) atomicOr(&ctl->edge_bad, 1);
   if (moving) atomicOr(&ctl->fmove, 1);
 }
@@ -258,22 +270,17 @@ __global__ void __launch_bounds__(kBlock) ks64_pass(ArgsS64 a, int c, int skip0,
 // step 4), x written in the input order.
 // A screening sweep of the precision freeze (fs 0, from the second sweep on) also
 // flags a node whose P moved since the previous sweep.
-template <int L>
-__global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
-  DevCtl *ctl = a.ctl;
-  if (ctl->done) return;
-  const bool screen = a.freeze && ctl->fstate == 0 && ctl->round >= 1;
+template <int L, bool COOP>
+__device__ __forceinline__ void s64_final_rows(const ArgsS64 &a, bool screen, int warp, int nwarps, int &bad,
+                                               int &moving) {
   constexpr int RPW = 32 / L;
   const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
-  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * kBlock) >> 5;
-  int bad = 0, moving = 0;
   for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
     const int j = base + sw;
     double P = 0.0, h = 0.0;
     if (j < a.n)
       for (int e = a.srp[j] + sl; e < a.srp[j + 1]; e += L) {
-        const double2 m = a.SM[e];
+        const double2 m = ld_mut<COOP>(a.SM + e);
         P += m.x;
         h += m.y;
       }
@@ -283,13 +290,44 @@ __global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
       P += a.sad[j];
       h += a.sb[j];
       bad |= is_zero64(P);
-      if (screen) moving |= ulp_apart(P, a.sPm[j]);
+      if (screen) moving |= ulp_apart(P, ld_mut<COOP>(a.sPm + j));
       a.sPm[j] = P;
       a.x[a.oid[j]] = h / P;
     }
   }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kBlock) ks64_final(ArgsS64 a) {
+  DevCtl *ctl = a.ctl;
+  if (ctl->done) return;
+  const bool screen = a.freeze && ctl->fstate == 0 && ctl->round >= 1;
+  const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * kBlock) >> 5;
+  int bad = 0, moving = 0;
+  s64_final_rows<L, false>(a, screen, warp, nwarps, bad, moving);
   if (bad) atomicOr(&ctl->edge_bad, 2);
   if (moving) atomicOr(&ctl->fmove, 1);
+}
+
+// This lane's share of ||b - A x||^2 for the sweep's x (input order).
+template <int L, bool COOP>
+__device__ __forceinline__ double s64_resid_rows(const ArgsS64 &a, int warp, int nwarps) {
+  constexpr int RPW = 32 / L;
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
+  double rr = 0.0;
+  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
+    const int i = base + sw;
+    double ax = 0.0;
+    if (i < a.n)
+      for (int p = a.rowptr[i] + sl; p < a.rowptr[i + 1]; p += L) ax = fma(a.val[p], ld_mut<COOP>(a.x + a.col[p]), ax);
+    ax = sub_sum<L>(ax);
+    if (i < a.n && sl == 0) {
+      const double r = a.b[i] - ax;
+      rr = fma(r, r, rr);
+    }
+  }
+  return rr;
 }
 
 // ||b - A x||^2 of the sweep's x (input order) and the decision (Algorithm 1
@@ -298,23 +336,9 @@ template <int L>
 __global__ void __launch_bounds__(kBlock) ks64_decide(ArgsS64 a) {
   DevCtl *ctl = a.ctl;
   if (ctl->done) return;
-  constexpr int RPW = 32 / L;
-  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L;
   const int warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * kBlock) >> 5;
-  double rr = 0.0;
-  for (int base = warp * RPW; base < a.n; base += nwarps * RPW) {
-    const int i = base + sw;
-    double ax = 0.0;
-    if (i < a.n)
-      for (int p = a.rowptr[i] + sl; p < a.rowptr[i + 1]; p += L) ax = fma(a.val[p], a.x[a.col[p]], ax);
-    ax = sub_sum<L>(ax);
-    if (i < a.n && sl == 0) {
-      const double r = a.b[i] - ax;
-      rr = fma(r, r, rr);
-    }
-  }
-  double v[1] = {rr}, tot[1];
+  double v[1] = {s64_resid_rows<L, false>(a, warp, nwarps)}, tot[1];
   const int modes[1] = {0};
   block_sum<1>(v);
   if (last_block_reduce<1>(v, modes, a.partials, &ctl->arrive, tot) && threadIdx.x == 0) {
@@ -338,6 +362,56 @@ __global__ void __launch_bounds__(kBlock) ks64_decide(ArgsS64 a) {
     ctl->arrive = 0;
     __threadfence();
   }
+}
+
+// Every sweep of a small graph in one thread-block cluster (up to 16 CTAs of NW
+// warps): the passes, the final x and the residual of each sweep are the kernels'
+// above, with a cluster barrier where a launch ended; the residual is summed by
+// cluster_sums and every warp takes the decision itself (CTA 0 records it), so all
+// CTAs leave after the same sweep.  With the precision freeze CTA 0 also advances
+// the freeze state, read by every CTA after one more barrier.  cstart: the colour
+// classes' first rows (C + 1 entries).
+template <int L, int NW>
+__global__ void __launch_bounds__(32 * NW) ks64_cluster(ArgsS64 a, const int *__restrict__ cstart, int max_sweeps) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+  __shared__ ClusterPart part[2][NW];
+  DevCtl *ctl = a.ctl;
+  const int t0 = ctl->round;  // read by every CTA before the first barrier, written only after it
+  const double tol2bb = ctl->tol2bb;
+  const int max_iter = ctl->max_iter;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int warp = (int)(rank * NW) + wib, nwarps = (int)(csize * NW);
+  for (int it = 0; it < max_sweeps; ++it) {
+    const int t = t0 + 1 + it;
+    const int fs = a.freeze ? __ldcg(&ctl->fstate) : -1;
+    int ebad = 0, nbad = 0, moving = 0;
+    for (int c = 0; c < a.C; ++c) {
+      s64_pass_rows<L, true>(a, c, cstart[c], cstart[c + 1] - cstart[c], fs, warp, nwarps, ebad, moving);
+      cl.sync();
+    }
+    s64_final_rows<L, true>(a, a.freeze && fs == 0 && t - 1 >= 1, warp, nwarps, nbad, moving);
+    cl.sync();
+    const double rr = s64_resid_rows<L, true>(a, warp, nwarps);
+    // flags: bit 0 a zero cavity precision, bit 1 a zero node precision, bit 2 a precision moved
+    const ClusterSums tot =
+        cluster_sums<NW>(cl, part[t & 1], rr, (ebad ? 1 : 0) | (nbad ? 2 : 0) | (moving ? 4 : 0), lane, wib, nwarps);
+    const int st = (tot.flags & 3) ? GABP_BREAKDOWN : !isfinite(tot.rr) ? GABP_DIVERGED
+                   : tot.rr <= tol2bb ? GABP_OK : t >= max_iter ? GABP_NOT_CONVERGED : -1;
+    if (rank == 0 && threadIdx.x == 0) {
+      ctl->round = t;
+      ctl->rr = tot.rr;
+      if (a.freeze && fs < 2 && (fs == 1 || t >= 2)) freeze_step(ctl, fs, t, (tot.flags & 4) ? 1.0 : 0.0);
+      if (st >= 0) {
+        ctl->edge_bad = tot.flags & 3;
+        ctl->status = st; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+      }
+    }
+    if (st >= 0) break;
+    if (a.freeze) cl.sync();  // the freeze state CTA 0 wrote is read by every CTA next sweep
+  }
+  cl.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
 // Steffensen's iterations on the serial schedule (Sec. "Convergence Acceleration"):
@@ -597,7 +671,7 @@ void free_ws(gabp_handle h) {
   cudaFree(s.oid); cudaFree(s.nid); cudaFree(s.srp); cudaFree(s.scol); cudaFree(s.sad); cudaFree(s.sb);
   cudaFree(s.SM); cudaFree(s.fire); cudaFree(s.sPm); cudaFree(s.sCF); cudaFree(s.sH); cudaFree(s.hfire);
   cudaFree(s.srhs); cudaFree(s.sinvP); cudaFree(s.bin); cudaFree(s.xin); cudaFree(s.sh1); cudaFree(s.sx0);
-  cudaFree(s.sx1); cudaFree(s.coef);
+  cudaFree(s.sx1); cudaFree(s.coef); cudaFree(s.dcstart);
   if (h->gS64) cudaGraphExecDestroy(h->gS64);
   if (h->gS32) cudaGraphExecDestroy(h->gS32);
   h->gS64 = h->gS32 = nullptr;
@@ -682,6 +756,9 @@ gabp_status serial_prepare(gabp_handle h) {
     srp[j + 1] = srp[j] + (rp[oid[j] + 1] - rp[oid[j]]);
     scol[j] = col[oid[j]];
   }
+  GABP_CUDA(cudaMalloc(&s.dcstart, sizeof(int) * (s.C + 1)));
+  GABP_CUDA(cudaMemcpyAsync(s.dcstart, s.cstart.data(), sizeof(int) * (s.C + 1), cudaMemcpyHostToDevice, h->stream));
+  s.clu = -1;
   GABP_CUDA(cudaMalloc(&s.oid, sizeof(int) * n));
   GABP_CUDA(cudaMalloc(&s.nid, sizeof(int) * n));
   GABP_CUDA(cudaMalloc(&s.srp, sizeof(int) * (n + 1)));
@@ -772,6 +849,89 @@ static ArgsS64 args_s64(gabp_handle h, const double *b, double *x) {
   return a;
 }
 
+// The one-cluster sweeps: up to 16 CTAs of NW = 2, 4 or 8 warps, the fewest warps a CTA that
+// give every warp one group of 32 / L rows in each pass; graphs needing more than 128 warps
+// take the launches.
+constexpr int kSerialClusterMax = 16;
+
+template <int L, int NW>
+static int serial_cluster_fits(gabp_handle h, int cs) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(32 * NW);
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cs > 8) cudaFuncSetAttribute(ks64_cluster<L, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  int nc = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&nc, (void *)ks64_cluster<L, NW>, &cfg) == cudaSuccess && nc > 0;
+  cudaGetLastError();
+  return ok ? cs : 0;
+}
+
+template <int L>
+static void serial_cluster_size(gabp_handle h) {
+  WorkS &s = h->ws;
+  s.clu = 0;
+  s.clu_nw = 0;
+  int attr = 0;
+  cudaDeviceGetAttribute(&attr, cudaDevAttrClusterLaunch, h->device);
+  if (!attr) return;
+  const int64_t warps = ((int64_t)h->g.n + 32 / L - 1) / (32 / L);
+  for (int nw : {2, 4, 8}) {
+    const int64_t cs = std::max<int64_t>(1, (warps + nw - 1) / nw);
+    if (cs > kSerialClusterMax) continue;
+    const int c = nw == 2 ? serial_cluster_fits<L, 2>(h, (int)cs)
+                  : nw == 4 ? serial_cluster_fits<L, 4>(h, (int)cs) : serial_cluster_fits<L, 8>(h, (int)cs);
+    if (c > 0) {
+      s.clu = c;
+      s.clu_nw = nw;
+    }
+    return;
+  }
+}
+
+template <int L, int NW>
+static gabp_status serial_cluster_run(gabp_handle h, const ArgsS64 &a, int max_sweeps) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = h->ws.clu;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(h->ws.clu);
+  cfg.blockDim = dim3(32 * NW);
+  cfg.stream = h->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  prof_begin(h);
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, ks64_cluster<L, NW>, a, (const int *)h->ws.dcstart, max_sweeps);
+  if (le != cudaSuccess) return cuda_fail(le, "FP64 serial cluster sweeps");
+  prof_end(h);
+  h->prof.launches += 1;
+  gabp_status st = read_ctl(h);
+  if (st != GABP_OK) return st;
+  prof_collect(h, PH_FP64, h->ctl_host->round);
+  if (!h->ctl_host->done) {
+    set_last_error("FP64 serial cluster sweeps ended without a decision");
+    return GABP_ERR_CUDA;
+  }
+  return GABP_OK;
+}
+
+template <int L>
+static gabp_status serial_cluster_dispatch(gabp_handle h, const ArgsS64 &a, int max_sweeps) {
+  switch (h->ws.clu_nw) {
+    case 2: return serial_cluster_run<L, 2>(h, a, max_sweeps);
+    case 4: return serial_cluster_run<L, 4>(h, a, max_sweeps);
+    default: return serial_cluster_run<L, 8>(h, a, max_sweeps);
+  }
+}
+
 // Plain FP64 GaBP under the serial schedule; the answer is the x of the last
 // sweep (Algorithm 1 step 4 over every current message).
 gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol, int max_iter, int *iters,
@@ -831,7 +991,21 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   const bool stf = h->opt.accel == 2;
   const int key = L | (s.C << 8) | (stf ? 1 << 30 : 0) | (a.freeze ? 1 << 29 : 0);
   gabp_status rs = GABP_OK;
-  GABP_DISPATCH_L(L, {
+  // small graphs without Steffensen's step: every sweep in one thread-block cluster
+  if (!stf && (L == 1 || L == 2 || L == 4)) {
+    if (s.clu < 0) {
+      if (L == 1) serial_cluster_size<1>(h);
+      else if (L == 2) serial_cluster_size<2>(h);
+      else serial_cluster_size<4>(h);
+    }
+    if (s.clu > 0) {
+      const int ms = std::max(1, max_iter);
+      rs = L == 1 ? serial_cluster_dispatch<1>(h, a, ms)
+           : L == 2 ? serial_cluster_dispatch<2>(h, a, ms) : serial_cluster_dispatch<4>(h, a, ms);
+      if (rs != GABP_OK) return rs;
+    }
+  }
+  if (!(s.clu > 0 && !stf)) GABP_DISPATCH_L(L, {
     const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_pass<LL>));
     const int ab = blocks_for(std::max(g.n, g.E), kBlock, resident_grid(h->num_sms, ks64_steff_a));
     rs = run_rounds(h, &h->gS64, &h->gS64_key, key, [&] {

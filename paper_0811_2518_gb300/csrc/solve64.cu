@@ -23,6 +23,7 @@
 // rows of equal degree share a warp, and the row epilogue runs on all 32 lanes.
 #include "gabp_internal.cuh"
 #include "devutil.cuh"
+#include "cluster.cuh"
 
 #include <cooperative_groups.h>
 
@@ -646,40 +647,6 @@ constexpr int kClusterMax = 16;
 #endif
 constexpr int kClusterMaxSlices = GABP_CLUSTER_MAX_SLICES;
 
-struct __align__(16) ClusterPart {
-  double rr;  // a warp's sum of its lanes' squared residuals
-  int flags;  // bit 0: a zero cavity or node precision; bit 1: a precision moved (the freeze's screen)
-  int pad;
-};
-struct ClusterSums {
-  double rr;
-  int flags;
-};
-// The sums of a cluster round, the same bits in every thread of the cluster: each warp adds its
-// lanes' residual terms by an xor butterfly (at every step a lane and its partner add the same two
-// values, so all lanes end equal) and lane 0 posts the sum in its CTA's shared memory; after the
-// cluster barrier lane l of every warp fetches the posts of warps l and l + 32 (warp w of CTA r
-// is warp NW r + w, at most 64 of them) and a second butterfly adds them.  The flags are or-ed.
-template <int NW>
-__device__ __forceinline__ ClusterSums cluster_sums(cooperative_groups::cluster_group &cl, ClusterPart *part,
-                                                    double rr, int flags, int lane, int wib, int nwarps) {
-  const double w = warp_sum(rr);
-  const int f = (int)__reduce_or_sync(0xffffffffu, (unsigned)flags);
-  if (lane == 0) {
-    part[wib].rr = w;
-    part[wib].flags = f;
-  }
-  cl.sync();
-  double x = 0.0;
-  unsigned g = 0;
-  for (int v = lane; v < nwarps; v += 32) {  // lane l: warps l and l + 32
-    const ClusterPart *q = cl.map_shared_rank(part + v % NW, (unsigned)(v / NW));
-    x += q->rr;
-    g |= (unsigned)q->flags;
-  }
-  return ClusterSums{warp_sum(x), (int)__reduce_or_sync(0xffffffffu, g)};
-}
-
 template <bool FRZ, int NW>
 __global__ void __launch_bounds__(32 * NW) k64_cluster(Args64 a, int max_rounds) {
   namespace cg = cooperative_groups;
@@ -708,6 +675,7 @@ __global__ void __launch_bounds__(32 * NW) k64_cluster(Args64 a, int max_rounds)
       else if (fs == 1) plain_slice<true, 2>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
       else plain_slice<true, 3>(a, sl, lane, b, Min, Mout, Nin, Nout, rr, bad, moving);
     }
+    // flags: bit 0 a zero cavity or node precision, bit 1 a precision moved (the freeze's screen)
     const ClusterSums tot =
         cluster_sums<NW>(cl, part[t & 1], rr, (bad ? 1 : 0) | (moving ? 2 : 0), lane, wib, nwarps);
     const bool stop = stops64(rule, t, tot.rr, tot.flags & 1);

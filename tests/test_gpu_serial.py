@@ -65,7 +65,13 @@ MATS = {
     "random": lambda: synth.random_sym(3001, 8, 1.1, 2),
     "rgg": lambda: synth.rgg_batch(1, 3000, 3001, 2.0, 4)[0],
     "tree": lambda: synth.random_tree(500, 3, dd=True),
+    "random_l2": lambda: synth.random_sym(1000, 8, 1.1, 6),
+    "random_l4": lambda: synth.random_sym(500, 16, 1.1, 7),
 }
+# Graphs of at most 128 warps' rows (32 / L rows a warp, L = 1, 2 or 4 lanes a row by the mean
+# degree) run every sweep in one thread-block cluster: grid2d and tree with two warps a CTA, star,
+# grid3d, random_l2 (L = 2) and random_l4 (L = 4) with four, path and rgg with eight; "random"
+# (3001 rows, L = 2: 188 warps) takes a launch per pass.
 
 
 @pytest.mark.parametrize("name", list(MATS))
@@ -98,7 +104,8 @@ def _fp64(gb, m, b, sweeps, tol=0.0):
     return st, it, x.cpu().numpy(), P.cpu().numpy(), hm.cpu().numpy(), Pi.cpu().numpy()
 
 
-@pytest.mark.parametrize("name", ["grid2d", "grid3d", "random", "rgg", "tree", "path", "star"])
+@pytest.mark.parametrize("name", ["grid2d", "grid3d", "random", "rgg", "tree", "path", "star", "random_l2",
+                                  "random_l4"])
 @pytest.mark.parametrize("sweeps", [1, 2, 7])
 def test_fp64_sweeps_match_oracle(gb, name, sweeps):
     m = MATS[name]()
@@ -120,7 +127,7 @@ def test_fp64_sweeps_match_oracle(gb, name, sweeps):
     assert np.all(np.abs(Pi - r["P"]) <= 1e-12 * absP)
 
 
-@pytest.mark.parametrize("name", ["grid2d", "random", "rgg"])
+@pytest.mark.parametrize("name", ["grid2d", "random", "rgg", "path", "random_l2", "random_l4"])
 def test_fp64_converged_equal_sweeps(gb, name):
     m = MATS[name]()
     b = synth.rhs(m.n, 3)
