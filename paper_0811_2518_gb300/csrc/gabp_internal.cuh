@@ -197,8 +197,11 @@ struct WorkS {
   double *sx0 = nullptr, *sx1 = nullptr;  // [n] Steffensen: iterates x_n, x_{n+1} (input order)
   double *coef = nullptr;      // [E] precision freeze: coefficients -A_kj / P_k\j in the serial order
   int *dcstart = nullptr;      // [C+1] cstart on the device (the one-cluster sweeps)
+  std::vector<int> srp_h;      // [n+1] srp on the host (sizes of the on-chip sweeps)
   int clu = -1;                // CTAs of the one-cluster FP64 sweeps (0: none; -1: not yet sized)
   int clu_nw = 0;              // warps per CTA there
+  int chip_bytes = 0;          // shared memory a CTA of those sweeps with the state on chip (0: no fit)
+  int chip_S = 0;              // slots of the largest CTA there
   bool valid = false;
   int result_round = 0;
   float2 *sCF = nullptr;       // [E] frozen coefficients in serial order

@@ -414,6 +414,167 @@ __global__ void __launch_bounds__(32 * NW) ks64_cluster(ArgsS64 a, const int *__
   cl.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
+// The one-cluster sweeps with the state in the cluster's shared memory (plain
+// sweeps, no freeze): CTA r owns the R = NW 32 / L rows from r R on -- their
+// messages (the slots of those rows), firing aggregates, marginal precisions and
+// iterate -- and every row keeps one group of L lanes for the whole solve.  A slot
+// reads the sender's firing aggregate and the reverse message from the sender's
+// CTA (the reverse slot lies in the sender's row) through distributed shared
+// memory; every write stays in its own CTA.  Messages, aggregates and iterates
+// are ks64_pass / ks64_final's, bit for bit; the residual adds each row's terms in
+// slot order.  The state is loaded at the start and written back at the end.
+struct ChipS {
+  int R;  // rows a CTA
+  int S;  // slots of the largest CTA
+};
+__host__ __device__ inline size_t chip_s_bytes(const ChipS &c, int C) {
+  return (size_t)32 * c.S + (size_t)c.R * (52 + 4 * (size_t)(C + 1));
+}
+
+template <int L, int NW>
+__global__ void __launch_bounds__(32 * NW) ks64_chip(ArgsS64 a, ChipS c, int max_sweeps) {
+  namespace cg = cooperative_groups;
+  constexpr int NT = 32 * NW, RPW = 32 / L;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+  const int R = c.R, S = c.S;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double2 *SMl = reinterpret_cast<double2 *>(smem);  // messages into the own rows, by local slot
+  double2 *firel = SMl + S;                          // firing aggregates, by local row
+  double *savl = reinterpret_cast<double *>(firel + R);
+  double *sPml = savl + S, *sadl = sPml + R, *sbl = sadl + R, *xl = sbl + R;
+  int *kref = reinterpret_cast<int *>(xl + R);  // sender: owner rank << 24 | its local row
+  int *rref = kref + S;                         // reverse slot: owner rank << 24 | its local slot
+  int *coL = rref + S;                          // [(C + 1) x R] colour segment bounds, local slots
+  int *scoll = coL + (size_t)(a.C + 1) * R;
+  __shared__ ClusterPart part[2][NW];
+  DevCtl *ctl = a.ctl;
+  const int t0 = ctl->round;
+  const double tol2bb = ctl->tol2bb;
+  const int max_iter = ctl->max_iter;
+  const int j0 = min((int)rank * R, a.n), jn = min(j0 + R, a.n);
+  const int e0 = a.srp[j0], eN = a.srp[jn];
+  for (int q = threadIdx.x; q < eN - e0; q += NT) {
+    const int e = e0 + q, k = a.sci[e], ok = k / R;
+    SMl[q] = a.SM[e];
+    savl[q] = a.sav[e];
+    kref[q] = (ok << 24) | (k - ok * R);
+    rref[q] = (ok << 24) | (a.srev[e] - a.srp[ok * R]);
+  }
+  for (int r = threadIdx.x; r < R; r += NT) {
+    const int j = j0 + r;
+    if (j < jn) {
+      firel[r] = a.fire[j];
+      sPml[r] = a.sPm[j];
+      sadl[r] = a.sad[j];
+      sbl[r] = a.sb[j];
+      scoll[r] = a.scol[j];
+      for (int cc = 0; cc <= a.C; ++cc) coL[(size_t)cc * R + r] = a.co[(size_t)cc * a.n + j] - e0;
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sl = lane & (L - 1), sw = lane / L, wib = threadIdx.x >> 5;
+  const int r = wib * RPW + sw;  // this lane group's row, for the whole solve
+  const int j = j0 + r;
+  const bool has = j < jn;
+  const int q0 = has ? a.srp[j] - e0 : 0, q1 = has ? a.srp[j + 1] - e0 : 0;
+  const int myc = has ? scoll[r] : -1;
+  const int lane_nw = (int)(csize * NW);
+  cl.sync();  // every CTA's state is in place before any peer reads it
+  int ran = 0;
+  for (int it = 0; it < max_sweeps; ++it) {
+    const int t = t0 + 1 + it;
+    int ebad = 0, nbad = 0;
+    for (int cc = 0; cc < a.C; ++cc) {  // pass cc: the nodes of colour cc fire
+      const int cn = cc + 1 == a.C ? 0 : cc + 1;
+      if (has) {
+        const int s0 = coL[(size_t)cc * R + r], s1 = coL[(size_t)(cc + 1) * R + r];
+        for (int q = s0 + sl; q < s1; q += L) {
+          const double A = savl[q];
+          const int kr = kref[q], rf = rref[q];
+          const double2 fk = *cl.map_shared_rank(firel + (kr & 0xffffff), (unsigned)(kr >> 24));  // k fires
+          const double2 rv = *cl.map_shared_rank(SMl + (rf & 0xffffff), (unsigned)(rf >> 24));  // j -> k
+          const double d = fk.x - rv.x;  // P_{k\j}
+          ebad |= is_zero64(d);
+          const double rc = rcp64(d);
+          SMl[q] = make_double2(-A * A * rc, -A * (fk.y - rv.y) * rc);
+        }
+      }
+      __syncwarp();
+      const bool fires_next = has && myc == cn;
+      double P = 0.0, h = 0.0;
+      if (fires_next)
+        for (int q = q0 + sl; q < q1; q += L) {
+          const double2 m = SMl[q];
+          P += m.x;
+          h += m.y;
+        }
+      P = sub_sum<L>(P);
+      h = sub_sum<L>(h);
+      if (fires_next && sl == 0) firel[r] = make_double2(sadl[r] + P, sbl[r] + h);
+      cl.sync();
+    }
+    {  // x = h~ / P~ and P from every current message
+      double P = 0.0, h = 0.0;
+      if (has)
+        for (int q = q0 + sl; q < q1; q += L) {
+          const double2 m = SMl[q];
+          P += m.x;
+          h += m.y;
+        }
+      P = sub_sum<L>(P);
+      h = sub_sum<L>(h);
+      if (has && sl == 0) {
+        P += sadl[r];
+        h += sbl[r];
+        nbad |= is_zero64(P);
+        sPml[r] = P;
+        xl[r] = h / P;
+      }
+    }
+    cl.sync();
+    double rr = 0.0;
+    {  // ||b - A x||^2, row j: b_j - (A_jj x_j + sum_k A_jk x_k)
+      double ax = 0.0;
+      if (has)
+        for (int q = q0 + sl; q < q1; q += L) {
+          const int kr = kref[q];
+          ax = fma(savl[q], *cl.map_shared_rank(xl + (kr & 0xffffff), (unsigned)(kr >> 24)), ax);
+        }
+      ax = sub_sum<L>(ax);
+      if (has && sl == 0) {
+        const double res = sbl[r] - fma(sadl[r], xl[r], ax);
+        rr = res * res;
+      }
+    }
+    ++ran;
+    const ClusterSums tot =
+        cluster_sums<NW>(cl, part[t & 1], rr, (ebad ? 1 : 0) | (nbad ? 2 : 0), lane, wib, lane_nw);
+    const int st = (tot.flags & 3) ? GABP_BREAKDOWN : !isfinite(tot.rr) ? GABP_DIVERGED
+                   : tot.rr <= tol2bb ? GABP_OK : t >= max_iter ? GABP_NOT_CONVERGED : -1;
+    if (rank == 0 && threadIdx.x == 0) {
+      ctl->round = t;
+      ctl->rr = tot.rr;
+      if (st >= 0) {
+        ctl->edge_bad = tot.flags & 3;
+        ctl->status = st; ctl->iters = t; ctl->result_round = t; ctl->done = 1;
+      }
+    }
+    if (st >= 0) break;
+  }
+  // back to the global arrays (the last sweep wrote before its barriers)
+  if (ran > 0) {
+    for (int q = threadIdx.x; q < eN - e0; q += NT) a.SM[e0 + q] = SMl[q];
+    for (int rr2 = threadIdx.x; rr2 < jn - j0; rr2 += NT) {
+      const int jj = j0 + rr2;
+      a.fire[jj] = firel[rr2];
+      a.sPm[jj] = sPml[rr2];
+      a.x[a.oid[jj]] = xl[rr2];
+    }
+  }
+  cl.sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
 // Steffensen's iterations on the serial schedule (Sec. "Convergence Acceleration"):
 // sweeps pair into cycles.  After the first sweep of a cycle (t odd) its mean
 // messages and iterate are kept; after the second (t even) the last block forms
@@ -756,6 +917,7 @@ gabp_status serial_prepare(gabp_handle h) {
     srp[j + 1] = srp[j] + (rp[oid[j] + 1] - rp[oid[j]]);
     scol[j] = col[oid[j]];
   }
+  s.srp_h = srp;
   GABP_CUDA(cudaMalloc(&s.dcstart, sizeof(int) * (s.C + 1)));
   GABP_CUDA(cudaMemcpyAsync(s.dcstart, s.cstart.data(), sizeof(int) * (s.C + 1), cudaMemcpyHostToDevice, h->stream));
   s.clu = -1;
@@ -873,11 +1035,56 @@ static int serial_cluster_fits(gabp_handle h, int cs) {
   return ok ? cs : 0;
 }
 
+// The on-chip flavour's shared memory for clusters of cs CTAs of NW warps, when it fits.
+template <int L, int NW>
+static void serial_chip_fit(gabp_handle h, int cs) {
+  WorkS &s = h->ws;
+  const int R = NW * (32 / L), n = h->g.n;
+  int64_t smax = 0;
+  for (int r = 0; r < cs; ++r) {
+    const int a0 = std::min(r * R, n), a1 = std::min(a0 + R, n);
+    smax = std::max<int64_t>(smax, s.srp_h[a1] - s.srp_h[a0]);
+  }
+  if (smax >= (1 << 24)) return;
+  const ChipS c{R, (int)smax};
+  const size_t bytes = chip_s_bytes(c, s.C);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  constexpr int kStaticRoom = 1024;  // the kernel's static shared memory fits below
+  if (bytes + kStaticRoom > (size_t)optin) return;
+  // one limit for the function, shared by every handle: the device's whole opt-in room
+  if (cudaFuncSetAttribute(ks64_chip<L, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - kStaticRoom) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (cs > 8) cudaFuncSetAttribute(ks64_chip<L, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(32 * NW);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, (void *)ks64_chip<L, NW>, &cfg) == cudaSuccess && nc > 0) {
+    s.chip_bytes = (int)bytes;
+    s.chip_S = c.S;
+  }
+  cudaGetLastError();
+}
+
 template <int L>
 static void serial_cluster_size(gabp_handle h) {
   WorkS &s = h->ws;
   s.clu = 0;
   s.clu_nw = 0;
+  s.chip_bytes = 0;
+  s.chip_S = 0;
   int attr = 0;
   cudaDeviceGetAttribute(&attr, cudaDevAttrClusterLaunch, h->device);
   if (!attr) return;
@@ -890,6 +1097,9 @@ static void serial_cluster_size(gabp_handle h) {
     if (c > 0) {
       s.clu = c;
       s.clu_nw = nw;
+      if (nw == 2) serial_chip_fit<L, 2>(h, c);
+      else if (nw == 4) serial_chip_fit<L, 4>(h, c);
+      else serial_chip_fit<L, 8>(h, c);
     }
     return;
   }
@@ -908,8 +1118,13 @@ static gabp_status serial_cluster_run(gabp_handle h, const ArgsS64 &a, int max_s
   cfg.stream = h->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  // plain sweeps with the state on chip where it fits (the same messages and iterates)
+  const bool chip = !a.freeze && h->ws.chip_bytes > 0;
+  if (chip) cfg.dynamicSmemBytes = h->ws.chip_bytes;
   prof_begin(h);
-  const cudaError_t le = cudaLaunchKernelEx(&cfg, ks64_cluster<L, NW>, a, (const int *)h->ws.dcstart, max_sweeps);
+  const cudaError_t le =
+      chip ? cudaLaunchKernelEx(&cfg, ks64_chip<L, NW>, a, ChipS{NW * (32 / L), h->ws.chip_S}, max_sweeps)
+           : cudaLaunchKernelEx(&cfg, ks64_cluster<L, NW>, a, (const int *)h->ws.dcstart, max_sweeps);
   if (le != cudaSuccess) return cuda_fail(le, "FP64 serial cluster sweeps");
   prof_end(h);
   h->prof.launches += 1;
