@@ -140,6 +140,26 @@ def test_fp64_converged_equal_sweeps(gb, name):
     assert it < par["iters"]  # the serial schedule needs fewer sweeps than rounds
 
 
+@pytest.mark.parametrize("name,one_launch", [("grid2d", True), ("path", True), ("random_l4", True),
+                                             ("random", False)])
+def test_fp64_small_graphs_one_launch(gb, name, one_launch):
+    """Graphs whose rows fit 128 warps (32 / L rows a warp) run every sweep of a solve in one
+    thread-block cluster launch; the 3001-row graph of mean degree 16 (two lanes a row: 188 warps)
+    launches its passes.  Both reach the oracle's sweep count and answer."""
+    m = MATS[name]()
+    b = synth.rhs(m.n, 5)
+    s = gb.Solver.from_csr(m, schedule=1, precision=gb.GABP_PREC_FP64, profile=1)
+    s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=5000)
+    s.profile(reset=True)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=5000)
+    launches = s.profile()["launches"]
+    s.close()
+    r = oracle.gabp_serial(m, b, max_iter=5000, tol=1e-12)
+    assert st == gb.GABP_OK and it == r["iters"]
+    assert _relerr(x.cpu().numpy(), r["x"]) <= 1e-12
+    assert (launches == 1) == one_launch, launches
+
+
 def test_fp64_tree_exact(gb):
     m = MATS["tree"]()
     b = synth.rhs(m.n, 4)
