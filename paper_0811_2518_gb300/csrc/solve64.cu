@@ -645,6 +645,17 @@ constexpr int kClusterMax = 16;
 #ifndef GABP_CLUSTER_MAX_SLICES
 #define GABP_CLUSTER_MAX_SLICES 64
 #endif
+// Two warps a CTA up to this many slices, four above.  Four from the start: 32x32 grid 4.69 against
+// 4.53 us per round (8x8: 4.00 against 4.22).
+#ifndef GABP_CLUSTER_NW2_MAX_SLICES
+#define GABP_CLUSTER_NW2_MAX_SLICES 32
+#endif
+// Slots per lane whose loads the on-chip round issues together: 4 against 2, 32x32 grid 4.44 against
+// 4.53 us per round, 2048-row random graph 13.2 against 13.4, 1280-row 15.1 against 14.95.
+#ifndef GABP_CHIP_UNROLL
+#define GABP_CHIP_UNROLL 4
+#endif
+constexpr int kUChip = GABP_CHIP_UNROLL;
 constexpr int kClusterMaxSlices = GABP_CLUSTER_MAX_SLICES;
 
 template <bool FRZ, int NW>
@@ -807,13 +818,13 @@ __global__ void __launch_bounds__(32 * NW) k64_chip(Args64 a, ChipShape c, int m
       const int lb = tab[sl].y, wd = (a.sp[sl + 1] - a.sp[sl]) >> 5;
       const int lr = qq * 32 + lane, i = srowl[lr];
       double accP = 0.0, acch = 0.0, accr = 0.0;
-      for (int j = 0; j < wd; j += kU64) {
-        int kr[kU64];
-        double A[kU64];
-        double2 rv[kU64];
-        NodeRec64 nk[kU64];
+      for (int j = 0; j < wd; j += kUChip) {
+        int kr[kUChip];
+        double A[kUChip];
+        double2 rv[kUChip];
+        NodeRec64 nk[kUChip];
 #pragma unroll
-        for (int u = 0; u < kU64; ++u) {
+        for (int u = 0; u < kUChip; ++u) {
           const int li = lb + 32 * (j + u) + lane;
           kr[u] = j + u < wd ? kref[li] : -1;
           if (kr[u] >= 0) {
@@ -824,7 +835,7 @@ __global__ void __launch_bounds__(32 * NW) k64_chip(Args64 a, ChipShape c, int m
           }
         }
 #pragma unroll
-        for (int u = 0; u < kU64; ++u) {
+        for (int u = 0; u < kUChip; ++u) {
           if (kr[u] < 0) continue;
           const double den = nk[u].P - rv[u].x;
           bad |= is_zero64(den);
@@ -1194,7 +1205,7 @@ static gabp_status ensure_sell64(gabp_handle h) {
     h->clu64 = h->clu64_nw = 0;
     h->chip64_bytes = h->chip64_smax = h->chip64_rmax = 0;
     if (S.ns <= kClusterMaxSlices) {
-      if (S.ns <= 32) cluster_setup<2>(h, sp);
+      if (S.ns <= GABP_CLUSTER_NW2_MAX_SLICES) cluster_setup<2>(h, sp);
       else cluster_setup<4>(h, sp);
     }
     // the cooperative launch for small graphs: one block per two slices, all co-resident
