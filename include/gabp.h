@@ -86,7 +86,8 @@ typedef struct {
   int check_every;      /* rounds per convergence read-back (CUDA-graph replay length), default 16.
                            Plain FP64 solves (node variant, no acceleration) of graphs of at most
                            131,072 rows run every round in one launch that decides on the device
-                           (up to 2,048 rows: one thread-block cluster; above: a cooperative grid),
+                           (up to 2,048 rows, or 4,096 in slices of at most 8 slots a row: one
+                           thread-block cluster; above: a cooperative grid),
                            and do not use it; nor do FP64 serial-schedule solves without
                            Steffensen's step of graphs of at most 4,096 rows (2,048 with a mean
                            degree of 8 or more, 1,024 with 24 or more): one cluster runs every sweep */

@@ -640,10 +640,14 @@ __global__ void __launch_bounds__(kCoopThreads, FRZ ? 8 : 0) k64_coop(Args64 a, 
 // the same round (no wait can be left open) and CTA 0 records it.  Data written by
 // other CTAs is read through L2 (plain_slice's cooperative flavour); the barrier
 // releases and acquires at cluster scope.  Two warps a CTA up to 32 slices; four (all
-// four schedulers of the SM, each with its own FP64 unit) up to 64.
+// four schedulers of the SM, each with its own FP64 unit) up to 64; eight (two a
+// scheduler) up to 128 when no slice is wider than kCluster8MaxWidth slots a row: two warps share
+// each FP64 unit, so the widest slices set the round (64x64 grid, width 4: 7.9 us per round against
+// 10.2 with the cooperative grid; 4096-row random graph of degree 4, width up to ~16: 19.9 against
+// 18.7).
 constexpr int kClusterMax = 16;
 #ifndef GABP_CLUSTER_MAX_SLICES
-#define GABP_CLUSTER_MAX_SLICES 64
+#define GABP_CLUSTER_MAX_SLICES 128
 #endif
 // Two warps a CTA up to this many slices, four above.  Four from the start: 32x32 grid 4.69 against
 // 4.53 us per round (8x8: 4.00 against 4.22).
@@ -657,6 +661,7 @@ constexpr int kClusterMax = 16;
 #endif
 constexpr int kUChip = GABP_CHIP_UNROLL;
 constexpr int kClusterMaxSlices = GABP_CLUSTER_MAX_SLICES;
+constexpr int kCluster8MaxWidth = 8;
 
 template <bool FRZ, int NW>
 __global__ void __launch_bounds__(32 * NW) k64_cluster(Args64 a, int max_rounds) {
@@ -1205,8 +1210,11 @@ static gabp_status ensure_sell64(gabp_handle h) {
     h->clu64 = h->clu64_nw = 0;
     h->chip64_bytes = h->chip64_smax = h->chip64_rmax = 0;
     if (S.ns <= kClusterMaxSlices) {
+      int wmax = 0;  // the widest slice's slots per row
+      for (int sl = 0; sl < ns; ++sl) wmax = std::max(wmax, (sp[sl + 1] - sp[sl]) >> 5);
       if (S.ns <= GABP_CLUSTER_NW2_MAX_SLICES) cluster_setup<2>(h, sp);
-      else cluster_setup<4>(h, sp);
+      else if (S.ns <= 64) cluster_setup<4>(h, sp);
+      else if (wmax <= kCluster8MaxWidth) cluster_setup<8>(h, sp);
     }
     // the cooperative launch for small graphs: one block per two slices, all co-resident
     h->coop64 = h->coop64f = 0;
@@ -1418,10 +1426,14 @@ gabp_status solve64(gabp_handle h, const double *b, double *x, double tol, int m
       le = chip ? cudaLaunchKernelEx(&cfg, k64_chip<2>, a, cs, max_rounds)
            : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true, 2>, a, max_rounds)
                       : cudaLaunchKernelEx(&cfg, k64_cluster<false, 2>, a, max_rounds);
-    else
+    else if (h->clu64_nw == 4)
       le = chip ? cudaLaunchKernelEx(&cfg, k64_chip<4>, a, cs, max_rounds)
            : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true, 4>, a, max_rounds)
                       : cudaLaunchKernelEx(&cfg, k64_cluster<false, 4>, a, max_rounds);
+    else
+      le = chip ? cudaLaunchKernelEx(&cfg, k64_chip<8>, a, cs, max_rounds)
+           : a.freeze ? cudaLaunchKernelEx(&cfg, k64_cluster<true, 8>, a, max_rounds)
+                      : cudaLaunchKernelEx(&cfg, k64_cluster<false, 8>, a, max_rounds);
     if (le != cudaSuccess) return cuda_fail(le, "FP64 cluster rounds");
     prof_end(h);
     h->prof.launches += 1;

@@ -373,6 +373,33 @@ def test_cooperative_threshold(gb, p):
         assert launches > 3
 
 
+@pytest.mark.parametrize("p", [64, 65])
+def test_cluster_rounds_grid64(gb, p):
+    """The 64x64 grid (128 slices of width 4) runs in one cluster of 16 CTAs of eight warps with its
+    state in shared memory; the 65x65 grid (133 slices) takes the cooperative grid.  Iterates and
+    messages at fixed rounds are the oracle's to 1e-13, the converged round count is the oracle's,
+    and the solve is three launches."""
+    m = synth.grid2d(p, -1.0, 4.5)
+    b = synth.rhs(m.n, 9)
+    off = ~_diag_mask(m)
+    for t in (1, 5):
+        r = oracle.gabp_broadcast(m, b, max_iter=t, tol=0.0, messages=True)
+        g = _gpu_solve(gb, m, b, 0.0, t)
+        assert g["iters"] == t and _relerr(g["x"], r["x"]) <= 1e-13, t
+        assert np.allclose(g["Pmsg"][off], r["Pmsg"][off], rtol=1e-13, atol=1e-15), t
+        assert np.allclose(g["hmsg"][off], (r["Pmsg"] * r["mumsg"])[off], rtol=1e-12, atol=1e-14), t
+    ref = oracle.gabp_broadcast(m, b, max_iter=3000, tol=1e-12)
+    s = _solver(gb, m, profile=1)
+    s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
+    s.profile(reset=True)
+    x, st, it, rel = s.solve(torch.from_numpy(b).cuda(), tol=1e-12, max_iter=3000)
+    launches = s.profile()["launches"]
+    s.close()
+    assert st == gb.GABP_OK and it == ref["iters"]
+    assert _relerr(x.cpu().numpy(), ref["x"]) <= 1e-12
+    assert launches == 3
+
+
 def test_cluster_handles_interleaved(gb):
     """The on-chip cluster rounds' shared memory differs per graph (about 80 KB a CTA on the
     1280-row random graph, 44 KB on the 45x45 grid with four warps a CTA, 4 KB on the 8x8 grid) and
@@ -395,15 +422,17 @@ def test_cluster_handles_interleaved(gb):
 
 
 @pytest.mark.parametrize("n,deg", [(1, 0), (33, 4), (200, 4), (1024, 4), (1280, 4), (1280, 20), (1281, 4),
-                                   (2048, 4), (2048, 20), (2049, 4), (4096, 4)])
+                                   (2048, 4), (2048, 20), (2049, 4), (4096, 4), (4096, 16), (4097, 4),
+                                   (8192, 4)])
 def test_cluster_rounds_small_graphs(gb, n, deg):
     """Graphs of at most 64 slices (2048 rows) run every plain FP64 round in one thread-block
     cluster (hardware cluster barrier, sums through distributed shared memory; two warps a CTA up
-    to 32 slices, four from 33); those whose state fits in the cluster's shared memory keep it
-    there (every degree-4 case up to 2048 rows), the graphs of degree 20 (about 270 and 330 KB a
-    CTA) read it from global memory; 2049 rows (65 slices) and 4096 take the cooperative grid.
-    Iterates and messages at fixed rounds equal the oracle's to 1e-13, the converged round count
-    is the oracle's, and the solve is three launches."""
+    to 32 slices, four up to 64); those whose state fits in the cluster's shared memory keep it
+    there (every degree-4 case up to 2048 rows), the graphs of degree 20 read it from global
+    memory.  From 65 to 128 slices (eight warps a CTA) only graphs whose slices are at most 8 slots
+    wide take the cluster (test_cluster_rounds_grid64): these random graphs of 4096 rows, and 4097
+    and 8192 rows, take the cooperative grid.  Iterates and messages at fixed rounds equal the
+    oracle's to 1e-13, the converged round count is the oracle's, and the solve is three launches."""
     m = synth.random_sym(n, deg, 1.1, 3) if n > 1 else synth.from_dense(np.array([[2.0]]))
     b = synth.rhs(m.n, 8)
     for t in (1, 2, 7):

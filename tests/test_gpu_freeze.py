@@ -56,12 +56,13 @@ def _offdiag(m):
     return rows != m.col
 
 
-# (name, matrix, tol): the first two run in one thread-block cluster (two and four warps a CTA;
-# the plain rounds with their state in shared memory), the next in the cooperative launch
+# (name, matrix, tol): the first three run in one thread-block cluster (two, four and eight warps
+# a CTA; the plain rounds with their state in shared memory), the next in the cooperative launch
 # (<= 131,072 rows), the last two in the launch-per-round path (CUDA graphs of check_every rounds)
 CASES = [
     ("grid2d_32", lambda: synth.grid2d(32, -1.0, 4.5), 1e-12),
     ("grid2d_45", lambda: synth.grid2d(45, -1.0, 4.5), 1e-12),
+    ("grid2d_64", lambda: synth.grid2d(64, -1.0, 4.5), 1e-12),
     ("random_20011", lambda: synth.random_sym(20011, 8, 1.1, 2), 1e-12),
     ("random_262144", lambda: synth.random_sym(1 << 18, 8, 1.1, 2), 1e-12),
     ("grid3d_64", lambda: synth.grid3d(64, 1.1, 2), 1e-10),
