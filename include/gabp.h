@@ -88,9 +88,10 @@ typedef struct {
                            131,072 rows run every round in one launch that decides on the device
                            (up to 2,048 rows, or 4,096 in slices of at most 8 slots a row: one
                            thread-block cluster; above: a cooperative grid),
-                           and do not use it; nor do FP64 serial-schedule solves without
-                           Steffensen's step of graphs of at most 4,096 rows (2,048 with a mean
-                           degree of 8 or more, 1,024 with 24 or more): one cluster runs every sweep */
+                           and do not use it; nor do FP64 serial-schedule solves of graphs of at
+                           most 4,096 rows (2,048 with a mean degree of 8 or more, 1,024 with 24 or
+                           more): one cluster runs every sweep (with Steffensen's step, where its
+                           state fits in the cluster's shared memory) */
   int freeze_precisions;/* plain FP64 solves (node variant or serial schedule, no acceleration): 1 =
                            freeze the precision messages once they have stopped moving (on the serial
                            schedule "round" below reads "sweep").  Screen: after two consecutive

@@ -43,4 +43,26 @@ __device__ __forceinline__ ClusterSums cluster_sums(cooperative_groups::cluster_
   return ClusterSums{warp_sum(x), (int)__reduce_or_sync(0xffffffffu, g)};
 }
 
+// Two sums of a cluster round in the same way, the same bits in every thread (no flags).
+struct __align__(16) ClusterPart2 {
+  double a, b;
+};
+template <int NW>
+__device__ __forceinline__ double2 cluster_sums2(cooperative_groups::cluster_group &cl, ClusterPart2 *part,
+                                                 double a, double b, int lane, int wib, int nwarps) {
+  const double wa = warp_sum(a), wb = warp_sum(b);
+  if (lane == 0) {
+    part[wib].a = wa;
+    part[wib].b = wb;
+  }
+  cl.sync();
+  double x = 0.0, y = 0.0;
+  for (int v = lane; v < nwarps; v += 32) {
+    const ClusterPart2 *q = cl.map_shared_rank(part + v % NW, (unsigned)(v / NW));
+    x += q->a;
+    y += q->b;
+  }
+  return make_double2(warp_sum(x), warp_sum(y));
+}
+
 }  // namespace gabp

@@ -201,6 +201,7 @@ struct WorkS {
   int clu = -1;                // CTAs of the one-cluster FP64 sweeps (0: none; -1: not yet sized)
   int clu_nw = 0;              // warps per CTA there
   int chip_bytes = 0;          // shared memory a CTA of those sweeps with the state on chip (0: no fit)
+  int chip_bytes_stf = 0;      // the same with Steffensen's step
   int chip_S = 0;              // slots of the largest CTA there
   bool valid = false;
   int result_round = 0;

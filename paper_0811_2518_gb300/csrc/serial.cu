@@ -427,11 +427,13 @@ struct ChipS {
   int R;  // rows a CTA
   int S;  // slots of the largest CTA
 };
-__host__ __device__ inline size_t chip_s_bytes(const ChipS &c, int C) {
-  return (size_t)32 * c.S + (size_t)c.R * (52 + 4 * (size_t)(C + 1));
+__host__ __device__ inline size_t chip_s_bytes(const ChipS &c, int C, bool stf) {
+  return (size_t)32 * c.S + (size_t)c.R * (52 + 4 * (size_t)(C + 1)) + (stf ? (size_t)8 * c.S + (size_t)16 * c.R : 0);
 }
 
-template <int L, int NW>
+// STF: Steffensen's iterations (ks64_steff_a / ks64_steff_b's steps, the cycle's scalar step from a
+// cluster sum): per slot the mean message after a cycle's first sweep, per row x_n and x_{n+1}.
+template <int L, int NW, bool STF>
 __global__ void __launch_bounds__(32 * NW) ks64_chip(ArgsS64 a, ChipS c, int max_sweeps) {
   namespace cg = cooperative_groups;
   constexpr int NT = 32 * NW, RPW = 32 / L;
@@ -443,11 +445,14 @@ __global__ void __launch_bounds__(32 * NW) ks64_chip(ArgsS64 a, ChipS c, int max
   double2 *firel = SMl + S;                          // firing aggregates, by local row
   double *savl = reinterpret_cast<double *>(firel + R);
   double *sPml = savl + S, *sadl = sPml + R, *sbl = sadl + R, *xl = sbl + R;
-  int *kref = reinterpret_cast<int *>(xl + R);  // sender: owner rank << 24 | its local row
+  double *sh1l = xl + R;                               // STF: mean messages after a cycle's first sweep
+  double *x0l = sh1l + (STF ? S : 0), *x1l = x0l + R;  // STF: x_n, x_{n+1}
+  int *kref = reinterpret_cast<int *>(STF ? x1l + R : xl + R);  // sender: owner rank << 24 | its local row
   int *rref = kref + S;                         // reverse slot: owner rank << 24 | its local slot
   int *coL = rref + S;                          // [(C + 1) x R] colour segment bounds, local slots
   int *scoll = coL + (size_t)(a.C + 1) * R;
   __shared__ ClusterPart part[2][NW];
+  __shared__ ClusterPart2 part2[2][NW];
   DevCtl *ctl = a.ctl;
   const int t0 = ctl->round;
   const double tol2bb = ctl->tol2bb;
@@ -470,6 +475,7 @@ __global__ void __launch_bounds__(32 * NW) ks64_chip(ArgsS64 a, ChipS c, int max
       sbl[r] = a.sb[j];
       scoll[r] = a.scol[j];
       for (int cc = 0; cc <= a.C; ++cc) coL[(size_t)cc * R + r] = a.co[(size_t)cc * a.n + j] - e0;
+      if (STF) x0l[r] = a.sx0[a.oid[j]];  // x^(0)
     }
   }
   __syncthreads();
@@ -530,6 +536,45 @@ __global__ void __launch_bounds__(32 * NW) ks64_chip(ArgsS64 a, ChipS c, int max
         nbad |= is_zero64(P);
         sPml[r] = P;
         xl[r] = h / P;
+      }
+    }
+    if (STF) {
+      __syncwarp();
+      if (t & 1) {  // a cycle's first sweep: keep its mean messages and iterate
+        if (has) {
+          for (int q = q0 + sl; q < q1; q += L) sh1l[q] = SMl[q].y;
+          if (sl == 0) x1l[r] = xl[r];
+        }
+      } else {  // after its second: lam = <d, D> / <D, D>, the mean messages and x moved by it
+        double sdD = 0.0, sDD = 0.0;
+        if (has && sl == 0) {
+          const double x0 = x0l[r], x1 = x1l[r], x2 = xl[r];
+          const double d = x2 - x1, D = d - (x1 - x0);
+          sdD = fma(d, D, sdD);
+          sDD = fma(D, D, sDD);
+        }
+        const double2 tot2 = cluster_sums2<NW>(cl, part2[t & 2 ? 1 : 0], sdD, sDD, lane, wib, lane_nw);
+        double lam = tot2.y > 0.0 ? tot2.x / tot2.y : 0.0;
+        lam = isfinite(lam) ? lam : 0.0;
+        double P = 0.0, h = 0.0;
+        if (has)
+          for (int q = q0 + sl; q < q1; q += L) {
+            const double2 m = SMl[q];
+            const double hn = m.y - lam * (m.y - sh1l[q]);
+            SMl[q].y = hn;
+            P += m.x;
+            h += hn;
+          }
+        P = sub_sum<L>(P);
+        h = sub_sum<L>(h);
+        if (has && sl == 0) {
+          P += sadl[r];
+          h += sbl[r];
+          const double x = h / P;
+          xl[r] = x;
+          x0l[r] = x;
+          if (myc == 0) firel[r] = make_double2(P, h);
+        }
       }
     }
     cl.sync();
@@ -1035,30 +1080,21 @@ static int serial_cluster_fits(gabp_handle h, int cs) {
   return ok ? cs : 0;
 }
 
-// The on-chip flavour's shared memory for clusters of cs CTAs of NW warps, when it fits.
-template <int L, int NW>
-static void serial_chip_fit(gabp_handle h, int cs) {
-  WorkS &s = h->ws;
-  const int R = NW * (32 / L), n = h->g.n;
-  int64_t smax = 0;
-  for (int r = 0; r < cs; ++r) {
-    const int a0 = std::min(r * R, n), a1 = std::min(a0 + R, n);
-    smax = std::max<int64_t>(smax, s.srp_h[a1] - s.srp_h[a0]);
-  }
-  if (smax >= (1 << 24)) return;
-  const ChipS c{R, (int)smax};
-  const size_t bytes = chip_s_bytes(c, s.C);
+// The on-chip flavour's shared memory for clusters of cs CTAs of NW warps, when it fits (0 if not).
+template <int L, int NW, bool STF>
+static int serial_chip_bytes(gabp_handle h, int cs, const ChipS &c) {
+  const size_t bytes = chip_s_bytes(c, h->ws.C, STF);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   constexpr int kStaticRoom = 1024;  // the kernel's static shared memory fits below
-  if (bytes + kStaticRoom > (size_t)optin) return;
+  if (bytes + kStaticRoom > (size_t)optin) return 0;
   // one limit for the function, shared by every handle: the device's whole opt-in room
-  if (cudaFuncSetAttribute(ks64_chip<L, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - kStaticRoom) !=
-      cudaSuccess) {
+  if (cudaFuncSetAttribute(ks64_chip<L, NW, STF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - kStaticRoom) != cudaSuccess) {
     cudaGetLastError();
-    return;
+    return 0;
   }
-  if (cs > 8) cudaFuncSetAttribute(ks64_chip<L, NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (cs > 8) cudaFuncSetAttribute(ks64_chip<L, NW, STF>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1071,11 +1107,25 @@ static void serial_chip_fit(gabp_handle h, int cs) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaOccupancyMaxActiveClusters(&nc, (void *)ks64_chip<L, NW>, &cfg) == cudaSuccess && nc > 0) {
-    s.chip_bytes = (int)bytes;
-    s.chip_S = c.S;
-  }
+  const bool ok = cudaOccupancyMaxActiveClusters(&nc, (void *)ks64_chip<L, NW, STF>, &cfg) == cudaSuccess && nc > 0;
   cudaGetLastError();
+  return ok ? (int)bytes : 0;
+}
+
+template <int L, int NW>
+static void serial_chip_fit(gabp_handle h, int cs) {
+  WorkS &s = h->ws;
+  const int R = NW * (32 / L), n = h->g.n;
+  int64_t smax = 0;
+  for (int r = 0; r < cs; ++r) {
+    const int a0 = std::min(r * R, n), a1 = std::min(a0 + R, n);
+    smax = std::max<int64_t>(smax, s.srp_h[a1] - s.srp_h[a0]);
+  }
+  if (smax >= (1 << 24)) return;
+  const ChipS c{R, (int)smax};
+  s.chip_S = c.S;
+  s.chip_bytes = serial_chip_bytes<L, NW, false>(h, cs, c);
+  s.chip_bytes_stf = serial_chip_bytes<L, NW, true>(h, cs, c);
 }
 
 template <int L>
@@ -1083,7 +1133,7 @@ static void serial_cluster_size(gabp_handle h) {
   WorkS &s = h->ws;
   s.clu = 0;
   s.clu_nw = 0;
-  s.chip_bytes = 0;
+  s.chip_bytes = s.chip_bytes_stf = 0;
   s.chip_S = 0;
   int attr = 0;
   cudaDeviceGetAttribute(&attr, cudaDevAttrClusterLaunch, h->device);
@@ -1118,12 +1168,17 @@ static gabp_status serial_cluster_run(gabp_handle h, const ArgsS64 &a, int max_s
   cfg.stream = h->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  // plain sweeps with the state on chip where it fits (the same messages and iterates)
-  const bool chip = !a.freeze && h->ws.chip_bytes > 0;
-  if (chip) cfg.dynamicSmemBytes = h->ws.chip_bytes;
+  // plain sweeps (and Steffensen's) with the state on chip where it fits (the same messages and
+  // iterates); the freeze's sweeps read it from global memory
+  const bool stf = a.sx0 != nullptr;
+  const int chip_bytes = stf ? h->ws.chip_bytes_stf : h->ws.chip_bytes;
+  const bool chip = !a.freeze && chip_bytes > 0;
+  if (chip) cfg.dynamicSmemBytes = chip_bytes;
+  const ChipS cs{NW * (32 / L), h->ws.chip_S};
   prof_begin(h);
   const cudaError_t le =
-      chip ? cudaLaunchKernelEx(&cfg, ks64_chip<L, NW>, a, ChipS{NW * (32 / L), h->ws.chip_S}, max_sweeps)
+      chip ? (stf ? cudaLaunchKernelEx(&cfg, ks64_chip<L, NW, true>, a, cs, max_sweeps)
+                  : cudaLaunchKernelEx(&cfg, ks64_chip<L, NW, false>, a, cs, max_sweeps))
            : cudaLaunchKernelEx(&cfg, ks64_cluster<L, NW>, a, (const int *)h->ws.dcstart, max_sweeps);
   if (le != cudaSuccess) return cuda_fail(le, "FP64 serial cluster sweeps");
   prof_end(h);
@@ -1206,21 +1261,24 @@ gabp_status solve64_serial(gabp_handle h, const double *b, double *x, double tol
   const bool stf = h->opt.accel == 2;
   const int key = L | (s.C << 8) | (stf ? 1 << 30 : 0) | (a.freeze ? 1 << 29 : 0);
   gabp_status rs = GABP_OK;
-  // small graphs without Steffensen's step: every sweep in one thread-block cluster
-  if (!stf && (L == 1 || L == 2 || L == 4)) {
+  // small graphs: every sweep in one thread-block cluster (Steffensen's step only with the state
+  // on chip)
+  bool one_launch = false;
+  if (L == 1 || L == 2 || L == 4) {
     if (s.clu < 0) {
       if (L == 1) serial_cluster_size<1>(h);
       else if (L == 2) serial_cluster_size<2>(h);
       else serial_cluster_size<4>(h);
     }
-    if (s.clu > 0) {
+    one_launch = s.clu > 0 && (!stf || s.chip_bytes_stf > 0);
+    if (one_launch) {
       const int ms = std::max(1, max_iter);
       rs = L == 1 ? serial_cluster_dispatch<1>(h, a, ms)
            : L == 2 ? serial_cluster_dispatch<2>(h, a, ms) : serial_cluster_dispatch<4>(h, a, ms);
       if (rs != GABP_OK) return rs;
     }
   }
-  if (!(s.clu > 0 && !stf)) GABP_DISPATCH_L(L, {
+  if (!one_launch) GABP_DISPATCH_L(L, {
     const int nb = blocks_for(g.n, kBlock / LL, resident_grid(h->num_sms, ks64_pass<LL>));
     const int ab = blocks_for(std::max(g.n, g.E), kBlock, resident_grid(h->num_sms, ks64_steff_a));
     rs = run_rounds(h, &h->gS64, &h->gS64_key, key, [&] {
