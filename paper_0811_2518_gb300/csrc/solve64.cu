@@ -139,9 +139,9 @@ __device__ __forceinline__ void record64(DevCtl *ctl, const StopRule &q, int t, 
   if (FENCE) __threadfence();
 }
 
-template <bool FENCE = true>
+// The same for a kernel that reads the stopping parameters from the control block each round.
 __device__ __forceinline__ void decide64(DevCtl *ctl, int t, double rr, double bad) {
-  record64<FENCE>(ctl, stop_rule(ctl), t, rr, bad);
+  record64<true>(ctl, stop_rule(ctl), t, rr, bad);
 }
 
 // Load flavours of the plain round body: the launch-per-round kernel streams its slot
